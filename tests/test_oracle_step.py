@@ -1,0 +1,176 @@
+"""Pins of the oracle's nodal forces and whole time step: discrete power
+balance between the damage-weighted forces and Fdot (Sec. 3.1, the forces
+follow from energy conservation), linear momentum, the fully damaged
+particle, rigid motion, energy conservation and first-order completeness
+through the step."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_07374_gb300 import specimen as S
+
+
+def _free_bar(dims=(5, 5, 9), seed=0, hg_alpha=0.0, mat=None, spacing=0.5e-3):
+    """A jittered bar with no velocity constraints."""
+    sp = S.tensile_bar(*dims, spacing, jitter=0.01, seed=seed)
+    sp.bc_mask[:] = 0
+    sp.bc_vel[:] = 0
+    mat = mat or S.material(A=1e12, damage=0)   # stays elastic
+    h = 1.5 * spacing
+    w = S.Workload("free", sp, [mat], h, 2 * h, S.cfl_dt(mat, spacing), hg_alpha, 0)
+    return oracle.Simulation.from_workload(w), sp
+
+
+def _random_state(sim, rng, dmax=0.5):
+    N = sim.N
+    sim["A"][:] = rng.normal(size=(N, 9)) * 1e14
+    sim["D"][:] = rng.uniform(0, dmax, size=N)
+    sim["F"][:] = (np.eye(3).ravel()[None, :] + 1e-2 * rng.normal(size=(N, 9)))
+    sim["u"][:] = 1e-6 * rng.normal(size=(N, 3))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_power_balance_forces_vs_fdot(seed):
+    """sum_i f_i . v_i = - sum_i V_i P_i : Fdot_i(v) for ANY stress state,
+    damage field and velocity field, with P_i = A_i L_i^T.  This is the
+    identity the paper derives the damage-weighted forces from; it fixes the
+    sign of the force, its (1 - D) weights and its transposes."""
+    rng = np.random.default_rng(seed)
+    sim, sp = _free_bar(seed=seed)
+    _random_state(sim, rng)
+    f = sim.forces()
+    v = rng.normal(size=(sim.N, 3))
+    Fd = oracle.velocity_gradient(sim.X, sim.vol, v, sim["D"], sim.Linv, sim.row_ptr, sim.col, sim.cfg.h)
+    P = np.einsum("nkm,nlm->nkl", sim["A"].reshape(-1, 3, 3), sim.L.reshape(-1, 3, 3))
+    power_int = np.sum(sim.vol[:, None, None] * P * Fd.reshape(-1, 3, 3))
+    power_f = np.sum(f * v)
+    scale = np.sum(np.abs(f * v))
+    assert abs(power_f + power_int) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("hg", [0.0, 10.0])
+def test_forces_sum_to_zero(hg):
+    """Antisymmetric pair forces conserve linear momentum (Sec. 3.1)."""
+    rng = np.random.default_rng(2)
+    sim, sp = _free_bar(seed=2, hg_alpha=hg)
+    _random_state(sim, rng)
+    f = sim.forces()
+    assert np.all(np.abs(f.sum(0)) <= 1e-12 * np.abs(f).sum(0))
+
+
+def test_fully_damaged_particle_exerts_no_force():
+    """With D_j = 1 and P_j = 0 particle j drops out of every neighbour's force
+    (Sec. 3.1): the forces equal those of the system without j."""
+    rng = np.random.default_rng(4)
+    sim, sp = _free_bar(seed=4, hg_alpha=10.0)
+    _random_state(sim, rng)
+    j = 97
+    sim["D"][j] = 1.0
+    sim["A"][j] = 0.0
+    f_with = sim.forces()
+    # rebuild the same system with j's bonds removed from the CSR
+    keep_rows = []
+    for i in range(sim.N):
+        r = sim.col[sim.row_ptr[i]:sim.row_ptr[i + 1]]
+        keep_rows.append(r[r != j] if i != j else r[:0])
+    row_ptr = np.concatenate([[0], np.cumsum([len(r) for r in keep_rows])]).astype(np.int64)
+    col = np.concatenate(keep_rows).astype(np.int32)
+    sim2 = oracle.Simulation(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, [S.material(A=1e12)],
+                             sim.cfg.h, sim.cfg.rc, sim.cfg.dt, 10.0, neighbors_csr=(row_ptr, col))
+    for k in ("A", "D", "F", "u"):
+        sim2[k][:] = sim[k]
+    f_without = sim2.forces()
+    others = np.arange(sim.N) != j
+    assert np.allclose(f_with[others], f_without[others], rtol=1e-12, atol=1e-12 * np.abs(f_with).max())
+
+
+def test_rigid_rotation_is_stress_free():
+    """F = R, u = (R - I) X, v = 0 and no stress: a step keeps every stress,
+    force and velocity at rounding level (polar decomposition removes R and
+    the hourglass error vector vanishes for rigid motion)."""
+    sim, sp = _free_bar(hg_alpha=10.0, mat=S.aluminium_cl())
+    th = 0.9
+    R = np.array([[np.cos(th), 0, np.sin(th)], [0, 1, 0], [-np.sin(th), 0, np.cos(th)]])
+    sim["F"][:] = R.ravel()
+    sim["u"][:] = sp.X @ (R - np.eye(3)).T
+    sim.step(1)
+    K, _ = S.moduli(S.aluminium_cl())
+    assert np.abs(sim["sigma"]).max() <= 1e-13 * K
+    assert np.abs(sim["v"]).max() <= 1e-9
+    assert sim.status == 0
+
+
+def test_patch_test_through_the_step():
+    """An affine initial velocity v = B X with no stress gives F^1 = I + dt B
+    at every particle after one step."""
+    sim, sp = _free_bar(seed=3)
+    rng = np.random.default_rng(3)
+    B = rng.normal(size=(3, 3)) * 10.0
+    sim["v"][:] = sp.X @ B.T
+    sim.step(1)
+    F1 = np.eye(3).ravel() + sim.cfg.dt * B.ravel()
+    assert np.max(np.abs(sim["F"] - F1[None, :])) <= 1e-14
+
+
+def test_momentum_conserved_over_free_trajectory():
+    sim, sp = _free_bar(seed=5, hg_alpha=10.0, mat=S.aluminium_cl())
+    rng = np.random.default_rng(5)
+    sim["v"][:] = rng.normal(size=(sim.N, 3)) * 0.5
+    m = sp.vol * 2700.0
+    p0 = (m[:, None] * sim["v"]).sum(0)
+    sim.step(100)
+    p1 = (m[:, None] * sim["v"]).sum(0)
+    assert np.all(np.abs(p1 - p0) <= 1e-10 * (m[:, None] * np.abs(sim["v"])).sum(0))
+
+
+def _energy(sim, rho0):
+    m = sim.vol * rho0
+    ek = 0.5 * np.sum(m[:, None] * sim["v"] ** 2)
+    F = sim["F"].reshape(-1, 3, 3)
+    eps = 0.5 * (F + F.transpose(0, 2, 1)) - np.eye(3)
+    sig = sim["sigma"].reshape(-1, 3, 3)
+    ei = 0.5 * np.sum(sim.vol[:, None, None] * sig * eps)
+    return ek + ei, ek, ei
+
+
+def test_elastic_free_vibration_conserves_energy():
+    """Elastic, no hourglass, no constraints, small amplitude: kinetic plus
+    strain energy stays constant (forces consistent with the stress)."""
+    mat = S.material(A=1e12, damage=0)
+    sim, sp = _free_bar(dims=(5, 5, 12), seed=6, mat=mat)
+    z = sp.X[:, 2] / sp.X[:, 2].max()
+    # first free-free axial mode (zero mean velocity)
+    sim["v"][:, 2] = 0.05 * np.cos(np.pi * z)
+    e0, _, _ = _energy(sim, mat["rho0"])
+    worst = 0.0
+    exchanged = False
+    for _ in range(20):
+        sim.step(10)
+        e, ek, ei = _energy(sim, mat["rho0"])
+        worst = max(worst, abs(e - e0) / e0)
+        exchanged |= ei > 0.9 * e0
+    assert exchanged          # energy really moved into the strain field
+    assert worst < 3e-3, worst
+
+
+def test_failure_trajectory_invariants():
+    """Failure-exercising tensile bar: failures are permanent, damage never
+    decreases, failed particles carry no stress and rest, grips move at the
+    prescribed speed."""
+    w = S.failure_variant(S.tensile_bar_cl(nx=5, ny=5, nz=20))
+    sim = oracle.Simulation.from_workload(w)
+    prev = sim.state()
+    for _ in range(8):
+        sim.step(60)
+        st = sim.state()
+        was = prev["fail_step"] >= 0
+        assert np.array_equal(st["fail_step"][was], prev["fail_step"][was])
+        assert np.all(st["dinit"] >= prev["dinit"]) and np.all(st["D"] >= prev["D"])
+        failed = st["fail_step"] >= 0
+        assert np.all(st["sigma"][failed] == 0) and np.all(st["A"][failed] == 0)
+        assert np.all(st["v"][failed] == 0)
+        grip = (w.specimen.bc_mask == 1) & ~failed
+        assert np.array_equal(st["v"][grip], w.specimen.bc_vel[grip])
+        prev = st
+    assert (prev["fail_step"] >= 0).sum() > 0
+    assert sim.status == 0
