@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark of the damage-weighted TLSPH step: pair-interactions per second.
+
+Workload (default): the Johnson-Cook tensile bar, a 40x40x640 jittered simple
+cubic lattice (1,024,000 particles, about 1.0e8 directed neighbour pairs) at
+0.5 mm spacing, cubic spline h = 1.5 spacing, neighbours within 2h, grips at
++-1 m/s, dt = 0.3 CFL.  Synthetic, seeded inputs.
+
+A pair-interaction is one directed pair (i, j in S_i) advanced through one
+full step (both gather passes).  `value` is device-timed with CUDA events on
+the stream the library launches on, inputs resident in HBM; `e2e` is the same
+metric through the C ABI with host buffers: upload of the specimen from
+pinned memory, neighbour build, the K steps and the download of the final
+fields, all inside the timed region.  The working set (about 1.8 GB touched
+per step) is far larger than the 129 MB L2, so no flush is needed between
+steps.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+prefix of the same bar (same metric and unit).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s (mixed vs FP64 GPU, same accuracy); served p50/p99 latency"
+UNIT = "pair-interactions/s"
+
+
+# ---------------------------------------------------------------- workloads
+def workload(name: str):
+    from paper_1901_07374_gb300 import specimen as S
+    if name == "tensile_bar_jc_40x40x640":
+        return S.tensile_bar_jc()
+    if name == "tensile_bar_cl_8x8x32":
+        return S.tensile_bar_cl()
+    if name == "notched_bar_gtn":
+        return S.notched_bar_gtn()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes(N: int, nnz: int, precision: str) -> dict:
+    """Bytes each pass must move between HBM and the SMs per step: the CSR
+    column index of every pair plus every particle's own state read and
+    written once (gathered neighbour data counts as on-chip reuse).  Per-pass
+    per-particle figures follow the state layout of the library."""
+    if precision == "fp64":
+        p1 = 4 * nnz + 592 * N     # row_ptr 8, X 24, v 24, Linv 72, F rw 144, sd rw 96, scalars rw 64,
+        #                            D r+w 16, fail 4, mat 4, sigma w 48, A w 72, vol 16 (gathered only)
+        p2 = 4 * nnz + 357 * N     # row_ptr 8, X 24, u 24, F 72, A 72, D 8, vol 8, sqrtE 8, mass 8,
+        #                            vh rw 48, v w 24, force w 24, u' w 24, fail 4, bc 1
+    else:
+        from paper_1901_07374_gb300 import tlsph
+        p1, p2 = tlsph.mixed_algorithmic_bytes(N, nnz)
+    return {"pass1": p1, "pass2": p2}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(seconds: float, max_steps: int | None = None, nz: int = 24):
+    """Pair-interactions/s of the FP64 oracle (single thread) on the first
+    `nz` layers of the 40x40 bar; runs until `seconds` of stepping or
+    max_steps.  Returns (rate, steps, pairs per step, N)."""
+    import oracle
+    from paper_1901_07374_gb300 import specimen as S
+    w = S.tensile_bar_jc(nx=40, ny=40, nz=nz)
+    sim = oracle.Simulation.from_workload(w)
+    sim.step(1)       # warm
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and steps >= max_steps):
+            break
+    return sim.nnz * steps / el, steps, sim.nnz, sim.N, el
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    rate, steps, nnz, N, el = oracle_rate(1e9, max_steps=args.steps)
+    sample = f"first 24 of 640 layers of the 40x40 bar ({N} particles, {nnz} pairs), {steps} steps in {el:.1f} s"
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": 1, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args, rank: int, world: int, dist):
+    import numpy as np
+    import torch
+
+    from paper_1901_07374_gb300 import tlsph
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    sp = w.specimen
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident timing
+    sim = tlsph.Simulation.from_workload(w, precision=args.precision, stream=stream)
+    N, nnz, _ = sim.info()
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.3)
+    sim.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    p1_ms, p2_ms, nprof = sim.profile_read()
+    sim.profile(False)
+    clocks = clk.stop()
+    sim.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    sim.close()
+    del sim
+    value = world * nnz * args.steps / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel
+    ab = algorithmic_bytes(N, nnz, args.precision)
+    kern = "pass2" if p2_ms >= p1_ms else "pass1"
+    k_ms = (p2_ms if kern == "pass2" else p1_ms) / max(1, nprof)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    src = "measured"
+    if not peak:
+        peak, src = 6800.0, "fallback"
+    achieved = ab[kern] / (k_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": src, "traffic": None,
+                "algorithmic_bytes_per_launch": ab[kern],
+                "ms_per_launch": {"pass1": p1_ms / max(1, nprof), "pass2": p2_ms / max(1, nprof)}}
+
+    # ---- end to end through the C ABI from pinned host buffers
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t, t.numpy()
+    X_t, X = pinned(sp.X)
+    V_t, vol = pinned(sp.vol)
+    M_t, mat = pinned(sp.mat_id)
+    B_t, bcm = pinned(sp.bc_mask)
+    BV_t, bcv = pinned(sp.bc_vel)
+    F0_t, f0 = pinned(sp.f0)
+    outs = {k: pinned(np.empty((N, c))) for k, c in (("U", 3), ("V", 3), ("SIGMA", 9), ("DAMAGE", 1))}
+    h2d = X.nbytes + vol.nbytes + mat.nbytes + bcm.nbytes + bcv.nbytes + f0.nbytes
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    s2 = tlsph.Simulation(X, vol, mat, bcm, bcv, f0, w.materials, w.h, w.rc, w.dt, w.hg_alpha,
+                          precision=args.precision, stream=stream)
+    s2.step(args.steps)
+    d2h = 0
+    for k, (t, a) in outs.items():
+        a = a.reshape(N, -1) if k != "DAMAGE" else a.reshape(N)
+        L = tlsph.load()
+        tlsph._check(L.tlsph_get_state(s2.ctx, tlsph.FIELD[k], a.ctypes.data_as(__import__("ctypes").c_void_p),
+                                       a.nbytes, 0), s2.ctx)
+        d2h += a.nbytes
+    el = time.perf_counter() - t0
+    s2.close()
+    if dist:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    e2e = {"value": world * nnz * args.steps / el, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "includes": "create (upload, neighbour build, L^-1) + K steps + download of u, v, sigma, D"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, steps, onnz, oN, oel = oracle_rate(args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first 24 of 640 layers of the bar ({oN} particles, {onnz} pairs), "
+                         f"{steps} steps in {oel:.1f} s, single thread"}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded jittered lattice)",
+            "config": {"workload": args.workload, "precision": args.precision, "particles": N,
+                       "pairs_per_step": nnz, "particle_steps_per_s": world * N * args.steps / (ms * 1e-3),
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (about 1.8 GB per step vs 129 MB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
+    ap.add_argument("--workload", default="tensile_bar_jc_40x40x640")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.precision is None:
+        from paper_1901_07374_gb300 import tlsph
+        args.precision = tlsph.DEFAULT_PRECISION
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, dist)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

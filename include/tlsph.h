@@ -1,0 +1,217 @@
+/*
+ * tlsph.h -- C ABI of the GB300 (sm_103a) damage-weighted Total-Lagrangian
+ * SPH step of de Vaucorbeil & Hutchinson, "A damage and failure implementation
+ * for the simulation of ductile solids with Total-Lagrangian Smooth Particle
+ * Hydrodynamics" (arXiv 1901.07374).
+ *
+ * The library advances a body of N particles through the explicit time step
+ * the paper builds:
+ *   - neighbour sets S_i fixed in the reference configuration (Sec. 1, 2.2),
+ *   - the correction matrix L_i and the corrected kernel gradient
+ *     (Sec. 2.2, Eq. correction_matrix),
+ *   - the damage-weighted velocity gradient and deformation gradient
+ *     (Sec. 3.1, Eqs. Crack_approx_Fdot, Crack_approx_F),
+ *   - the constitutive update: equation of state (Sec. 4, Eq. pH),
+ *     Johnson-Cook flow stress and radial return (Sec. 4, Eq.
+ *     JC_viscoplastic_model, Algorithm 1), GTN porous plasticity (Sec. 5.4,
+ *     Algorithm 2),
+ *   - Cockcroft-Latham, Johnson-Cook and GTN damage with failure
+ *     (Sec. 5.1-5.4); a fully damaged particle keeps no stress and rests
+ *     (Sec. 3.1),
+ *   - the damage-weighted nodal forces (Sec. 3.1, equation after
+ *     Crack_approx_F) with hourglass control (Sec. 2, cited scheme),
+ *   - velocity-Verlet integration.
+ *
+ * Units are SI.  Every floating-point array crossing this ABI is IEEE double,
+ * row-major, particle-major (particle i's 3-vector at [3i, 3i+3), its 3x3
+ * tensor at [9i, 9i+9) with T[9i + 3k + l] = T_kl).
+ *
+ * Ownership: inputs are copied at tlsph_create; the caller keeps its arrays.
+ * Device memory is either a caller-owned arena (carved, never freed by the
+ * library) or, when no arena is given, allocated and freed by the library.
+ *
+ * Errors: every entry point returns a tlsph_status.  Nothing aborts or
+ * throws across the ABI.  An error inside a context is sticky: later calls on
+ * that context return TLSPH_ERR_STATE until tlsph_destroy.  A text
+ * description is available from tlsph_last_error.
+ *
+ * Threading: a context is used from one host thread at a time.  Distinct
+ * contexts may be used concurrently.
+ */
+#ifndef TLSPH_H
+#define TLSPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlsph_ctx tlsph_ctx;
+
+typedef enum {
+    TLSPH_OK = 0,
+    TLSPH_ERR_ARG = -1,         /* a null pointer, size or value out of range */
+    TLSPH_ERR_SINGULAR_L = -2,  /* a correction matrix L_i is singular (e.g. a particle with no neighbours) */
+    TLSPH_ERR_NUMERICS = -3,    /* device status: non-finite state, det F <= 0, or an iteration cap reached */
+    TLSPH_ERR_NOMEM = -4,       /* arena too small / allocation failed / neighbour capacity exceeded */
+    TLSPH_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+    TLSPH_ERR_STATE = -6        /* the context holds an earlier error, or a call out of order */
+} tlsph_status;
+
+/* device status bits reported through tlsph_sync / tlsph_status_bits */
+#define TLSPH_ST_POLAR_CAP   1u   /* polar decomposition hit its iteration cap */
+#define TLSPH_ST_NEWTON_CAP  2u   /* a GTN Newton solve hit its iteration cap */
+#define TLSPH_ST_BAD_J       4u   /* det F^{n+1} <= 0 or non-finite */
+#define TLSPH_ST_NONFINITE   8u   /* a non-finite stress or force */
+
+/* arithmetic of the per-pair work */
+#define TLSPH_PRECISION_FP64  0   /* everything in FP64 */
+#define TLSPH_PRECISION_MIXED 1   /* FP32 pair gathers and sums, FP64 state, guards and constitutive update */
+
+typedef struct {
+    double h;          /* smoothing length [m]; the cubic-spline kernel has support 2h */
+    double rc;         /* neighbour cutoff [m]: S_i = { j != i : |X_j - X_i| < rc } (normally 2h) */
+    double dt;         /* time step [s], fixed for the run */
+    double hg_alpha;   /* hourglass-control coefficient (0 disables it) */
+    int32_t precision; /* TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED */
+    int32_t flags;     /* reserved, must be 0 */
+} tlsph_config;
+
+/* damage models */
+#define TLSPH_DAMAGE_NONE 0
+#define TLSPH_DAMAGE_CL   1   /* Cockcroft-Latham (Sec. 5.1) + linear evolution (Sec. 5.3) */
+#define TLSPH_DAMAGE_JC   2   /* Johnson-Cook (Sec. 5.2) + linear evolution (Sec. 5.3) */
+#define TLSPH_DAMAGE_GTN  3   /* Gurson-Tvergaard-Needleman (Sec. 5.4, Algorithm 2) */
+
+/* A material (Sec. 4 and 5).  Field meaning follows the paper's symbols. */
+typedef struct {
+    double rho0, E, nu;       /* reference density, Young modulus, Poisson ratio */
+    int32_t eos;              /* 0: linear sigma_m = K (J - 1); 1: Mie-Grueneisen (Eq. pH) */
+    double c0, S_alpha, Gamma0;               /* Mie-Grueneisen constants (eos = 1) */
+    double A, B, n, C, epsdot0;               /* Johnson-Cook flow stress (Eq. JC_viscoplastic_model), T* = 0 */
+    int32_t damage;                           /* TLSPH_DAMAGE_* */
+    double Wcr;                               /* Cockcroft-Latham critical plastic work [Pa] */
+    double D1, D2, D3, D4, D5;                /* Johnson-Cook damage constants */
+    double q1, q2, q3, fN, eN, sN, fc, fF, komega; /* GTN constants */
+} tlsph_material;
+
+#define TLSPH_MAX_MATERIALS 64
+
+/* Fields of tlsph_get_state / tlsph_set_state (element type and count). */
+typedef enum {
+    TLSPH_FIELD_X = 0,          /* f64 N*3  reference positions (read only) */
+    TLSPH_FIELD_U = 1,          /* f64 N*3  displacement u^n */
+    TLSPH_FIELD_V = 2,          /* f64 N*3  velocity v^n */
+    TLSPH_FIELD_F = 3,          /* f64 N*9  deformation gradient F^n */
+    TLSPH_FIELD_SIGMA = 4,      /* f64 N*9  Cauchy stress (current frame, read only) */
+    TLSPH_FIELD_STRESS_DEV = 5, /* f64 N*9  unrotated deviatoric stress (the constitutive state) */
+    TLSPH_FIELD_EPSP = 6,       /* f64 N    equivalent plastic strain (matrix strain for GTN) */
+    TLSPH_FIELD_EPSP_RATE = 7,  /* f64 N    plastic strain rate of the last step */
+    TLSPH_FIELD_DINIT = 8,      /* f64 N    damage initiation variable D_init */
+    TLSPH_FIELD_DAMAGE = 9,     /* f64 N    damage D */
+    TLSPH_FIELD_POROSITY = 10,  /* f64 N    GTN void volume fraction f */
+    TLSPH_FIELD_FAIL_STEP = 11, /* i32 N    step at which the particle failed, -1 while intact */
+    TLSPH_FIELD_FORCE = 12,     /* f64 N*3  nodal force f^n */
+    TLSPH_FIELD_A = 13,         /* f64 N*9  A_i = P_i L_i^{-T} (read only) */
+    TLSPH_FIELD_LINV = 14,      /* f64 N*9  L_i^{-1} (read only) */
+    TLSPH_FIELD_NBR_ROWPTR = 15,/* i64 N+1  neighbour CSR row pointers (read only) */
+    TLSPH_FIELD_NBR_COL = 16,   /* i32 nnz  neighbour CSR columns, rows ascending (read only) */
+    TLSPH_FIELD_COUNT = 17
+} tlsph_field;
+
+/* Bytes of device memory a context needs for N particles and up to nnz_cap
+ * neighbour pairs; 0 if the arguments are invalid. */
+size_t tlsph_workspace_bytes(const tlsph_config *cfg, int64_t N, int64_t nnz_cap);
+
+/* Create a context: copies the inputs to the device, builds the neighbour
+ * CSR (cell binning on the GPU, rows sorted ascending), computes L_i^{-1}
+ * and sets the initial state (u = 0, F = I, no stress, v = bc_vel, f = f0).
+ *   X       host, N*3 reference positions
+ *   vol     host, N reference volumes (> 0)
+ *   mat_id  host, N material indices in [0, TLSPH_MAX_MATERIALS), or NULL (all 0)
+ *   bc_mask host, N bytes, 1 = velocity prescribed to bc_vel every step, or NULL
+ *   bc_vel  host, N*3 prescribed velocities; also the initial velocity of
+ *           unconstrained particles when bc_mask[i] == 0 (may be NULL: zero)
+ *   f0      host, N initial porosity (GTN), or NULL (zero)
+ *   arena   device memory owned by the caller, 256-byte aligned, or NULL for
+ *           library-owned memory; arena_bytes its size
+ *   nnz_cap neighbour capacity when an arena is given (use
+ *           tlsph_workspace_bytes to size the arena); ignored otherwise
+ *   stream  cudaStream_t every launch of this context is ordered on (NULL:
+ *           the legacy default stream)
+ * Blocks until the set-up is done.  Returns TLSPH_ERR_SINGULAR_L if some L_i
+ * is singular, TLSPH_ERR_NOMEM if the arena or nnz_cap is too small (the
+ * needed pair count is in tlsph_last_error(NULL)); no context is created on
+ * error. */
+int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const double *vol,
+                 const int32_t *mat_id, const uint8_t *bc_mask, const double *bc_vel,
+                 const double *f0, void *arena, size_t arena_bytes, int64_t nnz_cap,
+                 void *stream, tlsph_ctx **out);
+
+/* Set material `mat_id` (Sec. 4-5 constants).  Every material referenced by
+ * mat_id must be set before the first tlsph_step.  Setting a GTN material
+ * before the first step also sets D = q1 f*(f0) on its particles. */
+int tlsph_set_material(tlsph_ctx *ctx, int mat_id, const tlsph_material *mat);
+
+/* Enqueue nsteps time steps on the context's stream (asynchronous; errors of
+ * the device work are reported by tlsph_sync). */
+int tlsph_step(tlsph_ctx *ctx, int nsteps);
+
+/* Wait for the context's stream; returns TLSPH_ERR_NUMERICS if the device
+ * status word has any TLSPH_ST_* bit set (the bits stay readable through
+ * tlsph_status_bits), TLSPH_ERR_CUDA on a CUDA error. */
+int tlsph_sync(tlsph_ctx *ctx);
+
+/* Device status bits accumulated since create (synchronises). */
+int tlsph_status_bits(tlsph_ctx *ctx, uint32_t *bits);
+
+/* N, nnz and the number of completed steps. */
+int tlsph_info(const tlsph_ctx *ctx, int64_t *N, int64_t *nnz, int64_t *steps);
+
+/* Copy a field (tlsph_field) at the current step boundary into dst (host
+ * memory, or device memory if dst_on_device), `bytes` must equal the field's
+ * size.  Synchronises the context's stream. */
+int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_on_device);
+
+/* Overwrite a writable field (U, V, F, STRESS_DEV, EPSP, EPSP_RATE, DINIT,
+ * DAMAGE, POROSITY, FAIL_STEP, FORCE) from src; the half-step velocity and
+ * the predicted displacement are recomputed from U, V and FORCE.  Used for
+ * checkpoint/resume and for tests that start from a chosen state. */
+int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, int src_on_device);
+
+/* Last error text of ctx, or of the calling thread's last failed
+ * tlsph_create when ctx is NULL.  Valid until the next call on ctx. */
+const char *tlsph_last_error(const tlsph_ctx *ctx);
+
+/* Release the context (and its device memory when the library owns it). */
+int tlsph_destroy(tlsph_ctx *ctx);
+
+/* Per-kernel device time of the step (CUDA events recorded around each
+ * launch on the context's stream).  enable != 0 clears the accumulators and
+ * starts recording; 0 stops.  Hot-path kernels: 0 = pass 1 (velocity
+ * gradient + constitutive update), 1 = pass 2 (forces + integration). */
+int tlsph_profile_enable(tlsph_ctx *ctx, int enable);
+
+/* Accumulated device milliseconds of kernel k into ms[k] for k < n and the
+ * number of profiled steps (synchronises). */
+int tlsph_profile_read(tlsph_ctx *ctx, double *ms, int n, int64_t *steps);
+
+/* Material-point update (the constitutive step of one particle, Sec. 4-5,
+ * Algorithms 1-2, with the damage update) applied to n independent points on
+ * the device.  All pointers are DEVICE memory:
+ *   deps   n*9 strain increments in the unrotated frame (symmetric)
+ *   J      n   det F^{n+1}
+ *   state  n*16 in/out: [0,9) unrotated deviator, 9 sigma_m, 10 eps_p,
+ *          11 eps_p rate, 12 D_init, 13 D, 14 f, 15 failed (0/1)
+ * Asynchronous on `stream`. */
+int tlsph_material_point_batch(const tlsph_material *mat, double dt, int64_t n,
+                               const double *deps, const double *J, double *state,
+                               void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TLSPH_H */

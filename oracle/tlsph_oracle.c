@@ -682,7 +682,8 @@ typedef struct {
  *   eps_a = F_a X_ab - x_ab,  eps_b = F_b X_ab - x_ab,
  *   delta = (eps_a + eps_b) . xhat_ab,
  *   f_hg = -1/2 alpha (1-D_a)(1-D_b) V_a V_b W(X_ab) E / X_ab^2 delta xhat_ab,
- * with x_ab = X_ab + u_b - u_a and E the mean Young modulus of the pair. */
+ * with x_ab = X_ab + u_b - u_a and E the geometric mean sqrt(E_a E_b) of
+ * the pair's Young moduli (symmetric in a, b; E itself for one material). */
 static void pair_force(const orc_system *s, const orc_config *c, int64_t a, int64_t b, double *t)
 {
     const double *Xa = s->X + 3 * a, *Xb = s->X + 3 * b;
@@ -712,7 +713,7 @@ static void pair_force(const orc_system *s, const orc_config *c, int64_t a, int6
                 ea -= x[k]; eb -= x[k];
                 delta += (ea + eb) * xh[k];
             }
-            double E = 0.5 * (s->mats[s->mat_id[a]].E + s->mats[s->mat_id[b]].E);
+            double E = sqrt(s->mats[s->mat_id[a]].E * s->mats[s->mat_id[b]].E);
             double coef = -0.5 * c->hg_alpha * (1.0 - Da) * (1.0 - Db) * Va * Vb
                         * orc_kernel_w(r, c->h) * E / (r * r) * delta;
             for (int k = 0; k < 3; ++k) t[k] += coef * xh[k];
@@ -851,14 +852,18 @@ void orc_step(orc_system *s, const orc_config *c, int64_t nsteps)
     }
 }
 
-/* Initial state: u = 0, F = I, no stress, v = prescribed velocity on the
- * constrained particles and zero elsewhere; GTN starts from D = q1 f*(f0). */
+/* Initial state: u = 0, F = I, no stress, v = bc_vel (the prescribed
+ * velocity on constrained particles, the initial velocity elsewhere); GTN
+ * starts from D = q1 f*(f0). */
 void orc_init_state(orc_system *s)
 {
     for (int64_t i = 0; i < s->N; ++i) {
         const orc_material *m = &s->mats[s->mat_id[i]];
-        for (int k = 0; k < 3; ++k) { s->u[3 * i + k] = 0.0; s->v[3 * i + k] = 0.0; s->force[3 * i + k] = 0.0; }
-        if (s->bc_mask[i]) for (int k = 0; k < 3; ++k) s->v[3 * i + k] = s->bc_vel[3 * i + k];
+        for (int k = 0; k < 3; ++k) {
+            s->u[3 * i + k] = 0.0;
+            s->v[3 * i + k] = s->bc_vel[3 * i + k];
+            s->force[3 * i + k] = 0.0;
+        }
         for (int k = 0; k < 9; ++k) {
             s->F[9 * i + k] = (k % 4 == 0) ? 1.0 : 0.0;
             s->sd[9 * i + k] = 0.0; s->sigma[9 * i + k] = 0.0; s->A[9 * i + k] = 0.0;

@@ -1,0 +1,625 @@
+// Host runtime behind the C ABI in include/tlsph.h: argument checks, arena
+// carving, the set-up sequence (copy in, neighbour CSR, L^{-1}, initial
+// state), stream-ordered stepping, state transfer and error reporting.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tlsph_internal.cuh"
+
+using namespace tlsph;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+// Byte layout of one context's device memory.  Offsets are relative to the
+// base and 256-byte aligned.  The neighbour-build scratch overlays the
+// F / sd / sig / A block, which is only initialised after the build.
+struct Layout {
+    size_t X, vol, mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
+    size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
+    size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
+    size_t overlay_end;
+    size_t total;
+    int64_t max_cells;
+    size_t scan_elems;
+};
+
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    }
+};
+
+Layout make_layout(int64_t N, int64_t nnz_cap)
+{
+    Layout L{};
+    const size_t n = (size_t)N, d = sizeof(double);
+    Carver c;
+    L.X = c.take(3 * n * d);
+    L.vol = c.take(n * d);
+    L.mass = c.take(n * d);
+    L.sqrtE = c.take(n * d);
+    L.mat = c.take(n * sizeof(int32_t));
+    L.bcm = c.take(n);
+    L.bcv = c.take(3 * n * d);
+    L.row_ptr = c.take((n + 1) * sizeof(int64_t));
+    L.Linv = c.take(9 * n * d);
+    L.u0 = c.take(3 * n * d);
+    L.u1 = c.take(3 * n * d);
+    L.v = c.take(3 * n * d);
+    L.vh = c.take(3 * n * d);
+    L.ep = c.take(n * d);
+    L.epdot = c.take(n * d);
+    L.dinit = c.take(n * d);
+    L.por = c.take(n * d);
+    L.D0 = c.take(n * d);
+    L.D1 = c.take(n * d);
+    L.force = c.take(3 * n * d);
+    L.fail = c.take(n * sizeof(int32_t));
+    L.status = c.take(sizeof(uint32_t));
+    L.mats = c.take(TLSPH_MAX_MATERIALS * sizeof(DevMat));
+    // overlay block: F, sd, sig, A  |  neighbour-build scratch
+    const size_t ov = c.off;
+    L.F = c.take(9 * n * d);
+    L.sd = c.take(6 * n * d);
+    L.sig = c.take(6 * n * d);
+    L.A = c.take(9 * n * d);
+    const size_t state_end = c.off;
+    L.max_cells = 2 * N + 4096;
+    L.scan_elems = scan_tmp_elems(std::max<int64_t>(L.max_cells + 1, N + 1));
+    Carver s;
+    s.off = ov;
+    L.cell_start = s.take((size_t)(L.max_cells + 1) * sizeof(int64_t));
+    L.cell_cursor = s.take((size_t)L.max_cells * sizeof(int64_t));
+    L.cell_items = s.take(n * sizeof(int32_t));
+    L.scan_tmp = s.take(L.scan_elems * sizeof(int64_t));
+    c.off = std::max(state_end, s.off);
+    L.overlay_end = c.off;
+    L.col = c.take((size_t)std::max<int64_t>(nnz_cap, 1) * sizeof(int32_t));
+    L.total = c.off;
+    return L;
+}
+
+template <class T>
+T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
+
+int fail_ctx(tlsph_ctx *ctx, int code, const std::string &msg)
+{
+    ctx->err = msg;
+    if (ctx->sticky == TLSPH_OK) ctx->sticky = code;
+    return code;
+}
+
+int cuda_fail(tlsph_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail_ctx(ctx, TLSPH_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_config(const tlsph_config *c, std::string &why)
+{
+    if (!c) { why = "config is NULL"; return false; }
+    if (!(c->h > 0.0) || !isfinite(c->h)) { why = "h must be positive"; return false; }
+    if (!(c->rc > 0.0) || !isfinite(c->rc)) { why = "rc must be positive"; return false; }
+    if (c->rc > 2.0 * c->h * (1.0 + 1e-12)) { why = "rc must not exceed the kernel support 2h"; return false; }
+    if (!(c->dt > 0.0) || !isfinite(c->dt)) { why = "dt must be positive"; return false; }
+    if (!(c->hg_alpha >= 0.0) || !isfinite(c->hg_alpha)) { why = "hg_alpha must be >= 0"; return false; }
+    if (c->precision != TLSPH_PRECISION_FP64 && c->precision != TLSPH_PRECISION_MIXED) {
+        why = "precision must be TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED";
+        return false;
+    }
+    if (c->flags != 0) { why = "flags must be 0"; return false; }
+    return true;
+}
+
+void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
+{
+    DevState &s = ctx->s;
+    s.N = ctx->N;
+    s.X = at<double>(base, L.X);
+    s.vol = at<double>(base, L.vol);
+    s.mass = at<double>(base, L.mass);
+    s.sqrtE = at<double>(base, L.sqrtE);
+    s.mat = at<int32_t>(base, L.mat);
+    s.bcm = at<uint8_t>(base, L.bcm);
+    s.bcv = at<double>(base, L.bcv);
+    s.row_ptr = at<int64_t>(base, L.row_ptr);
+    s.Linv = at<double>(base, L.Linv);
+    s.u[0] = at<double>(base, L.u0);
+    s.u[1] = at<double>(base, L.u1);
+    s.v = at<double>(base, L.v);
+    s.vh = at<double>(base, L.vh);
+    s.F = at<double>(base, L.F);
+    s.sd = at<double>(base, L.sd);
+    s.sig = at<double>(base, L.sig);
+    s.A = at<double>(base, L.A);
+    s.ep = at<double>(base, L.ep);
+    s.epdot = at<double>(base, L.epdot);
+    s.dinit = at<double>(base, L.dinit);
+    s.por = at<double>(base, L.por);
+    s.D[0] = at<double>(base, L.D0);
+    s.D[1] = at<double>(base, L.D1);
+    s.force = at<double>(base, L.force);
+    s.fail = at<int32_t>(base, L.fail);
+    s.status = at<uint32_t>(base, L.status);
+    s.mats = at<DevMat>(base, L.mats);
+}
+
+struct FieldInfo {
+    void *ptr;
+    size_t elem, count;
+    bool writable, sym;   // sym: stored as 6 per particle, exchanged as 9
+};
+
+FieldInfo field_info(tlsph_ctx *ctx, int field)
+{
+    DevState &s = ctx->s;
+    const size_t n = (size_t)ctx->N, d = sizeof(double);
+    switch (field) {
+    case TLSPH_FIELD_X: return { (void *)s.X, d, 3 * n, false, false };
+    case TLSPH_FIELD_U: return { s.u[ctx->ucur], d, 3 * n, true, false };
+    case TLSPH_FIELD_V: return { s.v, d, 3 * n, true, false };
+    case TLSPH_FIELD_F: return { s.F, d, 9 * n, true, false };
+    case TLSPH_FIELD_SIGMA: return { s.sig, d, 9 * n, false, true };
+    case TLSPH_FIELD_STRESS_DEV: return { s.sd, d, 9 * n, true, true };
+    case TLSPH_FIELD_EPSP: return { s.ep, d, n, true, false };
+    case TLSPH_FIELD_EPSP_RATE: return { s.epdot, d, n, true, false };
+    case TLSPH_FIELD_DINIT: return { s.dinit, d, n, true, false };
+    case TLSPH_FIELD_DAMAGE: return { s.D[ctx->dcur], d, n, true, false };
+    case TLSPH_FIELD_POROSITY: return { s.por, d, n, true, false };
+    case TLSPH_FIELD_FAIL_STEP: return { s.fail, sizeof(int32_t), n, true, false };
+    case TLSPH_FIELD_FORCE: return { s.force, d, 3 * n, true, false };
+    case TLSPH_FIELD_A: return { s.A, d, 9 * n, false, false };
+    case TLSPH_FIELD_LINV: return { (void *)s.Linv, d, 9 * n, false, false };
+    case TLSPH_FIELD_NBR_ROWPTR: return { (void *)s.row_ptr, sizeof(int64_t), n + 1, false, false };
+    case TLSPH_FIELD_NBR_COL: return { (void *)s.col, sizeof(int32_t), (size_t)ctx->nnz, false, false };
+    default: return { nullptr, 0, 0, false, false };
+    }
+}
+
+// fold the recorded events into the accumulators and free the slots
+cudaError_t prof_fold(tlsph_ctx *ctx)
+{
+    if (ctx->prof_used == 0) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(ctx->prof_ev[ctx->prof_used - 1]);
+    if (e != cudaSuccess) return e;
+    for (int b = 0; b + 2 < ctx->prof_used; b += 3) {
+        float a = 0.f, c = 0.f;
+        cudaEventElapsedTime(&a, ctx->prof_ev[b], ctx->prof_ev[b + 1]);
+        cudaEventElapsedTime(&c, ctx->prof_ev[b + 1], ctx->prof_ev[b + 2]);
+        ctx->prof_ms[0] += a;
+        ctx->prof_ms[1] += c;
+    }
+    ctx->prof_used = 0;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+namespace tlsph {
+
+DevMat make_dev_mat(const tlsph_material &m)
+{
+    DevMat d{};
+    d.rho0 = m.rho0;
+    d.E = m.E;
+    d.K = m.E / (3.0 * (1.0 - 2.0 * m.nu));
+    d.G = m.E / (2.0 * (1.0 + m.nu));
+    d.sqrtE = sqrt(m.E);
+    d.eos = m.eos;
+    d.damage = m.damage;
+    d.rho0c02 = m.rho0 * m.c0 * m.c0;
+    d.S_alpha = m.S_alpha;
+    d.Gamma0 = m.Gamma0;
+    d.A = m.A;
+    d.B = m.B;
+    d.n = m.n;
+    d.C = m.C;
+    d.inv_epsdot0 = m.epsdot0 > 0.0 ? 1.0 / m.epsdot0 : 0.0;
+    d.inv_Wcr = m.Wcr > 0.0 ? 1.0 / m.Wcr : 0.0;
+    d.D1 = m.D1; d.D2 = m.D2; d.D3 = m.D3; d.D4 = m.D4; d.D5 = m.D5;
+    d.q1 = m.q1; d.q2 = m.q2; d.q3 = m.q3;
+    d.fN = m.fN; d.eN = m.eN; d.sN = m.sN; d.fc = m.fc; d.fF = m.fF; d.komega = m.komega;
+    d.nucl_coef = m.sN > 0.0 ? m.fN / (m.sN * sqrt(2.0 * M_PI)) : 0.0;
+    d.fstar_slope = (m.fF > m.fc) ? (1.0 / m.q1 - m.fc) / (m.fF - m.fc) : 0.0;
+    return d;
+}
+
+}  // namespace tlsph
+
+extern "C" {
+
+size_t tlsph_workspace_bytes(const tlsph_config *cfg, int64_t N, int64_t nnz_cap)
+{
+    std::string why;
+    if (!valid_config(cfg, why) || N <= 0 || nnz_cap < 0) return 0;
+    return make_layout(N, nnz_cap).total + ALIGN;
+}
+
+int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const double *vol,
+                 const int32_t *mat_id, const uint8_t *bc_mask, const double *bc_vel,
+                 const double *f0, void *arena, size_t arena_bytes, int64_t nnz_cap,
+                 void *stream, tlsph_ctx **out)
+{
+    g_create_error.clear();
+    std::string why;
+    if (!out) { g_create_error = "out is NULL"; return TLSPH_ERR_ARG; }
+    *out = nullptr;
+    if (!valid_config(cfg, why)) { g_create_error = why; return TLSPH_ERR_ARG; }
+    if (N <= 0 || N > INT32_MAX) { g_create_error = "N must be in [1, 2^31)"; return TLSPH_ERR_ARG; }
+    if (!X || !vol) { g_create_error = "X and vol are required"; return TLSPH_ERR_ARG; }
+    for (int64_t i = 0; i < N; ++i) {
+        if (!(vol[i] > 0.0) || !isfinite(vol[i])) { g_create_error = "vol must be positive and finite"; return TLSPH_ERR_ARG; }
+        if (!isfinite(X[3 * i]) || !isfinite(X[3 * i + 1]) || !isfinite(X[3 * i + 2])) {
+            g_create_error = "X must be finite"; return TLSPH_ERR_ARG;
+        }
+        if (mat_id && (mat_id[i] < 0 || mat_id[i] >= TLSPH_MAX_MATERIALS)) {
+            g_create_error = "mat_id out of range"; return TLSPH_ERR_ARG;
+        }
+    }
+    if (arena && ((uintptr_t)arena % ALIGN) != 0) { g_create_error = "arena must be 256-byte aligned"; return TLSPH_ERR_ARG; }
+    if (arena && nnz_cap <= 0) { g_create_error = "nnz_cap is required with an arena"; return TLSPH_ERR_ARG; }
+
+    tlsph_ctx *ctx = new (std::nothrow) tlsph_ctx();
+    if (!ctx) { g_create_error = "host allocation failed"; return TLSPH_ERR_NOMEM; }
+    ctx->cfg = *cfg;
+    ctx->N = N;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    cudaStream_t st = ctx->stream;
+    auto bail = [&](int code, const std::string &msg) {
+        g_create_error = msg;
+        if (ctx->owns_mem && ctx->mem) cudaFree(ctx->mem);
+        delete ctx;
+        return code;
+    };
+
+    // ---- memory: arena (capacity nnz_cap) or library-owned (exact nnz after the count)
+    Layout L = make_layout(N, arena ? nnz_cap : 0);
+    void *base = nullptr;
+    if (arena) {
+        if (arena_bytes < L.total) return bail(TLSPH_ERR_NOMEM, "arena too small: need " + std::to_string(L.total) + " bytes");
+        base = arena;
+        ctx->nnz_cap = nnz_cap;
+    } else {
+        cudaError_t e = cudaMalloc(&base, L.overlay_end);
+        if (e != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+        ctx->owns_mem = true;
+        ctx->mem = base;
+        ctx->mem_bytes = L.overlay_end;
+    }
+    bind_state(ctx, base, L);
+    DevState &s = ctx->s;
+
+    // ---- copy inputs
+    const size_t n = (size_t)N;
+    std::vector<int32_t> mat_h(n, 0);
+    std::vector<uint8_t> bcm_h(n, 0);
+    std::vector<double> bcv_h(3 * n, 0.0), f0_h(n, 0.0);
+    if (mat_id) memcpy(mat_h.data(), mat_id, n * sizeof(int32_t));
+    if (bc_mask) memcpy(bcm_h.data(), bc_mask, n);
+    if (bc_vel) memcpy(bcv_h.data(), bc_vel, 3 * n * sizeof(double));
+    if (f0) memcpy(f0_h.data(), f0, n * sizeof(double));
+    for (size_t i = 0; i < n; ++i) ctx->mat_used[mat_h[i]] = true;
+    cudaError_t e = cudaSuccess;
+#define CK(x) do { if ((e = (x)) != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e)); } } while (0)
+    CK(cudaMemcpyAsync((void *)s.X, X, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void *)s.vol, vol, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void *)s.mat, mat_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void *)s.bcm, bcm_h.data(), n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void *)s.bcv, bcv_h.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s.por, f0_h.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
+    CK(cudaMemsetAsync((void *)s.mass, 0, n * sizeof(double), st));
+    CK(cudaMemsetAsync((void *)s.sqrtE, 0, n * sizeof(double), st));
+
+    // ---- neighbour CSR
+    const CellGrid grid = make_cell_grid(X, N, cfg->rc);
+    if (grid.ncells > L.max_cells) return bail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
+    Scratch sc{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
+                at<int64_t>(base, L.scan_tmp), L.scan_elems };
+    const double rc2 = cfg->rc * cfg->rc;
+    int64_t *row_ptr = const_cast<int64_t *>(s.row_ptr);
+    CK(build_neighbors_count(s, grid, sc, rc2, row_ptr, st));
+    int64_t nnz = 0;
+    CK(cudaMemcpyAsync(&nnz, row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (nnz > INT32_MAX) return bail(TLSPH_ERR_ARG, "more than 2^31 - 1 neighbour pairs");
+    if (arena) {
+        if (nnz > nnz_cap)
+            return bail(TLSPH_ERR_NOMEM, "neighbour capacity too small: need nnz_cap >= " + std::to_string(nnz));
+        s.col = at<int32_t>(base, L.col);
+    } else {
+        // grow the library-owned block to hold the columns after the overlay
+        void *nb = nullptr;
+        const size_t need = L.overlay_end + align_up((size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t));
+        e = cudaMalloc(&nb, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+        CK(cudaMemcpyAsync(nb, base, L.overlay_end, cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        cudaFree(base);
+        base = nb;
+        ctx->mem = nb;
+        ctx->mem_bytes = need;
+        bind_state(ctx, base, L);
+        sc = Scratch{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
+                      at<int64_t>(base, L.scan_tmp), L.scan_elems };
+        row_ptr = const_cast<int64_t *>(s.row_ptr);
+        s.col = at<int32_t>(base, L.overlay_end);
+        ctx->nnz_cap = nnz;
+    }
+    ctx->nnz = nnz;
+    CK(build_neighbors_fill(s, grid, sc, rc2, row_ptr, const_cast<int32_t *>(s.col), st));
+
+    // ---- correction matrices
+    CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
+    CK(shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), s.status, st));
+    uint32_t n_sing = 0;
+    CK(cudaMemcpyAsync(&n_sing, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_sing) return bail(TLSPH_ERR_SINGULAR_L, std::to_string(n_sing) + " particles have a singular correction matrix");
+    CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
+
+    // ---- initial state (overwrites the scratch overlay)
+    CK(launch_init_state(s, st));
+    CK(cudaStreamSynchronize(st));
+#undef CK
+    ctx->need_predict = true;
+    *out = ctx;
+    return TLSPH_OK;
+}
+
+int tlsph_set_material(tlsph_ctx *ctx, int mat_id, const tlsph_material *m)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    if (!m || mat_id < 0 || mat_id >= TLSPH_MAX_MATERIALS) { ctx->err = "bad material id or NULL material"; return TLSPH_ERR_ARG; }
+    std::string why;
+    if (!(m->rho0 > 0) || !(m->E > 0) || !(m->nu > -1.0 && m->nu < 0.5)) why = "need rho0 > 0, E > 0, -1 < nu < 0.5";
+    else if (m->eos != 0 && m->eos != 1) why = "eos must be 0 or 1";
+    else if (m->eos == 1 && !(m->c0 > 0)) why = "Mie-Grueneisen needs c0 > 0";
+    else if (m->damage < 0 || m->damage > 3) why = "damage model out of range";
+    else if (!(m->A >= 0) || !(m->B >= 0) || !(m->n > 0)) why = "need A >= 0, B >= 0, n > 0";
+    else if (m->damage == TLSPH_DAMAGE_CL && !(m->Wcr > 0)) why = "Cockcroft-Latham needs Wcr > 0";
+    else if (m->damage == TLSPH_DAMAGE_GTN && (!(m->q1 > 0) || !(m->sN > 0) || !(m->fF > m->fc) || !(m->fc >= 0)))
+        why = "GTN needs q1 > 0, sN > 0, fF > fc >= 0";
+    else if (m->damage == TLSPH_DAMAGE_GTN && !(m->A > 0)) why = "GTN needs A > 0";
+    if (!why.empty()) { ctx->err = why; return TLSPH_ERR_ARG; }
+    ctx->mats_host[mat_id] = make_dev_mat(*m);
+    ctx->mat_set[mat_id] = true;
+    cudaError_t e = cudaMemcpyAsync(const_cast<DevMat *>(ctx->s.mats) + mat_id, &ctx->mats_host[mat_id], sizeof(DevMat),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_material copy");
+    e = launch_material_fields(ctx->s, mat_id, ctx->dcur, ctx->steps == 0, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_material fields");
+    // the copy source lives in ctx; wait so a later overwrite cannot race it
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_material sync");
+    ctx->need_predict = true;
+    return TLSPH_OK;
+}
+
+int tlsph_step(tlsph_ctx *ctx, int nsteps)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    if (nsteps < 0) { ctx->err = "nsteps < 0"; return TLSPH_ERR_ARG; }
+    for (int k = 0; k < TLSPH_MAX_MATERIALS; ++k)
+        if (ctx->mat_used[k] && !ctx->mat_set[k]) {
+            ctx->err = "material " + std::to_string(k) + " is used but not set";
+            return TLSPH_ERR_STATE;
+        }
+    cudaError_t e;
+    if (ctx->need_predict) {
+        e = launch_predict(ctx->s, ctx->ucur, ctx->cfg.dt, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "predict");
+        ctx->need_predict = false;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        cudaEvent_t *ev = nullptr;
+        if (ctx->prof) {
+            if (ctx->prof_used + 3 > (int)ctx->prof_ev.size()) {
+                e = prof_fold(ctx);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "profile fold");
+            }
+            ev = &ctx->prof_ev[ctx->prof_used];
+            ctx->prof_used += 3;
+            ctx->prof_steps += 1;
+        }
+        if (ctx->cfg.precision == TLSPH_PRECISION_MIXED)
+            e = launch_step_mixed(*ctx, ctx->steps, ctx->stream, ev);
+        else
+            e = launch_step_fp64(ctx->s, ctx->cfg, ctx->ucur, ctx->dcur, ctx->steps, ctx->stream, ev);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+        ctx->ucur ^= 1;
+        ctx->dcur ^= 1;
+        ctx->steps += 1;
+    }
+    return TLSPH_OK;
+}
+
+int tlsph_status_bits(tlsph_ctx *ctx, uint32_t *bits)
+{
+    if (!ctx || !bits) return TLSPH_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(bits, ctx->s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    return TLSPH_OK;
+}
+
+int tlsph_sync(tlsph_ctx *ctx)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    uint32_t bits = 0;
+    int rc = tlsph_status_bits(ctx, &bits);
+    if (rc != TLSPH_OK) return rc;
+    if (bits) {
+        ctx->err = "device status bits " + std::to_string(bits);
+        return TLSPH_ERR_NUMERICS;
+    }
+    return TLSPH_OK;
+}
+
+int tlsph_info(const tlsph_ctx *ctx, int64_t *N, int64_t *nnz, int64_t *steps)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (N) *N = ctx->N;
+    if (nnz) *nnz = ctx->nnz;
+    if (steps) *steps = ctx->steps;
+    return TLSPH_OK;
+}
+
+int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_on_device)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    FieldInfo f = field_info(ctx, field);
+    if (!f.ptr || !dst) { ctx->err = "unknown field or NULL dst"; return TLSPH_ERR_ARG; }
+    if (bytes != f.elem * f.count) { ctx->err = "byte count does not match the field"; return TLSPH_ERR_ARG; }
+    cudaStream_t st = ctx->stream;
+    cudaError_t e;
+    if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
+        e = mixed_sync_to_fp64(*ctx, field, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "mixed export");
+    }
+    if (f.sym) {
+        const int64_t N = ctx->N;
+        if (dst_on_device) {
+            e = launch_export_sym(static_cast<const double *>(f.ptr), static_cast<double *>(dst), N, st);
+        } else {
+            std::vector<double> tmp(6 * (size_t)N);
+            e = cudaMemcpyAsync(tmp.data(), f.ptr, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) {
+                double *o = static_cast<double *>(dst);
+                for (int64_t i = 0; i < N; ++i) {
+                    const double *a = &tmp[6 * i];
+                    double *m = o + 9 * i;
+                    m[0] = a[0]; m[4] = a[1]; m[8] = a[2];
+                    m[1] = m[3] = a[3]; m[5] = m[7] = a[4]; m[2] = m[6] = a[5];
+                }
+            }
+        }
+    } else {
+        e = cudaMemcpyAsync(dst, f.ptr, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_state");
+    return TLSPH_OK;
+}
+
+int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, int src_on_device)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    FieldInfo f = field_info(ctx, field);
+    if (!f.ptr || !src) { ctx->err = "unknown field or NULL src"; return TLSPH_ERR_ARG; }
+    if (!f.writable) { ctx->err = "field is read only"; return TLSPH_ERR_ARG; }
+    if (bytes != f.elem * f.count) { ctx->err = "byte count does not match the field"; return TLSPH_ERR_ARG; }
+    cudaStream_t st = ctx->stream;
+    cudaError_t e;
+    if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
+        e = mixed_sync_to_fp64(*ctx, -1, st);   // bring every FP64 field up to date first
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "mixed export");
+    }
+    if (f.sym) {
+        const int64_t N = ctx->N;
+        if (src_on_device) {
+            e = launch_import_sym(static_cast<const double *>(src), static_cast<double *>(f.ptr), N, st);
+        } else {
+            std::vector<double> tmp(6 * (size_t)N);
+            const double *a = static_cast<const double *>(src);
+            for (int64_t i = 0; i < N; ++i) {
+                const double *m = a + 9 * i;
+                double *o = &tmp[6 * i];
+                o[0] = m[0]; o[1] = m[4]; o[2] = m[8];
+                o[3] = 0.5 * (m[1] + m[3]); o[4] = 0.5 * (m[5] + m[7]); o[5] = 0.5 * (m[2] + m[6]);
+            }
+            e = cudaMemcpyAsync(f.ptr, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+    } else {
+        e = cudaMemcpyAsync(f.ptr, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state");
+    if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) ctx->mixed_dirty = true;
+    ctx->need_predict = true;
+    return TLSPH_OK;
+}
+
+const char *tlsph_last_error(const tlsph_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int tlsph_destroy(tlsph_ctx *ctx)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->owns_mem && ctx->mem) cudaFree(ctx->mem);
+    for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
+    mixed_release(*ctx);
+    delete ctx;
+    return TLSPH_OK;
+}
+
+int tlsph_profile_enable(tlsph_ctx *ctx, int enable)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "profile sync");
+    if (enable && ctx->prof_ev.empty()) {
+        ctx->prof_ev.resize(3 * 1024);
+        for (auto &ev : ctx->prof_ev) {
+            e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+        }
+    }
+    if (enable) {
+        ctx->prof_used = 0;
+        ctx->prof_ms[0] = ctx->prof_ms[1] = 0.0;
+        ctx->prof_steps = 0;
+    } else {
+        e = prof_fold(ctx);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "profile fold");
+    }
+    ctx->prof = enable != 0;
+    return TLSPH_OK;
+}
+
+int tlsph_profile_read(tlsph_ctx *ctx, double *ms, int n, int64_t *steps)
+{
+    if (!ctx || (n > 0 && !ms)) return TLSPH_ERR_ARG;
+    cudaError_t e = prof_fold(ctx);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "profile fold");
+    for (int k = 0; k < n; ++k) ms[k] = k < 2 ? ctx->prof_ms[k] : 0.0;
+    if (steps) *steps = ctx->prof_steps;
+    return TLSPH_OK;
+}
+
+int tlsph_material_point_batch(const tlsph_material *mat, double dt, int64_t n, const double *deps,
+                               const double *J, double *state, void *stream)
+{
+    if (!mat || n < 0 || (n > 0 && (!deps || !J || !state)) || !(dt > 0)) return TLSPH_ERR_ARG;
+    if (n == 0) return TLSPH_OK;
+    // the material record travels as a kernel argument copy
+    DevMat dm = make_dev_mat(*mat);
+    cudaError_t e = launch_material_point_value(dm, dt, n, deps, J, state, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? TLSPH_OK : TLSPH_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,313 @@
+// Set-up kernels: exclusive scan, neighbour sets fixed in the reference
+// configuration (Sec. 1, Sec. 2.2: S_i = { j != i : |X_j - X_i| < rc },
+// never rebuilt) and the correction matrix L_i with its inverse (Sec. 2.2,
+// Eq. correction_matrix).
+//
+// Neighbour search: particles are binned into a uniform grid of cells at
+// least rc wide (count, scan, scatter); each particle then tests the 27
+// surrounding cells.  The distance predicate is evaluated in FP64 as
+// ((dx*dx + dy*dy) + dz*dz) < rc*rc with every product and sum rounded
+// separately (no fused multiply-add), so the pair set is exactly the one its
+// definition gives in IEEE double.  Rows are sorted ascending afterwards.
+#include <math.h>
+
+#include <algorithm>
+
+#include "tlsph_device.cuh"
+#include "tlsph_internal.cuh"
+
+namespace tlsph {
+
+// ---------------------------------------------------------------- scan
+static constexpr int SCAN_THREADS = 512;
+static constexpr int SCAN_TILE = 2 * SCAN_THREADS;
+
+size_t scan_tmp_elems(int64_t n)
+{
+    size_t total = 0;
+    int64_t m = n;
+    while (m > SCAN_TILE) {
+        m = (m + SCAN_TILE - 1) / SCAN_TILE;
+        total += (size_t)m + 1;
+    }
+    return total + 1;
+}
+
+// exclusive scan of one tile per block; block totals to part[blockIdx.x]
+__global__ void k_scan_tile(int64_t *data, int64_t n, int64_t *part)
+{
+    __shared__ int64_t sh[SCAN_TILE];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    const int t = threadIdx.x;
+    int64_t i0 = base + 2 * t, i1 = i0 + 1;
+    sh[2 * t] = i0 < n ? data[i0] : 0;
+    sh[2 * t + 1] = i1 < n ? data[i1] : 0;
+    // up-sweep
+    int off = 1;
+    for (int d = SCAN_TILE >> 1; d > 0; d >>= 1) {
+        __syncthreads();
+        if (t < d) {
+            int ai = off * (2 * t + 1) - 1, bi = off * (2 * t + 2) - 1;
+            sh[bi] += sh[ai];
+        }
+        off <<= 1;
+    }
+    __syncthreads();
+    if (t == 0) {
+        if (part) part[blockIdx.x] = sh[SCAN_TILE - 1];
+        sh[SCAN_TILE - 1] = 0;
+    }
+    // down-sweep
+    for (int d = 1; d < SCAN_TILE; d <<= 1) {
+        off >>= 1;
+        __syncthreads();
+        if (t < d) {
+            int ai = off * (2 * t + 1) - 1, bi = off * (2 * t + 2) - 1;
+            int64_t tmp = sh[ai];
+            sh[ai] = sh[bi];
+            sh[bi] += tmp;
+        }
+    }
+    __syncthreads();
+    if (i0 < n) data[i0] = sh[2 * t];
+    if (i1 < n) data[i1] = sh[2 * t + 1];
+}
+
+__global__ void k_scan_add(int64_t *data, int64_t n, const int64_t *part)
+{
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    const int64_t add = part[blockIdx.x];
+    for (int k = threadIdx.x; k < SCAN_TILE; k += blockDim.x) {
+        int64_t i = base + k;
+        if (i < n) data[i] += add;
+    }
+}
+
+cudaError_t scan_exclusive_i64(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 1) {
+        k_scan_tile<<<1, SCAN_THREADS, 0, st>>>(data, n, nullptr);
+        return cudaGetLastError();
+    }
+    int64_t *part = tmp;
+    k_scan_tile<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, n, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan_exclusive_i64(part, nb, tmp + nb + 1, st);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)nb, 256, 0, st>>>(data, n, part);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- cell grid
+CellGrid make_cell_grid(const double *X, int64_t N, double rc)
+{
+    CellGrid g{};
+    double lo[3] = { X[0], X[1], X[2] }, hi[3] = { X[0], X[1], X[2] };
+    for (int64_t i = 1; i < N; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], X[3 * i + k]);
+            hi[k] = std::max(hi[k], X[3 * i + k]);
+        }
+    // a little wider than rc so rounding in the cell coordinate can never put
+    // two particles closer than rc two cells apart
+    double cs = rc * (1.0 + 1e-6);
+    const double cap = 2.0 * (double)N + 4096.0;
+    for (;;) {
+        double cells = 1.0;
+        for (int k = 0; k < 3; ++k) cells *= floor((hi[k] - lo[k]) / cs) + 1.0;
+        if (cells <= cap) break;
+        cs *= 1.25;
+    }
+    for (int k = 0; k < 3; ++k) {
+        g.xmin[k] = lo[k];
+        g.nc[k] = (int32_t)(floor((hi[k] - lo[k]) / cs) + 1.0);
+    }
+    g.cs = cs;
+    g.ncells = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    return g;
+}
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc)
+{
+    int c = (int)floor((x - lo) * inv_cs);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+struct GridArgs {
+    double lo0, lo1, lo2, inv_cs;
+    int nc0, nc1, nc2;
+};
+
+static GridArgs grid_args(const CellGrid &g)
+{
+    return GridArgs{ g.xmin[0], g.xmin[1], g.xmin[2], 1.0 / g.cs, g.nc[0], g.nc[1], g.nc[2] };
+}
+
+__device__ __forceinline__ void cell_of(const GridArgs &a, const double *x, int &cx, int &cy, int &cz)
+{
+    cx = cell_coord(x[0], a.lo0, a.inv_cs, a.nc0);
+    cy = cell_coord(x[1], a.lo1, a.inv_cs, a.nc1);
+    cz = cell_coord(x[2], a.lo2, a.inv_cs, a.nc2);
+}
+
+__global__ void k_cell_count(const double *X, int64_t N, GridArgs a, int64_t *cell_count)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int cx, cy, cz;
+    cell_of(a, X + 3 * i, cx, cy, cz);
+    atomicAdd((unsigned long long *)&cell_count[((int64_t)cz * a.nc1 + cy) * a.nc0 + cx], 1ull);
+}
+
+__global__ void k_cell_scatter(const double *X, int64_t N, GridArgs a, const int64_t *cell_start,
+                               int64_t *cursor, int32_t *items)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int cx, cy, cz;
+    cell_of(a, X + 3 * i, cx, cy, cz);
+    int64_t c = ((int64_t)cz * a.nc1 + cy) * a.nc0 + cx;
+    unsigned long long slot = atomicAdd((unsigned long long *)&cursor[c], 1ull);
+    items[cell_start[c] + (int64_t)slot] = (int32_t)i;
+}
+
+// the neighbour predicate with every operation rounded on its own
+__device__ __forceinline__ bool within(const double *xi, const double *xj, double rc2)
+{
+    double dx = __dsub_rn(xj[0], xi[0]);
+    double dy = __dsub_rn(xj[1], xi[1]);
+    double dz = __dsub_rn(xj[2], xi[2]);
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return r2 < rc2;
+}
+
+// one thread per particle: count (out == nullptr) or write its neighbours
+__global__ void k_nbr(const double *X, int64_t N, GridArgs a, const int64_t *cell_start,
+                      const int32_t *items, double rc2, int64_t *count, const int64_t *row_ptr,
+                      int32_t *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double xi[3] = { X[3 * i], X[3 * i + 1], X[3 * i + 2] };
+    int cx, cy, cz;
+    cell_of(a, xi, cx, cy, cz);
+    int64_t n = 0;
+    int64_t w = out ? row_ptr[i] : 0;
+    for (int z = max(cz - 1, 0); z <= min(cz + 1, a.nc2 - 1); ++z)
+        for (int y = max(cy - 1, 0); y <= min(cy + 1, a.nc1 - 1); ++y) {
+            int64_t rowc = ((int64_t)z * a.nc1 + y) * a.nc0;
+            int x0 = max(cx - 1, 0), x1 = min(cx + 1, a.nc0 - 1);
+            // cells x0..x1 of this (y, z) line are contiguous in the cell order
+            int64_t b = cell_start[rowc + x0], e = cell_start[rowc + x1 + 1];
+            for (int64_t k = b; k < e; ++k) {
+                int32_t j = items[k];
+                if (j == i) continue;
+                if (within(xi, X + 3 * (int64_t)j, rc2)) {
+                    if (out) out[w + n] = j;
+                    ++n;
+                }
+            }
+        }
+    if (!out) count[i] = n;
+}
+
+// insertion sort of each row (rows are short; runs once)
+__global__ void k_sort_rows(const int64_t *row_ptr, int32_t *col, int64_t N)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int64_t b = row_ptr[i], e = row_ptr[i + 1];
+    for (int64_t k = b + 1; k < e; ++k) {
+        int32_t v = col[k];
+        int64_t m = k - 1;
+        while (m >= b && col[m] > v) { col[m + 1] = col[m]; --m; }
+        col[m + 1] = v;
+    }
+}
+
+static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
+                                  int64_t *row_ptr, cudaStream_t st)
+{
+    GridArgs a = grid_args(g);
+    cudaError_t e;
+    // cell histogram -> cell_start (exclusive scan) -> scatter with a cursor
+    if ((e = cudaMemsetAsync(sc.cell_start, 0, (g.ncells + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
+    k_cell_count<<<blocks_for(s.N, 256), 256, 0, st>>>(s.X, s.N, a, sc.cell_start);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive_i64(sc.cell_start, g.ncells + 1, sc.scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sc.cell_cursor, 0, g.ncells * sizeof(int64_t), st)) != cudaSuccess) return e;
+    k_cell_scatter<<<blocks_for(s.N, 256), 256, 0, st>>>(s.X, s.N, a, sc.cell_start, sc.cell_cursor,
+                                                         sc.cell_items);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_nbr<<<blocks_for(s.N, 128), 128, 0, st>>>(s.X, s.N, a, sc.cell_start, sc.cell_items, rc2, row_ptr,
+                                                 nullptr, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(row_ptr + s.N, 0, sizeof(int64_t), st)) != cudaSuccess) return e;
+    return scan_exclusive_i64(row_ptr, s.N + 1, sc.scan_tmp, st);
+}
+
+cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
+                                 const int64_t *row_ptr, int32_t *col, cudaStream_t st)
+{
+    GridArgs a = grid_args(g);
+    k_nbr<<<blocks_for(s.N, 128), 128, 0, st>>>(s.X, s.N, a, sc.cell_start, sc.cell_items, rc2, nullptr,
+                                                 row_ptr, col);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sort_rows<<<blocks_for(s.N, 128), 128, 0, st>>>(row_ptr, col, s.N);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- correction matrix
+// One warp per particle: L_i = sum_j V_j (X_j - X_i) (x) grad W_i(X_ij), with
+// grad W = W'(r) (X_j - X_i) / r, so L_i is symmetric; inverted by the
+// adjugate.  A row whose |det L| <= 1e-12 |L|_F^3 is reported singular and
+// gets L^{-1} = 0.
+__global__ void k_shape(const double *X, const double *vol, const int64_t *row_ptr, const int32_t *col,
+                        int64_t N, double inv_h, double dw_norm, double *Linv, uint32_t *n_singular)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
+    double l[6] = { 0, 0, 0, 0, 0, 0 };
+    for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
+        const int64_t j = col[p];
+        const double dx = X[3 * j] - xi, dy = X[3 * j + 1] - yi, dz = X[3 * j + 2] - zi;
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        const double c = vol[j] * dw_norm * spline_dw(r * inv_h) / r;
+        l[0] += c * dx * dx; l[1] += c * dy * dy; l[2] += c * dz * dz;
+        l[3] += c * dx * dy; l[4] += c * dy * dz; l[5] += c * dz * dx;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) l[k] = warp_allsum(l[k]);
+    if (lane == 0) {
+        double L[9], c[9];
+        sym_to_full(l, L);
+        cof3(L, c);
+        const double det = L[0] * c[0] + L[1] * c[1] + L[2] * c[2];
+        double fn2 = 0.0;
+        for (int k = 0; k < 9; ++k) fn2 += L[k] * L[k];
+        const double fn = sqrt(fn2);
+        const bool ok = isfinite(det) && fabs(det) > 1e-12 * fn * fn * fn;
+        // L^{-1} = adj(L) / det = cof(L)^T / det
+        for (int k = 0; k < 3; ++k)
+            for (int m = 0; m < 3; ++m) Linv[9 * i + 3 * k + m] = ok ? c[3 * m + k] / det : 0.0;
+        if (!ok) atomicAdd(n_singular, 1u);
+    }
+}
+
+cudaError_t shape_matrix(const DevState &s, double h, double *Linv, uint32_t *n_singular, cudaStream_t st)
+{
+    const double dw_norm = 1.0 / (M_PI * h * h * h * h);
+    k_shape<<<blocks_for(s.N * 32, 256), 256, 0, st>>>(s.X, s.vol, s.row_ptr, s.col, s.N, 1.0 / h, dw_norm, Linv,
+                                                       n_singular);
+    return cudaGetLastError();
+}
+
+}  // namespace tlsph

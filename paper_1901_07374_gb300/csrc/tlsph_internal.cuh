@@ -1,0 +1,133 @@
+// Internal declarations of the TLSPH CUDA library: the context, the device
+// material record and the launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tlsph.h"
+
+namespace tlsph {
+
+// Material constants as the kernels use them: the paper's symbols plus the
+// derived moduli (K = E / (3 (1 - 2 nu)), G = E / (2 (1 + nu))) and the
+// reciprocals the inner loops would otherwise divide by.
+struct DevMat {
+    double rho0, E, K, G, sqrtE;
+    int32_t eos, damage;
+    double rho0c02, S_alpha, Gamma0;
+    double A, B, n, C, inv_epsdot0;
+    double inv_Wcr;
+    double D1, D2, D3, D4, D5;
+    double q1, q2, q3, fN, eN, sN, fc, fF, komega;
+    double nucl_coef;    // fN / (sN sqrt(2 pi))
+    double fstar_slope;  // (1/q1 - fc) / (fF - fc)
+};
+
+// Device arrays of one context.  SoA per quantity; vectors and tensors of a
+// particle are contiguous (3 or 6/9 doubles) so the epilogues read them with
+// wide loads.  Symmetric tensors are stored as 6 values (xx, yy, zz, xy, yz, zx).
+struct DevState {
+    int64_t N;
+    const double *X;        // N*3
+    const double *vol;      // N
+    const double *mass;     // N   rho0 V
+    const double *sqrtE;    // N   sqrt of the particle's Young modulus (hourglass stiffness)
+    const int32_t *mat;     // N
+    const uint8_t *bcm;     // N
+    const double *bcv;      // N*3
+    const int64_t *row_ptr; // N+1
+    const int32_t *col;     // nnz
+    const double *Linv;     // N*9
+    double *u[2];           // N*3 ping-pong: u^n and the predicted u^{n+1}
+    double *v;              // N*3 v^n
+    double *vh;             // N*3 v^{n+1/2}
+    double *F;              // N*9
+    double *sd;             // N*6 unrotated deviator
+    double *sig;            // N*6 Cauchy stress
+    double *A;              // N*9
+    double *ep, *epdot, *dinit, *por;  // N
+    double *D[2];           // N ping-pong
+    double *force;          // N*3
+    int32_t *fail;          // N
+    uint32_t *status;       // 1
+    const DevMat *mats;     // TLSPH_MAX_MATERIALS
+};
+
+struct Scratch {            // neighbour-build scratch (set-up only)
+    int64_t *cell_start;    // ncells + 1
+    int64_t *cell_cursor;   // ncells
+    int32_t *cell_items;    // N
+    int64_t *scan_tmp;      // scan partial sums
+    size_t scan_tmp_elems;
+};
+
+}  // namespace tlsph
+
+struct tlsph_ctx {
+    tlsph_config cfg;
+    int64_t N = 0, nnz = 0, nnz_cap = 0, steps = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_mem = false;
+    void *mem = nullptr;
+    size_t mem_bytes = 0;
+    tlsph::DevState s{};
+    tlsph::DevMat mats_host[TLSPH_MAX_MATERIALS]{};
+    bool mat_set[TLSPH_MAX_MATERIALS]{};
+    bool mat_used[TLSPH_MAX_MATERIALS]{};
+    int ucur = 0;   // u[ucur] = u^n, u[ucur ^ 1] = predicted u^{n+1}
+    int dcur = 0;   // D[dcur] = D^n
+    bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
+    bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
+    void *mixed = nullptr;      // mixed-precision state (mixed.cu)
+    // profiling: 3 events per step (before pass 1, between, after pass 2)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_used = 0;
+    double prof_ms[2] = { 0.0, 0.0 };
+    int64_t prof_steps = 0;
+    int sticky = TLSPH_OK;
+    std::string err;
+};
+
+namespace tlsph {
+
+// scan.cu / nbr.cu
+size_t scan_tmp_elems(int64_t n);
+cudaError_t scan_exclusive_i64(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t st);
+struct CellGrid {
+    double xmin[3];
+    double cs;
+    int32_t nc[3];
+    int64_t ncells;
+};
+CellGrid make_cell_grid(const double *X_host, int64_t N, double rc);
+cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
+                                  int64_t *row_ptr, cudaStream_t st);
+cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
+                                 const int64_t *row_ptr, int32_t *col, cudaStream_t st);
+cudaError_t shape_matrix(const DevState &s, double h, double *Linv, uint32_t *n_singular, cudaStream_t st);
+
+// step64.cu
+cudaError_t launch_init_state(const DevState &s, cudaStream_t st);
+cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool gtn_damage, cudaStream_t st);
+cudaError_t launch_predict(const DevState &s, int ucur, double dt, cudaStream_t st);
+// ev: null, or 3 events recorded before pass 1, between the passes and after pass 2
+cudaError_t launch_step_fp64(const DevState &s, const tlsph_config &cfg, int ucur, int dcur,
+                             int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
+cudaError_t launch_material_point_value(const DevMat &m, double dt, int64_t n, const double *deps,
+                                        const double *J, double *state, cudaStream_t st);
+cudaError_t launch_export_sym(const double *src6, double *dst9, int64_t N, cudaStream_t st);
+cudaError_t launch_import_sym(const double *src9, double *dst6, int64_t N, cudaStream_t st);
+
+DevMat make_dev_mat(const tlsph_material &m);
+
+// mixed.cu
+cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
+cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st);
+void mixed_release(tlsph_ctx &ctx);
+
+}  // namespace tlsph

@@ -1,0 +1,314 @@
+"""ctypes binding of libtlsph.so (the C ABI in include/tlsph.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels behind the ABI.  PyTorch provides device memory (the optional arena)
+and the CUDA stream.  There is no CPU fallback: if the library is missing or
+the GPU is absent, constructing a Simulation raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PRECISION = {"fp64": 0, "mixed": 1}
+# precision bench.py reports by default
+DEFAULT_PRECISION = "fp64"
+# precisions the smoke check runs, with the field tolerance against the oracle
+SMOKE_PRECISIONS = (("fp64", 1e-10),)
+
+FIELD = dict(X=0, U=1, V=2, F=3, SIGMA=4, STRESS_DEV=5, EPSP=6, EPSP_RATE=7, DINIT=8, DAMAGE=9,
+             POROSITY=10, FAIL_STEP=11, FORCE=12, A=13, LINV=14, NBR_ROWPTR=15, NBR_COL=16)
+# (numpy dtype, components per particle); None = special count
+_FIELD_SHAPE = dict(X=(np.float64, 3), U=(np.float64, 3), V=(np.float64, 3), F=(np.float64, 9),
+                    SIGMA=(np.float64, 9), STRESS_DEV=(np.float64, 9), EPSP=(np.float64, 1),
+                    EPSP_RATE=(np.float64, 1), DINIT=(np.float64, 1), DAMAGE=(np.float64, 1),
+                    POROSITY=(np.float64, 1), FAIL_STEP=(np.int32, 1), FORCE=(np.float64, 3),
+                    A=(np.float64, 9), LINV=(np.float64, 9), NBR_ROWPTR=(np.int64, None),
+                    NBR_COL=(np.int32, None))
+
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_SINGULAR_L", -3: "ERR_NUMERICS", -4: "ERR_NOMEM",
+          -5: "ERR_CUDA", -6: "ERR_STATE"}
+ST_POLAR_CAP, ST_NEWTON_CAP, ST_BAD_J, ST_NONFINITE = 1, 2, 4, 8
+
+
+class TlsphError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("rc", ctypes.c_double), ("dt", ctypes.c_double),
+                ("hg_alpha", ctypes.c_double), ("precision", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_double), ("E", ctypes.c_double), ("nu", ctypes.c_double),
+                ("eos", ctypes.c_int32),
+                ("c0", ctypes.c_double), ("S_alpha", ctypes.c_double), ("Gamma0", ctypes.c_double),
+                ("A", ctypes.c_double), ("B", ctypes.c_double), ("n", ctypes.c_double),
+                ("C", ctypes.c_double), ("epsdot0", ctypes.c_double),
+                ("damage", ctypes.c_int32),
+                ("Wcr", ctypes.c_double),
+                ("D1", ctypes.c_double), ("D2", ctypes.c_double), ("D3", ctypes.c_double),
+                ("D4", ctypes.c_double), ("D5", ctypes.c_double),
+                ("q1", ctypes.c_double), ("q2", ctypes.c_double), ("q3", ctypes.c_double),
+                ("fN", ctypes.c_double), ("eN", ctypes.c_double), ("sN", ctypes.c_double),
+                ("fc", ctypes.c_double), ("fF", ctypes.c_double), ("komega", ctypes.c_double)]
+
+
+def make_material(d: dict) -> Material:
+    m = Material()
+    for name, _ in Material._fields_:
+        setattr(m, name, d[name])
+    return m
+
+
+EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph_step", "tlsph_sync",
+           "tlsph_status_bits", "tlsph_info", "tlsph_get_state", "tlsph_set_state", "tlsph_last_error",
+           "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read")
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libtlsph.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: build it first (paper_1901_07374_gb300.build.build())")
+            _build.build()
+        L = ctypes.CDLL(path)
+        vp, i64, i32, dbl, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        L.tlsph_workspace_bytes.restype = sz
+        L.tlsph_workspace_bytes.argtypes = [ctypes.POINTER(Config), i64, i64]
+        L.tlsph_create.restype = i32
+        L.tlsph_create.argtypes = [ctypes.POINTER(Config), i64, vp, vp, vp, vp, vp, vp, vp, sz, i64, vp,
+                                   ctypes.POINTER(vp)]
+        L.tlsph_set_material.restype = i32
+        L.tlsph_set_material.argtypes = [vp, i32, ctypes.POINTER(Material)]
+        L.tlsph_step.restype = i32
+        L.tlsph_step.argtypes = [vp, i32]
+        L.tlsph_sync.restype = i32
+        L.tlsph_sync.argtypes = [vp]
+        L.tlsph_status_bits.restype = i32
+        L.tlsph_status_bits.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+        L.tlsph_info.restype = i32
+        L.tlsph_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.tlsph_get_state.restype = i32
+        L.tlsph_get_state.argtypes = [vp, i32, vp, sz, i32]
+        L.tlsph_set_state.restype = i32
+        L.tlsph_set_state.argtypes = [vp, i32, vp, sz, i32]
+        L.tlsph_last_error.restype = ctypes.c_char_p
+        L.tlsph_last_error.argtypes = [vp]
+        L.tlsph_destroy.restype = i32
+        L.tlsph_destroy.argtypes = [vp]
+        L.tlsph_profile_enable.restype = i32
+        L.tlsph_profile_enable.argtypes = [vp, i32]
+        L.tlsph_profile_read.restype = i32
+        L.tlsph_profile_read.argtypes = [vp, ctypes.POINTER(dbl), i32, ctypes.POINTER(i64)]
+        L.tlsph_material_point_batch.restype = i32
+        L.tlsph_material_point_batch.argtypes = [ctypes.POINTER(Material), dbl, i64, vp, vp, vp, vp]
+        _lib = L
+        return L
+
+
+def _check(code: int, ctx=None):
+    if code != 0:
+        msg = load().tlsph_last_error(ctx).decode(errors="replace")
+        raise TlsphError(code, msg)
+
+
+def make_config(h, rc, dt, hg_alpha, precision="fp64") -> Config:
+    return Config(float(h), float(rc), float(dt), float(hg_alpha), PRECISION[precision], 0)
+
+
+def workspace_bytes(cfg: Config, N: int, nnz_cap: int) -> int:
+    return int(load().tlsph_workspace_bytes(ctypes.byref(cfg), int(N), int(nnz_cap)))
+
+
+def _host(a, dtype, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Simulation:
+    """One specimen resident on the GPU, advanced by the library's step.
+
+    X, vol, mat_id, bc_mask, bc_vel, f0: host arrays (see tlsph_create).
+    materials: list of material dicts (index = material id).
+    arena: optional torch.uint8 CUDA tensor the library carves (with
+    nnz_cap); otherwise the library owns its memory.
+    stream: torch.cuda.Stream or raw handle; default the current stream."""
+
+    def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
+                 precision="fp64", arena=None, nnz_cap=0, stream=None):
+        L = load()
+        X = _host(X, np.float64)
+        self.N = N = X.shape[0]
+        X = X.reshape(N, 3)
+        vol = _host(vol, np.float64)
+        mat_id = _host(mat_id, np.int32)
+        bc_mask = _host(bc_mask, np.uint8)
+        bc_vel = _host(bc_vel, np.float64, (N, 3))
+        f0 = _host(f0, np.float64)
+        self.cfg = make_config(h, rc, dt, hg_alpha, precision)
+        self.precision = precision
+        self.arena = arena
+        self.stream = _stream_handle(stream)
+        ctx = ctypes.c_void_p()
+        if arena is not None:
+            aptr, abytes = ctypes.c_void_p(arena.data_ptr()), arena.numel() * arena.element_size()
+        else:
+            aptr, abytes = None, 0
+        code = L.tlsph_create(ctypes.byref(self.cfg), N, _ptr(X), _ptr(vol), _ptr(mat_id), _ptr(bc_mask),
+                              _ptr(bc_vel), _ptr(f0), aptr, abytes, int(nnz_cap), ctypes.c_void_p(self.stream),
+                              ctypes.byref(ctx))
+        _check(code, None)
+        self.ctx = ctx
+        self._mats = []
+        for k, m in enumerate(materials):
+            mm = make_material(m)
+            self._mats.append(mm)
+            _check(L.tlsph_set_material(self.ctx, k, ctypes.byref(mm)), self.ctx)
+
+    @classmethod
+    def from_workload(cls, w, precision="fp64", **kw):
+        sp = w.specimen
+        return cls(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, w.materials, w.h, w.rc, w.dt,
+                   w.hg_alpha, precision=precision, **kw)
+
+    # ---------------------------------------------------------------- stepping
+    def step(self, n: int = 1) -> None:
+        _check(load().tlsph_step(self.ctx, int(n)), self.ctx)
+
+    def sync(self) -> None:
+        _check(load().tlsph_sync(self.ctx), self.ctx)
+
+    def status_bits(self) -> int:
+        b = ctypes.c_uint32(0)
+        _check(load().tlsph_status_bits(self.ctx, ctypes.byref(b)), self.ctx)
+        return int(b.value)
+
+    def profile(self, enable: bool = True) -> None:
+        _check(load().tlsph_profile_enable(self.ctx, 1 if enable else 0), self.ctx)
+
+    def profile_read(self):
+        """(ms of pass 1, ms of pass 2, profiled steps)."""
+        ms = (ctypes.c_double * 2)()
+        n = ctypes.c_int64()
+        _check(load().tlsph_profile_read(self.ctx, ms, 2, ctypes.byref(n)), self.ctx)
+        return ms[0], ms[1], n.value
+
+    def info(self):
+        N, nnz, steps = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().tlsph_info(self.ctx, ctypes.byref(N), ctypes.byref(nnz), ctypes.byref(steps)), self.ctx)
+        return N.value, nnz.value, steps.value
+
+    @property
+    def nnz(self) -> int:
+        return self.info()[1]
+
+    @property
+    def steps(self) -> int:
+        return self.info()[2]
+
+    # ---------------------------------------------------------------- state
+    def _shape(self, name):
+        dt, w = _FIELD_SHAPE[name]
+        if name == "NBR_ROWPTR":
+            return dt, (self.N + 1,)
+        if name == "NBR_COL":
+            return dt, (self.nnz,)
+        return dt, ((self.N,) if w == 1 else (self.N, w))
+
+    def get(self, name: str) -> np.ndarray:
+        """Copy a field to a new host array."""
+        dt, shape = self._shape(name)
+        out = np.empty(shape, dt)
+        _check(load().tlsph_get_state(self.ctx, FIELD[name], _ptr(out), out.nbytes, 0), self.ctx)
+        return out
+
+    def get_device(self, name: str, out=None):
+        """Copy a field into a torch CUDA tensor (device to device)."""
+        import torch
+        dt, shape = self._shape(name)
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dt]
+        if out is None:
+            out = torch.empty(shape, dtype=tdt, device="cuda")
+        _check(load().tlsph_get_state(self.ctx, FIELD[name], ctypes.c_void_p(out.data_ptr()),
+                                      out.numel() * out.element_size(), 1), self.ctx)
+        return out
+
+    def set(self, name: str, value) -> None:
+        dt, shape = self._shape(name)
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(value, dt), shape))
+        _check(load().tlsph_set_state(self.ctx, FIELD[name], _ptr(a), a.nbytes, 0), self.ctx)
+
+    def state(self) -> dict:
+        names = ("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY",
+                 "FAIL_STEP", "FORCE", "A")
+        return {k: self.get(k) for k in names}
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            load().tlsph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def material_point_batch(mat: dict, dt: float, deps, J, state, stream=None) -> None:
+    """Constitutive update of n material points on the GPU (torch CUDA float64
+    tensors: deps (n, 9), J (n,), state (n, 16) updated in place)."""
+    L = load()
+    m = make_material(mat)
+    n = int(J.numel())
+    for t in (deps, J, state):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("material_point_batch needs contiguous CUDA tensors")
+    code = L.tlsph_material_point_batch(ctypes.byref(m), float(dt), n, ctypes.c_void_p(deps.data_ptr()),
+                                        ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(state.data_ptr()),
+                                        ctypes.c_void_p(_stream_handle(stream)))
+    _check(code, None)

@@ -1,0 +1,86 @@
+"""Helpers shared by the GPU parity tests: error norms with field floors,
+mapping between the oracle's state and the library's fields, and the
+extraction of a ball of particles around sampled particles so the oracle can
+reproduce single particles of a full-size run."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+# library field name -> oracle state key
+ORACLE_KEY = {"U": "u", "V": "v", "F": "F", "SIGMA": "sigma", "STRESS_DEV": "sd", "EPSP": "ep",
+              "EPSP_RATE": "epdot", "DINIT": "dinit", "DAMAGE": "D", "POROSITY": "f", "FORCE": "force",
+              "A": "A", "FAIL_STEP": "fail_step"}
+
+# FP64 tolerance: normwise relative, per field (the FP64 GPU path reorders
+# the sums over j, nothing else)
+TOL_FP64 = 1e-10
+
+
+def floors(w) -> dict:
+    """Scale below which a field counts as zero: spacing for lengths, the grip
+    speed for velocities, the yield stress for stresses."""
+    sp = w.specimen
+    m = w.materials[0]
+    L = sp.spacing
+    vref = max(1e-3, float(np.abs(sp.bc_vel).max()))
+    s = max(m["A"], 1e6)
+    return dict(U=1e-3 * L, V=1e-3 * vref, F=1.0, SIGMA=1e-3 * s, STRESS_DEV=1e-3 * s, A=1e-3 * s,
+                EPSP=1e-6, EPSP_RATE=1e-6 / w.dt * 1e-3, DINIT=1e-6, DAMAGE=1e-6, POROSITY=1e-6,
+                FORCE=1e-3 * s * L * L)
+
+
+def relerr(a, b, floor):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if a.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), floor))
+
+
+def compare_state(gpu, orc, w, tol=TOL_FP64, fields=None, idx=None):
+    """Per-field normwise errors; returns {field: err} and asserts <= tol."""
+    fl = floors(w)
+    out = {}
+    for f in fields or ("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE",
+                        "POROSITY", "FORCE", "A"):
+        g = gpu[f]
+        o = orc[ORACLE_KEY[f]]
+        if idx is not None:
+            g, o = g[idx], o[idx]
+        out[f] = relerr(g.reshape(len(g), -1), o.reshape(len(o), -1), fl[f])
+    bad = {k: v for k, v in out.items() if not v <= tol}
+    assert not bad, f"fields above {tol}: {bad}"
+    return out
+
+
+def oracle_from_state(w, state: dict, step: int = 0) -> oracle.Simulation:
+    """A fresh oracle simulation of workload w whose state is overwritten by
+    `state` (oracle keys)."""
+    sim = oracle.Simulation.from_workload(w)
+    for k, v in state.items():
+        if k == "fail_step":
+            sim.fail_step[:] = v
+        else:
+            sim[k][:] = v
+    sim.sys.step = step
+    return sim
+
+
+def ball(X, centres, radius):
+    """Indices of all particles within `radius` of any centre (sorted)."""
+    keep = np.zeros(X.shape[0], bool)
+    for c in centres:
+        keep |= np.sum((X - X[c]) ** 2, axis=1) < radius * radius
+    return np.nonzero(keep)[0]
+
+
+def sub_workload(w, idx):
+    """The workload restricted to the particles idx (same materials, dt)."""
+    import dataclasses
+    sp = w.specimen
+    sub = dataclasses.replace(sp, X=np.ascontiguousarray(sp.X[idx]), vol=sp.vol[idx], mat_id=sp.mat_id[idx],
+                              bc_mask=sp.bc_mask[idx], bc_vel=np.ascontiguousarray(sp.bc_vel[idx]), f0=sp.f0[idx],
+                              dims=())
+    return dataclasses.replace(w, specimen=sub)

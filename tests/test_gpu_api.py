@@ -1,0 +1,97 @@
+"""C-ABI behaviour on the GPU: caller-owned arenas, checkpoint/resume,
+error reporting and status bits (raised from the host or from inputs the
+kernels handle, never by faulting the device)."""
+import numpy as np
+import pytest
+
+from paper_1901_07374_gb300 import specimen as S
+from paper_1901_07374_gb300 import tlsph
+
+pytestmark = pytest.mark.gpu
+
+WRITABLE = ("U", "V", "F", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY", "FAIL_STEP", "FORCE")
+
+
+def test_resume_is_bitwise():
+    """Checkpoint at step k into a new context, continue: identical bits to
+    the uninterrupted run."""
+    w = S.failure_variant(S.tensile_bar_cl())
+    a = tlsph.Simulation.from_workload(w)
+    a.step(150)
+    ck = {k: a.get(k) for k in WRITABLE}
+    a.step(100)
+    ref = a.state()
+    b = tlsph.Simulation.from_workload(w)
+    for k, v in ck.items():
+        b.set(k, v)
+    b.step(100)
+    got = b.state()
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_arena_matches_owned_memory():
+    import torch
+    w = S.tensile_bar_cl(nx=6, ny=6, nz=16)
+    a = tlsph.Simulation.from_workload(w)
+    nnz = a.nnz
+    cfg = tlsph.make_config(w.h, w.rc, w.dt, w.hg_alpha)
+    nbytes = tlsph.workspace_bytes(cfg, w.specimen.N, nnz)
+    arena = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    b = tlsph.Simulation.from_workload(w, arena=arena, nnz_cap=nnz)
+    a.step(20)
+    b.step(20)
+    for k, v in a.state().items():
+        assert np.array_equal(b.get(k), v), k
+
+
+def test_arena_too_small_and_capacity_errors():
+    import torch
+    w = S.tensile_bar_cl(nx=5, ny=5, nz=8)
+    cfg = tlsph.make_config(w.h, w.rc, w.dt, w.hg_alpha)
+    need = tlsph.workspace_bytes(cfg, w.specimen.N, 10)
+    arena = torch.empty(need, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tlsph.TlsphError) as e:
+        tlsph.Simulation.from_workload(w, arena=arena, nnz_cap=10)
+    assert e.value.code == -4 and "nnz_cap" in str(e.value)
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tlsph.TlsphError) as e:
+        tlsph.Simulation.from_workload(w, arena=small, nnz_cap=10)
+    assert e.value.code == -4
+
+
+def test_isolated_particle_is_singular():
+    sp = S.tensile_bar(4, 4, 6, 1e-3, jitter=0.0)
+    X = np.vstack([sp.X, [[1.0, 1.0, 1.0]]])
+    N = X.shape[0]
+    with pytest.raises(tlsph.TlsphError) as e:
+        tlsph.Simulation(X, np.full(N, 1e-9), None, None, None, None, [S.aluminium_cl()], 1.5e-3, 3e-3, 1e-8, 0.0)
+    assert e.value.code == -2
+
+
+def test_unset_material_is_reported():
+    w = S.tensile_bar_cl(nx=4, ny=4, nz=6)
+    sp = w.specimen
+    sp.mat_id[:] = 1
+    g = tlsph.Simulation(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, [S.aluminium_cl()], w.h, w.rc, w.dt,
+                         w.hg_alpha)
+    with pytest.raises(tlsph.TlsphError) as e:
+        g.step(1)
+    assert e.value.code == -6
+
+
+def test_nonfinite_input_sets_status_bits():
+    """A NaN velocity (set from the host) propagates to a non-finite state:
+    tlsph_sync reports ERR_NUMERICS with the status bits, the context stays
+    usable for reading."""
+    w = S.tensile_bar_cl(nx=5, ny=5, nz=8)
+    g = tlsph.Simulation.from_workload(w)
+    v = g.get("V")
+    v[10] = np.nan
+    g.set("V", v)
+    g.step(2)
+    with pytest.raises(tlsph.TlsphError) as e:
+        g.sync()
+    assert e.value.code == -3
+    assert g.status_bits() != 0
+    assert g.get("U").shape == (w.specimen.N, 3)

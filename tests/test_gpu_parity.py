@@ -1,0 +1,223 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Neighbour sets and failure sets must match bit for bit; every floating-point
+field must match within TOL_FP64 (normwise relative, per field) -- the FP64
+GPU path only regroups the sums over j.  Full-size runs are checked on
+sampled particles the oracle reproduces from a ball of particles around
+them, and through properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_07374_gb300 import specimen as S
+from paper_1901_07374_gb300 import tlsph
+from parity import TOL_FP64, ball, compare_state, floors, oracle_from_state, relerr, sub_workload
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_sim(w, precision="fp64", **kw):
+    return tlsph.Simulation.from_workload(w, precision=precision, **kw)
+
+
+SMALL = [
+    ("bar_cl_5x6x9", lambda: S.tensile_bar_cl(nx=5, ny=6, nz=9)),
+    ("bar_cl_8x8x32", lambda: S.tensile_bar_cl()),
+    ("bar_jc_7x9x33_seed3", lambda: S.tensile_bar_jc(nx=7, ny=9, nz=33, seed=3, steps=50)),
+]
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_neighbors_bit_exact(name, make):
+    w = make()
+    g = gpu_sim(w)
+    row_ptr, col = oracle.neighbors(w.specimen.X, w.rc)
+    assert np.array_equal(g.get("NBR_ROWPTR"), row_ptr)
+    assert np.array_equal(g.get("NBR_COL"), col)
+
+
+def test_neighbors_exact_lattice_ties():
+    """Exact lattice: pairs at exactly rc are excluded on both sides."""
+    sp = S.tensile_bar(7, 7, 11, 0.5e-3, jitter=0.0)
+    w = S.Workload("exact", sp, [S.aluminium_cl()], 0.75e-3, 1.5e-3, 2e-8, 10.0, 1)
+    g = gpu_sim(w)
+    row_ptr, col = oracle.neighbors(sp.X, w.rc)
+    assert np.array_equal(g.get("NBR_ROWPTR"), row_ptr)
+    assert np.array_equal(g.get("NBR_COL"), col)
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_correction_matrix(name, make):
+    w = make()
+    g = gpu_sim(w)
+    o = oracle.Simulation.from_workload(w)
+    assert relerr(g.get("LINV"), o.Linv, 1.0) <= 1e-12
+
+
+def _run_both(w, steps, precision="fp64"):
+    g = gpu_sim(w, precision)
+    o = oracle.Simulation.from_workload(w)
+    g.step(steps)
+    o.step(steps)
+    g.sync()
+    return g.state(), o.state()
+
+
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_first_steps_all_fields(steps):
+    w = S.tensile_bar_cl()
+    gs, os_ = _run_both(w, steps)
+    compare_state(gs, os_, w)
+
+
+def test_config0_full_500_steps():
+    """The 8x8x32 Cockcroft-Latham bar for its full 500 steps."""
+    w = S.tensile_bar_cl()
+    gs, os_ = _run_both(w, 500)
+    compare_state(gs, os_, w, tol=1e-9)
+
+
+def test_failure_variant_sets_bit_exact():
+    """Grips at +-20 m/s, W_cr x 0.02: plastic flow, damage and failure.  The
+    failure set and the failure steps must match exactly; the fields within
+    tolerance."""
+    w = S.failure_variant(S.tensile_bar_cl())
+    gs, os_ = _run_both(w, 500)
+    assert (os_["fail_step"] >= 0).sum() > 50
+    assert np.array_equal(gs["FAIL_STEP"], os_["fail_step"])
+    compare_state(gs, os_, w, tol=1e-8)
+
+
+def test_failure_variant_jc_sets_bit_exact():
+    w = S.failure_variant(S.tensile_bar_jc(nx=8, ny=8, nz=32, steps=400))
+    gs, os_ = _run_both(w, 400)
+    assert (os_["fail_step"] >= 0).sum() > 0
+    assert np.array_equal(gs["FAIL_STEP"], os_["fail_step"])
+    compare_state(gs, os_, w, tol=1e-8)
+
+
+def test_one_step_from_plastic_damaged_state():
+    """Run the oracle into a plastic, partly failed state, load that state into
+    both sides and compare one step (the per-step tolerance)."""
+    w = S.failure_variant(S.tensile_bar_cl())
+    o = oracle.Simulation.from_workload(w)
+    o.step(300)
+    st = o.state()
+    assert (st["fail_step"] >= 0).sum() > 0 and st["ep"].max() > 0.01
+    g = gpu_sim(w)
+    for name, key in (("U", "u"), ("V", "v"), ("F", "F"), ("STRESS_DEV", "sd"), ("EPSP", "ep"),
+                      ("EPSP_RATE", "epdot"), ("DINIT", "dinit"), ("DAMAGE", "D"), ("POROSITY", "f"),
+                      ("FORCE", "force"), ("FAIL_STEP", "fail_step")):
+        g.set(name, st[key])
+    g.step(1)
+    o.step(1)
+    gs, os_ = g.state(), o.state()
+    assert np.array_equal(gs["FAIL_STEP"], os_["fail_step"])
+    compare_state(gs, os_, w)
+
+
+def test_gtn_notched_bar_small():
+    """GTN porous plasticity on a small notched round bar (f0 from the seed)."""
+    w = S.notched_bar_gtn(radius=2.0e-3, height=6e-3, spacing=0.3e-3, notch_radius=0.6e-3, v_grip=20.0, steps=300)
+    gs, os_ = _run_both(w, 300)
+    assert os_["ep"].max() > 0
+    assert np.array_equal(gs["FAIL_STEP"], os_["fail_step"])
+    compare_state(gs, os_, w, tol=1e-8)
+
+
+def test_free_body_momentum_and_patch():
+    """No constraints: forces sum to zero; an affine velocity gives F = I + dt B
+    everywhere after one step (first-order completeness)."""
+    w = S.tensile_bar_cl(nx=10, ny=9, nz=20)
+    w.specimen.bc_mask[:] = 0
+    w.specimen.bc_vel[:] = 0
+    g = gpu_sim(w)
+    B = np.random.default_rng(0).normal(size=(3, 3)) * 5.0
+    g.set("V", w.specimen.X @ B.T)
+    g.step(1)
+    F = g.get("F")
+    assert np.max(np.abs(F - (np.eye(3).ravel() + w.dt * B.ravel()))) <= 1e-13
+    g.step(5)
+    f = g.get("FORCE")
+    assert np.all(np.abs(f.sum(0)) <= 1e-11 * np.abs(f).sum(0))
+
+
+def test_material_point_batch_matches_oracle():
+    import torch
+    rng = np.random.default_rng(1)
+    mats = [S.aluminium_cl(wcr=2e6), S.aluminium_jc(scale=0.05), S.material(damage=S.DAMAGE_GTN, fN=0.04),
+            S.weldox("700E")]
+    for m in mats:
+        n = 64
+        steps = 40
+        dt = 1e-7
+        deps = rng.normal(size=(steps, n, 3, 3)) * 1.5e-3
+        deps = 0.5 * (deps + deps.transpose(0, 1, 3, 2))
+        J = 1.0 + rng.uniform(-3e-3, 6e-3, size=(steps, n))
+        f0 = rng.uniform(0.0, 0.05, size=n) if m["damage"] == S.DAMAGE_GTN else np.zeros(n)
+        state = np.zeros((n, 16))
+        state[:, 14] = f0
+        if m["damage"] == S.DAMAGE_GTN:
+            state[:, 13] = [m["q1"] * oracle.gtn_fstar(m, f) for f in f0]
+        ref = np.zeros((steps, n, 16))
+        for p in range(n):
+            init = {"f": state[p, 14], "D": state[p, 13]}
+            out, _ = oracle.material_point(m, dt, deps[:, p], J[:, p], init=init)
+            ref[:, p] = out
+        st = torch.tensor(state, device="cuda")
+        for k in range(steps):
+            tlsph.material_point_batch(m, dt, torch.tensor(deps[k].reshape(n, 9), device="cuda"),
+                                       torch.tensor(J[k], device="cuda"), st)
+            got = st.cpu().numpy()
+            assert np.array_equal(got[:, 15], ref[k, :, 15])
+            scale = max(m["A"], 1e6)
+            assert relerr(got[:, :10], ref[k, :, :10], 1e-3 * scale) <= 1e-10
+            for c in (10, 12, 13, 14):
+                assert relerr(got[:, c], ref[k, :, c], 1e-9) <= 1e-10, (m["damage"], k, c)
+
+
+# ------------------------------------------------------------------ full size
+
+def _full_size_sample_check(w, steps, samples):
+    """Run the whole workload on the GPU (the benchmark's launch
+    configuration) and reproduce sampled particles with the oracle on a ball
+    of radius (2 steps + 1) rc + rc around each."""
+    g = gpu_sim(w)
+    g.step(steps)
+    gs = g.state()
+    X = w.specimen.X
+    for c in samples:
+        idx = ball(X, [c], (2 * steps + 2) * w.rc)
+        sub = sub_workload(w, idx)
+        o = oracle.Simulation.from_workload(sub)
+        o.step(steps)
+        k = int(np.searchsorted(idx, c))
+        os_ = o.state()
+        compare_state({f: v[[c]] for f, v in gs.items()}, {f: v[[k]] for f, v in os_.items()}, w)
+    return g
+
+
+def test_full_size_tensile_bar_jc_sampled():
+    """1,024,000-particle Johnson-Cook bar: sampled neighbour rows bit-exact,
+    sampled particles after two steps within tolerance, and the patch test on
+    every particle."""
+    w = S.tensile_bar_jc()
+    sp = w.specimen
+    nx, ny, nz = sp.dims
+    rng = np.random.default_rng(0)
+    samples = [0, nx * ny * 2 + nx + 1, (nz // 2) * nx * ny + (ny // 2) * nx + nx // 2,
+               sp.N - 1, int(rng.integers(sp.N)), int(rng.integers(sp.N))]
+    g = _full_size_sample_check(w, 2, samples)
+    row_ptr = g.get("NBR_ROWPTR")
+    col = g.get("NBR_COL")
+    for c in samples:
+        idx = ball(sp.X, [c], 1.01 * w.rc)
+        rp, cl = oracle.neighbors(sp.X[idx], w.rc)
+        k = int(np.searchsorted(idx, c))
+        assert np.array_equal(col[row_ptr[c]:row_ptr[c + 1]], idx[cl[rp[k]:rp[k + 1]]])
+    # symmetry (j in S_i <=> i in S_j) on 20000 random rows
+    for i in rng.integers(0, sp.N, size=20000):
+        for j in col[row_ptr[i]:row_ptr[i + 1]]:
+            rj = col[row_ptr[j]:row_ptr[j + 1]]
+            k = np.searchsorted(rj, i)
+            assert k < len(rj) and rj[k] == i
