@@ -26,6 +26,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 struct Layout {
     size_t X, vol, mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
+    size_t xh, xl, s0, linv32, r1, r2;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
     size_t overlay_end;
     size_t total;
@@ -43,7 +44,7 @@ struct Carver {
     }
 };
 
-Layout make_layout(int64_t N, int64_t nnz_cap)
+Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
 {
     Layout L{};
     const size_t n = (size_t)N, d = sizeof(double);
@@ -71,6 +72,14 @@ Layout make_layout(int64_t N, int64_t nnz_cap)
     L.fail = c.take(n * sizeof(int32_t));
     L.status = c.take(sizeof(uint32_t));
     L.mats = c.take(TLSPH_MAX_MATERIALS * sizeof(DevMat));
+    if (mixed) {
+        L.xh = c.take(n * 16);
+        L.xl = c.take(n * 16);
+        L.s0 = c.take(n * 16);
+        L.linv32 = c.take(9 * n * sizeof(float));
+        L.r1 = c.take(n * 16);
+        L.r2 = c.take(6 * n * 16);
+    }
     // overlay block: F, sd, sig, A  |  neighbour-build scratch
     const size_t ov = c.off;
     L.F = c.take(9 * n * d);
@@ -127,6 +136,17 @@ bool valid_config(const tlsph_config *c, std::string &why)
 void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
 {
     DevState &s = ctx->s;
+    if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
+        s.xh = at<float4>(base, L.xh);
+        s.xl = at<float4>(base, L.xl);
+        s.s0 = at<float4>(base, L.s0);
+        s.linv32 = at<float>(base, L.linv32);
+        s.r1 = at<float4>(base, L.r1);
+        s.r2 = at<float4>(base, L.r2);
+    } else {
+        s.xh = s.xl = s.s0 = s.r1 = s.r2 = nullptr;
+        s.linv32 = nullptr;
+    }
     s.N = ctx->N;
     s.X = at<double>(base, L.X);
     s.vol = at<double>(base, L.vol);
@@ -245,7 +265,7 @@ size_t tlsph_workspace_bytes(const tlsph_config *cfg, int64_t N, int64_t nnz_cap
 {
     std::string why;
     if (!valid_config(cfg, why) || N <= 0 || nnz_cap < 0) return 0;
-    return make_layout(N, nnz_cap).total + ALIGN;
+    return make_layout(N, nnz_cap, cfg->precision == TLSPH_PRECISION_MIXED).total + ALIGN;
 }
 
 int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const double *vol,
@@ -286,7 +306,8 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     };
 
     // ---- memory: arena (capacity nnz_cap) or library-owned (exact nnz after the count)
-    Layout L = make_layout(N, arena ? nnz_cap : 0);
+    const bool mixed = cfg->precision == TLSPH_PRECISION_MIXED;
+    Layout L = make_layout(N, arena ? nnz_cap : 0, mixed);
     void *base = nullptr;
     if (arena) {
         if (arena_bytes < L.total) return bail(TLSPH_ERR_NOMEM, "arena too small: need " + std::to_string(L.total) + " bytes");
@@ -364,12 +385,21 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
 
     // ---- correction matrices
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
-    CK(shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), s.status, st));
+    // S0 (mixed only) goes to the force array, which init_state clears afterwards
+    CK(shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), mixed ? s.force : nullptr, s.status, st));
     uint32_t n_sing = 0;
     CK(cudaMemcpyAsync(&n_sing, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (n_sing) return bail(TLSPH_ERR_SINGULAR_L, std::to_string(n_sing) + " particles have a singular correction matrix");
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
+    if (mixed) {
+        // bulk reference velocity of the FP32 velocity mirror: the mean initial velocity
+        double vr[3] = { 0, 0, 0 };
+        for (size_t i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) vr[k] += bcv_h[3 * i + k];
+        for (int k = 0; k < 3; ++k) s.vref[k] = vr[k] / (double)n;
+        CK(mixed_init_static(s, s.force, st));
+    }
 
     // ---- initial state (overwrites the scratch overlay)
     CK(launch_init_state(s, st));
@@ -402,6 +432,7 @@ int tlsph_set_material(tlsph_ctx *ctx, int mat_id, const tlsph_material *m)
                                     cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_material copy");
     e = launch_material_fields(ctx->s, mat_id, ctx->dcur, ctx->steps == 0, ctx->stream);
+    if (e == cudaSuccess && ctx->cfg.precision == TLSPH_PRECISION_MIXED) e = mixed_material(ctx->s, mat_id, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_material fields");
     // the copy source lives in ctx; wait so a later overwrite cannot race it
     e = cudaStreamSynchronize(ctx->stream);
@@ -423,6 +454,8 @@ int tlsph_step(tlsph_ctx *ctx, int nsteps)
     cudaError_t e;
     if (ctx->need_predict) {
         e = launch_predict(ctx->s, ctx->ucur, ctx->cfg.dt, ctx->stream);
+        if (e == cudaSuccess && ctx->cfg.precision == TLSPH_PRECISION_MIXED)
+            e = mixed_after_predict(ctx->s, ctx->dcur, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "predict");
         ctx->need_predict = false;
     }

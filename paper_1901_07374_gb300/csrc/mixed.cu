@@ -1,10 +1,510 @@
-// Mixed-precision step (FP32 pair gathers and sums, FP64 state): not built yet.
+// Mixed-precision time step: FP32 pair gathers and FP32 sums over j, FP64
+// particle state.
+//
+// What stays FP64: positions and displacements (u accumulated in FP64), the
+// deformation gradient F and its determinant J, the correction matrix
+// inverse (computed once in FP64, used rounded), the stress deviator and the
+// whole constitutive + damage update (the radial return and the failure
+// threshold decisions), the nodal force handed to the integrator and the
+// velocity-Verlet update.
+//
+// What is FP32: every per-pair term of both passes, the warp sums, the polar
+// decomposition, the rotations and P = J sigma F^{-T}, A = P L^{-T}.
+//
+// The pair terms are arranged so the FP32 sums carry no large cancellation:
+//  - positions travel as hi + lo float pairs, X_ij = (hi_j - hi_i) + (lo_j - lo_i);
+//  - velocities are mirrored relative to a bulk reference velocity;
+//  - the hourglass error vector uses F - I and u, e = (F_i - I) X_ij - u_ij;
+//  - the stress term is written with differences (Sec. 3.1 force, rearranged):
+//      f_i = V_i (1-D_i) sum_j V_j (A_j - A_i) grad W_ij
+//          + V_i A_i [ (2 - D_i) S0_i - sum_j V_j D_j grad W_ij ],
+//    with the static S0_i = sum_j V_j grad W_ij computed once in FP64.
+#include <math.h>
+
+#include "tlsph_device.cuh"
 #include "tlsph_internal.cuh"
 
 namespace tlsph {
 
-cudaError_t launch_step_mixed(tlsph_ctx &, int64_t, cudaStream_t, cudaEvent_t *) { return cudaErrorNotSupported; }
-cudaError_t mixed_sync_to_fp64(tlsph_ctx &, int, cudaStream_t) { return cudaSuccess; }
+static constexpr int MIX_THREADS = 128;
+
+struct MixConst {
+    double dt, half_dt;
+    float dtf, inv_h, dw_norm, w_norm, hg_coef;
+    double vref0, vref1, vref2;
+    int64_t step_index;
+    int ucur, dcur;
+};
+
+static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
+{
+    MixConst c;
+    const tlsph_config &cfg = ctx.cfg;
+    c.dt = cfg.dt;
+    c.half_dt = 0.5 * cfg.dt;
+    c.dtf = (float)cfg.dt;
+    c.inv_h = (float)(1.0 / cfg.h);
+    c.dw_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
+    c.w_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h));
+    c.hg_coef = (float)(-0.5 * cfg.hg_alpha);
+    c.vref0 = ctx.s.vref[0];
+    c.vref1 = ctx.s.vref[1];
+    c.vref2 = ctx.s.vref[2];
+    c.step_index = step_index;
+    c.ucur = ctx.ucur;
+    c.dcur = ctx.dcur;
+    return c;
+}
+
+// ------------------------------------------------------------------ FP32 3x3 helpers
+__device__ __forceinline__ void mul3f(const float *a, const float *b, float *c)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            c[3 * k + l] = a[3 * k] * b[l] + a[3 * k + 1] * b[3 + l] + a[3 * k + 2] * b[6 + l];
+}
+__device__ __forceinline__ void mul3f_bt(const float *a, const float *b, float *c)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            c[3 * k + l] = a[3 * k] * b[3 * l] + a[3 * k + 1] * b[3 * l + 1] + a[3 * k + 2] * b[3 * l + 2];
+}
+__device__ __forceinline__ void cof3f(const float *m, float *c)
+{
+    c[0] = m[4] * m[8] - m[5] * m[7];
+    c[1] = m[5] * m[6] - m[3] * m[8];
+    c[2] = m[3] * m[7] - m[4] * m[6];
+    c[3] = m[2] * m[7] - m[1] * m[8];
+    c[4] = m[0] * m[8] - m[2] * m[6];
+    c[5] = m[1] * m[6] - m[0] * m[7];
+    c[6] = m[1] * m[5] - m[2] * m[4];
+    c[7] = m[2] * m[3] - m[0] * m[5];
+    c[8] = m[0] * m[4] - m[1] * m[3];
+}
+
+// FP32 rotation of the polar decomposition, same iteration as the FP64
+// path (determinant-scaled Newton), stop at a step below 1e-5, cap 30.
+__device__ __forceinline__ bool polar_rotation_f(const float *F, float *R)
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = F[k];
+    bool last = false;
+    for (int it = 0; it < 30; ++it) {
+        float c[9];
+        cof3f(R, c);
+        const float d = R[0] * c[0] + R[1] * c[1] + R[2] * c[2];
+        const float g = rcbrtf(fabsf(d));
+        const float gi = 1.0f / (g * d);
+        float diff = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float xn = 0.5f * (g * R[k] + c[k] * gi);
+            const float e = xn - R[k];
+            diff += e * e;
+            R[k] = xn;
+        }
+        if (last) return true;
+        if (diff < 1e-10f) last = true;
+    }
+    return false;
+}
+
+// symmetric (6) sandwich products in FP32
+__device__ __forceinline__ void sym_rotate_t_f(const float *Q, const float *s, float *out)
+{
+    float S[9] = { s[0], s[3], s[5], s[3], s[1], s[4], s[5], s[4], s[2] }, T[9];
+    mul3f(S, Q, T);
+#define QTT(k, l) (Q[k] * T[l] + Q[3 + k] * T[3 + l] + Q[6 + k] * T[6 + l])
+    out[0] = QTT(0, 0); out[1] = QTT(1, 1); out[2] = QTT(2, 2);
+    out[3] = QTT(0, 1); out[4] = QTT(1, 2); out[5] = QTT(2, 0);
+#undef QTT
+}
+__device__ __forceinline__ void sym_rotate_f(const float *Q, const float *s, float *out)
+{
+    float S[9] = { s[0], s[3], s[5], s[3], s[1], s[4], s[5], s[4], s[2] }, T[9];
+    mul3f_bt(S, Q, T);
+#define QT(k, l) (Q[3 * k] * T[l] + Q[3 * k + 1] * T[3 + l] + Q[3 * k + 2] * T[6 + l])
+    out[0] = QT(0, 0); out[1] = QT(1, 1); out[2] = QT(2, 2);
+    out[3] = QT(0, 1); out[4] = QT(1, 2); out[5] = QT(2, 0);
+#undef QT
+}
+
+__device__ __forceinline__ float3 xdiff(const float4 hi_j, const float4 lo_j, const float4 hi_i, const float4 lo_i)
+{
+    return make_float3((hi_j.x - hi_i.x) + (lo_j.x - lo_i.x), (hi_j.y - hi_i.y) + (lo_j.y - lo_i.y),
+                       (hi_j.z - hi_i.z) + (lo_j.z - lo_i.z));
+}
+
+// ------------------------------------------------------------------ pass 1
+__global__ void __launch_bounds__(MIX_THREADS) k_pass1_mixed(DevState s, MixConst c)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (row0 >= s.N) return;
+    const int nrows = (int)min((int64_t)32, s.N - row0);
+    const float4 *__restrict__ xh = s.xh;
+    const float4 *__restrict__ xl = s.xl;
+    const float4 *__restrict__ r1 = s.r1;
+    float keep[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
+
+    for (int r = 0; r < nrows; ++r) {
+        const int64_t i = row0 + r;
+        const float4 hi = xh[i], lo = xl[i], vi = r1[i];
+        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+        float m[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) m[k] = 0.0f;
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
+            const int j = s.col[p];
+            const float4 hj = xh[j], lj = xl[j], vj = r1[j];
+            const float3 d = xdiff(hj, lj, hi, lo);
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float rinv = rsqrtf(r2);
+            const float q = r2 * rinv * c.inv_h;
+            const float cw = hj.w * vj.w * spline_dw(q) * rinv;   // V_j (1 - D_j) W'/r
+            const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
+            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
+            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
+            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float t = warp_allsum(m[k]);
+            keep[k] = (lane == r) ? t : keep[k];
+        }
+    }
+    if (lane >= nrows) return;
+
+    const int64_t i = row0 + lane;
+    const double *__restrict__ Dn = s.D[c.dcur];
+    double *__restrict__ Dnext = s.D[c.dcur ^ 1];
+    float4 *__restrict__ r2o = s.r2 + 6 * i;
+    const int fail = s.fail[i];
+    const double *un = s.u[c.ucur ^ 1];   // u^{n+1}, mirrored for pass 2's hourglass term
+    if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
+        Dnext[i] = Dn[i];
+        const double *F = s.F + 9 * i;
+        r2o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2o[2] = make_float4(0.f, 0.f, (float)un[3 * i], (float)un[3 * i + 1]);
+        r2o[3] = make_float4((float)un[3 * i + 2], (float)(F[0] - 1.0), (float)F[1], (float)F[2]);
+        r2o[4] = make_float4((float)F[3], (float)(F[4] - 1.0), (float)F[5], (float)F[6]);
+        r2o[5] = make_float4((float)F[7], (float)(F[8] - 1.0), 0.f, 0.f);
+        return;
+    }
+    float Li[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Li[k] = s.linv32[9 * i + k];
+    float Fdf[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            Fdf[3 * k + l] = c.dw_norm * (keep[3 * k] * Li[l] + keep[3 * k + 1] * Li[3 + l] + keep[3 * k + 2] * Li[6 + l]);
+    // F^{n+1} and J in FP64
+    double Fn[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fn[k] = s.F[9 * i + k] + c.dt * (double)Fdf[k];
+    const double J = Fn[0] * (Fn[4] * Fn[8] - Fn[5] * Fn[7]) + Fn[1] * (Fn[5] * Fn[6] - Fn[3] * Fn[8])
+                   + Fn[2] * (Fn[3] * Fn[7] - Fn[4] * Fn[6]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.F[9 * i + k] = Fn[k];
+    if (!(J > 0.0) || !isfinite(J)) {
+        atomicOr(s.status, TLSPH_ST_BAD_J);
+        Dnext[i] = Dn[i];
+        return;
+    }
+    // kinematics in FP32
+    float Ff[9], cf[9], Fi[9], Lv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ff[k] = (float)Fn[k];
+    cof3f(Ff, cf);
+    const float iJ = (float)(1.0 / J);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) Fi[3 * k + l] = cf[3 * l + k] * iJ;
+    mul3f(Fdf, Fi, Lv);
+    const float d[6] = { Lv[0], Lv[4], Lv[8], 0.5f * (Lv[1] + Lv[3]), 0.5f * (Lv[5] + Lv[7]), 0.5f * (Lv[2] + Lv[6]) };
+    float R[9];
+    uint32_t st = polar_rotation_f(Ff, R) ? 0u : TLSPH_ST_POLAR_CAP;
+    float dh[6];
+    sym_rotate_t_f(R, d, dh);
+    double de[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) de[k] = c.dt * (double)dh[k];
+
+    // constitutive and damage update in FP64
+    MPState mp;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mp.sd[k] = s.sd[6 * i + k];
+    mp.sm = 0.0;
+    mp.ep = s.ep[i];
+    mp.epdot = s.epdot[i];
+    mp.dinit = s.dinit[i];
+    mp.D = Dn[i];
+    mp.f = s.por[i];
+    mp.failed = 0;
+    const DevMat &mat = s.mats[s.mat[i]];
+    st |= material_update(mat, c.dt, de, J, mp);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s.sd[6 * i + k] = mp.sd[k];
+    s.ep[i] = mp.ep;
+    s.epdot[i] = mp.epdot;
+    s.dinit[i] = mp.dinit;
+    s.por[i] = mp.f;
+    Dnext[i] = mp.D;
+
+    float A[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
+    if (mp.failed) {
+        s.fail[i] = (int32_t)(c.step_index + 1);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s.sig[6 * i + k] = 0.0;
+    } else {
+        const float sh[6] = { (float)(mp.sd[0] + mp.sm), (float)(mp.sd[1] + mp.sm), (float)(mp.sd[2] + mp.sm),
+                              (float)mp.sd[3], (float)mp.sd[4], (float)mp.sd[5] };
+        float sg[6];
+        sym_rotate_f(R, sh, sg);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s.sig[6 * i + k] = (double)sg[k];
+        float S[9] = { sg[0], sg[3], sg[5], sg[3], sg[1], sg[4], sg[5], sg[4], sg[2] }, P[9];
+        mul3f_bt(S, Fi, P);
+        const float Jf = (float)J;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) P[k] *= Jf;
+        mul3f_bt(P, Li, A);
+        bool fin = true;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) fin &= isfinite(A[k]);
+        if (!fin) st |= TLSPH_ST_NONFINITE;
+    }
+    // pass-2 record: A (9), 1 - D, u (3), F - I (9)
+    const float omd = (float)(1.0 - mp.D);
+    r2o[0] = make_float4(A[0], A[1], A[2], A[3]);
+    r2o[1] = make_float4(A[4], A[5], A[6], A[7]);
+    r2o[2] = make_float4(A[8], omd, (float)un[3 * i], (float)un[3 * i + 1]);
+    r2o[3] = make_float4((float)un[3 * i + 2], (float)(Fn[0] - 1.0), (float)Fn[1], (float)Fn[2]);
+    r2o[4] = make_float4((float)Fn[3], (float)(Fn[4] - 1.0), (float)Fn[5], (float)Fn[6]);
+    r2o[5] = make_float4((float)Fn[7], (float)(Fn[8] - 1.0), 0.f, 0.f);
+    if (st) atomicOr(s.status, st);
+}
+
+// ------------------------------------------------------------------ pass 2
+template <bool HG>
+__global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixConst c)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (row0 >= s.N) return;
+    const int nrows = (int)min((int64_t)32, s.N - row0);
+    const float4 *__restrict__ xh = s.xh;
+    const float4 *__restrict__ xl = s.xl;
+    const float4 *__restrict__ r2 = s.r2;
+    float keep[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
+
+    for (int r = 0; r < nrows; ++r) {
+        const int64_t i = row0 + r;
+        const float4 hi = xh[i], lo = xl[i];
+        const float4 a0 = r2[6 * i], a1 = r2[6 * i + 1], a2 = r2[6 * i + 2];
+        float4 a3, a4, a5;
+        if (HG) { a3 = r2[6 * i + 3]; a4 = r2[6 * i + 4]; a5 = r2[6 * i + 5]; }
+        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+        float acc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
+            const int j = s.col[p];
+            const float4 hj = xh[j], lj = xl[j];
+            const float4 b0 = r2[6 * j], b1 = r2[6 * j + 1], b2 = r2[6 * j + 2];
+            const float3 d = xdiff(hj, lj, hi, lo);
+            const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float rinv = rsqrtf(r2v);
+            const float q = r2v * rinv * c.inv_h;
+            const float g = hj.w * spline_dw(q) * rinv;           // V_j W'/r
+            // sum_j V_j D_j grad W
+            const float gd = g * (1.0f - b2.y);
+            acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
+            // sum_j V_j (A_j - A_i) grad W
+            const float t0 = (b0.x - a0.x) * d.x + (b0.y - a0.y) * d.y + (b0.z - a0.z) * d.z;
+            const float t1 = (b0.w - a0.w) * d.x + (b1.x - a1.x) * d.y + (b1.y - a1.y) * d.z;
+            const float t2 = (b1.z - a1.z) * d.x + (b1.w - a1.w) * d.y + (b2.x - a2.x) * d.z;
+            acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
+            if (HG) {
+                const float4 b3 = r2[6 * j + 3], b4 = r2[6 * j + 4], b5 = r2[6 * j + 5];
+                // u_ij, x_ij = X_ij + u_ij, e = ((F_i - I) + (F_j - I)) X_ij - 2 u_ij
+                const float ux = b2.z - a2.z, uy = b2.w - a2.w, uz = b3.x - a3.x;
+                const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
+                const float lx2 = xx * xx + xy * xy + xz * xz;
+                const float lxi = rsqrtf(lx2);
+                const float ex = (a3.y + b3.y) * d.x + (a3.z + b3.z) * d.y + (a3.w + b3.w) * d.z - 2.0f * ux;
+                const float ey = (a4.x + b4.x) * d.x + (a4.y + b4.y) * d.y + (a4.z + b4.z) * d.z - 2.0f * uy;
+                const float ez = (a4.w + b4.w) * d.x + (a5.x + b5.x) * d.y + (a5.y + b5.y) * d.z - 2.0f * uz;
+                const float delta = (ex * xx + ey * xy + ez * xz) * lxi;
+                const float ch = lj.w * b2.y * hj.w * spline_w(q) * rinv * rinv * delta * lxi;
+                acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if (!HG && k >= 6) continue;
+            const float t = warp_allsum(acc[k]);
+            keep[k] = (lane == r) ? t : keep[k];
+        }
+    }
+    if (lane >= nrows) return;
+
+    // ---- epilogue: force (rearranged Sec. 3.1 form) and velocity Verlet in FP64
+    const int64_t i = row0 + lane;
+    const double Vi = s.vol[i];
+    const double Di = s.D[c.dcur ^ 1][i];
+    const double omdi = 1.0 - Di;
+    const float4 a0 = r2[6 * i], a1 = r2[6 * i + 1], a2 = r2[6 * i + 2];
+    const float Ai[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
+    const float4 s0 = s.s0[i];
+    const float w2 = (float)(2.0 - Di);
+    const float bx = w2 * s0.x - keep[0], by = w2 * s0.y - keep[1], bz = w2 * s0.z - keep[2];
+    double f[3];
+    f[0] = Vi * (double)c.dw_norm * ((double)(Ai[0] * bx + Ai[1] * by + Ai[2] * bz) + omdi * (double)keep[3]);
+    f[1] = Vi * (double)c.dw_norm * ((double)(Ai[3] * bx + Ai[4] * by + Ai[5] * bz) + omdi * (double)keep[4]);
+    f[2] = Vi * (double)c.dw_norm * ((double)(Ai[6] * bx + Ai[7] * by + Ai[8] * bz) + omdi * (double)keep[5]);
+    if (HG) {
+        const double hc = (double)c.hg_coef * s.sqrtE[i] * omdi * Vi * (double)c.w_norm;
+        f[0] += hc * (double)keep[6];
+        f[1] += hc * (double)keep[7];
+        f[2] += hc * (double)keep[8];
+    }
+    const double im = 1.0 / s.mass[i];
+    const int fail = s.fail[i];
+    double vn[3], v2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.force[3 * i + k] = f[k];
+        vn[k] = s.vh[3 * i + k] + c.half_dt * (f[k] * im);
+    }
+    if (fail >= 0) {
+        vn[0] = vn[1] = vn[2] = 0.0;
+    } else if (s.bcm[i]) {
+        vn[0] = s.bcv[3 * i]; vn[1] = s.bcv[3 * i + 1]; vn[2] = s.bcv[3 * i + 2];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * (f[k] * im);
+    if (fail >= 0) {
+        v2[0] = v2[1] = v2[2] = 0.0;
+    } else if (s.bcm[i]) {
+        v2[0] = s.bcv[3 * i]; v2[1] = s.bcv[3 * i + 1]; v2[2] = s.bcv[3 * i + 2];
+    }
+    const double *un = s.u[c.ucur ^ 1];
+    double *unext = s.u[c.ucur];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.v[3 * i + k] = vn[k];
+        s.vh[3 * i + k] = v2[k];
+        unext[3 * i + k] = un[3 * i + k] + c.dt * v2[k];
+    }
+    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2), (float)omdi);
+    if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
+}
+
+// ------------------------------------------------------------------ mirrors
+// static records from the FP64 inputs: X as hi + lo floats, V, L^{-1}, S0
+__global__ void k_mixed_static(DevState s, const double *S0)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float hi[3], lo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double x = s.X[3 * i + k];
+        hi[k] = (float)x;
+        lo[k] = (float)(x - (double)hi[k]);
+    }
+    s.xh[i] = make_float4(hi[0], hi[1], hi[2], (float)s.vol[i]);
+    s.xl[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    s.s0[i] = make_float4((float)S0[3 * i], (float)S0[3 * i + 1], (float)S0[3 * i + 2], 0.0f);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.linv32[9 * i + k] = (float)s.Linv[9 * i + k];
+}
+
+// pass-1 record from the FP64 half-step velocity and D^n
+__global__ void k_mixed_r1(DevState s, int dcur)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    s.r1[i] = make_float4((float)(s.vh[3 * i] - s.vref[0]), (float)(s.vh[3 * i + 1] - s.vref[1]),
+                          (float)(s.vh[3 * i + 2] - s.vref[2]), (float)(1.0 - s.D[dcur][i]));
+}
+
+// FP64 copy of A from the pass-2 records (for reading the state)
+__global__ void k_mixed_export_A(DevState s)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    const float4 a0 = s.r2[6 * i], a1 = s.r2[6 * i + 1], a2 = s.r2[6 * i + 2];
+    const float A[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.A[9 * i + k] = (double)A[k];
+}
+
+__global__ void k_mixed_sqrtE(DevState s, int mat_id)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N || s.mat[i] != mat_id) return;
+    s.xl[i].w = (float)s.mats[mat_id].sqrtE;
+}
+
+static unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t mixed_init_static(const DevState &s, const double *S0, cudaStream_t st)
+{
+    k_mixed_static<<<nb(s.N, 256), 256, 0, st>>>(s, S0);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_material(const DevState &s, int mat_id, cudaStream_t st)
+{
+    k_mixed_sqrtE<<<nb(s.N, 256), 256, 0, st>>>(s, mat_id);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st)
+{
+    k_mixed_r1<<<nb(s.N, 256), 256, 0, st>>>(s, dcur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev)
+{
+    const MixConst c = make_mix_const(ctx, step_index);
+    const DevState &s = ctx.s;
+    const unsigned grid = nb((s.N + 31) / 32 * 32, MIX_THREADS);
+    if (ev) cudaEventRecord(ev[0], st);
+    k_pass1_mixed<<<grid, MIX_THREADS, 0, st>>>(s, c);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (ctx.cfg.hg_alpha != 0.0)
+        k_pass2_mixed<true><<<grid, MIX_THREADS, 0, st>>>(s, c);
+    else
+        k_pass2_mixed<false><<<grid, MIX_THREADS, 0, st>>>(s, c);
+    if (ev) cudaEventRecord(ev[2], st);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st)
+{
+    if (field == TLSPH_FIELD_A && ctx.steps > 0) {
+        k_mixed_export_A<<<nb(ctx.N, 256), 256, 0, st>>>(ctx.s);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 void mixed_release(tlsph_ctx &) {}
 
 }  // namespace tlsph

@@ -269,23 +269,31 @@ cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scr
 // adjugate.  A row whose |det L| <= 1e-12 |L|_F^3 is reported singular and
 // gets L^{-1} = 0.
 __global__ void k_shape(const double *X, const double *vol, const int64_t *row_ptr, const int32_t *col,
-                        int64_t N, double inv_h, double dw_norm, double *Linv, uint32_t *n_singular)
+                        int64_t N, double inv_h, double dw_norm, double *Linv, double *S0, uint32_t *n_singular)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= N) return;
     const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
     double l[6] = { 0, 0, 0, 0, 0, 0 };
+    double g[3] = { 0, 0, 0 };
     for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
         const int64_t j = col[p];
         const double dx = X[3 * j] - xi, dy = X[3 * j + 1] - yi, dz = X[3 * j + 2] - zi;
         const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        const double c = vol[j] * dw_norm * spline_dw(r * inv_h) / r;
+        const double c0 = vol[j] * spline_dw(r * inv_h) / r;
+        g[0] += c0 * dx; g[1] += c0 * dy; g[2] += c0 * dz;
+        const double c = dw_norm * c0;
         l[0] += c * dx * dx; l[1] += c * dy * dy; l[2] += c * dz * dz;
         l[3] += c * dx * dy; l[4] += c * dy * dz; l[5] += c * dz * dx;
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) l[k] = warp_allsum(l[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = warp_allsum(g[k]);
+    if (lane == 0 && S0) {
+        S0[3 * i] = g[0]; S0[3 * i + 1] = g[1]; S0[3 * i + 2] = g[2];
+    }
     if (lane == 0) {
         double L[9], c[9];
         sym_to_full(l, L);
@@ -302,11 +310,12 @@ __global__ void k_shape(const double *X, const double *vol, const int64_t *row_p
     }
 }
 
-cudaError_t shape_matrix(const DevState &s, double h, double *Linv, uint32_t *n_singular, cudaStream_t st)
+cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
+                         cudaStream_t st)
 {
     const double dw_norm = 1.0 / (M_PI * h * h * h * h);
     k_shape<<<blocks_for(s.N * 32, 256), 256, 0, st>>>(s.X, s.vol, s.row_ptr, s.col, s.N, 1.0 / h, dw_norm, Linv,
-                                                       n_singular);
+                                                       S0, n_singular);
     return cudaGetLastError();
 }
 

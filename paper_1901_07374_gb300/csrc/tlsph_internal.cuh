@@ -55,6 +55,14 @@ struct DevState {
     int32_t *fail;          // N
     uint32_t *status;       // 1
     const DevMat *mats;     // TLSPH_MAX_MATERIALS
+    // mixed-precision records (null in the FP64 path)
+    float4 *xh;             // N   {X hi, V}
+    float4 *xl;             // N   {X lo, sqrt E}
+    float4 *s0;             // N   {sum_j V_j W'(r)/r (X_j - X_i), 0}  (static, FP64-accurate)
+    float *linv32;          // N*9 L^{-1} rounded
+    float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
+    float4 *r2;             // N*6 pass-2 gather record {A (9), 1 - D, u (3), F - I (9), 0, 0}
+    double vref[3];         // bulk reference velocity of the r1 mirror
 };
 
 struct Scratch {            // neighbour-build scratch (set-up only)
@@ -109,7 +117,9 @@ cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Sc
                                   int64_t *row_ptr, cudaStream_t st);
 cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
                                  const int64_t *row_ptr, int32_t *col, cudaStream_t st);
-cudaError_t shape_matrix(const DevState &s, double h, double *Linv, uint32_t *n_singular, cudaStream_t st);
+// S0: optional N*3 output of sum_j V_j W'(r)/r (X_j - X_i) (kernel-normalisation free)
+cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
+                         cudaStream_t st);
 
 // step64.cu
 cudaError_t launch_init_state(const DevState &s, cudaStream_t st);
@@ -126,6 +136,9 @@ cudaError_t launch_import_sym(const double *src9, double *dst6, int64_t N, cudaS
 DevMat make_dev_mat(const tlsph_material &m);
 
 // mixed.cu
+cudaError_t mixed_init_static(const DevState &s, const double *S0, cudaStream_t st);
+cudaError_t mixed_material(const DevState &s, int mat_id, cudaStream_t st);
+cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st);
 void mixed_release(tlsph_ctx &ctx);

@@ -133,6 +133,19 @@ def _check(code: int, ctx=None):
         raise TlsphError(code, msg)
 
 
+def mixed_algorithmic_bytes(N: int, nnz: int):
+    """HBM bytes per launch of (pass 1, pass 2) in the mixed path: the 4-byte
+    column index of every pair plus each particle's own records and FP64 state
+    read and written once.
+    pass 1: row_ptr 8, X hi/lo 32, v record 16, L^-1 36, F rw 144, deviator rw 96,
+            eps_p / rate / D_init / f rw 64, D r+w 16, fail 4, material 4, u 24,
+            sigma w 48, pass-2 record w 96                              = 588
+    pass 2: row_ptr 8, X hi/lo 32, own pass-2 record 96, S0 16, V 8, D 8, sqrt E 8,
+            mass 8, v_half rw 48, v w 24, force w 24, u r+w 48, fail 4, bc 1,
+            v record w 16                                               = 349"""
+    return 4 * nnz + 588 * N, 4 * nnz + 349 * N
+
+
 def make_config(h, rc, dt, hg_alpha, precision="fp64") -> Config:
     return Config(float(h), float(rc), float(dt), float(hg_alpha), PRECISION[precision], 0)
 

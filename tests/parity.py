@@ -19,16 +19,17 @@ TOL_FP64 = 1e-10
 
 
 def floors(w) -> dict:
-    """Scale below which a field counts as zero: spacing for lengths, the grip
-    speed for velocities, the yield stress for stresses."""
+    """Scale of each field, the floor of its normwise relative error: the
+    lattice spacing for lengths, the grip speed for velocities, the yield
+    stress for stresses (and A = P L^{-T}), yield stress x spacing^2 for
+    forces, 1e-3 for the dimensionless strains, damage and porosity."""
     sp = w.specimen
     m = w.materials[0]
     L = sp.spacing
-    vref = max(1e-3, float(np.abs(sp.bc_vel).max()))
+    vref = float(np.abs(sp.bc_vel).max()) or 1.0
     s = max(m["A"], 1e6)
-    return dict(U=1e-3 * L, V=1e-3 * vref, F=1.0, SIGMA=1e-3 * s, STRESS_DEV=1e-3 * s, A=1e-3 * s,
-                EPSP=1e-6, EPSP_RATE=1e-6 / w.dt * 1e-3, DINIT=1e-6, DAMAGE=1e-6, POROSITY=1e-6,
-                FORCE=1e-3 * s * L * L)
+    return dict(U=L, V=vref, F=1.0, SIGMA=s, STRESS_DEV=s, A=s, EPSP=1e-3, EPSP_RATE=1e-3 / w.dt,
+                DINIT=1e-3, DAMAGE=1e-3, POROSITY=1e-3, FORCE=s * L * L)
 
 
 def relerr(a, b, floor):

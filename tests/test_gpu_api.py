@@ -87,7 +87,8 @@ def test_nonfinite_input_sets_status_bits():
     w = S.tensile_bar_cl(nx=5, ny=5, nz=8)
     g = tlsph.Simulation.from_workload(w)
     v = g.get("V")
-    v[10] = np.nan
+    interior = int(np.nonzero(w.specimen.bc_mask == 0)[0][len(v) // 4])
+    v[interior] = np.nan
     g.set("V", v)
     g.step(2)
     with pytest.raises(tlsph.TlsphError) as e:

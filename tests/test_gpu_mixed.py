@@ -1,0 +1,76 @@
+"""The mixed-precision path (FP32 pair gathers and sums, FP64 state and
+constitutive update) against the FP64 oracle and the FP64 GPU path.
+
+Its error is a stated property, not parity: these tests bound it loosely
+(MIXED_TOL per field after a few steps of an elastic run; first-order
+completeness and momentum to FP32 rounding) and the benchmark reports the
+measured per-field errors."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_07374_gb300 import specimen as S
+from paper_1901_07374_gb300 import tlsph
+from parity import compare_state
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 2e-4
+
+
+def test_mixed_first_steps_vs_oracle():
+    w = S.tensile_bar_cl()
+    g = tlsph.Simulation.from_workload(w, precision="mixed")
+    o = oracle.Simulation.from_workload(w)
+    for steps in (1, 9, 40):
+        g.step(steps)
+        o.step(steps)
+        errs = compare_state(g.state(), o.state(), w, tol=MIXED_TOL,
+                             fields=("U", "V", "F", "SIGMA", "STRESS_DEV", "FORCE", "A"))
+        print("mixed vs oracle", g.steps, errs)
+
+
+def test_mixed_patch_test_and_momentum():
+    w = S.tensile_bar_cl(nx=10, ny=9, nz=20)
+    w.specimen.bc_mask[:] = 0
+    w.specimen.bc_vel[:] = 0
+    g = tlsph.Simulation.from_workload(w, precision="mixed")
+    B = np.random.default_rng(0).normal(size=(3, 3)) * 5.0
+    g.set("V", w.specimen.X @ B.T)
+    g.step(1)
+    F = g.get("F")
+    assert np.max(np.abs(F - (np.eye(3).ravel() + w.dt * B.ravel()))) <= 1e-6 * w.dt * np.abs(B).max()
+    g.step(5)
+    f = g.get("FORCE")
+    assert np.all(np.abs(f.sum(0)) <= 1e-5 * np.abs(f).sum(0))
+
+
+def test_mixed_failure_variant_runs_and_fails_close_to_fp64():
+    """Plastic flow, damage and failure in mixed precision: status clean, the
+    failure set close to the FP64 path's (the decisions are FP64, their inputs
+    carry the FP32 pair sums)."""
+    w = S.failure_variant(S.tensile_bar_cl())
+    a = tlsph.Simulation.from_workload(w, precision="fp64")
+    b = tlsph.Simulation.from_workload(w, precision="mixed")
+    a.step(500)
+    b.step(500)
+    b.sync()
+    fa, fb = a.get("FAIL_STEP") >= 0, b.get("FAIL_STEP") >= 0
+    assert fa.sum() > 50
+    assert (fa ^ fb).sum() <= 0.05 * fa.sum()
+
+
+def test_mixed_resume_is_bitwise():
+    w = S.failure_variant(S.tensile_bar_cl(nx=6, ny=6, nz=16))
+    names = ("U", "V", "F", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY", "FAIL_STEP", "FORCE")
+    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    a.step(120)
+    ck = {k: a.get(k) for k in names}
+    a.step(80)
+    ref = a.state()
+    b = tlsph.Simulation.from_workload(w, precision="mixed")
+    for k, v in ck.items():
+        b.set(k, v)
+    b.step(80)
+    for k, v in b.state().items():
+        assert np.array_equal(v, ref[k]), k
