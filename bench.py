@@ -41,6 +41,8 @@ def workload(name: str):
     from paper_1901_07374_gb300 import specimen as S
     if name == "tensile_bar_jc_40x40x640":
         return S.tensile_bar_jc()
+    if name == "tensile_bar_jc_40x40x160":
+        return S.tensile_bar_jc(nz=160)
     if name == "tensile_bar_cl_8x8x32":
         return S.tensile_bar_cl()
     if name == "notched_bar_gtn":
@@ -165,7 +167,47 @@ def run_reference(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------- GPU arm
+FIELDS = ("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "DINIT", "DAMAGE", "FORCE")
+
+
+def field_scales(w) -> dict:
+    """Floor of the normwise relative error of each field: spacing, grip
+    speed, yield stress, yield stress x spacing^2, 1e-3 for strains/damage."""
+    import numpy as np
+    sp = w.specimen
+    L = sp.spacing
+    v = float(np.abs(sp.bc_vel).max()) or 1.0
+    s = max(w.materials[0]["A"], 1e6)
+    return dict(U=L, V=v, F=1.0, SIGMA=s, STRESS_DEV=s, EPSP=1e-3, DINIT=1e-3, DAMAGE=1e-3, FORCE=s * L * L)
+
+
+def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None):
+    """Create, warm up, then time `steps` steps with CUDA events on the
+    library's stream; per-kernel times from the library's own events."""
+    sim = tlsph.Simulation.from_workload(w, precision=precision, stream=stream)
+    N, nnz, _ = sim.info()
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    sim.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    p1, p2, nprof = sim.profile_read()
+    sim.profile(False)
+    clk = clocks.stop() if clocks else None
+    sim.sync()
+    return sim, dict(ms=ms, p1=p1 / max(1, nprof), p2=p2 / max(1, nprof), N=N, nnz=nnz, clocks=clk)
+
+
 def run_ours(args, rank: int, world: int, dist):
+    import ctypes
+
     import numpy as np
     import torch
 
@@ -176,65 +218,57 @@ def run_ours(args, rank: int, world: int, dist):
     w = workload(args.workload)
     sp = w.specimen
     stream = torch.cuda.current_stream()
-
-    # ---- device-resident timing
-    sim = tlsph.Simulation.from_workload(w, precision=args.precision, stream=stream)
-    N, nnz, _ = sim.info()
-    sim.step(args.warmup)
-    torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = ClockSampler(torch.cuda.current_device())
-    clk.start()
-    time.sleep(0.3)
-    sim.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    p1_ms, p2_ms, nprof = sim.profile_read()
-    sim.profile(False)
-    clocks = clk.stop()
-    sim.sync()
+
+    # ---- FP64 GPU path (the comparison) and the headline precision
+    ref_sim, ref = (None, None)
+    if args.precision != "fp64" and not args.skip_fp64:
+        ref_sim, ref = timed_run(tlsph, torch, w, "fp64", args.steps, args.warmup, stream)
+    sim, r = timed_run(tlsph, torch, w, args.precision, args.steps, args.warmup, stream,
+                       clocks=ClockSampler(torch.cuda.current_device()))
+    N, nnz, ms = r["N"], r["nnz"], r["ms"]
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-        dist.barrier()
-    sim.close()
-    del sim
     value = world * nnz * args.steps / (ms * 1e-3)
+
+    # ---- accuracy of the headline path against the FP64 GPU path (same steps)
+    accuracy = None
+    if ref_sim is not None:
+        sc = field_scales(w)
+        accuracy = {"steps": args.warmup + args.steps}
+        for f in FIELDS:
+            a, b = sim.get(f), ref_sim.get(f)
+            accuracy[f] = float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), sc[f]))
+        fa, fb = sim.get("FAIL_STEP") >= 0, ref_sim.get("FAIL_STEP") >= 0
+        accuracy["failure_set_symdiff"] = int((fa ^ fb).sum())
+        ref_sim.close()
+    sim.close()
 
     # ---- roofline of the dominant kernel
     ab = algorithmic_bytes(N, nnz, args.precision)
-    kern = "pass2" if p2_ms >= p1_ms else "pass1"
-    k_ms = (p2_ms if kern == "pass2" else p1_ms) / max(1, nprof)
+    kern = "pass2" if r["p2"] >= r["p1"] else "pass1"
+    k_ms = r[{"pass1": "p1", "pass2": "p2"}[kern]]
     peaks = measured_peaks()
-    peak = peaks.get("hbm_gbs")
-    src = "measured"
+    peak, src = peaks.get("hbm_gbs"), "measured"
     if not peak:
         peak, src = 6800.0, "fallback"
     achieved = ab[kern] / (k_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": src, "traffic": None,
                 "algorithmic_bytes_per_launch": ab[kern],
-                "ms_per_launch": {"pass1": p1_ms / max(1, nprof), "pass2": p2_ms / max(1, nprof)}}
+                "ms_per_launch": {"pass1": r["p1"], "pass2": r["p2"]}}
 
     # ---- end to end through the C ABI from pinned host buffers
     def pinned(a):
         t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         return t, t.numpy()
-    X_t, X = pinned(sp.X)
-    V_t, vol = pinned(sp.vol)
-    M_t, mat = pinned(sp.mat_id)
-    B_t, bcm = pinned(sp.bc_mask)
-    BV_t, bcv = pinned(sp.bc_vel)
-    F0_t, f0 = pinned(sp.f0)
+    keep = [pinned(a) for a in (sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0)]
+    X, vol, mat, bcm, bcv, f0 = (k[1] for k in keep)
     outs = {k: pinned(np.empty((N, c))) for k, c in (("U", 3), ("V", 3), ("SIGMA", 9), ("DAMAGE", 1))}
-    h2d = X.nbytes + vol.nbytes + mat.nbytes + bcm.nbytes + bcv.nbytes + f0.nbytes
+    h2d = sum(k[1].nbytes for k in keep)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -243,11 +277,10 @@ def run_ours(args, rank: int, world: int, dist):
                           precision=args.precision, stream=stream)
     s2.step(args.steps)
     d2h = 0
+    L = tlsph.load()
     for k, (t, a) in outs.items():
-        a = a.reshape(N, -1) if k != "DAMAGE" else a.reshape(N)
-        L = tlsph.load()
-        tlsph._check(L.tlsph_get_state(s2.ctx, tlsph.FIELD[k], a.ctypes.data_as(__import__("ctypes").c_void_p),
-                                       a.nbytes, 0), s2.ctx)
+        tlsph._check(L.tlsph_get_state(s2.ctx, tlsph.FIELD[k], a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0),
+                     s2.ctx)
         d2h += a.nbytes
     el = time.perf_counter() - t0
     s2.close()
@@ -267,16 +300,20 @@ def run_ours(args, rank: int, world: int, dist):
                          f"{steps} steps in {oel:.1f} s, single thread"}
     if rank != 0:
         return
+    cfg = {"workload": args.workload, "precision": args.precision, "particles": N, "pairs_per_step": nnz,
+           "particle_steps_per_s": world * N * args.steps / (ms * 1e-3),
+           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+           "l2": "inputs larger than L2 (about 1.8 GB per step vs 129 MB)"}
+    if ref is not None:
+        cfg["fp64_gpu_value"] = world * nnz * args.steps / (ref["ms"] * 1e-3)
+        cfg["fp64_ms_per_launch"] = {"pass1": ref["p1"], "pass2": ref["p2"]}
+        cfg["accuracy_vs_fp64"] = accuracy
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic (seeded jittered lattice)",
-            "config": {"workload": args.workload, "precision": args.precision, "particles": N,
-                       "pairs_per_step": nnz, "particle_steps_per_s": world * N * args.steps / (ms * 1e-3),
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "l2": "inputs larger than L2 (about 1.8 GB per step vs 129 MB)"},
+            "data": "synthetic (seeded jittered lattice)", "config": cfg,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-            "clocks": clocks}
+            "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -290,6 +327,7 @@ def main():
     ap.add_argument("--workload", default="tensile_bar_jc_40x40x640")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true", help="do not run the FP64 comparison path")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -17,9 +17,9 @@ from . import build as _build
 
 PRECISION = {"fp64": 0, "mixed": 1}
 # precision bench.py reports by default
-DEFAULT_PRECISION = "fp64"
+DEFAULT_PRECISION = "mixed"
 # precisions the smoke check runs, with the field tolerance against the oracle
-SMOKE_PRECISIONS = (("fp64", 1e-10),)
+SMOKE_PRECISIONS = (("fp64", 1e-10), ("mixed", 1e-4))
 
 FIELD = dict(X=0, U=1, V=2, F=3, SIGMA=4, STRESS_DEV=5, EPSP=6, EPSP_RATE=7, DINIT=8, DAMAGE=9,
              POROSITY=10, FAIL_STEP=11, FORCE=12, A=13, LINV=14, NBR_ROWPTR=15, NBR_COL=16)
