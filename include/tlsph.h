@@ -182,7 +182,8 @@ int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_
 int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, int src_on_device);
 
 /* Last error text of ctx, or of the calling thread's last failed
- * tlsph_create when ctx is NULL.  Valid until the next call on ctx. */
+ * tlsph_create or tlsph_neighbors_noalloc when ctx is NULL.  Valid until the
+ * next call on ctx. */
 const char *tlsph_last_error(const tlsph_ctx *ctx);
 
 /* Release the context (and its device memory when the library owns it). */
@@ -209,6 +210,36 @@ int tlsph_profile_read(tlsph_ctx *ctx, double *ms, int n, int64_t *steps);
 int tlsph_material_point_batch(const tlsph_material *mat, double dt, int64_t n,
                                const double *deps, const double *J, double *state,
                                void *stream);
+
+/* Neighbour CSR of N reference positions without allocating any memory.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory -- code running under a host framework that owns
+ * all device memory through its own pool, loops that must not take the
+ * device-wide synchronisation a cudaMalloc/cudaFree implies, or plugins with
+ * no allocator of their own.  It computes the same rows as tlsph_create
+ * (S_i = { j != i : |X_j - X_i| < rc } with the same FP64 predicate, rows
+ * ascending) but takes device inputs and outputs and keeps its scratch in a
+ * fixed 10 MiB device array inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   X        device, N*3 reference positions
+ *   N        1 <= N <= 262144 (larger N is rejected with TLSPH_ERR_ARG)
+ *   rc       cutoff (> 0)
+ *   row_ptr  device, N+1 int64 output
+ *   col      device, nnz_cap int32 output (may be NULL when nnz_cap == 0)
+ *   nnz_out  host, receives the number of pairs
+ *   stream   cudaStream_t for every launch (NULL: legacy default stream)
+ * Returns TLSPH_ERR_NOMEM, with row_ptr and *nnz_out filled but col not
+ * written, when nnz_cap is smaller than the pair count (call again with a
+ * larger col).  It synchronises the stream twice (to read the bounding box
+ * and the pair count); the column fill is still in flight on `stream` when
+ * it returns.  The first call on a device looks up the scratch address on
+ * that device (make it before any stream capture).  All calls share the one
+ * scratch array and leave their contents in it: calls whose work overlaps on
+ * the GPU (different streams, or another thread) race and must be
+ * serialised by the caller.  Nothing is allocated, freed or pinned. */
+int tlsph_neighbors_noalloc(const double *X, int64_t N, double rc, int64_t *row_ptr, int32_t *col,
+                            int64_t nnz_cap, int64_t *nnz_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -230,6 +230,8 @@ cudaError_t prof_fold(tlsph_ctx *ctx)
 
 namespace tlsph {
 
+void set_last_error_text(const std::string &msg) { g_create_error = msg; }
+
 DevMat make_dev_mat(const tlsph_material &m)
 {
     DevMat d{};

@@ -12,6 +12,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "tlsph_device.cuh"
 #include "tlsph_internal.cuh"
@@ -319,4 +321,147 @@ cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- neighbour build without allocation
+// Scratch of tlsph_neighbors_noalloc: one file-scope device array, present
+// on every GPU that loads the library until the process exits.  Sized for
+// NOALLOC_MAX_N particles: cell starts and cursors for 2N + 4096 cells,
+// the cell item list, scan partial sums and the bounding box.
+static constexpr int64_t NOALLOC_MAX_N = 262144;
+static constexpr size_t NOALLOC_SCRATCH_BYTES = 10u << 20;   // 10 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// bounding box of X (one block, deterministic min / max)
+__global__ void k_bounds(const double *X, int64_t N, double *out6)
+{
+    __shared__ double lo[3][256], hi[3][256];
+    const int t = threadIdx.x;
+    double l[3] = { INFINITY, INFINITY, INFINITY }, h[3] = { -INFINITY, -INFINITY, -INFINITY };
+    for (int64_t i = t; i < N; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            l[k] = fmin(l[k], X[3 * i + k]);
+            h[k] = fmax(h[k], X[3 * i + k]);
+        }
+    for (int k = 0; k < 3; ++k) { lo[k][t] = l[k]; hi[k][t] = h[k]; }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int k = 0; k < 3; ++k) {
+                lo[k][t] = fmin(lo[k][t], lo[k][t + w]);
+                hi[k][t] = fmax(hi[k][t], hi[k][t + w]);
+            }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int k = 0; k < 3; ++k) { out6[k] = lo[k][0]; out6[3 + k] = hi[k][0]; }
+}
+
+// the cell grid of make_cell_grid, from a bounding box instead of host positions
+static CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc)
+{
+    CellGrid g{};
+    double cs = rc * (1.0 + 1e-6);
+    const double cap = 2.0 * (double)N + 4096.0;
+    for (;;) {
+        double cells = 1.0;
+        for (int k = 0; k < 3; ++k) cells *= floor((hi[k] - lo[k]) / cs) + 1.0;
+        if (cells <= cap) break;
+        cs *= 1.25;
+    }
+    for (int k = 0; k < 3; ++k) {
+        g.xmin[k] = lo[k];
+        g.nc[k] = (int32_t)(floor((hi[k] - lo[k]) / cs) + 1.0);
+    }
+    g.cs = cs;
+    g.ncells = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    return g;
+}
+
+// device address of g_noalloc_scratch, looked up once per device with that
+// device current
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_base[256];
+
+static cudaError_t noalloc_scratch(void **base)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_base[dev] = p;
+    }
+    *base = g_noalloc_base[dev];
+    return cudaSuccess;
+}
+
 }  // namespace tlsph
+
+extern "C" int tlsph_neighbors_noalloc(const double *X, int64_t N, double rc, int64_t *row_ptr, int32_t *col,
+                                       int64_t nnz_cap, int64_t *nnz_out, void *stream)
+{
+    using namespace tlsph;
+    auto fail = [](int code, const std::string &msg) {
+        set_last_error_text(msg);
+        return code;
+    };
+    if (!X || !row_ptr || !nnz_out) return fail(TLSPH_ERR_ARG, "X, row_ptr and nnz_out are required");
+    if (N <= 0) return fail(TLSPH_ERR_ARG, "N must be positive");
+    if (N > NOALLOC_MAX_N)
+        return fail(TLSPH_ERR_ARG, "tlsph_neighbors_noalloc handles at most " + std::to_string(NOALLOC_MAX_N) +
+                                   " particles (its scratch is a fixed 10 MiB device array); got N = " +
+                                   std::to_string(N));
+    if (!(rc > 0.0) || !isfinite(rc)) return fail(TLSPH_ERR_ARG, "rc must be positive and finite");
+    if (nnz_cap < 0 || (nnz_cap > 0 && !col)) return fail(TLSPH_ERR_ARG, "col is required when nnz_cap > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *base = nullptr;
+    cudaError_t e = noalloc_scratch(&base);
+    if (e != cudaSuccess) return fail(TLSPH_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));
+
+    // carve the scratch (256-byte aligned pieces)
+    const int64_t max_cells = 2 * N + 4096;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = static_cast<char *>(base) + off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    Scratch sc{};
+    sc.cell_start = reinterpret_cast<int64_t *>(take((size_t)(max_cells + 1) * sizeof(int64_t)));
+    sc.cell_cursor = reinterpret_cast<int64_t *>(take((size_t)max_cells * sizeof(int64_t)));
+    sc.cell_items = reinterpret_cast<int32_t *>(take((size_t)N * sizeof(int32_t)));
+    sc.scan_tmp_elems = scan_tmp_elems(max_cells + 1);
+    sc.scan_tmp = reinterpret_cast<int64_t *>(take(sc.scan_tmp_elems * sizeof(int64_t)));
+    double *bounds = reinterpret_cast<double *>(take(6 * sizeof(double)));
+    if (off > NOALLOC_SCRATCH_BYTES) return fail(TLSPH_ERR_NOMEM, "scratch layout exceeds its array");
+
+    double bb[6];
+    k_bounds<<<1, 256, 0, st>>>(X, N, bounds);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(bb, bounds, sizeof bb, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(TLSPH_ERR_CUDA, std::string("bounds: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 6; ++k)
+        if (!isfinite(bb[k])) return fail(TLSPH_ERR_ARG, "X must be finite");
+    const CellGrid g = cell_grid_from_bounds(bb, bb + 3, N, rc);
+    if (g.ncells > max_cells) return fail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
+
+    DevState s{};
+    s.N = N;
+    s.X = X;
+    const double rc2 = rc * rc;
+    int64_t nnz = 0;
+    if ((e = build_neighbors_count(s, g, sc, rc2, row_ptr, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&nnz, row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(TLSPH_ERR_CUDA, std::string("neighbour count: ") + cudaGetErrorString(e));
+    *nnz_out = nnz;
+    if (nnz > nnz_cap)
+        return fail(TLSPH_ERR_NOMEM, "col capacity too small: need nnz_cap >= " + std::to_string(nnz));
+    if ((e = build_neighbors_fill(s, g, sc, rc2, row_ptr, col, st)) != cudaSuccess)
+        return fail(TLSPH_ERR_CUDA, std::string("neighbour fill: ") + cudaGetErrorString(e));
+    return TLSPH_OK;
+}

@@ -135,6 +135,9 @@ cudaError_t launch_import_sym(const double *src9, double *dst6, int64_t N, cudaS
 
 DevMat make_dev_mat(const tlsph_material &m);
 
+// text returned by tlsph_last_error(NULL) on the calling thread
+void set_last_error_text(const std::string &msg);
+
 // mixed.cu
 cudaError_t mixed_init_static(const DevState &s, const double *S0, cudaStream_t st);
 cudaError_t mixed_material(const DevState &s, int mat_id, cudaStream_t st);

@@ -325,3 +325,24 @@ def material_point_batch(mat: dict, dt: float, deps, J, state, stream=None) -> N
                                         ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(state.data_ptr()),
                                         ctypes.c_void_p(_stream_handle(stream)))
     _check(code, None)
+
+
+def neighbors_noalloc(X, rc: float, row_ptr, col, stream=None) -> int:
+    """tlsph_neighbors_noalloc on torch CUDA tensors: X (N, 3) float64,
+    row_ptr (N + 1,) int64, col (capacity,) int32.  Returns the pair count;
+    raises TlsphError (code -4) when col is too small."""
+    L = load()
+    fn = L.tlsph_neighbors_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    nnz = ctypes.c_int64(0)
+    cap = int(col.numel()) if col is not None else 0
+    code = fn(ctypes.c_void_p(X.data_ptr()), int(X.shape[0]), float(rc), ctypes.c_void_p(row_ptr.data_ptr()),
+              ctypes.c_void_p(col.data_ptr()) if col is not None else None, cap, ctypes.byref(nnz),
+              ctypes.c_void_p(_stream_handle(stream)))
+    if code != 0:
+        err = TlsphError(code, L.tlsph_last_error(None).decode(errors="replace"))
+        err.nnz = nnz.value
+        raise err
+    return nnz.value
