@@ -118,7 +118,8 @@ typedef enum {
     TLSPH_FIELD_LINV = 14,      /* f64 N*9  L_i^{-1} (read only) */
     TLSPH_FIELD_NBR_ROWPTR = 15,/* i64 N+1  neighbour CSR row pointers (read only) */
     TLSPH_FIELD_NBR_COL = 16,   /* i32 nnz  neighbour CSR columns, rows ascending (read only) */
-    TLSPH_FIELD_COUNT = 17
+    TLSPH_FIELD_STEP = 17,      /* i64 1    number of completed steps (failure steps count from it) */
+    TLSPH_FIELD_COUNT = 18
 } tlsph_field;
 
 /* Bytes of device memory a context needs for N particles and up to nnz_cap
@@ -176,7 +177,7 @@ int tlsph_info(const tlsph_ctx *ctx, int64_t *N, int64_t *nnz, int64_t *steps);
 int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_on_device);
 
 /* Overwrite a writable field (U, V, F, STRESS_DEV, EPSP, EPSP_RATE, DINIT,
- * DAMAGE, POROSITY, FAIL_STEP, FORCE) from src; the half-step velocity and
+ * DAMAGE, POROSITY, FAIL_STEP, FORCE, STEP) from src; the half-step velocity and
  * the predicted displacement are recomputed from U, V and FORCE.  Used for
  * checkpoint/resume and for tests that start from a chosen state. */
 int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, int src_on_device);
@@ -188,6 +189,16 @@ const char *tlsph_last_error(const tlsph_ctx *ctx);
 
 /* Release the context (and its device memory when the library owns it). */
 int tlsph_destroy(tlsph_ctx *ctx);
+
+/* Launch plan of the mixed-precision step: plan[0] pass-1 form (0 warp per
+ * 32 rows; 1 thread per row; 2 thread-per-row gather + per-particle kernel;
+ * 3 warp-per-32-rows gather + per-particle kernel), plan[1] its block size,
+ * plan[2] pass-2 form (0 warp per 32 rows; 1 thread per row), plan[3] its
+ * block size (multiples of 32 up to 256).  Every plan computes the same
+ * method; sums over a row are grouped differently, so results differ only
+ * by FP32 rounding.  n must be 4.  The FP64 path ignores the plan. */
+int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);
+int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
 
 /* Per-kernel device time of the step (CUDA events recorded around each
  * launch on the context's stream).  enable != 0 clears the accumulators and

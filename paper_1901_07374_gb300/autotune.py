@@ -1,0 +1,107 @@
+"""Launch-plan autotuner of the mixed-precision step.
+
+A plan is (pass-1 form, pass-1 block, pass-2 form, pass-2 block); every plan
+computes the same method (see tlsph_set_plan).  The tuner times each
+candidate of a pass with the library's own CUDA events on the context's
+stream, keeps the fastest per pass, and restores the simulation state
+bit for bit afterwards (checkpoint of every resumable field, step counter
+included), so tuning never changes a trajectory.  Results are cached per
+(GPU, precision, particle-count bucket, neighbours-per-row bucket, hourglass
+on/off) in a JSON file ($TLSPH_PLAN_CACHE, default
+~/.cache/tlsph_gb300/plans.json).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+PASS1 = [(0, 128), (1, 64), (1, 128), (2, 64), (2, 128), (2, 256), (3, 128), (3, 256)]
+PASS2 = [(0, 128), (1, 64), (1, 128), (1, 256)]
+DEFAULT = (2, 256, 1, 256)
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("TLSPH_PLAN_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "tlsph_gb300",
+                                                              "plans.json")
+
+
+def _key(sim) -> str:
+    import torch
+    N, nnz, _ = sim.info()
+    name = torch.cuda.get_device_name()
+    hg = "hg" if sim.cfg.hg_alpha != 0 else "nohg"
+    return f"{name}|{sim.precision}|N2^{int(math.log2(max(N, 1)))}|row{int(round(nnz / max(N, 1) / 8.0)) * 8}|{hg}"
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, plan) -> None:
+    path = cache_path()
+    with _lock:
+        d = _load()
+        d[key] = list(plan)
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + f".{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(d, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+
+
+def _time(sim, plan, steps: int, warmup: int):
+    sim.set_plan(plan)
+    sim.step(warmup)
+    sim.profile(True)
+    sim.step(steps)
+    p1, p2, n = sim.profile_read()
+    sim.profile(False)
+    return p1 / max(n, 1), p2 / max(n, 1)
+
+
+def tune(sim, steps: int = 3, warmup: int = 1, use_cache: bool = True, record=None):
+    """Choose and set the fastest plan for `sim` (a mixed-precision
+    tlsph.Simulation); returns it.  `record`, if a list, receives
+    (plan, ms pass 1, ms pass 2) for every timed candidate."""
+    if sim.precision != "mixed":
+        return None
+    key = _key(sim)
+    if use_cache:
+        cached = _load().get(key)
+        if cached:
+            sim.set_plan(cached)
+            return tuple(cached)
+    ck = sim.checkpoint(device=True)
+    plan0 = sim.get_plan()
+    best1, best2 = None, None
+    for v1, b1 in PASS1:
+        plan = (v1, b1, DEFAULT[2], DEFAULT[3])
+        t1, t2 = _time(sim, plan, steps, warmup)
+        if record is not None:
+            record.append((plan, t1, t2))
+        if best1 is None or t1 < best1[0]:
+            best1 = (t1, v1, b1)
+    for v2, b2 in PASS2:
+        plan = (best1[1], best1[2], v2, b2)
+        t1, t2 = _time(sim, plan, steps, warmup)
+        if record is not None:
+            record.append((plan, t1, t2))
+        if best2 is None or t2 < best2[0]:
+            best2 = (t2, v2, b2)
+    sim.restore(ck)
+    best = (best1[1], best1[2], best2[1], best2[2])
+    sim.set_plan(best if best else plan0)
+    if use_cache:
+        _store(key, best)
+    return best

@@ -26,7 +26,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 struct Layout {
     size_t X, vol, mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
-    size_t xh, xl, s0, linv32, r1, r2;
+    size_t xh, xl, s0, linv32, r1, r2, fsum;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
     size_t overlay_end;
     size_t total;
@@ -79,6 +79,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
         L.linv32 = c.take(9 * n * sizeof(float));
         L.r1 = c.take(n * 16);
         L.r2 = c.take(6 * n * 16);
+        L.fsum = c.take(9 * n * sizeof(float));
     }
     // overlay block: F, sd, sig, A  |  neighbour-build scratch
     const size_t ov = c.off;
@@ -143,7 +144,9 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.linv32 = at<float>(base, L.linv32);
         s.r1 = at<float4>(base, L.r1);
         s.r2 = at<float4>(base, L.r2);
+        s.fsum = at<float>(base, L.fsum);
     } else {
+        s.fsum = nullptr;
         s.xh = s.xl = s.s0 = s.r1 = s.r2 = nullptr;
         s.linv32 = nullptr;
     }
@@ -205,6 +208,7 @@ FieldInfo field_info(tlsph_ctx *ctx, int field)
     case TLSPH_FIELD_LINV: return { (void *)s.Linv, d, 9 * n, false, false };
     case TLSPH_FIELD_NBR_ROWPTR: return { (void *)s.row_ptr, sizeof(int64_t), n + 1, false, false };
     case TLSPH_FIELD_NBR_COL: return { (void *)s.col, sizeof(int32_t), (size_t)ctx->nnz, false, false };
+    case TLSPH_FIELD_STEP: return { &ctx->steps, sizeof(int64_t), 1, true, false };
     default: return { nullptr, 0, 0, false, false };
     }
 }
@@ -525,6 +529,12 @@ int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_
     if (bytes != f.elem * f.count) { ctx->err = "byte count does not match the field"; return TLSPH_ERR_ARG; }
     cudaStream_t st = ctx->stream;
     cudaError_t e;
+    if (field == TLSPH_FIELD_STEP) {   // host-side counter
+        e = dst_on_device ? cudaMemcpy(dst, &ctx->steps, sizeof(int64_t), cudaMemcpyHostToDevice) : cudaSuccess;
+        if (!dst_on_device) memcpy(dst, &ctx->steps, sizeof(int64_t));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "get_state step");
+        return TLSPH_OK;
+    }
     if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
         e = mixed_sync_to_fp64(*ctx, field, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "mixed export");
@@ -565,6 +575,16 @@ int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, in
     if (bytes != f.elem * f.count) { ctx->err = "byte count does not match the field"; return TLSPH_ERR_ARG; }
     cudaStream_t st = ctx->stream;
     cudaError_t e;
+    if (field == TLSPH_FIELD_STEP) {   // host-side counter
+        int64_t v = 0;
+        e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && src_on_device) e = cudaMemcpy(&v, src, sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (!src_on_device) memcpy(&v, src, sizeof(int64_t));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state step");
+        if (v < 0) { ctx->err = "step count must be >= 0"; return TLSPH_ERR_ARG; }
+        ctx->steps = v;
+        return TLSPH_OK;
+    }
     if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
         e = mixed_sync_to_fp64(*ctx, -1, st);   // bring every FP64 field up to date first
         if (e != cudaSuccess) return cuda_fail(ctx, e, "mixed export");
@@ -608,6 +628,27 @@ int tlsph_destroy(tlsph_ctx *ctx)
     for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
     mixed_release(*ctx);
     delete ctx;
+    return TLSPH_OK;
+}
+
+int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n)
+{
+    if (!ctx || !plan || n != 4) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    const int32_t v1 = plan[0], b1 = plan[1], v2 = plan[2], b2 = plan[3];
+    const bool ok = v1 >= 0 && v1 <= 3 && v2 >= 0 && v2 <= 1 && b1 >= 32 && b1 <= 256 && b1 % 32 == 0 &&
+                    b2 >= 32 && b2 <= 256 && b2 % 32 == 0;
+    if (!ok) { ctx->err = "plan out of range"; return TLSPH_ERR_ARG; }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_plan sync");
+    for (int k = 0; k < 4; ++k) ctx->plan[k] = plan[k];
+    return TLSPH_OK;
+}
+
+int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n)
+{
+    if (!ctx || !plan || n != 4) return TLSPH_ERR_ARG;
+    for (int k = 0; k < 4; ++k) plan[k] = ctx->plan[k];
     return TLSPH_OK;
 }
 

@@ -140,48 +140,11 @@ __device__ __forceinline__ float3 xdiff(const float4 hi_j, const float4 lo_j, co
 }
 
 // ------------------------------------------------------------------ pass 1
-__global__ void __launch_bounds__(MIX_THREADS) k_pass1_mixed(DevState s, MixConst c)
+// per-particle part of pass 1: F^{n+1}, J, kinematics, constitutive and
+// damage update, stress, A and the pass-2 record of particle i from its
+// velocity-gradient sums keep[9]
+__device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
-    if (row0 >= s.N) return;
-    const int nrows = (int)min((int64_t)32, s.N - row0);
-    const float4 *__restrict__ xh = s.xh;
-    const float4 *__restrict__ xl = s.xl;
-    const float4 *__restrict__ r1 = s.r1;
-    float keep[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
-
-    for (int r = 0; r < nrows; ++r) {
-        const int64_t i = row0 + r;
-        const float4 hi = xh[i], lo = xl[i], vi = r1[i];
-        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
-        float m[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) m[k] = 0.0f;
-        for (int64_t p = p0 + lane; p < p1; p += 32) {
-            const int j = s.col[p];
-            const float4 hj = xh[j], lj = xl[j], vj = r1[j];
-            const float3 d = xdiff(hj, lj, hi, lo);
-            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-            const float rinv = rsqrtf(r2);
-            const float q = r2 * rinv * c.inv_h;
-            const float cw = hj.w * vj.w * spline_dw(q) * rinv;   // V_j (1 - D_j) W'/r
-            const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
-            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
-            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
-            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float t = warp_allsum(m[k]);
-            keep[k] = (lane == r) ? t : keep[k];
-        }
-    }
-    if (lane >= nrows) return;
-
-    const int64_t i = row0 + lane;
     const double *__restrict__ Dn = s.D[c.dcur];
     double *__restrict__ Dnext = s.D[c.dcur ^ 1];
     float4 *__restrict__ r2o = s.r2 + 6 * i;
@@ -295,7 +258,106 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass1_mixed(DevState s, MixCons
     if (st) atomicOr(s.status, st);
 }
 
+__global__ void __launch_bounds__(MIX_THREADS) k_pass1_mixed(DevState s, MixConst c)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (row0 >= s.N) return;
+    const int nrows = (int)min((int64_t)32, s.N - row0);
+    const float4 *__restrict__ xh = s.xh;
+    const float4 *__restrict__ xl = s.xl;
+    const float4 *__restrict__ r1 = s.r1;
+    float keep[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
+
+    for (int r = 0; r < nrows; ++r) {
+        const int64_t i = row0 + r;
+        const float4 hi = xh[i], lo = xl[i], vi = r1[i];
+        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+        float m[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) m[k] = 0.0f;
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
+            const int j = s.col[p];
+            const float4 hj = xh[j], lj = xl[j], vj = r1[j];
+            const float3 d = xdiff(hj, lj, hi, lo);
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float rinv = rsqrtf(r2);
+            const float q = r2 * rinv * c.inv_h;
+            const float cw = hj.w * vj.w * spline_dw(q) * rinv;   // V_j (1 - D_j) W'/r
+            const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
+            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
+            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
+            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float t = warp_allsum(m[k]);
+            keep[k] = (lane == r) ? t : keep[k];
+        }
+    }
+    if (lane >= nrows) return;
+
+    epi1_mixed(s, c, row0 + lane, keep);
+}
+
 // ------------------------------------------------------------------ pass 2
+// per-particle part of pass 2: force (rearranged Sec. 3.1 form) and the
+// velocity-Verlet update in FP64 from the pair sums keep[9]
+template <bool HG>
+__device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
+{
+    const double Vi = s.vol[i];
+    const double Di = s.D[c.dcur ^ 1][i];
+    const double omdi = 1.0 - Di;
+    const float4 a0 = s.r2[6 * i], a1 = s.r2[6 * i + 1], a2 = s.r2[6 * i + 2];
+    const float Ai[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
+    const float4 s0 = s.s0[i];
+    const float w2 = (float)(2.0 - Di);
+    const float bx = w2 * s0.x - keep[0], by = w2 * s0.y - keep[1], bz = w2 * s0.z - keep[2];
+    double f[3];
+    f[0] = Vi * (double)c.dw_norm * ((double)(Ai[0] * bx + Ai[1] * by + Ai[2] * bz) + omdi * (double)keep[3]);
+    f[1] = Vi * (double)c.dw_norm * ((double)(Ai[3] * bx + Ai[4] * by + Ai[5] * bz) + omdi * (double)keep[4]);
+    f[2] = Vi * (double)c.dw_norm * ((double)(Ai[6] * bx + Ai[7] * by + Ai[8] * bz) + omdi * (double)keep[5]);
+    if (HG) {
+        const double hc = (double)c.hg_coef * s.sqrtE[i] * omdi * Vi * (double)c.w_norm;
+        f[0] += hc * (double)keep[6];
+        f[1] += hc * (double)keep[7];
+        f[2] += hc * (double)keep[8];
+    }
+    const double im = 1.0 / s.mass[i];
+    const int fail = s.fail[i];
+    double vn[3], v2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.force[3 * i + k] = f[k];
+        vn[k] = s.vh[3 * i + k] + c.half_dt * (f[k] * im);
+    }
+    if (fail >= 0) {
+        vn[0] = vn[1] = vn[2] = 0.0;
+    } else if (s.bcm[i]) {
+        vn[0] = s.bcv[3 * i]; vn[1] = s.bcv[3 * i + 1]; vn[2] = s.bcv[3 * i + 2];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * (f[k] * im);
+    if (fail >= 0) {
+        v2[0] = v2[1] = v2[2] = 0.0;
+    } else if (s.bcm[i]) {
+        v2[0] = s.bcv[3 * i]; v2[1] = s.bcv[3 * i + 1]; v2[2] = s.bcv[3 * i + 2];
+    }
+    const double *un = s.u[c.ucur ^ 1];
+    double *unext = s.u[c.ucur];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s.v[3 * i + k] = vn[k];
+        s.vh[3 * i + k] = v2[k];
+        unext[3 * i + k] = un[3 * i + k] + c.dt * v2[k];
+    }
+    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2), (float)omdi);
+    if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
+}
+
 template <bool HG>
 __global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixConst c)
 {
@@ -361,56 +423,177 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixCons
     }
     if (lane >= nrows) return;
 
-    // ---- epilogue: force (rearranged Sec. 3.1 form) and velocity Verlet in FP64
+    epi2_mixed<HG>(s, c, row0 + lane, keep);
+}
+
+// ------------------------------------------------------------------ thread-per-row variants
+// One thread owns one row: no reductions, and the neighbour loop is unrolled
+// twice so each thread keeps two pairs' gathers in flight.  A padded pair
+// (odd row length) reuses the last neighbour with weight zero.
+__device__ __forceinline__ void gather1_row(const DevState &s, const MixConst &c, int64_t i, float *m)
+{
+    const float4 hi = s.xh[i], lo = s.xl[i], vi = s.r1[i];
+    const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = 0.0f;
+    for (int64_t p = p0; p < p1; p += 2) {
+        const bool two = p + 1 < p1;
+        const int j0 = s.col[p];
+        const int j1 = two ? s.col[p + 1] : j0;
+        const float4 h0 = s.xh[j0], l0 = s.xl[j0], v0 = s.r1[j0];
+        const float4 h1 = s.xh[j1], l1 = s.xl[j1], v1 = s.r1[j1];
+        {
+            const float3 d = xdiff(h0, l0, hi, lo);
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float rinv = rsqrtf(r2);
+            const float cw = h0.w * v0.w * spline_dw(r2 * rinv * c.inv_h) * rinv;
+            const float cx = cw * (v0.x - vi.x), cy = cw * (v0.y - vi.y), cz = cw * (v0.z - vi.z);
+            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
+            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
+            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
+        }
+        {
+            const float3 d = xdiff(h1, l1, hi, lo);
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float rinv = rsqrtf(r2);
+            const float cw = two ? h1.w * v1.w * spline_dw(r2 * rinv * c.inv_h) * rinv : 0.0f;
+            const float cx = cw * (v1.x - vi.x), cy = cw * (v1.y - vi.y), cz = cw * (v1.z - vi.z);
+            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
+            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
+            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pass1_mixed_t(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+    gather1_row(s, c, i, m);
+    epi1_mixed(s, c, i, m);
+}
+
+// split form of pass 1: the gather kernel stores the 9 sums, a second kernel
+// runs the per-particle update (lighter registers in the gather)
+__global__ void __launch_bounds__(256) k_gather1_mixed_t(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+    gather1_row(s, c, i, m);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.fsum[9 * i + k] = m[k];
+}
+
+__global__ void __launch_bounds__(256) k_gather1_mixed_w32(DevState s, MixConst c)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (row0 >= s.N) return;
+    const int nrows = (int)min((int64_t)32, s.N - row0);
+    float keep[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
+    for (int r = 0; r < nrows; ++r) {
+        const int64_t i = row0 + r;
+        const float4 hi = s.xh[i], lo = s.xl[i], vi = s.r1[i];
+        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+        float m[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) m[k] = 0.0f;
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
+            const int j = s.col[p];
+            const float4 hj = s.xh[j], lj = s.xl[j], vj = s.r1[j];
+            const float3 d = xdiff(hj, lj, hi, lo);
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float rinv = rsqrtf(r2);
+            const float cw = hj.w * vj.w * spline_dw(r2 * rinv * c.inv_h) * rinv;
+            const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
+            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
+            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
+            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float t = warp_allsum(m[k]);
+            keep[k] = (lane == r) ? t : keep[k];
+        }
+    }
+    if (lane >= nrows) return;
     const int64_t i = row0 + lane;
-    const double Vi = s.vol[i];
-    const double Di = s.D[c.dcur ^ 1][i];
-    const double omdi = 1.0 - Di;
-    const float4 a0 = r2[6 * i], a1 = r2[6 * i + 1], a2 = r2[6 * i + 2];
-    const float Ai[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
-    const float4 s0 = s.s0[i];
-    const float w2 = (float)(2.0 - Di);
-    const float bx = w2 * s0.x - keep[0], by = w2 * s0.y - keep[1], bz = w2 * s0.z - keep[2];
-    double f[3];
-    f[0] = Vi * (double)c.dw_norm * ((double)(Ai[0] * bx + Ai[1] * by + Ai[2] * bz) + omdi * (double)keep[3]);
-    f[1] = Vi * (double)c.dw_norm * ((double)(Ai[3] * bx + Ai[4] * by + Ai[5] * bz) + omdi * (double)keep[4]);
-    f[2] = Vi * (double)c.dw_norm * ((double)(Ai[6] * bx + Ai[7] * by + Ai[8] * bz) + omdi * (double)keep[5]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.fsum[9 * i + k] = keep[k];
+}
+
+__global__ void __launch_bounds__(128) k_epi1_mixed(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = s.fsum[9 * i + k];
+    epi1_mixed(s, c, i, m);
+}
+
+// pass 2, thread per row
+template <bool HG>
+__device__ __forceinline__ void pair2(const MixConst &c, const float4 hi, const float4 lo, const float4 a0,
+                                      const float4 a1, const float4 a2, const float4 a3, const float4 a4,
+                                      const float4 a5, const float4 *__restrict__ xh, const float4 *__restrict__ xl,
+                                      const float4 *__restrict__ r2, int j, float wmask, float *acc)
+{
+    const float4 hj = xh[j], lj = xl[j];
+    const float4 b0 = r2[6 * j], b1 = r2[6 * j + 1], b2 = r2[6 * j + 2];
+    const float3 d = xdiff(hj, lj, hi, lo);
+    const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
+    const float rinv = rsqrtf(r2v);
+    const float q = r2v * rinv * c.inv_h;
+    const float g = wmask * hj.w * spline_dw(q) * rinv;
+    const float gd = g * (1.0f - b2.y);
+    acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
+    const float t0 = (b0.x - a0.x) * d.x + (b0.y - a0.y) * d.y + (b0.z - a0.z) * d.z;
+    const float t1 = (b0.w - a0.w) * d.x + (b1.x - a1.x) * d.y + (b1.y - a1.y) * d.z;
+    const float t2 = (b1.z - a1.z) * d.x + (b1.w - a1.w) * d.y + (b2.x - a2.x) * d.z;
+    acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
     if (HG) {
-        const double hc = (double)c.hg_coef * s.sqrtE[i] * omdi * Vi * (double)c.w_norm;
-        f[0] += hc * (double)keep[6];
-        f[1] += hc * (double)keep[7];
-        f[2] += hc * (double)keep[8];
+        const float4 b3 = r2[6 * j + 3], b4 = r2[6 * j + 4], b5 = r2[6 * j + 5];
+        const float ux = b2.z - a2.z, uy = b2.w - a2.w, uz = b3.x - a3.x;
+        const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
+        const float lxi = rsqrtf(xx * xx + xy * xy + xz * xz);
+        const float ex = (a3.y + b3.y) * d.x + (a3.z + b3.z) * d.y + (a3.w + b3.w) * d.z - 2.0f * ux;
+        const float ey = (a4.x + b4.x) * d.x + (a4.y + b4.y) * d.y + (a4.z + b4.z) * d.z - 2.0f * uy;
+        const float ez = (a4.w + b4.w) * d.x + (a5.x + b5.x) * d.y + (a5.y + b5.y) * d.z - 2.0f * uz;
+        const float delta = (ex * xx + ey * xy + ez * xz) * lxi;
+        const float ch = wmask * lj.w * b2.y * hj.w * spline_w(q) * rinv * rinv * delta * lxi;
+        acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
     }
-    const double im = 1.0 / s.mass[i];
-    const int fail = s.fail[i];
-    double vn[3], v2[3];
+}
+
+template <bool HG>
+__global__ void __launch_bounds__(256) k_pass2_mixed_t(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    const float4 *__restrict__ xh = s.xh;
+    const float4 *__restrict__ xl = s.xl;
+    const float4 *__restrict__ r2 = s.r2;
+    const float4 hi = xh[i], lo = xl[i];
+    const float4 a0 = r2[6 * i], a1 = r2[6 * i + 1], a2 = r2[6 * i + 2];
+    float4 a3 = make_float4(0.f, 0.f, 0.f, 0.f), a4 = a3, a5 = a3;
+    if (HG) { a3 = r2[6 * i + 3]; a4 = r2[6 * i + 4]; a5 = r2[6 * i + 5]; }
+    const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+    float acc[9];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        s.force[3 * i + k] = f[k];
-        vn[k] = s.vh[3 * i + k] + c.half_dt * (f[k] * im);
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+    for (int64_t p = p0; p < p1; p += 2) {
+        const bool two = p + 1 < p1;
+        const int j0 = s.col[p];
+        const int j1 = two ? s.col[p + 1] : j0;
+        pair2<HG>(c, hi, lo, a0, a1, a2, a3, a4, a5, xh, xl, r2, j0, 1.0f, acc);
+        pair2<HG>(c, hi, lo, a0, a1, a2, a3, a4, a5, xh, xl, r2, j1, two ? 1.0f : 0.0f, acc);
     }
-    if (fail >= 0) {
-        vn[0] = vn[1] = vn[2] = 0.0;
-    } else if (s.bcm[i]) {
-        vn[0] = s.bcv[3 * i]; vn[1] = s.bcv[3 * i + 1]; vn[2] = s.bcv[3 * i + 2];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * (f[k] * im);
-    if (fail >= 0) {
-        v2[0] = v2[1] = v2[2] = 0.0;
-    } else if (s.bcm[i]) {
-        v2[0] = s.bcv[3 * i]; v2[1] = s.bcv[3 * i + 1]; v2[2] = s.bcv[3 * i + 2];
-    }
-    const double *un = s.u[c.ucur ^ 1];
-    double *unext = s.u[c.ucur];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        s.v[3 * i + k] = vn[k];
-        s.vh[3 * i + k] = v2[k];
-        unext[3 * i + k] = un[3 * i + k] + c.dt * v2[k];
-    }
-    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2), (float)omdi);
-    if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
+    epi2_mixed<HG>(s, c, i, acc);
 }
 
 // ------------------------------------------------------------------ mirrors
@@ -480,21 +663,44 @@ cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Launch plans (chosen per context, e.g. by the autotuner):
+//   pass 1: 0 = warp per 32 rows, fused;  1 = thread per row, fused;
+//           2 = thread-per-row gather + per-particle kernel;  3 = warp-per-32-rows gather + per-particle kernel
+//   pass 2: 0 = warp per 32 rows;  1 = thread per row
+// block sizes are multiples of 32 up to 256 (128 for the fused warp forms).
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev)
 {
     const MixConst c = make_mix_const(ctx, step_index);
     const DevState &s = ctx.s;
-    const unsigned grid = nb((s.N + 31) / 32 * 32, MIX_THREADS);
+    const int v1 = ctx.plan[0], b1 = ctx.plan[1], v2 = ctx.plan[2], b2 = ctx.plan[3];
+    const bool hg = ctx.cfg.hg_alpha != 0.0;
+    const int64_t rows32 = (s.N + 31) / 32 * 32;
     if (ev) cudaEventRecord(ev[0], st);
-    k_pass1_mixed<<<grid, MIX_THREADS, 0, st>>>(s, c);
+    switch (v1) {
+    case 1: k_pass1_mixed_t<<<nb(s.N, b1), b1, 0, st>>>(s, c); break;
+    case 2:
+        k_gather1_mixed_t<<<nb(s.N, b1), b1, 0, st>>>(s, c);
+        k_epi1_mixed<<<nb(s.N, 128), 128, 0, st>>>(s, c);
+        break;
+    case 3:
+        k_gather1_mixed_w32<<<nb(rows32, b1), b1, 0, st>>>(s, c);
+        k_epi1_mixed<<<nb(s.N, 128), 128, 0, st>>>(s, c);
+        break;
+    default: k_pass1_mixed<<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c); break;
+    }
     if (ev) cudaEventRecord(ev[1], st);
-    if (ctx.cfg.hg_alpha != 0.0)
-        k_pass2_mixed<true><<<grid, MIX_THREADS, 0, st>>>(s, c);
-    else
-        k_pass2_mixed<false><<<grid, MIX_THREADS, 0, st>>>(s, c);
+    if (v2 == 1) {
+        if (hg) k_pass2_mixed_t<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+        else k_pass2_mixed_t<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+    } else {
+        if (hg) k_pass2_mixed<true><<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c);
+        else k_pass2_mixed<false><<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c);
+    }
     if (ev) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }
+
+int mixed_kernels_per_step(const tlsph_ctx &ctx) { return (ctx.plan[0] >= 2 ? 3 : 2); }
 
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st)
 {

@@ -62,6 +62,7 @@ struct DevState {
     float *linv32;          // N*9 L^{-1} rounded
     float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
     float4 *r2;             // N*6 pass-2 gather record {A (9), 1 - D, u (3), F - I (9), 0, 0}
+    float *fsum;            // N*9 pass-1 pair sums (split launch plans)
     double vref[3];         // bulk reference velocity of the r1 mirror
 };
 
@@ -88,6 +89,9 @@ struct tlsph_ctx {
     bool mat_used[TLSPH_MAX_MATERIALS]{};
     int ucur = 0;   // u[ucur] = u^n, u[ucur ^ 1] = predicted u^{n+1}
     int dcur = 0;   // D[dcur] = D^n
+    // mixed launch plan: pass-1 form, block, pass-2 form, block (the fastest on
+    // GB300 for the 1M-particle bar; the autotuner may choose another)
+    int32_t plan[4] = { 2, 256, 1, 256 };
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
     bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
     void *mixed = nullptr;      // mixed-precision state (mixed.cu)
@@ -144,6 +148,7 @@ cudaError_t mixed_material(const DevState &s, int mat_id, cudaStream_t st);
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st);
+int mixed_kernels_per_step(const tlsph_ctx &ctx);
 void mixed_release(tlsph_ctx &ctx);
 
 }  // namespace tlsph

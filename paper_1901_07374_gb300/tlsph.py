@@ -22,14 +22,18 @@ DEFAULT_PRECISION = "mixed"
 SMOKE_PRECISIONS = (("fp64", 1e-10), ("mixed", 1e-4))
 
 FIELD = dict(X=0, U=1, V=2, F=3, SIGMA=4, STRESS_DEV=5, EPSP=6, EPSP_RATE=7, DINIT=8, DAMAGE=9,
-             POROSITY=10, FAIL_STEP=11, FORCE=12, A=13, LINV=14, NBR_ROWPTR=15, NBR_COL=16)
+             POROSITY=10, FAIL_STEP=11, FORCE=12, A=13, LINV=14, NBR_ROWPTR=15, NBR_COL=16, STEP=17)
 # (numpy dtype, components per particle); None = special count
 _FIELD_SHAPE = dict(X=(np.float64, 3), U=(np.float64, 3), V=(np.float64, 3), F=(np.float64, 9),
                     SIGMA=(np.float64, 9), STRESS_DEV=(np.float64, 9), EPSP=(np.float64, 1),
                     EPSP_RATE=(np.float64, 1), DINIT=(np.float64, 1), DAMAGE=(np.float64, 1),
                     POROSITY=(np.float64, 1), FAIL_STEP=(np.int32, 1), FORCE=(np.float64, 3),
                     A=(np.float64, 9), LINV=(np.float64, 9), NBR_ROWPTR=(np.int64, None),
-                    NBR_COL=(np.int32, None))
+                    NBR_COL=(np.int32, None), STEP=(np.int64, None))
+
+# fields that together are the resumable state of a context
+CHECKPOINT_FIELDS = ("U", "V", "F", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY",
+                     "FAIL_STEP", "FORCE", "STEP")
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_SINGULAR_L", -3: "ERR_NUMERICS", -4: "ERR_NOMEM",
           -5: "ERR_CUDA", -6: "ERR_STATE"}
@@ -71,7 +75,8 @@ def make_material(d: dict) -> Material:
 
 EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph_step", "tlsph_sync",
            "tlsph_status_bits", "tlsph_info", "tlsph_get_state", "tlsph_set_state", "tlsph_last_error",
-           "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read")
+           "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
+           "tlsph_set_plan", "tlsph_get_plan")
 
 _lib = None
 _lock = threading.Lock()
@@ -121,6 +126,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_profile_enable.argtypes = [vp, i32]
         L.tlsph_profile_read.restype = i32
         L.tlsph_profile_read.argtypes = [vp, ctypes.POINTER(dbl), i32, ctypes.POINTER(i64)]
+        L.tlsph_set_plan.restype = i32
+        L.tlsph_set_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
+        L.tlsph_get_plan.restype = i32
+        L.tlsph_get_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
         L.tlsph_material_point_batch.restype = i32
         L.tlsph_material_point_batch.argtypes = [ctypes.POINTER(Material), dbl, i64, vp, vp, vp, vp]
         _lib = L
@@ -244,6 +253,16 @@ class Simulation:
         _check(load().tlsph_profile_read(self.ctx, ms, 2, ctypes.byref(n)), self.ctx)
         return ms[0], ms[1], n.value
 
+    def set_plan(self, plan) -> None:
+        """Mixed-path launch plan (pass-1 form, block, pass-2 form, block)."""
+        a = (ctypes.c_int32 * 4)(*[int(x) for x in plan])
+        _check(load().tlsph_set_plan(self.ctx, a, 4), self.ctx)
+
+    def get_plan(self):
+        a = (ctypes.c_int32 * 4)()
+        _check(load().tlsph_get_plan(self.ctx, a, 4), self.ctx)
+        return tuple(a)
+
     def info(self):
         N, nnz, steps = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(load().tlsph_info(self.ctx, ctypes.byref(N), ctypes.byref(nnz), ctypes.byref(steps)), self.ctx)
@@ -264,6 +283,8 @@ class Simulation:
             return dt, (self.N + 1,)
         if name == "NBR_COL":
             return dt, (self.nnz,)
+        if name == "STEP":
+            return dt, (1,)
         return dt, ((self.N,) if w == 1 else (self.N, w))
 
     def get(self, name: str) -> np.ndarray:
@@ -288,6 +309,22 @@ class Simulation:
         dt, shape = self._shape(name)
         a = np.ascontiguousarray(np.broadcast_to(np.asarray(value, dt), shape))
         _check(load().tlsph_set_state(self.ctx, FIELD[name], _ptr(a), a.nbytes, 0), self.ctx)
+
+    def checkpoint(self, device: bool = True) -> dict:
+        """Every resumable field (torch CUDA tensors if device, else numpy)."""
+        if device:
+            return {k: (self.get_device(k) if k != "STEP" else self.get("STEP")) for k in CHECKPOINT_FIELDS}
+        return {k: self.get(k) for k in CHECKPOINT_FIELDS}
+
+    def restore(self, ck: dict) -> None:
+        """Load a checkpoint taken by checkpoint() (same particle count)."""
+        L = load()
+        for k, v in ck.items():
+            if hasattr(v, "data_ptr"):
+                _check(L.tlsph_set_state(self.ctx, FIELD[k], ctypes.c_void_p(v.data_ptr()),
+                                         v.numel() * v.element_size(), 1), self.ctx)
+            else:
+                self.set(k, v)
 
     def state(self) -> dict:
         names = ("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY",

@@ -9,7 +9,7 @@ from paper_1901_07374_gb300 import tlsph
 
 pytestmark = pytest.mark.gpu
 
-WRITABLE = ("U", "V", "F", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY", "FAIL_STEP", "FORCE")
+WRITABLE = tlsph.CHECKPOINT_FIELDS
 
 
 def test_resume_is_bitwise():
@@ -96,3 +96,14 @@ def test_nonfinite_input_sets_status_bits():
     assert e.value.code == -3
     assert g.status_bits() != 0
     assert g.get("U").shape == (w.specimen.N, 3)
+
+
+def test_step_counter_is_part_of_the_checkpoint():
+    w = S.tensile_bar_cl(nx=5, ny=5, nz=8)
+    g = tlsph.Simulation.from_workload(w)
+    g.step(7)
+    assert g.get("STEP")[0] == 7 == g.steps
+    g.set("STEP", np.array([41], np.int64))
+    assert g.steps == 41
+    g.step(2)
+    assert g.get("STEP")[0] == 43

@@ -62,7 +62,7 @@ def test_mixed_failure_variant_runs_and_fails_close_to_fp64():
 
 def test_mixed_resume_is_bitwise():
     w = S.failure_variant(S.tensile_bar_cl(nx=6, ny=6, nz=16))
-    names = ("U", "V", "F", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY", "FAIL_STEP", "FORCE")
+    names = tlsph.CHECKPOINT_FIELDS
     a = tlsph.Simulation.from_workload(w, precision="mixed")
     a.step(120)
     ck = {k: a.get(k) for k in names}
@@ -74,3 +74,55 @@ def test_mixed_resume_is_bitwise():
     b.step(80)
     for k, v in b.state().items():
         assert np.array_equal(v, ref[k]), k
+
+
+PLANS = [(0, 128, 0, 128), (1, 64, 1, 64), (2, 256, 1, 256), (3, 128, 0, 128), (1, 128, 1, 256)]
+
+
+def test_every_launch_plan_computes_the_same_step():
+    """The launch plans only regroup the FP32 sums: each stays within the mixed
+    tolerance of the oracle and within FP32 rounding of the others."""
+    w = S.failure_variant(S.tensile_bar_cl(), v_grip=10.0, scale=0.05)
+    o = oracle.Simulation.from_workload(w)
+    o.step(30)
+    ref = o.state()
+    states = []
+    for plan in PLANS:
+        g = tlsph.Simulation.from_workload(w, precision="mixed")
+        g.set_plan(plan)
+        assert g.get_plan() == plan
+        g.step(30)
+        st = g.state()
+        compare_state(st, ref, w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
+        states.append(st)
+    for st in states[1:]:
+        for k in ("U", "V", "F", "SIGMA"):
+            a, b = st[k], states[0][k]
+            assert np.max(np.abs(a - b)) <= 1e-5 * max(np.max(np.abs(b)), 1e-30), k
+
+
+def test_autotune_restores_the_state_bitwise(tmp_path, monkeypatch):
+    from paper_1901_07374_gb300 import autotune
+    monkeypatch.setenv("TLSPH_PLAN_CACHE", str(tmp_path / "plans.json"))
+    w = S.failure_variant(S.tensile_bar_cl(nx=8, ny=8, nz=24))
+    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    a.step(40)
+    before = a.checkpoint(device=False)
+    rec = []
+    plan = autotune.tune(a, steps=2, warmup=1, record=rec)
+    assert len(rec) == len(autotune.PASS1) + len(autotune.PASS2)
+    after = a.checkpoint(device=False)
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    assert a.get_plan() == tuple(plan)
+    # the tuned run continues exactly like an untuned one with the same plan
+    b = tlsph.Simulation.from_workload(w, precision="mixed")
+    b.step(40)
+    b.set_plan(plan)
+    a.step(20)
+    b.step(20)
+    for k, v in a.state().items():
+        assert np.array_equal(v, b.get(k)), k
+    # a second call is served from the cache without stepping
+    steps = a.steps
+    assert autotune.tune(a) == tuple(plan) and a.steps == steps
