@@ -76,8 +76,17 @@ typedef struct {
     double dt;         /* time step [s], fixed for the run */
     double hg_alpha;   /* hourglass-control coefficient (0 disables it) */
     int32_t precision; /* TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED */
-    int32_t flags;     /* reserved, must be 0 */
+    int32_t flags;     /* 0 or TLSPH_FLAG_SPATIAL_ORDER */
 } tlsph_config;
+
+/* Store particles in a spatially compact internal order (cells of the
+ * neighbour grid grouped into 4x4x4-cell bricks, caller index inside a
+ * cell).  Every field crossing the ABI stays in the caller's order.  Off by
+ * default: for particles generated lattice-row by lattice-row the caller's
+ * order is faster, because the k-th neighbours of consecutive rows are then
+ * consecutive particles and a warp's gathers coalesce; the brick order helps
+ * inputs in arbitrary order. */
+#define TLSPH_FLAG_SPATIAL_ORDER 1
 
 /* damage models */
 #define TLSPH_DAMAGE_NONE 0

@@ -26,9 +26,10 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 struct Layout {
     size_t X, vol, mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
-    size_t xh, xl, s0, linv32, r1, r2, fsum;
+    size_t xo, s0, linv32, r1, r2, fsum, ell_off;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
-    size_t overlay_end;
+    size_t perm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order + staged caller-order inputs
+    size_t overlay_end, ell;
     size_t total;
     int64_t max_cells;
     size_t scan_elems;
@@ -43,6 +44,14 @@ struct Carver {
         return o;
     }
 };
+
+// sliced-ELL capacity carved from a caller arena: the pairs plus half again
+// for slice padding and one row of padding per slice; when a specimen needs
+// more, the context keeps to the warp-per-row plans
+int64_t ell_capacity(int64_t N, int64_t nnz_cap)
+{
+    return std::max<int64_t>(nnz_cap + nnz_cap / 2 + 128 * ((N + 31) / 32), 32);
+}
 
 Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
 {
@@ -71,11 +80,12 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.force = c.take(3 * n * d);
     L.fail = c.take(n * sizeof(int32_t));
     L.status = c.take(sizeof(uint32_t));
+    L.perm = c.take(n * sizeof(int32_t));
     L.mats = c.take(TLSPH_MAX_MATERIALS * sizeof(DevMat));
     if (mixed) {
-        L.xh = c.take(n * 16);
-        L.xl = c.take(n * 16);
+        L.xo = c.take(n * 16);
         L.s0 = c.take(n * 16);
+        L.ell_off = c.take(((n + 31) / 32 + 1) * sizeof(int64_t));
         L.linv32 = c.take(9 * n * sizeof(float));
         L.r1 = c.take(n * 16);
         L.r2 = c.take(6 * n * 16);
@@ -92,6 +102,13 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.scan_elems = scan_tmp_elems(std::max<int64_t>(L.max_cells + 1, N + 1));
     Carver s;
     s.off = ov;
+    // caller-order inputs staged for the reordering gather, then the scratch
+    L.stX = s.take(3 * n * d);
+    L.stvol = s.take(n * d);
+    L.stmat = s.take(n * sizeof(int32_t));
+    L.stbcm = s.take(n);
+    L.stbcv = s.take(3 * n * d);
+    L.stf0 = s.take(n * d);
     L.cell_start = s.take((size_t)(L.max_cells + 1) * sizeof(int64_t));
     L.cell_cursor = s.take((size_t)L.max_cells * sizeof(int64_t));
     L.cell_items = s.take(n * sizeof(int32_t));
@@ -99,6 +116,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     c.off = std::max(state_end, s.off);
     L.overlay_end = c.off;
     L.col = c.take((size_t)std::max<int64_t>(nnz_cap, 1) * sizeof(int32_t));
+    if (mixed) L.ell = c.take((size_t)ell_capacity(N, nnz_cap) * sizeof(int32_t));
     L.total = c.off;
     return L;
 }
@@ -130,7 +148,7 @@ bool valid_config(const tlsph_config *c, std::string &why)
         why = "precision must be TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED";
         return false;
     }
-    if (c->flags != 0) { why = "flags must be 0"; return false; }
+    if ((c->flags & ~TLSPH_FLAG_SPATIAL_ORDER) != 0) { why = "unknown flags"; return false; }
     return true;
 }
 
@@ -138,16 +156,18 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
 {
     DevState &s = ctx->s;
     if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
-        s.xh = at<float4>(base, L.xh);
-        s.xl = at<float4>(base, L.xl);
+        s.xo = at<float4>(base, L.xo);
         s.s0 = at<float4>(base, L.s0);
+        s.ell_off = at<int64_t>(base, L.ell_off);
         s.linv32 = at<float>(base, L.linv32);
         s.r1 = at<float4>(base, L.r1);
         s.r2 = at<float4>(base, L.r2);
         s.fsum = at<float>(base, L.fsum);
     } else {
         s.fsum = nullptr;
-        s.xh = s.xl = s.s0 = s.r1 = s.r2 = nullptr;
+        s.xo = s.s0 = s.r1 = s.r2 = nullptr;
+        s.ell_off = nullptr;
+        s.colE = nullptr;
         s.linv32 = nullptr;
     }
     s.N = ctx->N;
@@ -307,6 +327,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     auto bail = [&](int code, const std::string &msg) {
         g_create_error = msg;
         if (ctx->owns_mem && ctx->mem) cudaFree(ctx->mem);
+        if (ctx->ell_mem) cudaFree(ctx->ell_mem);
         delete ctx;
         return code;
     };
@@ -341,12 +362,16 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     for (size_t i = 0; i < n; ++i) ctx->mat_used[mat_h[i]] = true;
     cudaError_t e = cudaSuccess;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e)); } } while (0)
-    CK(cudaMemcpyAsync((void *)s.X, X, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync((void *)s.vol, vol, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync((void *)s.mat, mat_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync((void *)s.bcm, bcm_h.data(), n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync((void *)s.bcv, bcv_h.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s.por, f0_h.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    double *stX = at<double>(base, L.stX), *stvol = at<double>(base, L.stvol), *stbcv = at<double>(base, L.stbcv);
+    double *stf0 = at<double>(base, L.stf0);
+    int32_t *stmat = at<int32_t>(base, L.stmat);
+    uint8_t *stbcm = at<uint8_t>(base, L.stbcm);
+    CK(cudaMemcpyAsync(stX, X, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(stvol, vol, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(stmat, mat_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(stbcm, bcm_h.data(), n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(stbcv, bcv_h.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(stf0, f0_h.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
     CK(cudaMemsetAsync((void *)s.mass, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync((void *)s.sqrtE, 0, n * sizeof(double), st));
@@ -356,6 +381,17 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     if (grid.ncells > L.max_cells) return bail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
     Scratch sc{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
                 at<int64_t>(base, L.scan_tmp), L.scan_elems };
+    // ---- internal order (brick-major cells, caller index inside a cell) and the gather into it
+    ctx->reordered = (cfg->flags & TLSPH_FLAG_SPATIAL_ORDER) != 0;
+    ctx->perm_dev = at<int32_t>(base, L.perm);
+    CK(build_order(stX, N, grid, sc, !ctx->reordered, ctx->perm_dev, st));
+    CK(launch_gather_inputs(ctx->perm_dev, N, stX, stvol, stmat, stbcm, stbcv, stf0, s, st));
+    ctx->perm.resize(n);
+    ctx->inv.resize(n);
+    CK(cudaMemcpyAsync(ctx->perm.data(), ctx->perm_dev, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < n; ++k) ctx->inv[ctx->perm[k]] = (int32_t)k;
+
     const double rc2 = cfg->rc * cfg->rc;
     int64_t *row_ptr = const_cast<int64_t *>(s.row_ptr);
     CK(build_neighbors_count(s, grid, sc, rc2, row_ptr, st));
@@ -380,6 +416,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         ctx->mem = nb;
         ctx->mem_bytes = need;
         bind_state(ctx, base, L);
+        ctx->perm_dev = at<int32_t>(base, L.perm);
         sc = Scratch{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
                       at<int64_t>(base, L.scan_tmp), L.scan_elems };
         row_ptr = const_cast<int64_t *>(s.row_ptr);
@@ -404,7 +441,50 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         for (size_t i = 0; i < n; ++i)
             for (int k = 0; k < 3; ++k) vr[k] += bcv_h[3 * i + k];
         for (int k = 0; k < 3; ++k) s.vref[k] = vr[k] / (double)n;
-        CK(mixed_init_static(s, s.force, st));
+        // packed cell coordinates: b_k bits hold c + 2 <= nc + 1
+        CellPack pk{};
+        int bits[3];
+        for (int k = 0; k < 3; ++k) {
+            pk.lo[k] = grid.xmin[k];
+            pk.nc[k] = grid.nc[k];
+            bits[k] = 1;
+            while ((1 << bits[k]) < grid.nc[k] + 2) ++bits[k];
+        }
+        if (bits[0] + bits[1] + bits[2] > 31) return bail(TLSPH_ERR_ARG, "specimen spans too many neighbour cells for the mixed path");
+        pk.cs = (float)grid.cs;
+        pk.inv_cs = 1.0 / (double)pk.cs;
+        pk.sh1 = bits[0];
+        pk.sh2 = bits[0] + bits[1];
+        pk.m0 = (1 << bits[0]) - 1;
+        pk.m1 = (1 << bits[1]) - 1;
+        pk.m2 = (1 << bits[2]) - 1;
+        s.pack = pk;
+        CK(mixed_init_static(s, s.force, pk, st));
+        // sliced-ELL columns for the thread-per-row plans
+        const int64_t ng = (N + 31) / 32;
+        int64_t *ell_off = const_cast<int64_t *>(s.ell_off);
+        CK(cudaMemsetAsync(ell_off + ng, 0, sizeof(int64_t), st));
+        CK(mixed_ell_widths(s, ell_off, st));
+        CK(scan_exclusive_i64(ell_off, ng + 1, sc.scan_tmp, st));
+        int64_t ell_n = 0;
+        CK(cudaMemcpyAsync(&ell_n, ell_off + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int32_t *colE = nullptr;
+        if (arena) {
+            if (ell_n <= ell_capacity(N, nnz_cap)) colE = at<int32_t>(base, L.ell);
+        } else {
+            e = cudaMalloc(&ctx->ell_mem, (size_t)std::max<int64_t>(ell_n, 1) * sizeof(int32_t));
+            if (e == cudaSuccess) colE = static_cast<int32_t *>(ctx->ell_mem);
+            else cudaGetLastError();
+        }
+        if (colE) {
+            CK(mixed_ell_fill(s, ell_off, colE, st));
+            s.colE = colE;
+            ctx->ell_ok = true;
+        } else {
+            ctx->ell_ok = false;   // warp-per-row plans only
+            ctx->plan[0] = 3; ctx->plan[1] = 256; ctx->plan[2] = 0; ctx->plan[3] = 128;
+        }
     }
 
     // ---- initial state (overwrites the scratch overlay)
@@ -438,7 +518,6 @@ int tlsph_set_material(tlsph_ctx *ctx, int mat_id, const tlsph_material *m)
                                     cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_material copy");
     e = launch_material_fields(ctx->s, mat_id, ctx->dcur, ctx->steps == 0, ctx->stream);
-    if (e == cudaSuccess && ctx->cfg.precision == TLSPH_PRECISION_MIXED) e = mixed_material(ctx->s, mat_id, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_material fields");
     // the copy source lives in ctx; wait so a later overwrite cannot race it
     e = cudaStreamSynchronize(ctx->stream);
@@ -520,6 +599,35 @@ int tlsph_info(const tlsph_ctx *ctx, int64_t *N, int64_t *nnz, int64_t *steps)
     return TLSPH_OK;
 }
 
+// neighbour CSR in caller indices (rows of caller particles, columns mapped
+// back and sorted ascending) from the internal CSR
+static cudaError_t caller_csr(tlsph_ctx *ctx, std::vector<int64_t> &rp, std::vector<int32_t> &col)
+{
+    const int64_t N = ctx->N, nnz = ctx->nnz;
+    std::vector<int64_t> rpi(N + 1);
+    std::vector<int32_t> ci(nnz);
+    cudaError_t e = cudaMemcpyAsync(rpi.data(), ctx->s.row_ptr, (N + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(ci.data(), ctx->s.col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return e;
+    rp.assign(N + 1, 0);
+    col.resize(nnz);
+    for (int64_t i = 0; i < N; ++i) {
+        const int32_t k = ctx->inv[i];
+        rp[i + 1] = rp[i] + (rpi[k + 1] - rpi[k]);
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        const int32_t k = ctx->inv[i];
+        int32_t *o = col.data() + rp[i];
+        int64_t m = 0;
+        for (int64_t p = rpi[k]; p < rpi[k + 1]; ++p) o[m++] = ctx->perm[ci[p]];
+        std::sort(o, o + m);
+    }
+    return cudaSuccess;
+}
+
 int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_on_device)
 {
     if (!ctx) return TLSPH_ERR_ARG;
@@ -539,26 +647,49 @@ int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_
         e = mixed_sync_to_fp64(*ctx, field, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "mixed export");
     }
-    if (f.sym) {
-        const int64_t N = ctx->N;
-        if (dst_on_device) {
-            e = launch_export_sym(static_cast<const double *>(f.ptr), static_cast<double *>(dst), N, st);
+    const int64_t N = ctx->N;
+    if (field == TLSPH_FIELD_NBR_ROWPTR || field == TLSPH_FIELD_NBR_COL) {
+        if (!ctx->reordered) {
+            e = cudaMemcpyAsync(dst, f.ptr, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
         } else {
-            std::vector<double> tmp(6 * (size_t)N);
-            e = cudaMemcpyAsync(tmp.data(), f.ptr, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e == cudaSuccess) {
-                double *o = static_cast<double *>(dst);
-                for (int64_t i = 0; i < N; ++i) {
-                    const double *a = &tmp[6 * i];
-                    double *m = o + 9 * i;
+            std::vector<int64_t> rp;
+            std::vector<int32_t> col;
+            e = caller_csr(ctx, rp, col);
+            const void *src = field == TLSPH_FIELD_NBR_ROWPTR ? (const void *)rp.data() : (const void *)col.data();
+            if (e == cudaSuccess)
+                e = cudaMemcpy(dst, src, bytes, dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "get_state");
+        return TLSPH_OK;
+    }
+    // per-particle field: stored comps (6 for symmetric tensors) -> exchanged comps
+    const int comps = (int)(f.count / (size_t)N);
+    const int scomps = f.sym ? 6 : comps;
+    const size_t sbytes = (size_t)N * scomps * f.elem;
+    if (dst_on_device) {
+        if (f.sym || ctx->reordered)
+            e = launch_permute(f.ptr, dst, ctx->perm_dev, N, scomps, (int)f.elem, true, f.sym, st);
+        else
+            e = cudaMemcpyAsync(dst, f.ptr, bytes, cudaMemcpyDeviceToDevice, st);
+    } else {
+        std::vector<unsigned char> tmp(sbytes);
+        e = cudaMemcpyAsync(tmp.data(), f.ptr, sbytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            unsigned char *o = static_cast<unsigned char *>(dst);
+            for (int64_t k = 0; k < N; ++k) {
+                const int64_t i = ctx->perm[k];
+                if (f.sym) {
+                    const double *a = reinterpret_cast<const double *>(tmp.data()) + 6 * k;
+                    double *m = reinterpret_cast<double *>(o) + 9 * i;
                     m[0] = a[0]; m[4] = a[1]; m[8] = a[2];
                     m[1] = m[3] = a[3]; m[5] = m[7] = a[4]; m[2] = m[6] = a[5];
+                } else {
+                    memcpy(o + (size_t)i * comps * f.elem, tmp.data() + (size_t)k * comps * f.elem, comps * f.elem);
                 }
             }
         }
-    } else {
-        e = cudaMemcpyAsync(dst, f.ptr, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "get_state");
@@ -589,28 +720,33 @@ int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, in
         e = mixed_sync_to_fp64(*ctx, -1, st);   // bring every FP64 field up to date first
         if (e != cudaSuccess) return cuda_fail(ctx, e, "mixed export");
     }
-    if (f.sym) {
-        const int64_t N = ctx->N;
-        if (src_on_device) {
-            e = launch_import_sym(static_cast<const double *>(src), static_cast<double *>(f.ptr), N, st);
-        } else {
-            std::vector<double> tmp(6 * (size_t)N);
-            const double *a = static_cast<const double *>(src);
-            for (int64_t i = 0; i < N; ++i) {
-                const double *m = a + 9 * i;
-                double *o = &tmp[6 * i];
+    const int64_t N = ctx->N;
+    const int comps = (int)(f.count / (size_t)N);
+    const int scomps = f.sym ? 6 : comps;
+    if (src_on_device) {
+        if (f.sym || ctx->reordered)
+            e = launch_permute(src, f.ptr, ctx->perm_dev, N, scomps, (int)f.elem, false, f.sym, st);
+        else
+            e = cudaMemcpyAsync(f.ptr, src, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    } else {
+        std::vector<unsigned char> tmp((size_t)N * scomps * f.elem);
+        const unsigned char *a = static_cast<const unsigned char *>(src);
+        for (int64_t k = 0; k < N; ++k) {
+            const int64_t i = ctx->perm[k];
+            if (f.sym) {
+                const double *m = reinterpret_cast<const double *>(a) + 9 * i;
+                double *o = reinterpret_cast<double *>(tmp.data()) + 6 * k;
                 o[0] = m[0]; o[1] = m[4]; o[2] = m[8];
                 o[3] = 0.5 * (m[1] + m[3]); o[4] = 0.5 * (m[5] + m[7]); o[5] = 0.5 * (m[2] + m[6]);
+            } else {
+                memcpy(tmp.data() + (size_t)k * comps * f.elem, a + (size_t)i * comps * f.elem, comps * f.elem);
             }
-            e = cudaMemcpyAsync(f.ptr, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         }
-    } else {
-        e = cudaMemcpyAsync(f.ptr, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(f.ptr, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state");
-    if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) ctx->mixed_dirty = true;
     ctx->need_predict = true;
     return TLSPH_OK;
 }
@@ -625,6 +761,7 @@ int tlsph_destroy(tlsph_ctx *ctx)
     if (!ctx) return TLSPH_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
     if (ctx->owns_mem && ctx->mem) cudaFree(ctx->mem);
+    if (ctx->ell_mem) cudaFree(ctx->ell_mem);
     for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
     mixed_release(*ctx);
     delete ctx;
@@ -639,6 +776,10 @@ int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n)
     const bool ok = v1 >= 0 && v1 <= 3 && v2 >= 0 && v2 <= 1 && b1 >= 32 && b1 <= 256 && b1 % 32 == 0 &&
                     b2 >= 32 && b2 <= 256 && b2 % 32 == 0;
     if (!ok) { ctx->err = "plan out of range"; return TLSPH_ERR_ARG; }
+    if (!ctx->ell_ok && (v1 == 1 || v1 == 2 || v2 == 1)) {
+        ctx->err = "this context has no sliced-ELL columns: only the warp-per-row plans (0, 3 / 0) apply";
+        return TLSPH_ERR_ARG;
+    }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_plan sync");
     for (int k = 0; k < 4; ++k) ctx->plan[k] = plan[k];

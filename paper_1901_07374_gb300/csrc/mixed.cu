@@ -8,17 +8,31 @@
 // threshold decisions), the nodal force handed to the integrator and the
 // velocity-Verlet update.
 //
-// What is FP32: every per-pair term of both passes, the warp sums, the polar
-// decomposition, the rotations and P = J sigma F^{-T}, A = P L^{-T}.
+// What is FP32: every per-pair term of both passes, the sums over j, the
+// polar decomposition, the rotations and P = J sigma F^{-T}, A = P L^{-T}.
 //
 // The pair terms are arranged so the FP32 sums carry no large cancellation:
-//  - positions travel as hi + lo float pairs, X_ij = (hi_j - hi_i) + (lo_j - lo_i);
+//  - a position travels as its offset from the origin of its neighbour-grid
+//    cell plus the cell's integer coordinates, so X_ij = dc * cs + (o_j - o_i)
+//    with dc in {-1, 0, 1} per axis and offsets no longer than a cell;
 //  - velocities are mirrored relative to a bulk reference velocity;
 //  - the hourglass error vector uses F - I and u, e = (F_i - I) X_ij - u_ij;
 //  - the stress term is written with differences (Sec. 3.1 force, rearranged):
 //      f_i = V_i (1-D_i) sum_j V_j (A_j - A_i) grad W_ij
 //          + V_i A_i [ (2 - D_i) S0_i - sum_j V_j D_j grad W_ij ],
 //    with the static S0_i = sum_j V_j grad W_ij computed once in FP64.
+//
+// Data layout (float4 arrays indexed by particle, "SoA of float4", so a warp
+// gathering consecutive particles reads consecutive 16-byte words):
+//   xo   {offset to cell origin, packed cell coordinates}
+//   r1   {v^{n+1/2} - v_ref, V (1 - D)}                       pass-1 gather record
+//   r2k  k = 0..5 (at r2 + k N):                               pass-2 gather record
+//        {A00 A01 A02 A10} {A11 A12 A20 A21} {A22, V(1-D), V, u_x}
+//        {u_y, u_z, G00, G01} {G02 G10 G11 G12} {G20, G21, G22, sqrt(E) V (1-D)}
+//        with G = F - I.
+// Thread-per-row kernels read their neighbour indices from a sliced-ELL copy
+// of the CSR (slice = one warp of 32 consecutive rows, column-major inside
+// the slice), so the 32 lanes' k-th neighbour indices are one 128-byte line.
 #include <math.h>
 
 #include "tlsph_device.cuh"
@@ -30,10 +44,12 @@ static constexpr int MIX_THREADS = 128;
 
 struct MixConst {
     double dt, half_dt;
-    float dtf, inv_h, dw_norm, w_norm, hg_coef;
+    float inv_h, dw_norm, w_norm, hg_coef, cs;
     double vref0, vref1, vref2;
+    int64_t N;
     int64_t step_index;
     int ucur, dcur;
+    int sh1, sh2, m0, m1, m2, bias;   // packed cell coordinates
 };
 
 static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
@@ -42,17 +58,24 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     const tlsph_config &cfg = ctx.cfg;
     c.dt = cfg.dt;
     c.half_dt = 0.5 * cfg.dt;
-    c.dtf = (float)cfg.dt;
     c.inv_h = (float)(1.0 / cfg.h);
     c.dw_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
     c.w_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h));
     c.hg_coef = (float)(-0.5 * cfg.hg_alpha);
+    c.cs = ctx.s.pack.cs;
     c.vref0 = ctx.s.vref[0];
     c.vref1 = ctx.s.vref[1];
     c.vref2 = ctx.s.vref[2];
+    c.N = ctx.N;
     c.step_index = step_index;
     c.ucur = ctx.ucur;
     c.dcur = ctx.dcur;
+    c.sh1 = ctx.s.pack.sh1;
+    c.sh2 = ctx.s.pack.sh2;
+    c.m0 = ctx.s.pack.m0;
+    c.m1 = ctx.s.pack.m1;
+    c.m2 = ctx.s.pack.m2;
+    c.bias = 1 | (1 << c.sh1) | (1 << c.sh2);
     return c;
 }
 
@@ -87,7 +110,7 @@ __device__ __forceinline__ void cof3f(const float *m, float *c)
 }
 
 // FP32 rotation of the polar decomposition, same iteration as the FP64
-// path (determinant-scaled Newton), stop at a step below 1e-5, cap 30.
+// path (determinant-scaled Newton), stop after a step below 1e-5, cap 30.
 __device__ __forceinline__ bool polar_rotation_f(const float *F, float *R)
 {
 #pragma unroll
@@ -133,32 +156,40 @@ __device__ __forceinline__ void sym_rotate_f(const float *Q, const float *s, flo
 #undef QT
 }
 
-__device__ __forceinline__ float3 xdiff(const float4 hi_j, const float4 lo_j, const float4 hi_i, const float4 lo_i)
+// X_j - X_i from cell offsets; t_i = bias - packed_i (per row).  Each biased
+// field of packed_j + t_i is c_j - c_i + 1 in {0, 1, 2}, so no field borrows.
+__device__ __forceinline__ float3 xdiff(const MixConst &c, const float4 oj, const float4 oi, int t_i)
 {
-    return make_float3((hi_j.x - hi_i.x) + (lo_j.x - lo_i.x), (hi_j.y - hi_i.y) + (lo_j.y - lo_i.y),
-                       (hi_j.z - hi_i.z) + (lo_j.z - lo_i.z));
+    const int D = __float_as_int(oj.w) + t_i;
+    const float dx = (float)(D & c.m0) - 1.0f;
+    const float dy = (float)((D >> c.sh1) & c.m1) - 1.0f;
+    const float dz = (float)((D >> c.sh2) & c.m2) - 1.0f;
+    return make_float3(fmaf(dx, c.cs, oj.x - oi.x), fmaf(dy, c.cs, oj.y - oi.y), fmaf(dz, c.cs, oj.z - oi.z));
 }
 
-// ------------------------------------------------------------------ pass 1
-// per-particle part of pass 1: F^{n+1}, J, kinematics, constitutive and
-// damage update, stress, A and the pass-2 record of particle i from its
-// velocity-gradient sums keep[9]
+__device__ __forceinline__ int row_bias(const MixConst &c, const float4 oi) { return c.bias - __float_as_int(oi.w); }
+
+// ------------------------------------------------------------------ pass 1, per particle
+// F^{n+1}, J, kinematics, constitutive and damage update, stress, A and the
+// pass-2 record of particle i from its velocity-gradient sums keep[9]
 __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
     const double *__restrict__ Dn = s.D[c.dcur];
     double *__restrict__ Dnext = s.D[c.dcur ^ 1];
-    float4 *__restrict__ r2o = s.r2 + 6 * i;
+    float4 *__restrict__ r2 = s.r2;
+    const int64_t N = c.N;
     const int fail = s.fail[i];
     const double *un = s.u[c.ucur ^ 1];   // u^{n+1}, mirrored for pass 2's hourglass term
+    const double Vi = s.vol[i];
     if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
         Dnext[i] = Dn[i];
         const double *F = s.F + 9 * i;
-        r2o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2o[2] = make_float4(0.f, 0.f, (float)un[3 * i], (float)un[3 * i + 1]);
-        r2o[3] = make_float4((float)un[3 * i + 2], (float)(F[0] - 1.0), (float)F[1], (float)F[2]);
-        r2o[4] = make_float4((float)F[3], (float)(F[4] - 1.0), (float)F[5], (float)F[6]);
-        r2o[5] = make_float4((float)F[7], (float)(F[8] - 1.0), 0.f, 0.f);
+        r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2[N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2[2 * N + i] = make_float4(0.f, 0.f, (float)Vi, (float)un[3 * i]);
+        r2[3 * N + i] = make_float4((float)un[3 * i + 1], (float)un[3 * i + 2], (float)(F[0] - 1.0), (float)F[1]);
+        r2[4 * N + i] = make_float4((float)F[2], (float)F[3], (float)(F[4] - 1.0), (float)F[5]);
+        r2[5 * N + i] = make_float4((float)F[6], (float)F[7], (float)(F[8] - 1.0), 0.f);
         return;
     }
     float Li[9];
@@ -247,15 +278,74 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
         for (int k = 0; k < 9; ++k) fin &= isfinite(A[k]);
         if (!fin) st |= TLSPH_ST_NONFINITE;
     }
-    // pass-2 record: A (9), 1 - D, u (3), F - I (9)
-    const float omd = (float)(1.0 - mp.D);
-    r2o[0] = make_float4(A[0], A[1], A[2], A[3]);
-    r2o[1] = make_float4(A[4], A[5], A[6], A[7]);
-    r2o[2] = make_float4(A[8], omd, (float)un[3 * i], (float)un[3 * i + 1]);
-    r2o[3] = make_float4((float)un[3 * i + 2], (float)(Fn[0] - 1.0), (float)Fn[1], (float)Fn[2]);
-    r2o[4] = make_float4((float)Fn[3], (float)(Fn[4] - 1.0), (float)Fn[5], (float)Fn[6]);
-    r2o[5] = make_float4((float)Fn[7], (float)(Fn[8] - 1.0), 0.f, 0.f);
+    const double omd = 1.0 - mp.D;
+    r2[i] = make_float4(A[0], A[1], A[2], A[3]);
+    r2[N + i] = make_float4(A[4], A[5], A[6], A[7]);
+    r2[2 * N + i] = make_float4(A[8], (float)(Vi * omd), (float)Vi, (float)un[3 * i]);
+    r2[3 * N + i] = make_float4((float)un[3 * i + 1], (float)un[3 * i + 2], (float)(Fn[0] - 1.0), (float)Fn[1]);
+    r2[4 * N + i] = make_float4((float)Fn[2], (float)Fn[3], (float)(Fn[4] - 1.0), (float)Fn[5]);
+    r2[5 * N + i] = make_float4((float)Fn[6], (float)Fn[7], (float)(Fn[8] - 1.0), (float)(s.sqrtE[i] * Vi * omd));
     if (st) atomicOr(s.status, st);
+}
+
+// ------------------------------------------------------------------ pass 1 pair terms
+__device__ __forceinline__ void pair1(const MixConst &c, const float4 oi, int ti, const float4 vi, const float4 oj,
+                                      const float4 vj, float wmask, float *m)
+{
+    const float3 d = xdiff(c, oj, oi, ti);
+    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    const float rinv = rsqrtf(r2);
+    const float cw = wmask * vj.w * spline_dw(r2 * rinv * c.inv_h) * rinv;   // V_j (1 - D_j) W'/r
+    const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
+    m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
+    m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
+    m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
+}
+
+// thread per row over the sliced-ELL columns, two pairs in flight
+__device__ __forceinline__ void gather1_row(const DevState &s, const MixConst &c, int64_t i, float *m)
+{
+    const float4 oi = s.xo[i], vi = s.r1[i];
+    const int ti = row_bias(c, oi);
+    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
+    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = 0.0f;
+    for (int k = 0; k < n; k += 2) {
+        const bool two = k + 1 < n;
+        const int j0 = cp[32 * k];
+        const int j1 = two ? cp[32 * (k + 1)] : j0;
+        const float4 o0 = s.xo[j0], v0 = s.r1[j0];
+        const float4 o1 = s.xo[j1], v1 = s.r1[j1];
+        pair1(c, oi, ti, vi, o0, v0, 1.0f, m);
+        pair1(c, oi, ti, vi, o1, v1, two ? 1.0f : 0.0f, m);
+    }
+}
+
+// warp per 32 consecutive rows over the CSR (lanes stride a row)
+__device__ __forceinline__ void gather1_w32(const DevState &s, const MixConst &c, int64_t row0, int nrows, int lane,
+                                            float *keep)
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
+    for (int r = 0; r < nrows; ++r) {
+        const int64_t i = row0 + r;
+        const float4 oi = s.xo[i], vi = s.r1[i];
+        const int ti = row_bias(c, oi);
+        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+        float m[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) m[k] = 0.0f;
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
+            const int j = s.col[p];
+            pair1(c, oi, ti, vi, s.xo[j], s.r1[j], 1.0f, m);
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float t = warp_allsum(m[k]);
+            keep[k] = (lane == r) ? t : keep[k];
+        }
+    }
 }
 
 __global__ void __launch_bounds__(MIX_THREADS) k_pass1_mixed(DevState s, MixConst c)
@@ -264,54 +354,67 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass1_mixed(DevState s, MixCons
     const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
     if (row0 >= s.N) return;
     const int nrows = (int)min((int64_t)32, s.N - row0);
-    const float4 *__restrict__ xh = s.xh;
-    const float4 *__restrict__ xl = s.xl;
-    const float4 *__restrict__ r1 = s.r1;
     float keep[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
-
-    for (int r = 0; r < nrows; ++r) {
-        const int64_t i = row0 + r;
-        const float4 hi = xh[i], lo = xl[i], vi = r1[i];
-        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
-        float m[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) m[k] = 0.0f;
-        for (int64_t p = p0 + lane; p < p1; p += 32) {
-            const int j = s.col[p];
-            const float4 hj = xh[j], lj = xl[j], vj = r1[j];
-            const float3 d = xdiff(hj, lj, hi, lo);
-            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-            const float rinv = rsqrtf(r2);
-            const float q = r2 * rinv * c.inv_h;
-            const float cw = hj.w * vj.w * spline_dw(q) * rinv;   // V_j (1 - D_j) W'/r
-            const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
-            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
-            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
-            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float t = warp_allsum(m[k]);
-            keep[k] = (lane == r) ? t : keep[k];
-        }
-    }
+    gather1_w32(s, c, row0, nrows, lane, keep);
     if (lane >= nrows) return;
-
     epi1_mixed(s, c, row0 + lane, keep);
 }
 
+__global__ void __launch_bounds__(256) k_pass1_mixed_t(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+    gather1_row(s, c, i, m);
+    epi1_mixed(s, c, i, m);
+}
+
+// split form of pass 1: the gather kernel stores the 9 sums, a second kernel
+// runs the per-particle update (lighter registers in the gather)
+__global__ void __launch_bounds__(256) k_gather1_mixed_t(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+    gather1_row(s, c, i, m);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = m[k];
+}
+
+__global__ void __launch_bounds__(256) k_gather1_mixed_w32(DevState s, MixConst c)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (row0 >= s.N) return;
+    const int nrows = (int)min((int64_t)32, s.N - row0);
+    float keep[9];
+    gather1_w32(s, c, row0, nrows, lane, keep);
+    if (lane >= nrows) return;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.fsum[k * s.N + row0 + lane] = keep[k];
+}
+
+__global__ void __launch_bounds__(128) k_epi1_mixed(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = s.fsum[k * s.N + i];
+    epi1_mixed(s, c, i, m);
+}
+
 // ------------------------------------------------------------------ pass 2
-// per-particle part of pass 2: force (rearranged Sec. 3.1 form) and the
-// velocity-Verlet update in FP64 from the pair sums keep[9]
+// per-particle part: force (rearranged Sec. 3.1 form) and the velocity-Verlet
+// update in FP64 from the pair sums keep[9]
 template <bool HG>
 __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
+    const int64_t N = c.N;
     const double Vi = s.vol[i];
     const double Di = s.D[c.dcur ^ 1][i];
     const double omdi = 1.0 - Di;
-    const float4 a0 = s.r2[6 * i], a1 = s.r2[6 * i + 1], a2 = s.r2[6 * i + 2];
+    const float4 a0 = s.r2[i], a1 = s.r2[N + i], a2 = s.r2[2 * N + i];
     const float Ai[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
     const float4 s0 = s.s0[i];
     const float w2 = (float)(2.0 - Di);
@@ -354,8 +457,67 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         s.vh[3 * i + k] = v2[k];
         unext[3 * i + k] = un[3 * i + k] + c.dt * v2[k];
     }
-    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2), (float)omdi);
+    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2),
+                          (float)(Vi * omdi));
     if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
+}
+
+struct Row2 {   // row i's own pass-2 record
+    float4 o, a0, a1, a2, a3, a4, a5;
+    int t;
+};
+
+template <bool HG>
+__device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, int64_t i)
+{
+    const int64_t N = c.N;
+    Row2 w;
+    w.o = s.xo[i];
+    w.t = row_bias(c, w.o);
+    w.a0 = s.r2[i];
+    w.a1 = s.r2[N + i];
+    w.a2 = s.r2[2 * N + i];
+    w.a3 = w.a4 = w.a5 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (HG) {
+        w.a3 = s.r2[3 * N + i];
+        w.a4 = s.r2[4 * N + i];
+        w.a5 = s.r2[5 * N + i];
+    }
+    return w;
+}
+
+template <bool HG>
+__device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, const Row2 &w, int j, float wmask,
+                                      float *acc)
+{
+    const int64_t N = c.N;
+    const float4 oj = s.xo[j];
+    const float4 b0 = s.r2[j], b1 = s.r2[N + j], b2 = s.r2[2 * N + j];
+    const float3 d = xdiff(c, oj, w.o, w.t);
+    const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
+    const float rinv = rsqrtf(r2v);
+    const float q = r2v * rinv * c.inv_h;
+    const float g0 = wmask * spline_dw(q) * rinv;
+    const float g = b2.z * g0;                     // V_j W'/r
+    const float gd = (b2.z - b2.y) * g0;           // V_j D_j W'/r
+    acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
+    const float t0 = (b0.x - w.a0.x) * d.x + (b0.y - w.a0.y) * d.y + (b0.z - w.a0.z) * d.z;
+    const float t1 = (b0.w - w.a0.w) * d.x + (b1.x - w.a1.x) * d.y + (b1.y - w.a1.y) * d.z;
+    const float t2 = (b1.z - w.a1.z) * d.x + (b1.w - w.a1.w) * d.y + (b2.x - w.a2.x) * d.z;
+    acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
+    if (HG) {
+        const float4 b3 = s.r2[3 * N + j], b4 = s.r2[4 * N + j], b5 = s.r2[5 * N + j];
+        // u_ij, x_ij = X_ij + u_ij, e = ((F_i - I) + (F_j - I)) X_ij - 2 u_ij
+        const float ux = b2.w - w.a2.w, uy = b3.x - w.a3.x, uz = b3.y - w.a3.y;
+        const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
+        const float lxi = rsqrtf(xx * xx + xy * xy + xz * xz);
+        const float ex = (w.a3.z + b3.z) * d.x + (w.a3.w + b3.w) * d.y + (w.a4.x + b4.x) * d.z - 2.0f * ux;
+        const float ey = (w.a4.y + b4.y) * d.x + (w.a4.z + b4.z) * d.y + (w.a4.w + b4.w) * d.z - 2.0f * uy;
+        const float ez = (w.a5.x + b5.x) * d.x + (w.a5.y + b5.y) * d.y + (w.a5.z + b5.z) * d.z - 2.0f * uz;
+        const float delta = (ex * xx + ey * xy + ez * xz) * lxi;
+        const float ch = wmask * b5.w * spline_w(q) * rinv * rinv * delta * lxi;   // sqrt(E_j) V_j (1 - D_j) ...
+        acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
+    }
 }
 
 template <bool HG>
@@ -365,55 +527,17 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixCons
     const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
     if (row0 >= s.N) return;
     const int nrows = (int)min((int64_t)32, s.N - row0);
-    const float4 *__restrict__ xh = s.xh;
-    const float4 *__restrict__ xl = s.xl;
-    const float4 *__restrict__ r2 = s.r2;
     float keep[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
-
     for (int r = 0; r < nrows; ++r) {
         const int64_t i = row0 + r;
-        const float4 hi = xh[i], lo = xl[i];
-        const float4 a0 = r2[6 * i], a1 = r2[6 * i + 1], a2 = r2[6 * i + 2];
-        float4 a3, a4, a5;
-        if (HG) { a3 = r2[6 * i + 3]; a4 = r2[6 * i + 4]; a5 = r2[6 * i + 5]; }
+        const Row2 w = load_row2<HG>(s, c, i);
         const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
         float acc[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-        for (int64_t p = p0 + lane; p < p1; p += 32) {
-            const int j = s.col[p];
-            const float4 hj = xh[j], lj = xl[j];
-            const float4 b0 = r2[6 * j], b1 = r2[6 * j + 1], b2 = r2[6 * j + 2];
-            const float3 d = xdiff(hj, lj, hi, lo);
-            const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
-            const float rinv = rsqrtf(r2v);
-            const float q = r2v * rinv * c.inv_h;
-            const float g = hj.w * spline_dw(q) * rinv;           // V_j W'/r
-            // sum_j V_j D_j grad W
-            const float gd = g * (1.0f - b2.y);
-            acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
-            // sum_j V_j (A_j - A_i) grad W
-            const float t0 = (b0.x - a0.x) * d.x + (b0.y - a0.y) * d.y + (b0.z - a0.z) * d.z;
-            const float t1 = (b0.w - a0.w) * d.x + (b1.x - a1.x) * d.y + (b1.y - a1.y) * d.z;
-            const float t2 = (b1.z - a1.z) * d.x + (b1.w - a1.w) * d.y + (b2.x - a2.x) * d.z;
-            acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
-            if (HG) {
-                const float4 b3 = r2[6 * j + 3], b4 = r2[6 * j + 4], b5 = r2[6 * j + 5];
-                // u_ij, x_ij = X_ij + u_ij, e = ((F_i - I) + (F_j - I)) X_ij - 2 u_ij
-                const float ux = b2.z - a2.z, uy = b2.w - a2.w, uz = b3.x - a3.x;
-                const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
-                const float lx2 = xx * xx + xy * xy + xz * xz;
-                const float lxi = rsqrtf(lx2);
-                const float ex = (a3.y + b3.y) * d.x + (a3.z + b3.z) * d.y + (a3.w + b3.w) * d.z - 2.0f * ux;
-                const float ey = (a4.x + b4.x) * d.x + (a4.y + b4.y) * d.y + (a4.z + b4.z) * d.z - 2.0f * uy;
-                const float ez = (a4.w + b4.w) * d.x + (a5.x + b5.x) * d.y + (a5.y + b5.y) * d.z - 2.0f * uz;
-                const float delta = (ex * xx + ey * xy + ez * xz) * lxi;
-                const float ch = lj.w * b2.y * hj.w * spline_w(q) * rinv * rinv * delta * lxi;
-                acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
-            }
-        }
+        for (int64_t p = p0 + lane; p < p1; p += 32) pair2<HG>(s, c, w, s.col[p], 1.0f, acc);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             if (!HG && k >= 6) continue;
@@ -422,152 +546,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixCons
         }
     }
     if (lane >= nrows) return;
-
     epi2_mixed<HG>(s, c, row0 + lane, keep);
-}
-
-// ------------------------------------------------------------------ thread-per-row variants
-// One thread owns one row: no reductions, and the neighbour loop is unrolled
-// twice so each thread keeps two pairs' gathers in flight.  A padded pair
-// (odd row length) reuses the last neighbour with weight zero.
-__device__ __forceinline__ void gather1_row(const DevState &s, const MixConst &c, int64_t i, float *m)
-{
-    const float4 hi = s.xh[i], lo = s.xl[i], vi = s.r1[i];
-    const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) m[k] = 0.0f;
-    for (int64_t p = p0; p < p1; p += 2) {
-        const bool two = p + 1 < p1;
-        const int j0 = s.col[p];
-        const int j1 = two ? s.col[p + 1] : j0;
-        const float4 h0 = s.xh[j0], l0 = s.xl[j0], v0 = s.r1[j0];
-        const float4 h1 = s.xh[j1], l1 = s.xl[j1], v1 = s.r1[j1];
-        {
-            const float3 d = xdiff(h0, l0, hi, lo);
-            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-            const float rinv = rsqrtf(r2);
-            const float cw = h0.w * v0.w * spline_dw(r2 * rinv * c.inv_h) * rinv;
-            const float cx = cw * (v0.x - vi.x), cy = cw * (v0.y - vi.y), cz = cw * (v0.z - vi.z);
-            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
-            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
-            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
-        }
-        {
-            const float3 d = xdiff(h1, l1, hi, lo);
-            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-            const float rinv = rsqrtf(r2);
-            const float cw = two ? h1.w * v1.w * spline_dw(r2 * rinv * c.inv_h) * rinv : 0.0f;
-            const float cx = cw * (v1.x - vi.x), cy = cw * (v1.y - vi.y), cz = cw * (v1.z - vi.z);
-            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
-            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
-            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) k_pass1_mixed_t(DevState s, MixConst c)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.N) return;
-    float m[9];
-    gather1_row(s, c, i, m);
-    epi1_mixed(s, c, i, m);
-}
-
-// split form of pass 1: the gather kernel stores the 9 sums, a second kernel
-// runs the per-particle update (lighter registers in the gather)
-__global__ void __launch_bounds__(256) k_gather1_mixed_t(DevState s, MixConst c)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.N) return;
-    float m[9];
-    gather1_row(s, c, i, m);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s.fsum[9 * i + k] = m[k];
-}
-
-__global__ void __launch_bounds__(256) k_gather1_mixed_w32(DevState s, MixConst c)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
-    if (row0 >= s.N) return;
-    const int nrows = (int)min((int64_t)32, s.N - row0);
-    float keep[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
-    for (int r = 0; r < nrows; ++r) {
-        const int64_t i = row0 + r;
-        const float4 hi = s.xh[i], lo = s.xl[i], vi = s.r1[i];
-        const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
-        float m[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) m[k] = 0.0f;
-        for (int64_t p = p0 + lane; p < p1; p += 32) {
-            const int j = s.col[p];
-            const float4 hj = s.xh[j], lj = s.xl[j], vj = s.r1[j];
-            const float3 d = xdiff(hj, lj, hi, lo);
-            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-            const float rinv = rsqrtf(r2);
-            const float cw = hj.w * vj.w * spline_dw(r2 * rinv * c.inv_h) * rinv;
-            const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
-            m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
-            m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
-            m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float t = warp_allsum(m[k]);
-            keep[k] = (lane == r) ? t : keep[k];
-        }
-    }
-    if (lane >= nrows) return;
-    const int64_t i = row0 + lane;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s.fsum[9 * i + k] = keep[k];
-}
-
-__global__ void __launch_bounds__(128) k_epi1_mixed(DevState s, MixConst c)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.N) return;
-    float m[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) m[k] = s.fsum[9 * i + k];
-    epi1_mixed(s, c, i, m);
-}
-
-// pass 2, thread per row
-template <bool HG>
-__device__ __forceinline__ void pair2(const MixConst &c, const float4 hi, const float4 lo, const float4 a0,
-                                      const float4 a1, const float4 a2, const float4 a3, const float4 a4,
-                                      const float4 a5, const float4 *__restrict__ xh, const float4 *__restrict__ xl,
-                                      const float4 *__restrict__ r2, int j, float wmask, float *acc)
-{
-    const float4 hj = xh[j], lj = xl[j];
-    const float4 b0 = r2[6 * j], b1 = r2[6 * j + 1], b2 = r2[6 * j + 2];
-    const float3 d = xdiff(hj, lj, hi, lo);
-    const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
-    const float rinv = rsqrtf(r2v);
-    const float q = r2v * rinv * c.inv_h;
-    const float g = wmask * hj.w * spline_dw(q) * rinv;
-    const float gd = g * (1.0f - b2.y);
-    acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
-    const float t0 = (b0.x - a0.x) * d.x + (b0.y - a0.y) * d.y + (b0.z - a0.z) * d.z;
-    const float t1 = (b0.w - a0.w) * d.x + (b1.x - a1.x) * d.y + (b1.y - a1.y) * d.z;
-    const float t2 = (b1.z - a1.z) * d.x + (b1.w - a1.w) * d.y + (b2.x - a2.x) * d.z;
-    acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
-    if (HG) {
-        const float4 b3 = r2[6 * j + 3], b4 = r2[6 * j + 4], b5 = r2[6 * j + 5];
-        const float ux = b2.z - a2.z, uy = b2.w - a2.w, uz = b3.x - a3.x;
-        const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
-        const float lxi = rsqrtf(xx * xx + xy * xy + xz * xz);
-        const float ex = (a3.y + b3.y) * d.x + (a3.z + b3.z) * d.y + (a3.w + b3.w) * d.z - 2.0f * ux;
-        const float ey = (a4.x + b4.x) * d.x + (a4.y + b4.y) * d.y + (a4.z + b4.z) * d.z - 2.0f * uy;
-        const float ez = (a4.w + b4.w) * d.x + (a5.x + b5.x) * d.y + (a5.y + b5.y) * d.z - 2.0f * uz;
-        const float delta = (ex * xx + ey * xy + ez * xz) * lxi;
-        const float ch = wmask * lj.w * b2.y * hj.w * spline_w(q) * rinv * rinv * delta * lxi;
-        acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
-    }
 }
 
 template <bool HG>
@@ -575,42 +554,66 @@ __global__ void __launch_bounds__(256) k_pass2_mixed_t(DevState s, MixConst c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    const float4 *__restrict__ xh = s.xh;
-    const float4 *__restrict__ xl = s.xl;
-    const float4 *__restrict__ r2 = s.r2;
-    const float4 hi = xh[i], lo = xl[i];
-    const float4 a0 = r2[6 * i], a1 = r2[6 * i + 1], a2 = r2[6 * i + 2];
-    float4 a3 = make_float4(0.f, 0.f, 0.f, 0.f), a4 = a3, a5 = a3;
-    if (HG) { a3 = r2[6 * i + 3]; a4 = r2[6 * i + 4]; a5 = r2[6 * i + 5]; }
-    const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
+    const Row2 w = load_row2<HG>(s, c, i);
+    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
+    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
     float acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-    for (int64_t p = p0; p < p1; p += 2) {
-        const bool two = p + 1 < p1;
-        const int j0 = s.col[p];
-        const int j1 = two ? s.col[p + 1] : j0;
-        pair2<HG>(c, hi, lo, a0, a1, a2, a3, a4, a5, xh, xl, r2, j0, 1.0f, acc);
-        pair2<HG>(c, hi, lo, a0, a1, a2, a3, a4, a5, xh, xl, r2, j1, two ? 1.0f : 0.0f, acc);
+    for (int k = 0; k < n; k += 2) {
+        const bool two = k + 1 < n;
+        const int j0 = cp[32 * k];
+        const int j1 = two ? cp[32 * (k + 1)] : j0;
+        pair2<HG>(s, c, w, j0, 1.0f, acc);
+        pair2<HG>(s, c, w, j1, two ? 1.0f : 0.0f, acc);
     }
     epi2_mixed<HG>(s, c, i, acc);
 }
 
+// ------------------------------------------------------------------ sliced ELL
+// slice g = rows 32g .. 32g+31; its width is the longest row; entry k of
+// lane l sits at ell_off[g] + 32 k + l
+__global__ void k_ell_width(const int64_t *row_ptr, int64_t N, int64_t *ell_off)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long len = i < N ? (long long)(row_ptr[i + 1] - row_ptr[i]) : 0;
+    long long m = len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && (i >> 5) < (N + 31) / 32) ell_off[i >> 5] = 32 * (int64_t)m;
+}
+
+__global__ void k_ell_fill(const int64_t *row_ptr, const int32_t *col, int64_t N, const int64_t *ell_off, int32_t *colE)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = i >> 5;
+    if (g >= (N + 31) / 32) return;
+    const int lane = (int)(i & 31);
+    const int64_t width = (ell_off[g + 1] - ell_off[g]) / 32;
+    const int64_t b = i < N ? row_ptr[i] : 0, n = i < N ? row_ptr[i + 1] - row_ptr[i] : 0;
+    int32_t *o = colE + ell_off[g] + lane;
+    for (int64_t k = 0; k < width; ++k) o[32 * k] = k < n ? col[b + k] : (int32_t)(i < N ? i : 0);
+}
+
 // ------------------------------------------------------------------ mirrors
-// static records from the FP64 inputs: X as hi + lo floats, V, L^{-1}, S0
-__global__ void k_mixed_static(DevState s, const double *S0)
+// static records from the FP64 inputs: cell offsets, S0, L^{-1}
+__global__ void k_mixed_static(DevState s, const double *S0, CellPack pk)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    float hi[3], lo[3];
+    int cc[3];
+    float off[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double x = s.X[3 * i + k];
-        hi[k] = (float)x;
-        lo[k] = (float)(x - (double)hi[k]);
+        const double x = s.X[3 * i + k] - pk.lo[k];
+        int ck = (int)floor(x * pk.inv_cs);
+        ck = ck < 0 ? 0 : (ck > pk.nc[k] - 1 ? pk.nc[k] - 1 : ck);
+        cc[k] = ck;
+        off[k] = (float)(x - (double)ck * (double)pk.cs);
     }
-    s.xh[i] = make_float4(hi[0], hi[1], hi[2], (float)s.vol[i]);
-    s.xl[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    const int packed = (cc[0] + 1) | ((cc[1] + 1) << pk.sh1) | ((cc[2] + 1) << pk.sh2);
+    s.xo[i] = make_float4(off[0], off[1], off[2], __int_as_float(packed));
     s.s0[i] = make_float4((float)S0[3 * i], (float)S0[3 * i + 1], (float)S0[3 * i + 2], 0.0f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.linv32[9 * i + k] = (float)s.Linv[9 * i + k];
@@ -622,7 +625,7 @@ __global__ void k_mixed_r1(DevState s, int dcur)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
     s.r1[i] = make_float4((float)(s.vh[3 * i] - s.vref[0]), (float)(s.vh[3 * i + 1] - s.vref[1]),
-                          (float)(s.vh[3 * i + 2] - s.vref[2]), (float)(1.0 - s.D[dcur][i]));
+                          (float)(s.vh[3 * i + 2] - s.vref[2]), (float)(s.vol[i] * (1.0 - s.D[dcur][i])));
 }
 
 // FP64 copy of A from the pass-2 records (for reading the state)
@@ -630,30 +633,31 @@ __global__ void k_mixed_export_A(DevState s)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    const float4 a0 = s.r2[6 * i], a1 = s.r2[6 * i + 1], a2 = s.r2[6 * i + 2];
+    const float4 a0 = s.r2[i], a1 = s.r2[s.N + i], a2 = s.r2[2 * s.N + i];
     const float A[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.A[9 * i + k] = (double)A[k];
 }
 
-__global__ void k_mixed_sqrtE(DevState s, int mat_id)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.N || s.mat[i] != mat_id) return;
-    s.xl[i].w = (float)s.mats[mat_id].sqrtE;
-}
-
 static unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t mixed_init_static(const DevState &s, const double *S0, cudaStream_t st)
+cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPack &pk, cudaStream_t st)
 {
-    k_mixed_static<<<nb(s.N, 256), 256, 0, st>>>(s, S0);
+    k_mixed_static<<<nb(s.N, 256), 256, 0, st>>>(s, S0, pk);
     return cudaGetLastError();
 }
 
-cudaError_t mixed_material(const DevState &s, int mat_id, cudaStream_t st)
+cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st)
 {
-    k_mixed_sqrtE<<<nb(s.N, 256), 256, 0, st>>>(s, mat_id);
+    const int64_t rows = (s.N + 31) / 32 * 32;
+    k_ell_width<<<nb(rows, 256), 256, 0, st>>>(s.row_ptr, s.N, ell_off);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st)
+{
+    const int64_t rows = (s.N + 31) / 32 * 32;
+    k_ell_fill<<<nb(rows, 256), 256, 0, st>>>(s.row_ptr, s.col, s.N, ell_off, colE);
     return cudaGetLastError();
 }
 

@@ -265,6 +265,84 @@ cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scr
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- particle order
+// Internal particle order: cells of the neighbour grid grouped into bricks of
+// 4 x 4 x 4 cells, bricks in row-major order, cells row-major inside a brick,
+// particles of a cell by ascending caller index.  brick_rank is a dense
+// bijection of the cells onto [0, ncells) (bricks at the far faces are
+// clipped), so the counting sort needs no more buckets than the grid has
+// cells.  Consecutive rows are then spatially compact, which keeps the
+// neighbour gathers of a thread block inside a small region of L1/L2.
+__device__ __forceinline__ int64_t brick_rank(int cx, int cy, int cz, int ncx, int ncy, int ncz)
+{
+    const int bx = cx >> 2, by = cy >> 2, bz = cz >> 2;
+    const int lx = cx & 3, ly = cy & 3, lz = cz & 3;
+    const int hz = min(4, ncz - 4 * bz), hy = min(4, ncy - 4 * by), wx = min(4, ncx - 4 * bx);
+    return (int64_t)ncx * ncy * (4 * bz) + (int64_t)ncx * (4 * by) * hz + (int64_t)(4 * bx) * hy * hz +
+           (int64_t)(lz * hy + ly) * wx + lx;
+}
+
+__global__ void k_order_count(const double *X, int64_t N, GridArgs a, int64_t *count)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int cx, cy, cz;
+    cell_of(a, X + 3 * i, cx, cy, cz);
+    atomicAdd((unsigned long long *)&count[brick_rank(cx, cy, cz, a.nc0, a.nc1, a.nc2)], 1ull);
+}
+
+__global__ void k_order_scatter(const double *X, int64_t N, GridArgs a, const int64_t *start, int64_t *cursor,
+                                int32_t *perm)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int cx, cy, cz;
+    cell_of(a, X + 3 * i, cx, cy, cz);
+    const int64_t c = brick_rank(cx, cy, cz, a.nc0, a.nc1, a.nc2);
+    unsigned long long slot = atomicAdd((unsigned long long *)&cursor[c], 1ull);
+    perm[start[c] + (int64_t)slot] = (int32_t)i;
+}
+
+// ascending caller index inside each cell (cells are short)
+__global__ void k_sort_segments(const int64_t *start, int32_t *v, int64_t nseg)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nseg) return;
+    const int64_t b = start[c], e = start[c + 1];
+    for (int64_t k = b + 1; k < e; ++k) {
+        const int32_t x = v[k];
+        int64_t m = k - 1;
+        while (m >= b && v[m] > x) { v[m + 1] = v[m]; --m; }
+        v[m + 1] = x;
+    }
+}
+
+__global__ void k_identity(int32_t *perm, int64_t N)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) perm[i] = (int32_t)i;
+}
+
+cudaError_t build_order(const double *X_user, int64_t N, const CellGrid &g, const Scratch &sc, bool keep,
+                        int32_t *perm, cudaStream_t st)
+{
+    cudaError_t e;
+    if (keep) {
+        k_identity<<<blocks_for(N, 256), 256, 0, st>>>(perm, N);
+        return cudaGetLastError();
+    }
+    GridArgs a = grid_args(g);
+    if ((e = cudaMemsetAsync(sc.cell_start, 0, (g.ncells + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
+    k_order_count<<<blocks_for(N, 256), 256, 0, st>>>(X_user, N, a, sc.cell_start);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive_i64(sc.cell_start, g.ncells + 1, sc.scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sc.cell_cursor, 0, g.ncells * sizeof(int64_t), st)) != cudaSuccess) return e;
+    k_order_scatter<<<blocks_for(N, 256), 256, 0, st>>>(X_user, N, a, sc.cell_start, sc.cell_cursor, perm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_sort_segments<<<blocks_for(g.ncells, 128), 128, 0, st>>>(sc.cell_start, perm, g.ncells);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- correction matrix
 // One warp per particle: L_i = sum_j V_j (X_j - X_i) (x) grad W_i(X_ij), with
 // grad W = W'(r) (X_j - X_i) / r, so L_i is symmetric; inverted by the

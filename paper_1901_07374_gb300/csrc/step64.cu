@@ -406,7 +406,77 @@ __global__ void k_import_sym(const double *src9, double *dst6, int64_t N)
     o[3] = 0.5 * (a[1] + a[3]); o[4] = 0.5 * (a[5] + a[7]); o[5] = 0.5 * (a[2] + a[6]);
 }
 
+__global__ void k_gather_inputs(const int32_t *perm, int64_t N, const double *X, const double *vol, const int32_t *mat,
+                                const uint8_t *bcm, const double *bcv, const double *f0, DevState s)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int64_t i = perm[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const_cast<double *>(s.X)[3 * k + c] = X[3 * i + c];
+        const_cast<double *>(s.bcv)[3 * k + c] = bcv[3 * i + c];
+    }
+    const_cast<double *>(s.vol)[k] = vol[i];
+    const_cast<int32_t *>(s.mat)[k] = mat[i];
+    const_cast<uint8_t *>(s.bcm)[k] = bcm[i];
+    s.por[k] = f0[i];
+}
+
+template <class T>
+__global__ void k_permute(const T *src, T *dst, const int32_t *perm, int64_t N, int comps, bool out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int64_t i = perm[k];
+    if (out)
+        for (int c = 0; c < comps; ++c) dst[comps * i + c] = src[comps * k + c];
+    else
+        for (int c = 0; c < comps; ++c) dst[comps * k + c] = src[comps * i + c];
+}
+
+__global__ void k_permute_sym(const double *src, double *dst, const int32_t *perm, int64_t N, bool out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int64_t i = perm[k];
+    if (out) {
+        sym_to_full(src + 6 * k, dst + 9 * i);
+    } else {
+        const double *a = src + 9 * i;
+        double *o = dst + 6 * k;
+        o[0] = a[0]; o[1] = a[4]; o[2] = a[8];
+        o[3] = 0.5 * (a[1] + a[3]); o[4] = 0.5 * (a[5] + a[7]); o[5] = 0.5 * (a[2] + a[6]);
+    }
+}
+
 static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_gather_inputs(const int32_t *perm, int64_t N, const double *X, const double *vol,
+                                 const int32_t *mat, const uint8_t *bcm, const double *bcv, const double *f0,
+                                 const DevState &s, cudaStream_t st)
+{
+    k_gather_inputs<<<nblk(N, 256), 256, 0, st>>>(perm, N, X, vol, mat, bcm, bcv, f0, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const void *src, void *dst, const int32_t *perm, int64_t N, int comps, int elem,
+                           bool out, bool sym, cudaStream_t st)
+{
+    const unsigned g = nblk(N, 256);
+    if (sym)
+        k_permute_sym<<<g, 256, 0, st>>>(static_cast<const double *>(src), static_cast<double *>(dst), perm, N, out);
+    else if (elem == 8)
+        k_permute<double><<<g, 256, 0, st>>>(static_cast<const double *>(src), static_cast<double *>(dst), perm, N,
+                                             comps, out);
+    else if (elem == 4)
+        k_permute<int32_t><<<g, 256, 0, st>>>(static_cast<const int32_t *>(src), static_cast<int32_t *>(dst), perm,
+                                              N, comps, out);
+    else
+        k_permute<uint8_t><<<g, 256, 0, st>>>(static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst), perm,
+                                              N, comps, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_state(const DevState &s, cudaStream_t st)
 {

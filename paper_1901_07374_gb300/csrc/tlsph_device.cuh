@@ -216,7 +216,8 @@ __device__ __forceinline__ double eos_sm(const DevMat &m, double J, double D)
 __device__ __forceinline__ double jc_rate(const DevMat &m, double epdot)
 {
     if (m.C == 0.0 || m.inv_epsdot0 <= 0.0) return 1.0;
-    return 1.0 + m.C * log(fmax(epdot * m.inv_epsdot0, 1.0));
+    const double r = epdot * m.inv_epsdot0;
+    return r > 1.0 ? 1.0 + m.C * log(r) : 1.0;   // log(1) = 0 exactly below the reference rate
 }
 __device__ __forceinline__ double jc_hard(const DevMat &m, double ep)
 {
@@ -339,13 +340,14 @@ __device__ __forceinline__ uint32_t material_update(const DevMat &m, double dt, 
         double tr[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) tr[k] = s.sd[k] + 2.0 * m.G * omD * ed[k];
-        const double seq = vm_eq(tr);
+        const double s2 = 1.5 * sym_ddot(tr, tr);
         const double sf = jc_hard(m, s.ep) * jc_rate(m, s.epdot) * omD;
         dep = 0.0;
-        if (seq <= sf) {
+        if (s2 <= sf * sf) {            // sigma_eq <= sigma_f, decided without the square root
 #pragma unroll
             for (int k = 0; k < 6; ++k) s.sd[k] = tr[k];
         } else {
+            const double seq = sqrt(s2);
             dep = (seq - sf) / (3.0 * m.G * omD);
             const double sc = sf / seq;
 #pragma unroll
@@ -355,8 +357,9 @@ __device__ __forceinline__ uint32_t material_update(const DevMat &m, double dt, 
         s.epdot = dep / dt;
         s.sm = eos_sm(m, J, s.D);
     }
-    // damage initiation and evolution
-    if (m.damage == TLSPH_DAMAGE_CL) {
+    // damage initiation and evolution (no plastic increment: D_init unchanged)
+    if (dep == 0.0) {
+    } else if (m.damage == TLSPH_DAMAGE_CL) {
         double full[6] = { s.sd[0] + s.sm, s.sd[1] + s.sm, s.sd[2] + s.sm, s.sd[3], s.sd[4], s.sd[5] };
         double s1 = sym_max_eig(full);
         s.dinit += fmax(s1, 0.0) * dep * m.inv_Wcr;

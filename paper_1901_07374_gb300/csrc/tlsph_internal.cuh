@@ -27,6 +27,18 @@ struct DevMat {
     double fstar_slope;  // (1/q1 - fc) / (fF - fc)
 };
 
+// Packed cell coordinates of the mixed path: positions travel as the offset
+// from the origin of a neighbour-grid cell (size cs >= rc) plus the cell's
+// coordinates packed in one int32 (fields of m_k = 2^b_k - 1 at shifts 0,
+// sh1, sh2).
+struct CellPack {
+    double lo[3];
+    double inv_cs;
+    float cs;
+    int32_t nc[3];
+    int32_t sh1, sh2, m0, m1, m2;
+};
+
 // Device arrays of one context.  SoA per quantity; vectors and tensors of a
 // particle are contiguous (3 or 6/9 doubles) so the epilogues read them with
 // wide loads.  Symmetric tensors are stored as 6 values (xx, yy, zz, xy, yz, zx).
@@ -56,14 +68,16 @@ struct DevState {
     uint32_t *status;       // 1
     const DevMat *mats;     // TLSPH_MAX_MATERIALS
     // mixed-precision records (null in the FP64 path)
-    float4 *xh;             // N   {X hi, V}
-    float4 *xl;             // N   {X lo, sqrt E}
+    float4 *xo;             // N   {offset to cell origin, packed cell coordinates}
     float4 *s0;             // N   {sum_j V_j W'(r)/r (X_j - X_i), 0}  (static, FP64-accurate)
     float *linv32;          // N*9 L^{-1} rounded
     float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
-    float4 *r2;             // N*6 pass-2 gather record {A (9), 1 - D, u (3), F - I (9), 0, 0}
-    float *fsum;            // N*9 pass-1 pair sums (split launch plans)
+    float4 *r2;             // 6 x N pass-2 gather record (SoA of float4, see mixed.cu)
+    float *fsum;            // 9 x N pass-1 pair sums (split launch plans)
+    const int32_t *colE;    // sliced-ELL neighbour columns (slices of 32 rows)
+    const int64_t *ell_off; // (N + 31) / 32 + 1 slice offsets
     double vref[3];         // bulk reference velocity of the r1 mirror
+    CellPack pack;
 };
 
 struct Scratch {            // neighbour-build scratch (set-up only)
@@ -91,7 +105,7 @@ struct tlsph_ctx {
     int dcur = 0;   // D[dcur] = D^n
     // mixed launch plan: pass-1 form, block, pass-2 form, block (the fastest on
     // GB300 for the 1M-particle bar; the autotuner may choose another)
-    int32_t plan[4] = { 2, 256, 1, 256 };
+    int32_t plan[4] = { 2, 128, 1, 128 };
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
     bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
     void *mixed = nullptr;      // mixed-precision state (mixed.cu)
@@ -103,6 +117,12 @@ struct tlsph_ctx {
     int64_t prof_steps = 0;
     int sticky = TLSPH_OK;
     std::string err;
+    // internal order: perm[k] = caller index of internal particle k, inv its inverse
+    bool reordered = false;
+    bool ell_ok = false;        // sliced-ELL columns built (thread-per-row plans allowed)
+    void *ell_mem = nullptr;    // library-owned sliced-ELL columns
+    int32_t *perm_dev = nullptr;
+    std::vector<int32_t> perm, inv;
 };
 
 namespace tlsph {
@@ -122,6 +142,10 @@ cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Sc
 cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
                                  const int64_t *row_ptr, int32_t *col, cudaStream_t st);
 // S0: optional N*3 output of sum_j V_j W'(r)/r (X_j - X_i) (kernel-normalisation free)
+// internal particle order (perm[k] = caller index of internal particle k);
+// keep = identity
+cudaError_t build_order(const double *X_user, int64_t N, const CellGrid &g, const Scratch &sc, bool keep,
+                        int32_t *perm, cudaStream_t st);
 cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
                          cudaStream_t st);
 
@@ -136,6 +160,15 @@ cudaError_t launch_material_point_value(const DevMat &m, double dt, int64_t n, c
                                         const double *J, double *state, cudaStream_t st);
 cudaError_t launch_export_sym(const double *src6, double *dst9, int64_t N, cudaStream_t st);
 cudaError_t launch_import_sym(const double *src9, double *dst6, int64_t N, cudaStream_t st);
+// staged caller-order inputs -> internal arrays (dst[k] = src[perm[k]])
+cudaError_t launch_gather_inputs(const int32_t *perm, int64_t N, const double *X, const double *vol,
+                                 const int32_t *mat, const uint8_t *bcm, const double *bcv, const double *f0,
+                                 const DevState &s, cudaStream_t st);
+// per-particle field transfer between internal and caller order on the device:
+// out: dst[perm[k]] = src[k]; in: dst[k] = src[perm[k]] (comps per particle,
+// elem bytes 1/4/8; sym = 6 stored <-> 9 exchanged)
+cudaError_t launch_permute(const void *src, void *dst, const int32_t *perm, int64_t N, int comps, int elem,
+                           bool out, bool sym, cudaStream_t st);
 
 DevMat make_dev_mat(const tlsph_material &m);
 
@@ -143,8 +176,9 @@ DevMat make_dev_mat(const tlsph_material &m);
 void set_last_error_text(const std::string &msg);
 
 // mixed.cu
-cudaError_t mixed_init_static(const DevState &s, const double *S0, cudaStream_t st);
-cudaError_t mixed_material(const DevState &s, int mat_id, cudaStream_t st);
+cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPack &pk, cudaStream_t st);
+cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st);
+cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st);
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st);

@@ -143,20 +143,23 @@ def _check(code: int, ctx=None):
 
 
 def mixed_algorithmic_bytes(N: int, nnz: int):
-    """HBM bytes per launch of (pass 1, pass 2) in the mixed path: the 4-byte
-    column index of every pair plus each particle's own records and FP64 state
-    read and written once.
-    pass 1: row_ptr 8, X hi/lo 32, v record 16, L^-1 36, F rw 144, deviator rw 96,
-            eps_p / rate / D_init / f rw 64, D r+w 16, fail 4, material 4, u 24,
-            sigma w 48, pass-2 record w 96                              = 588
-    pass 2: row_ptr 8, X hi/lo 32, own pass-2 record 96, S0 16, V 8, D 8, sqrt E 8,
-            mass 8, v_half rw 48, v w 24, force w 24, u r+w 48, fail 4, bc 1,
-            v record w 16                                               = 349"""
-    return 4 * nnz + 588 * N, 4 * nnz + 349 * N
+    """HBM bytes per step of (pass 1, pass 2) in the mixed path that the method
+    must move: the 4-byte column index of every pair plus each particle's own
+    records and FP64 state read and written once.
+    pass 1: row_ptr 8, cell offsets 16, v record 16, L^-1 36, F rw 144,
+            deviator rw 96, eps_p / rate / D_init / f rw 64, D r+w 16, fail 4,
+            material 4, u 24, V 8, sqrt E 8, sigma w 48, pass-2 record w 96 = 588
+    pass 2: row_ptr 8, cell offsets 16, own pass-2 record 96, S0 16, V 8, D 8,
+            sqrt E 8, mass 8, v_half rw 48, v w 24, force w 24, u r+w 48,
+            fail 4, bc 1, v record w 16                                   = 333"""
+    return 4 * nnz + 588 * N, 4 * nnz + 333 * N
 
 
-def make_config(h, rc, dt, hg_alpha, precision="fp64") -> Config:
-    return Config(float(h), float(rc), float(dt), float(hg_alpha), PRECISION[precision], 0)
+FLAG_SPATIAL_ORDER = 1
+
+
+def make_config(h, rc, dt, hg_alpha, precision="fp64", flags=0) -> Config:
+    return Config(float(h), float(rc), float(dt), float(hg_alpha), PRECISION[precision], int(flags))
 
 
 def workspace_bytes(cfg: Config, N: int, nnz_cap: int) -> int:
@@ -195,7 +198,7 @@ class Simulation:
     stream: torch.cuda.Stream or raw handle; default the current stream."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
-                 precision="fp64", arena=None, nnz_cap=0, stream=None):
+                 precision="fp64", arena=None, nnz_cap=0, stream=None, spatial_order=False):
         L = load()
         X = _host(X, np.float64)
         self.N = N = X.shape[0]
@@ -205,7 +208,7 @@ class Simulation:
         bc_mask = _host(bc_mask, np.uint8)
         bc_vel = _host(bc_vel, np.float64, (N, 3))
         f0 = _host(f0, np.float64)
-        self.cfg = make_config(h, rc, dt, hg_alpha, precision)
+        self.cfg = make_config(h, rc, dt, hg_alpha, precision, FLAG_SPATIAL_ORDER if spatial_order else 0)
         self.precision = precision
         self.arena = arena
         self.stream = _stream_handle(stream)

@@ -107,3 +107,25 @@ def test_step_counter_is_part_of_the_checkpoint():
     assert g.steps == 41
     g.step(2)
     assert g.get("STEP")[0] == 43
+
+
+def test_internal_order_is_invisible():
+    """A spatially reordered context and one keeping the caller's order
+    return the same neighbour CSR bit for bit and the same fields to FP64
+    rounding (only the order of the sums over j differs)."""
+    from parity import ORACLE_KEY, compare_state
+    w = S.failure_variant(S.tensile_bar_jc(nx=9, ny=7, nz=30, seed=2, steps=60))
+    a = tlsph.Simulation.from_workload(w, spatial_order=True)
+    b = tlsph.Simulation.from_workload(w)
+    assert np.array_equal(a.get("NBR_ROWPTR"), b.get("NBR_ROWPTR"))
+    assert np.array_equal(a.get("NBR_COL"), b.get("NBR_COL"))
+    assert np.array_equal(a.get("X"), w.specimen.X)
+    a.step(60)
+    b.step(60)
+    ref = {ORACLE_KEY[k]: v for k, v in b.state().items()}
+    compare_state(a.state(), ref, w, tol=1e-9)
+    assert np.array_equal(a.get("FAIL_STEP"), b.get("FAIL_STEP"))
+    for precision in ("mixed",):
+        c = tlsph.Simulation.from_workload(w, precision=precision, spatial_order=True)
+        c.step(60)
+        compare_state(c.state(), ref, w, tol=2e-4, fields=("U", "V", "F", "SIGMA", "FORCE"))
