@@ -201,9 +201,10 @@ int tlsph_destroy(tlsph_ctx *ctx);
 
 /* Launch plan of the mixed-precision step: plan[0] pass-1 form (0 warp per
  * 32 rows; 1 thread per row; 2 thread-per-row gather + per-particle kernel;
- * 3 warp-per-32-rows gather + per-particle kernel), plan[1] its block size,
- * plan[2] pass-2 form (0 warp per 32 rows; 1 thread per row), plan[3] its
- * block size (multiples of 32 up to 256).  Every plan computes the same
+ * 3 warp-per-32-rows gather + per-particle kernel; 4 as 2 with four pairs in
+ * flight per thread), plan[1] its block size, plan[2] pass-2 form (0 warp
+ * per 32 rows; 1 thread per row; 2 thread-per-row gather + per-particle
+ * kernel), plan[3] its block size (multiples of 32 up to 256).  Every plan computes the same
  * method; sums over a row are grouped differently, so results differ only
  * by FP32 rounding.  n must be 4.  The FP64 path ignores the plan. */
 int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);

@@ -570,6 +570,77 @@ __global__ void __launch_bounds__(256) k_pass2_mixed_t(DevState s, MixConst c)
     epi2_mixed<HG>(s, c, i, acc);
 }
 
+// four pairs in flight per thread (pass 1)
+__device__ __forceinline__ void gather1_row4(const DevState &s, const MixConst &c, int64_t i, float *m)
+{
+    const float4 oi = s.xo[i], vi = s.r1[i];
+    const int ti = row_bias(c, oi);
+    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
+    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = 0.0f;
+    for (int k = 0; k < n; k += 4) {
+        int j[4];
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = k + u < n;
+            j[u] = ok ? cp[32 * (k + u)] : (int)i;
+            w[u] = ok ? 1.0f : 0.0f;
+        }
+        float4 o[4], v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { o[u] = s.xo[j[u]]; v[u] = s.r1[j[u]]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pair1(c, oi, ti, vi, o[u], v[u], w[u], m);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gather1_mixed_t4(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+    gather1_row4(s, c, i, m);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = m[k];
+}
+
+// split form of pass 2: a gather kernel with no FP64 epilogue stores the 9
+// pair sums; a second kernel computes the force and integrates
+template <bool HG>
+__global__ void __launch_bounds__(256) k_gather2_mixed_t(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    const Row2 w = load_row2<HG>(s, c, i);
+    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
+    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
+    float acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+    for (int k = 0; k < n; k += 2) {
+        const bool two = k + 1 < n;
+        const int j0 = cp[32 * k];
+        const int j1 = two ? cp[32 * (k + 1)] : j0;
+        pair2<HG>(s, c, w, j0, 1.0f, acc);
+        pair2<HG>(s, c, w, j1, two ? 1.0f : 0.0f, acc);
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = acc[k];
+}
+
+template <bool HG>
+__global__ void __launch_bounds__(128) k_epi2_mixed(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = s.fsum[k * s.N + i];
+    epi2_mixed<HG>(s, c, i, m);
+}
+
 // ------------------------------------------------------------------ sliced ELL
 // slice g = rows 32g .. 32g+31; its width is the longest row; entry k of
 // lane l sits at ell_off[g] + 32 k + l
@@ -669,8 +740,9 @@ cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st)
 
 // Launch plans (chosen per context, e.g. by the autotuner):
 //   pass 1: 0 = warp per 32 rows, fused;  1 = thread per row, fused;
-//           2 = thread-per-row gather + per-particle kernel;  3 = warp-per-32-rows gather + per-particle kernel
-//   pass 2: 0 = warp per 32 rows;  1 = thread per row
+//           2 = thread-per-row gather + per-particle kernel;  3 = warp-per-32-rows gather + per-particle kernel;
+//           4 = as 2 with four pairs in flight per thread
+//   pass 2: 0 = warp per 32 rows;  1 = thread per row;  2 = thread-per-row gather + per-particle kernel
 // block sizes are multiples of 32 up to 256 (128 for the fused warp forms).
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev)
 {
@@ -690,12 +762,24 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
         k_gather1_mixed_w32<<<nb(rows32, b1), b1, 0, st>>>(s, c);
         k_epi1_mixed<<<nb(s.N, 128), 128, 0, st>>>(s, c);
         break;
+    case 4:
+        k_gather1_mixed_t4<<<nb(s.N, b1), b1, 0, st>>>(s, c);
+        k_epi1_mixed<<<nb(s.N, 128), 128, 0, st>>>(s, c);
+        break;
     default: k_pass1_mixed<<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c); break;
     }
     if (ev) cudaEventRecord(ev[1], st);
     if (v2 == 1) {
         if (hg) k_pass2_mixed_t<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
         else k_pass2_mixed_t<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+    } else if (v2 == 2) {
+        if (hg) {
+            k_gather2_mixed_t<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+            k_epi2_mixed<true><<<nb(s.N, 128), 128, 0, st>>>(s, c);
+        } else {
+            k_gather2_mixed_t<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+            k_epi2_mixed<false><<<nb(s.N, 128), 128, 0, st>>>(s, c);
+        }
     } else {
         if (hg) k_pass2_mixed<true><<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c);
         else k_pass2_mixed<false><<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c);
@@ -704,7 +788,7 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
     return cudaGetLastError();
 }
 
-int mixed_kernels_per_step(const tlsph_ctx &ctx) { return (ctx.plan[0] >= 2 ? 3 : 2); }
+int mixed_kernels_per_step(const tlsph_ctx &ctx) { return (ctx.plan[0] >= 2 ? 2 : 1) + (ctx.plan[2] == 2 ? 2 : 1); }
 
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st)
 {
