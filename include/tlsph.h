@@ -210,6 +210,38 @@ int tlsph_destroy(tlsph_ctx *ctx);
 int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);
 int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
 
+/* ---- Batched stepping (many specimens advanced together) ----------------
+ * A batch advances every member context with one launch per kernel kind and
+ * step over all members (a persistent grid striding over every member's
+ * blocks of rows), optionally replayed from a captured CUDA graph.  Members
+ * must be mixed-precision contexts (TLSPH_PRECISION_MIXED) that all use
+ * hourglass control or all do not.  A member's rows are computed by the
+ * same kernels whatever else is in the batch, so its result alone in a batch
+ * and in any mix is identical bit for bit; against the context's own
+ * tlsph_step launches it agrees to FP32 rounding.  The member set can change
+ * between calls (continuous batching) without recapturing the graph. */
+typedef struct tlsph_batch tlsph_batch;
+
+/* capacity: most members at once; stream: the caller's cudaStream_t the
+ * batch's work is ordered with (the launches themselves run on a stream the
+ * batch owns, so a CUDA graph can be captured even when `stream` is the
+ * legacy default stream) */
+int tlsph_batch_create(int capacity, void *stream, tlsph_batch **out);
+
+/* Replace the member set (n <= capacity contexts, no repeats).  Waits for
+ * each member's own stream.  A member stepped or modified outside the batch
+ * must be set again before the next tlsph_batch_step. */
+int tlsph_batch_set(tlsph_batch *b, tlsph_ctx *const *ctxs, int n);
+
+/* Enqueue nsteps steps of every member on the batch stream (use_graph != 0:
+ * capture one step as a CUDA graph on first use and replay it).  Later work
+ * on a member's own stream (tlsph_get_state, tlsph_sync) is ordered after it. */
+int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph);
+
+int tlsph_batch_sync(tlsph_batch *b);
+const char *tlsph_batch_last_error(const tlsph_batch *b);
+int tlsph_batch_destroy(tlsph_batch *b);
+
 /* Per-kernel device time of the step (CUDA events recorded around each
  * launch on the context's stream).  enable != 0 clears the accumulators and
  * starts recording; 0 stops.  Hot-path kernels: 0 = pass 1 (velocity

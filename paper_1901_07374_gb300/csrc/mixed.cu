@@ -35,22 +35,14 @@
 // the slice), so the 32 lanes' k-th neighbour indices are one 128-byte line.
 #include <math.h>
 
+#include <algorithm>
+
 #include "tlsph_device.cuh"
 #include "tlsph_internal.cuh"
 
 namespace tlsph {
 
 static constexpr int MIX_THREADS = 128;
-
-struct MixConst {
-    double dt, half_dt;
-    float inv_h, dw_norm, w_norm, hg_coef, cs;
-    double vref0, vref1, vref2;
-    int64_t N;
-    int64_t step_index;
-    int ucur, dcur;
-    int sh1, sh2, m0, m1, m2, bias;   // packed cell coordinates
-};
 
 static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
 {
@@ -580,12 +572,15 @@ __device__ __forceinline__ void gather1_row4(const DevState &s, const MixConst &
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = 0.0f;
     for (int k = 0; k < n; k += 4) {
+        // a padded slot repeats the first (real) neighbour with weight 0
         int j[4];
         float w[4];
+        j[0] = cp[32 * k];
+        w[0] = 1.0f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 1; u < 4; ++u) {
             const bool ok = k + u < n;
-            j[u] = ok ? cp[32 * (k + u)] : (int)i;
+            j[u] = ok ? cp[32 * (k + u)] : j[0];
             w[u] = ok ? 1.0f : 0.0f;
         }
         float4 o[4], v[4];
@@ -800,5 +795,120 @@ cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st)
 }
 
 void mixed_release(tlsph_ctx &) {}
+
+}  // namespace tlsph
+
+// ====================================================================== batched step
+// Many contexts advance together: a device table holds one slot per context
+// (its device arrays and step constants).  Every kernel runs a persistent
+// grid that strides over the flattened work list of (context, block of rows);
+// a block finds its context by binary search on the slots' first work block.
+// The ping-pong indices and the step counter live in the slots and are
+// advanced on the device at the end of each step, so one captured step can be
+// replayed as a CUDA graph, and the membership can change by rewriting the
+// table without touching the graph.  A context's rows are computed by these
+// kernels alone, independently of the other members, so its result does not
+// depend on the company it keeps.
+namespace tlsph {
+
+__device__ __forceinline__ int batch_find(const BatchSlot *slots, int n, int64_t w)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (slots[mid].blk0 <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int KIND, bool HG>
+__global__ void __launch_bounds__(128) k_batch(const BatchHdr *hdr, BatchSlot *slots)
+{
+    __shared__ int sidx;
+    const int nspec = hdr->nspec;
+    const int64_t total = hdr->total_blk;
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        if (threadIdx.x == 0) sidx = batch_find(slots, nspec, w);
+        __syncthreads();
+        const BatchSlot &sl = slots[sidx];
+        const int64_t i = (w - sl.blk0) * blockDim.x + threadIdx.x;
+        if (i < sl.s.N) {
+            if (KIND == 0) {            // pass-1 gather
+                float m[9];
+                gather1_row4(sl.s, sl.c, i, m);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) sl.s.fsum[k * sl.s.N + i] = m[k];
+            } else if (KIND == 1) {     // pass-1 per-particle update
+                float m[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) m[k] = sl.s.fsum[k * sl.s.N + i];
+                epi1_mixed(sl.s, sl.c, i, m);
+            } else {                    // pass 2
+                const Row2 r = load_row2<HG>(sl.s, sl.c, i);
+                const int n = (int)(sl.s.row_ptr[i + 1] - sl.s.row_ptr[i]);
+                const int32_t *__restrict__ cp = sl.s.colE + sl.s.ell_off[i >> 5] + (i & 31);
+                float acc[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+                for (int k = 0; k < n; k += 2) {
+                    const bool two = k + 1 < n;
+                    const int j0 = cp[32 * k];
+                    const int j1 = two ? cp[32 * (k + 1)] : j0;
+                    pair2<HG>(sl.s, sl.c, r, j0, 1.0f, acc);
+                    pair2<HG>(sl.s, sl.c, r, j1, two ? 1.0f : 0.0f, acc);
+                }
+                epi2_mixed<HG>(sl.s, sl.c, i, acc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// end of a step: flip the ping-pong buffers and count the step, per slot
+__global__ void k_batch_advance(const BatchHdr *hdr, BatchSlot *slots)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= hdr->nspec) return;
+    slots[k].c.ucur ^= 1;
+    slots[k].c.dcur ^= 1;
+    slots[k].c.step_index += 1;
+}
+
+BatchSlot make_batch_slot(const tlsph_ctx &ctx)
+{
+    BatchSlot b;
+    b.s = ctx.s;
+    b.c = make_mix_const(ctx, ctx.steps);
+    b.blk0 = 0;
+    return b;
+}
+
+// two HG flavours x three kernel kinds; grid is persistent
+cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, int grid, cudaStream_t st)
+{
+    if (hg) {
+        k_batch<0, true><<<grid, 128, 0, st>>>(hdr, slots);
+        k_batch<1, true><<<grid, 128, 0, st>>>(hdr, slots);
+        k_batch<2, true><<<grid, 128, 0, st>>>(hdr, slots);
+    } else {
+        k_batch<0, false><<<grid, 128, 0, st>>>(hdr, slots);
+        k_batch<1, false><<<grid, 128, 0, st>>>(hdr, slots);
+        k_batch<2, false><<<grid, 128, 0, st>>>(hdr, slots);
+    }
+    k_batch_advance<<<(nspec + 127) / 128, 128, 0, st>>>(hdr, slots);
+    return cudaGetLastError();
+}
+
+int batch_grid(bool hg)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (hg)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2, true>, 128, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2, false>, 128, 0);
+    return std::max(1, sms) * std::max(1, per);
+}
 
 }  // namespace tlsph

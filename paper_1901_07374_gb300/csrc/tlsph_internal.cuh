@@ -175,7 +175,31 @@ DevMat make_dev_mat(const tlsph_material &m);
 // text returned by tlsph_last_error(NULL) on the calling thread
 void set_last_error_text(const std::string &msg);
 
-// mixed.cu
+// mixed.cu -- step constants of the mixed path (defined there)
+struct MixConst {
+    double dt, half_dt;
+    float inv_h, dw_norm, w_norm, hg_coef, cs;
+    double vref0, vref1, vref2;
+    int64_t N;
+    int64_t step_index;
+    int ucur, dcur;
+    int sh1, sh2, m0, m1, m2, bias;   // packed cell coordinates
+};
+
+// one context in a batch table (device memory)
+struct BatchSlot {
+    DevState s;
+    MixConst c;
+    int64_t blk0;      // first work block of this context
+};
+struct BatchHdr {
+    int nspec;
+    int64_t total_blk;
+};
+BatchSlot make_batch_slot(const tlsph_ctx &ctx);
+cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, int grid, cudaStream_t st);
+int batch_grid(bool hg);
+
 cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPack &pk, cudaStream_t st);
 cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st);
 cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st);

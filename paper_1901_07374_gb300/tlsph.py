@@ -76,7 +76,8 @@ def make_material(d: dict) -> Material:
 EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph_step", "tlsph_sync",
            "tlsph_status_bits", "tlsph_info", "tlsph_get_state", "tlsph_set_state", "tlsph_last_error",
            "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
-           "tlsph_set_plan", "tlsph_get_plan")
+           "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
+           "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy")
 
 _lib = None
 _lock = threading.Lock()
@@ -130,6 +131,18 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_set_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
         L.tlsph_get_plan.restype = i32
         L.tlsph_get_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
+        L.tlsph_batch_create.restype = i32
+        L.tlsph_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
+        L.tlsph_batch_set.restype = i32
+        L.tlsph_batch_set.argtypes = [vp, ctypes.POINTER(vp), i32]
+        L.tlsph_batch_step.restype = i32
+        L.tlsph_batch_step.argtypes = [vp, i32, i32]
+        L.tlsph_batch_sync.restype = i32
+        L.tlsph_batch_sync.argtypes = [vp]
+        L.tlsph_batch_last_error.restype = ctypes.c_char_p
+        L.tlsph_batch_last_error.argtypes = [vp]
+        L.tlsph_batch_destroy.restype = i32
+        L.tlsph_batch_destroy.argtypes = [vp]
         L.tlsph_material_point_batch.restype = i32
         L.tlsph_material_point_batch.argtypes = [ctypes.POINTER(Material), dbl, i64, vp, vp, vp, vp]
         _lib = L
@@ -386,3 +399,46 @@ def neighbors_noalloc(X, rc: float, row_ptr, col, stream=None) -> int:
         err.nnz = nnz.value
         raise err
     return nnz.value
+
+
+class Batch:
+    """Many mixed-precision Simulations advanced together (tlsph_batch_*):
+    one persistent launch per kernel kind and step over all members, replayed
+    from a CUDA graph when graph=True.  Members can change between steps."""
+
+    def __init__(self, capacity: int, stream=None):
+        L = load()
+        self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        code = L.tlsph_batch_create(int(capacity), ctypes.c_void_p(self.stream), ctypes.byref(h))
+        if code != 0:
+            raise TlsphError(code, "tlsph_batch_create failed")
+        self.h = h
+        self.members = []
+
+    def _check(self, code):
+        if code != 0:
+            raise TlsphError(code, load().tlsph_batch_last_error(self.h).decode(errors="replace"))
+
+    def set(self, sims) -> None:
+        sims = list(sims)
+        arr = (ctypes.c_void_p * max(1, len(sims)))(*[s.ctx.value for s in sims])
+        self._check(load().tlsph_batch_set(self.h, arr, len(sims)))
+        self.members = sims
+
+    def step(self, n: int = 1, graph: bool = True) -> None:
+        self._check(load().tlsph_batch_step(self.h, int(n), 1 if graph else 0))
+
+    def sync(self) -> None:
+        self._check(load().tlsph_batch_sync(self.h))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().tlsph_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
