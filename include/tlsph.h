@@ -76,7 +76,7 @@ typedef struct {
     double dt;         /* time step [s], fixed for the run */
     double hg_alpha;   /* hourglass-control coefficient (0 disables it) */
     int32_t precision; /* TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED */
-    int32_t flags;     /* 0 or TLSPH_FLAG_SPATIAL_ORDER */
+    int32_t flags;     /* 0 or TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_WALL */
 } tlsph_config;
 
 /* Store particles in a spatially compact internal order (cells of the
@@ -87,6 +87,12 @@ typedef struct {
  * consecutive particles and a warp's gathers coalesce; the brick order helps
  * inputs in arbitrary order. */
 #define TLSPH_FLAG_SPATIAL_ORDER 1
+
+/* A rigid frictionless wall on the plane z = 0 (current configuration): a
+ * particle that would drift below it is put back on the plane and its
+ * velocity may not point into it (a kinematic contact; the paper has none).
+ * Used by the Taylor-impact workload. */
+#define TLSPH_FLAG_WALL 2
 
 /* damage models */
 #define TLSPH_DAMAGE_NONE 0

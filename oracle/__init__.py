@@ -58,7 +58,7 @@ class Material(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("rc", ctypes.c_double), ("dt", ctypes.c_double),
-                ("hg_alpha", ctypes.c_double)]
+                ("hg_alpha", ctypes.c_double), ("wall", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER
@@ -277,14 +277,14 @@ class Simulation:
     matrices computed on construction (Sec. 2.2: both fixed for the run)."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
-                 neighbors_csr=None):
+                 neighbors_csr=None, wall=False):
         self.N = N = int(np.asarray(X).shape[0])
         self.X = np.ascontiguousarray(X, np.float64).reshape(N, 3).copy()
         self.vol = np.ascontiguousarray(vol, np.float64).copy()
         self.mat_id = np.ascontiguousarray(mat_id, np.int32).copy()
         self.bc_mask = np.ascontiguousarray(bc_mask, np.uint8).copy()
         self.bc_vel = np.ascontiguousarray(bc_vel, np.float64).reshape(N, 3).copy()
-        self.cfg = Config(float(h), float(rc), float(dt), float(hg_alpha))
+        self.cfg = Config(float(h), float(rc), float(dt), float(hg_alpha), 1 if wall else 0)
         mats = [make_material(m) for m in materials]
         self._mats = (Material * len(mats))(*mats)
         if neighbors_csr is None:
@@ -318,6 +318,7 @@ class Simulation:
     @classmethod
     def from_workload(cls, w, **kw):
         sp = w.specimen
+        kw.setdefault("wall", getattr(w, "wall", False))
         return cls(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, w.materials,
                    w.h, w.rc, w.dt, w.hg_alpha, **kw)
 

@@ -63,6 +63,7 @@ typedef struct {
 
 typedef struct {
     double h, rc, dt, hg_alpha;
+    int32_t wall;             /* 1: rigid frictionless wall on the plane z = 0 */
 } orc_config;
 
 /* status bits */
@@ -838,6 +839,15 @@ void orc_step(orc_system *s, const orc_config *c, int64_t nsteps)
             apply_bc(s, i, s->vh + 3 * i);
         }
         for (int64_t i = 0; i < 3 * N; ++i) s->u[i] += c->dt * s->vh[i];
+        /* Reading (rigid wall; the paper has no contact): a kinematic plane
+         * z = 0 -- a particle that drifted below it is put back on it and its
+         * velocity may not point into it */
+        if (c->wall)
+            for (int64_t i = 0; i < N; ++i)
+                if (s->X[3 * i + 2] + s->u[3 * i + 2] < 0.0) {
+                    s->u[3 * i + 2] = -s->X[3 * i + 2];
+                    if (s->vh[3 * i + 2] < 0.0) s->vh[3 * i + 2] = 0.0;
+                }
         orc_velocity_gradient(N, s->X, s->vol, s->vh, s->D, s->Linv, s->row_ptr, s->col,
                               c->h, s->Fdot);
         for (int64_t i = 0; i < N; ++i) particle_update(s, c, i);

@@ -148,7 +148,7 @@ bool valid_config(const tlsph_config *c, std::string &why)
         why = "precision must be TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED";
         return false;
     }
-    if ((c->flags & ~TLSPH_FLAG_SPATIAL_ORDER) != 0) { why = "unknown flags"; return false; }
+    if ((c->flags & ~(TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_WALL)) != 0) { why = "unknown flags"; return false; }
     return true;
 }
 
@@ -538,7 +538,7 @@ int tlsph_step(tlsph_ctx *ctx, int nsteps)
         }
     cudaError_t e;
     if (ctx->need_predict) {
-        e = launch_predict(ctx->s, ctx->ucur, ctx->cfg.dt, ctx->stream);
+        e = launch_predict(ctx->s, ctx->ucur, ctx->cfg.dt, (ctx->cfg.flags & TLSPH_FLAG_WALL) != 0, ctx->stream);
         if (e == cudaSuccess && ctx->cfg.precision == TLSPH_PRECISION_MIXED)
             e = mixed_after_predict(ctx->s, ctx->dcur, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "predict");

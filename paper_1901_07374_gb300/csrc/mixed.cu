@@ -68,6 +68,7 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     c.m1 = ctx.s.pack.m1;
     c.m2 = ctx.s.pack.m2;
     c.bias = 1 | (1 << c.sh1) | (1 << c.sh2);
+    c.wall = (cfg.flags & TLSPH_FLAG_WALL) != 0;
     return c;
 }
 
@@ -443,11 +444,15 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
     }
     const double *un = s.u[c.ucur ^ 1];
     double *unext = s.u[c.ucur];
+    double un2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) un2[k] = un[3 * i + k] + c.dt * v2[k];
+    if (c.wall) wall_contact(s.X[3 * i + 2], un2[2], v2[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         s.v[3 * i + k] = vn[k];
         s.vh[3 * i + k] = v2[k];
-        unext[3 * i + k] = un[3 * i + k] + c.dt * v2[k];
+        unext[3 * i + k] = un2[k];
     }
     s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2),
                           (float)(Vi * omdi));

@@ -31,7 +31,7 @@ static constexpr int STEP_THREADS = 128;
 struct StepConst {
     double dt, half_dt, inv_h, dw_norm, w_norm, hg_coef;
     int64_t step_index;
-    int ucur, dcur;
+    int ucur, dcur, wall;
 };
 
 static StepConst make_const(const tlsph_config &cfg, int ucur, int dcur, int64_t step_index)
@@ -46,6 +46,7 @@ static StepConst make_const(const tlsph_config &cfg, int ucur, int dcur, int64_t
     c.step_index = step_index;
     c.ucur = ucur;
     c.dcur = dcur;
+    c.wall = (cfg.flags & TLSPH_FLAG_WALL) != 0;
     return c;
 }
 
@@ -302,11 +303,15 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass2_fp64(DevState s, StepCon
     for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * (f[k] * im);
     apply_bc(s, i, fail, v2);
     double *__restrict__ unext = s.u[c.ucur];
+    double un2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) un2[k] = un[3 * i + k] + c.dt * v2[k];
+    if (c.wall) wall_contact(s.X[3 * i + 2], un2[2], v2[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         s.v[3 * i + k] = vn[k];
         s.vh[3 * i + k] = v2[k];
-        unext[3 * i + k] = un[3 * i + k] + c.dt * v2[k];
+        unext[3 * i + k] = un2[k];
     }
     if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
 }
@@ -355,19 +360,22 @@ __global__ void k_material_fields(DevState s, int mat_id, int dcur, int set_gtn_
 }
 
 // v^{n+1/2} = v^n + dt/2 f^n / m and u^{n+1} = u^n + dt v^{n+1/2} (constraints applied)
-__global__ void k_predict(DevState s, int ucur, double dt)
+__global__ void k_predict(DevState s, int ucur, double dt, int wall)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
     const double im = 1.0 / s.mass[i];
-    double v[3];
+    double v[3], u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) v[k] = s.v[3 * i + k] + 0.5 * dt * (s.force[3 * i + k] * im);
     apply_bc(s, i, s.fail[i], v);
 #pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = s.u[ucur][3 * i + k] + dt * v[k];
+    if (wall) wall_contact(s.X[3 * i + 2], u[2], v[2]);
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
         s.vh[3 * i + k] = v[k];
-        s.u[ucur ^ 1][3 * i + k] = s.u[ucur][3 * i + k] + dt * v[k];
+        s.u[ucur ^ 1][3 * i + k] = u[k];
     }
 }
 
@@ -490,9 +498,9 @@ cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool
     return cudaGetLastError();
 }
 
-cudaError_t launch_predict(const DevState &s, int ucur, double dt, cudaStream_t st)
+cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, cudaStream_t st)
 {
-    k_predict<<<nblk(s.N, 256), 256, 0, st>>>(s, ucur, dt);
+    k_predict<<<nblk(s.N, 256), 256, 0, st>>>(s, ucur, dt, wall ? 1 : 0);
     return cudaGetLastError();
 }
 

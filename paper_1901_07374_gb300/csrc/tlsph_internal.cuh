@@ -152,7 +152,17 @@ cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, 
 // step64.cu
 cudaError_t launch_init_state(const DevState &s, cudaStream_t st);
 cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool gtn_damage, cudaStream_t st);
-cudaError_t launch_predict(const DevState &s, int ucur, double dt, cudaStream_t st);
+cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, cudaStream_t st);
+
+// rigid wall on z = 0: put a particle that drifted below it back on the plane
+// and remove the velocity component into it
+__host__ __device__ inline void wall_contact(double Xz, double &uz, double &vz)
+{
+    if (Xz + uz < 0.0) {
+        uz = -Xz;
+        if (vz < 0.0) vz = 0.0;
+    }
+}
 // ev: null, or 3 events recorded before pass 1, between the passes and after pass 2
 cudaError_t launch_step_fp64(const DevState &s, const tlsph_config &cfg, int ucur, int dcur,
                              int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
@@ -184,6 +194,7 @@ struct MixConst {
     int64_t step_index;
     int ucur, dcur;
     int sh1, sh2, m0, m1, m2, bias;   // packed cell coordinates
+    int wall;
 };
 
 // one context in a batch table (device memory)

@@ -232,6 +232,7 @@ class Workload:
     dt: float
     hg_alpha: float
     steps: int
+    wall: bool = False     # rigid frictionless wall on the plane z = 0
 
     def sim_params(self) -> dict:
         return dict(h=self.h, rc=self.rc, dt=self.dt, hg_alpha=self.hg_alpha)
@@ -284,3 +285,61 @@ def failure_variant(w: Workload, v_grip: float = 20.0, scale: float = 0.02) -> W
         m["D2"] *= scale
         mats.append(m)
     return dataclasses.replace(w, name=w.name + "_failure", specimen=sp, materials=mats)
+
+
+def taylor_impact(n_particles: int = 12000, spacing: float = 0.5e-3, v_impact: float = 200.0, seed: int = 0,
+                  steps: int = 1000, scale: float = 1.0, hg_alpha: float = HG_ALPHA) -> Workload:
+    """Taylor impact: a cylinder (length/diameter 3.2, about n_particles
+    particles on a cubic lattice) moving at v_impact onto a rigid wall at
+    z = 0, Johnson-Cook material of the 1M-particle bar (damage constants x
+    scale)."""
+    sp = taylor_cylinder(n_particles, spacing, v_impact, seed=seed)
+    mat = aluminium_jc(scale)
+    w = _workload(f"taylor_{sp.N}", sp, [mat], steps, hg_alpha)
+    w.wall = True
+    return w
+
+
+def batched_specimens(count: int = 256, seed: int = 0, n_min: int = 2000, n_max: int = 200000,
+                      spacing: float = 0.5e-3, jitter: float = 0.01) -> list:
+    """Independent tensile bars with particle counts log-uniform in
+    [n_min, n_max] (lattice nx = ny, nz = 4 nx drawn from the seed) and
+    Johnson-Cook damage constants D1, D2, D3 and C each drawn uniformly within
+    +-20% of the 1M-particle bar's."""
+    u = uniform(seed, 5 * count, stream=11).reshape(count, 5)
+    out = []
+    for k in range(count):
+        n = math.exp(math.log(n_min) + u[k, 0] * (math.log(n_max) - math.log(n_min)))
+        nx = max(3, int(round((n / 4.0) ** (1.0 / 3.0))))
+        nz = 4 * nx
+        mat = aluminium_jc()
+        for c, key in enumerate(("D1", "D2", "D3", "C"), start=1):
+            mat[key] *= 0.8 + 0.4 * u[k, c]
+        sp = tensile_bar(nx, nx, nz, spacing, jitter, seed=seed * 100003 + k, name=f"bar_{k}")
+        out.append(_workload(f"batched_bar_{k}_{nx}x{nx}x{nz}", sp, [mat], 0))
+    return out
+
+
+def serving_requests(count: int = 64, rate: float = 20.0, seed: int = 0, steps_range=(1000, 5000),
+                     taylor_fraction: float = 0.5, n_range=(12000, 500000), bar_range=(2000, 200000)) -> list:
+    """A Poisson request stream: (arrival time [s], workload, steps).  Half the
+    requests (in expectation) are Taylor-impact cylinders (12k-500k particles
+    log-uniform, v_impact uniform in [150, 300] m/s), the others tensile bars
+    as in the batched workload; each asks for a uniform number of steps in
+    steps_range."""
+    u = uniform(seed, 6 * count, stream=13).reshape(count, 6)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += -math.log(1.0 - u[k, 0]) / rate
+        steps = int(steps_range[0] + u[k, 1] * (steps_range[1] - steps_range[0]))
+        if u[k, 2] < taylor_fraction:
+            n = math.exp(math.log(n_range[0]) + u[k, 3] * (math.log(n_range[1]) - math.log(n_range[0])))
+            w = taylor_impact(int(n), v_impact=150.0 + 150.0 * u[k, 4], seed=seed * 7919 + k, steps=steps)
+        else:
+            n = math.exp(math.log(bar_range[0]) + u[k, 3] * (math.log(bar_range[1]) - math.log(bar_range[0])))
+            nx = max(3, int(round((n / 4.0) ** (1.0 / 3.0))))
+            sp = tensile_bar(nx, nx, 4 * nx, 0.5e-3, 0.01, seed=seed * 7919 + k, name=f"req_bar_{k}")
+            w = _workload(f"req_bar_{k}", sp, [aluminium_jc()], steps)
+        out.append((t, w, steps))
+    return out

@@ -169,6 +169,7 @@ def mixed_algorithmic_bytes(N: int, nnz: int):
 
 
 FLAG_SPATIAL_ORDER = 1
+FLAG_WALL = 2
 
 
 def make_config(h, rc, dt, hg_alpha, precision="fp64", flags=0) -> Config:
@@ -211,7 +212,7 @@ class Simulation:
     stream: torch.cuda.Stream or raw handle; default the current stream."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
-                 precision="fp64", arena=None, nnz_cap=0, stream=None, spatial_order=False):
+                 precision="fp64", arena=None, nnz_cap=0, stream=None, spatial_order=False, wall=False):
         L = load()
         X = _host(X, np.float64)
         self.N = N = X.shape[0]
@@ -221,7 +222,8 @@ class Simulation:
         bc_mask = _host(bc_mask, np.uint8)
         bc_vel = _host(bc_vel, np.float64, (N, 3))
         f0 = _host(f0, np.float64)
-        self.cfg = make_config(h, rc, dt, hg_alpha, precision, FLAG_SPATIAL_ORDER if spatial_order else 0)
+        self.cfg = make_config(h, rc, dt, hg_alpha, precision,
+                               (FLAG_SPATIAL_ORDER if spatial_order else 0) | (FLAG_WALL if wall else 0))
         self.precision = precision
         self.arena = arena
         self.stream = _stream_handle(stream)
@@ -244,6 +246,7 @@ class Simulation:
     @classmethod
     def from_workload(cls, w, precision="fp64", **kw):
         sp = w.specimen
+        kw.setdefault("wall", getattr(w, "wall", False))
         return cls(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, w.materials, w.h, w.rc, w.dt,
                    w.hg_alpha, precision=precision, **kw)
 

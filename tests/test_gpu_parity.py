@@ -248,3 +248,16 @@ def test_full_size_tensile_bar_jc_sampled():
             rj = col[row_ptr[j]:row_ptr[j + 1]]
             k = np.searchsorted(rj, i)
             assert k < len(rj) and rj[k] == i
+
+
+def test_taylor_impact_with_wall():
+    """Rigid-wall impact at 250 m/s: FP64 GPU against the oracle through and
+    after first contact; the mixed path within its tolerance."""
+    w = S.taylor_impact(3000, v_impact=250.0, steps=120)
+    gs, os_ = _run_both(w, 120)
+    assert os_["ep"].max() > 0.01
+    assert np.min(w.specimen.X[:, 2] + gs["U"][:, 2]) >= 0.0
+    compare_state(gs, os_, w, tol=TRAJ_TOL)
+    gm = gpu_sim(w, "mixed")
+    gm.step(120)
+    compare_state(gm.state(), os_, w, tol=2e-3, fields=("U", "V", "F"))

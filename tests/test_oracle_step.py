@@ -174,3 +174,35 @@ def test_failure_trajectory_invariants():
         prev = st
     assert (prev["fail_step"] >= 0).sum() > 0
     assert sim.status == 0
+
+
+def test_rigid_wall_contact():
+    """Kinematic wall on z = 0 (Taylor impact): no particle ever ends below
+    the plane, the run is untouched before first contact, the wall's impulse
+    points out of it, and kinetic energy is lost to plastic work."""
+    w = S.taylor_impact(2000, v_impact=250.0, steps=150)
+    free = oracle.Simulation.from_workload(w, wall=False)
+    o = oracle.Simulation.from_workload(w)
+    X = w.specimen.X
+    m = w.specimen.vol * w.materials[0]["rho0"]
+    pz0 = np.sum(m * o["v"][:, 2])
+    # first contact: the lowest layer (z = spacing/2) reaches the plane after
+    # about z / v / dt steps
+    first = int(0.5 * w.specimen.spacing / 250.0 / w.dt)
+    o.step(first - 1)
+    free.step(first - 1)
+    assert np.array_equal(o["u"], free["u"]) and np.array_equal(o["v"], free["v"])
+    ke = [0.5 * np.sum(m * np.sum(o["v"] ** 2, 1))]
+    for _ in range(6):
+        o.step(20)
+        assert np.min(X[:, 2] + o["u"][:, 2]) >= 0.0
+        ke.append(0.5 * np.sum(m * np.sum(o["v"] ** 2, 1)))
+    assert np.sum(m * o["v"][:, 2]) > pz0          # impulse along +z
+    assert ke[-1] < 0.9 * ke[0] and o["ep"].max() > 0.01
+
+
+def test_body_resting_on_the_wall_stays_at_rest():
+    w = S.taylor_impact(1500, v_impact=0.0, steps=10)
+    o = oracle.Simulation.from_workload(w)
+    o.step(30)
+    assert np.abs(o["v"]).max() == 0.0 and np.abs(o["sigma"]).max() == 0.0
