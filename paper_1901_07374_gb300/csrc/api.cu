@@ -24,9 +24,10 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 // base and 256-byte aligned.  The neighbour-build scratch overlays the
 // F / sd / sig / A block, which is only initialised after the build.
 struct Layout {
-    size_t X, vol, mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
+    size_t X, vol, mass, inv_mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
     size_t xo, s0, linv32, r1, r2, fsum, ell_off;
+    size_t Fh, Fl, sdh, sdl, sigf;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
     size_t perm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order + staged caller-order inputs
     size_t overlay_end, ell;
@@ -61,6 +62,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.X = c.take(3 * n * d);
     L.vol = c.take(n * d);
     L.mass = c.take(n * d);
+    L.inv_mass = c.take(n * d);
     L.sqrtE = c.take(n * d);
     L.mat = c.take(n * sizeof(int32_t));
     L.bcm = c.take(n);
@@ -90,6 +92,10 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
         L.r1 = c.take(n * 16);
         L.r2 = c.take(6 * n * 16);
         L.fsum = c.take(9 * n * sizeof(float));
+        const size_t f = sizeof(float);
+        L.Fh = c.take(9 * n * f); L.Fl = c.take(9 * n * f);
+        L.sdh = c.take(6 * n * f); L.sdl = c.take(6 * n * f);
+        L.sigf = c.take(6 * n * f);
     }
     // overlay block: F, sd, sig, A  |  neighbour-build scratch
     const size_t ov = c.off;
@@ -163,6 +169,9 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.r1 = at<float4>(base, L.r1);
         s.r2 = at<float4>(base, L.r2);
         s.fsum = at<float>(base, L.fsum);
+        s.Fh = at<float>(base, L.Fh); s.Fl = at<float>(base, L.Fl);
+        s.sdh = at<float>(base, L.sdh); s.sdl = at<float>(base, L.sdl);
+        s.sigf = at<float>(base, L.sigf);
     } else {
         s.fsum = nullptr;
         s.xo = s.s0 = s.r1 = s.r2 = nullptr;
@@ -174,6 +183,7 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
     s.X = at<double>(base, L.X);
     s.vol = at<double>(base, L.vol);
     s.mass = at<double>(base, L.mass);
+    s.inv_mass = at<double>(base, L.inv_mass);
     s.sqrtE = at<double>(base, L.sqrtE);
     s.mat = at<int32_t>(base, L.mat);
     s.bcm = at<uint8_t>(base, L.bcm);
@@ -280,6 +290,9 @@ DevMat make_dev_mat(const tlsph_material &m)
     d.fN = m.fN; d.eN = m.eN; d.sN = m.sN; d.fc = m.fc; d.fF = m.fF; d.komega = m.komega;
     d.nucl_coef = m.sN > 0.0 ? m.fN / (m.sN * sqrt(2.0 * M_PI)) : 0.0;
     d.fstar_slope = (m.fF > m.fc) ? (1.0 / m.q1 - m.fc) / (m.fF - m.fc) : 0.0;
+    d.Kf = (float)d.K; d.Gf = (float)d.G; d.Af = (float)d.A; d.Bf = (float)d.B; d.nf = (float)d.n;
+    d.Cf = (float)d.C; d.inv_epsdot0f = (float)d.inv_epsdot0; d.rho0c02f = (float)d.rho0c02;
+    d.S_alphaf = (float)d.S_alpha; d.Gamma0f = (float)d.Gamma0; d.sqrtEf = (float)d.sqrtE;
     return d;
 }
 
@@ -374,6 +387,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     CK(cudaMemcpyAsync(stf0, f0_h.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
     CK(cudaMemsetAsync((void *)s.mass, 0, n * sizeof(double), st));
+    CK(cudaMemsetAsync((void *)s.inv_mass, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync((void *)s.sqrtE, 0, n * sizeof(double), st));
 
     // ---- neighbour CSR
@@ -489,6 +503,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
 
     // ---- initial state (overwrites the scratch overlay)
     CK(launch_init_state(s, st));
+    if (mixed) CK(mixed_import(*ctx, -1, st));
     CK(cudaStreamSynchronize(st));
 #undef CK
     ctx->need_predict = true;
@@ -744,6 +759,10 @@ int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, in
             }
         }
         e = cudaMemcpyAsync(f.ptr, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess && ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
+        e = mixed_import(*ctx, field, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state");

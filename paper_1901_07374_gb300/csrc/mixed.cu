@@ -51,6 +51,7 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     c.dt = cfg.dt;
     c.half_dt = 0.5 * cfg.dt;
     c.inv_h = (float)(1.0 / cfg.h);
+    c.dt_dw = (float)(cfg.dt / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
     c.dw_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
     c.w_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h));
     c.hg_coef = (float)(-0.5 * cfg.hg_alpha);
@@ -162,9 +163,90 @@ __device__ __forceinline__ float3 xdiff(const MixConst &c, const float4 oj, cons
 
 __device__ __forceinline__ int row_bias(const MixConst &c, const float4 oi) { return c.bias - __float_as_int(oi.w); }
 
+// ------------------------------------------------------------------ compensated FP32
+// A value carried as an unevaluated sum hi + lo of two floats keeps about 46
+// significant bits, enough for quantities that accumulate small increments
+// over many steps (F, the stress deviator).  The pair is kept canonical
+// (hi = round(hi + lo)) and lo is rounded to 2^-45 of hi's binade, so
+// hi + lo is exactly a double: export to FP64 and import back reproduce the
+// pair bit for bit (checkpoints resume exactly).  The __fadd_rn forms keep
+// the compiler from contracting or reordering the error-free transformations
+// (Knuth's TwoSum, Dekker's FastTwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// canonical pair from h + l with |l| <= ulp(h): l on the grid 2^(E(h) - 45)
+__device__ __forceinline__ void df_norm(float &h, float &l)
+{
+    const float p = __int_as_float(__float_as_int(h) & 0x7f800000);   // 2^E(h); 0 below the normal range
+    const float C = p * 3.5762786865234375e-7f;                          // 1.5 * 2^(E - 22)
+    const float lq = __fsub_rn(__fadd_rn(l, C), C);
+    const float hn = __fadd_rn(h, lq);
+    l = __fsub_rn(lq, __fsub_rn(hn, h));
+    h = hn;
+}
+// (h, l) += x
+__device__ __forceinline__ void df_add(float &h, float &l, float x)
+{
+    float s, e;
+    two_sum(h, x, s, e);
+    e = __fadd_rn(e, l);
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+    df_norm(h, l);
+}
+__device__ __forceinline__ void df_split(double x, float &h, float &l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+    df_norm(h, l);
+}
+__device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
+
+// single-precision flow stress sigma_f of Algorithm 1 (Johnson-Cook hardening
+// and lagged rate factor, as jc_hard * jc_rate)
+__device__ __forceinline__ float jc_flow_f(const DevMat &m, float ep, float epdot)
+{
+    float r = 1.0f;
+    if (m.Cf != 0.0f && m.inv_epsdot0f > 0.0f) {
+        const float x = epdot * m.inv_epsdot0f;
+        if (x > 1.0f) r = 1.0f + m.Cf * logf(x);
+    }
+    return (ep > 0.0f ? m.Af + m.Bf * powf(ep, m.nf) : m.Af) * r;
+}
+// single-precision mean stress (eos_sm) from J - 1
+__device__ __forceinline__ float eos_sm_f(const DevMat &m, float Jm1, float J, float D)
+{
+    float sm;
+    if (m.eos == 0) {
+        sm = m.Kf * Jm1;
+    } else {
+        const float eta = 1.0f / J, mu = -Jm1 * eta;
+        const float den = eta - m.S_alphaf * mu;
+        sm = -m.rho0c02f * mu * (eta - 0.5f * m.Gamma0f * mu) / (den * den);
+    }
+    return sm > 0.0f ? sm * (1.0f - D) : sm;
+}
+
+// relative guard band of the single-precision yield screen: the FP32 values
+// of sigma_eq^2 and sigma_f^2 are within 2e-6 of their FP64 counterparts, so
+// sigma_eq^2 <= sigma_f^2 (1 - 1e-5) in FP32 implies the FP64 test passes
+static constexpr float YIELD_GUARD = 1.0f - 1e-5f;
+
 // ------------------------------------------------------------------ pass 1, per particle
 // F^{n+1}, J, kinematics, constitutive and damage update, stress, A and the
-// pass-2 record of particle i from its velocity-gradient sums keep[9]
+// pass-2 record of particle i from its velocity-gradient sums keep[9].
+//
+// F and the stress deviator are compensated FP32 pairs.  J - 1 comes from the
+// invariants of G = F - I (det(I + G) = 1 + tr G + m2(G) + det G), accurate
+// to FP32 rounding of J - 1 itself.  A particle whose FP32 trial stress lies
+// inside the yield surface by more than the guard band takes the elastic
+// branch of Algorithm 1 in FP32 (no plastic increment, so no damage
+// increment); every other particle (yielding, near yield, GTN, damage at or
+// past initiation) runs the FP64 material update.
 __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
     const double *__restrict__ Dn = s.D[c.dcur];
@@ -173,96 +255,138 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     const int64_t N = c.N;
     const int fail = s.fail[i];
     const double *un = s.u[c.ucur ^ 1];   // u^{n+1}, mirrored for pass 2's hourglass term
-    const double Vi = s.vol[i];
+    const float Vf = (float)s.vol[i];
+    float Fh[9], Fl[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { Fh[k] = s.Fh[k * N + i]; Fl[k] = s.Fl[k * N + i]; }
+    const float u0 = (float)un[3 * i], u1 = (float)un[3 * i + 1], u2 = (float)un[3 * i + 2];
     if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
         Dnext[i] = Dn[i];
-        const double *F = s.F + 9 * i;
         r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         r2[N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2[2 * N + i] = make_float4(0.f, 0.f, (float)Vi, (float)un[3 * i]);
-        r2[3 * N + i] = make_float4((float)un[3 * i + 1], (float)un[3 * i + 2], (float)(F[0] - 1.0), (float)F[1]);
-        r2[4 * N + i] = make_float4((float)F[2], (float)F[3], (float)(F[4] - 1.0), (float)F[5]);
-        r2[5 * N + i] = make_float4((float)F[6], (float)F[7], (float)(F[8] - 1.0), 0.f);
+        r2[2 * N + i] = make_float4(0.f, 0.f, Vf, u0);
+        r2[3 * N + i] = make_float4(u1, u2, (Fh[0] - 1.0f) + Fl[0], Fh[1] + Fl[1]);
+        r2[4 * N + i] = make_float4(Fh[2] + Fl[2], Fh[3] + Fl[3], (Fh[4] - 1.0f) + Fl[4], Fh[5] + Fl[5]);
+        r2[5 * N + i] = make_float4(Fh[6] + Fl[6], Fh[7] + Fl[7], (Fh[8] - 1.0f) + Fl[8], 0.f);
         return;
     }
     float Li[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Li[k] = s.linv32[9 * i + k];
-    float Fdf[9];
+    // dF = dt Fdot (Fdot = M L^{-1}, Sec. 3.1); F^{n+1} = F^n + dF compensated
+    float dF[9];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int l = 0; l < 3; ++l)
-            Fdf[3 * k + l] = c.dw_norm * (keep[3 * k] * Li[l] + keep[3 * k + 1] * Li[3 + l] + keep[3 * k + 2] * Li[6 + l]);
-    // F^{n+1} and J in FP64
-    double Fn[9];
+            dF[3 * k + l] = c.dt_dw * (keep[3 * k] * Li[l] + keep[3 * k + 1] * Li[3 + l] + keep[3 * k + 2] * Li[6 + l]);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Fn[k] = s.F[9 * i + k] + c.dt * (double)Fdf[k];
-    const double J = Fn[0] * (Fn[4] * Fn[8] - Fn[5] * Fn[7]) + Fn[1] * (Fn[5] * Fn[6] - Fn[3] * Fn[8])
-                   + Fn[2] * (Fn[3] * Fn[7] - Fn[4] * Fn[6]);
+    for (int k = 0; k < 9; ++k) {
+        df_add(Fh[k], Fl[k], dF[k]);
+        s.Fh[k * N + i] = Fh[k];
+        s.Fl[k * N + i] = Fl[k];
+    }
+    // G = F - I (the diagonal's hi - 1 is exact for hi in [0.5, 2])
+    float G[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s.F[9 * i + k] = Fn[k];
-    if (!(J > 0.0) || !isfinite(J)) {
+    for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? Fh[k] - 1.0f : Fh[k]) + Fl[k];
+    const float m2 = (G[0] * G[4] - G[1] * G[3]) + (G[4] * G[8] - G[5] * G[7]) + (G[0] * G[8] - G[2] * G[6]);
+    const float m3 = G[0] * (G[4] * G[8] - G[5] * G[7]) + G[1] * (G[5] * G[6] - G[3] * G[8])
+                   + G[2] * (G[3] * G[7] - G[4] * G[6]);
+    const float Jm1 = (G[0] + G[4] + G[8]) + (m2 + m3);
+    const float Jf = 1.0f + Jm1;
+    if (!(Jf > 0.0f) || !isfinite(Jm1)) {
         atomicOr(s.status, TLSPH_ST_BAD_J);
         Dnext[i] = Dn[i];
         return;
     }
-    // kinematics in FP32
-    float Ff[9], cf[9], Fi[9], Lv[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Ff[k] = (float)Fn[k];
-    cof3f(Ff, cf);
-    const float iJ = (float)(1.0 / J);
+    // kinematics: F^{-1} = cof^T / J, dt L_v = dF F^{-1}, rotation R of F^{n+1},
+    // unrotated strain increment dh = R^T sym(dt L_v) R
+    float cf[9], Fi[9], Lv[9];
+    cof3f(Fh, cf);
+    const float iJ = 1.0f / Jf;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int l = 0; l < 3; ++l) Fi[3 * k + l] = cf[3 * l + k] * iJ;
-    mul3f(Fdf, Fi, Lv);
+    mul3f(dF, Fi, Lv);
     const float d[6] = { Lv[0], Lv[4], Lv[8], 0.5f * (Lv[1] + Lv[3]), 0.5f * (Lv[5] + Lv[7]), 0.5f * (Lv[2] + Lv[6]) };
     float R[9];
-    uint32_t st = polar_rotation_f(Ff, R) ? 0u : TLSPH_ST_POLAR_CAP;
+    uint32_t st = polar_rotation_f(Fh, R) ? 0u : TLSPH_ST_POLAR_CAP;
     float dh[6];
     sym_rotate_t_f(R, d, dh);
-    double de[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) de[k] = c.dt * (double)dh[k];
 
-    // constitutive and damage update in FP64
-    MPState mp;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) mp.sd[k] = s.sd[6 * i + k];
-    mp.sm = 0.0;
-    mp.ep = s.ep[i];
-    mp.epdot = s.epdot[i];
-    mp.dinit = s.dinit[i];
-    mp.D = Dn[i];
-    mp.f = s.por[i];
-    mp.failed = 0;
     const DevMat &mat = s.mats[s.mat[i]];
-    st |= material_update(mat, c.dt, de, J, mp);
+    const double Dd = Dn[i];
+    const double dinit = s.dinit[i];
+    const double epdot = s.epdot[i];
+    float sdh[6], sdl[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) s.sd[6 * i + k] = mp.sd[k];
-    s.ep[i] = mp.ep;
-    s.epdot[i] = mp.epdot;
-    s.dinit[i] = mp.dinit;
-    s.por[i] = mp.f;
-    Dnext[i] = mp.D;
+    for (int k = 0; k < 6; ++k) { sdh[k] = s.sdh[k * N + i]; sdl[k] = s.sdl[k * N + i]; }
+    // FP32 screen (elastic branch of Algorithm 1)
+    const float omDf = 1.0f - (float)Dd;
+    const float trc = (dh[0] + dh[1] + dh[2]) * (1.0f / 3.0f);
+    const float g2 = 2.0f * mat.Gf * omDf;
+    float inc[6] = { g2 * (dh[0] - trc), g2 * (dh[1] - trc), g2 * (dh[2] - trc), g2 * dh[3], g2 * dh[4], g2 * dh[5] };
+    float tr[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) tr[k] = sdh[k] + inc[k];
+    const float s2 = 1.5f * ((tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]) +
+                             2.0f * (tr[3] * tr[3] + tr[4] * tr[4] + tr[5] * tr[5]));
+    const float sf = jc_flow_f(mat, (float)s.ep[i], (float)epdot) * omDf;
+    const bool fast = mat.damage != TLSPH_DAMAGE_GTN && dinit < 1.0 && sf > 0.0f && s2 <= sf * sf * YIELD_GUARD;
+    float sm;
+    double Dnew;
+    bool failed = false;
+    if (fast) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) df_add(sdh[k], sdl[k], inc[k]);
+        if (epdot != 0.0) s.epdot[i] = 0.0;
+        sm = eos_sm_f(mat, Jm1, Jf, (float)Dd);
+        Dnew = mat.damage == TLSPH_DAMAGE_NONE ? Dd : 0.0;   // D from D_init < 1
+    } else {
+        MPState mp;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) mp.sd[k] = df_value(sdh[k], sdl[k]);
+        mp.sm = 0.0;
+        mp.ep = s.ep[i];
+        mp.epdot = epdot;
+        mp.dinit = dinit;
+        mp.D = Dd;
+        mp.f = s.por[i];
+        mp.failed = 0;
+        double de[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) de[k] = (double)dh[k];
+        st |= material_update(mat, c.dt, de, 1.0 + (double)Jm1, mp);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) df_split(mp.sd[k], sdh[k], sdl[k]);
+        s.ep[i] = mp.ep;
+        s.epdot[i] = mp.epdot;
+        s.dinit[i] = mp.dinit;
+        s.por[i] = mp.f;
+        sm = (float)mp.sm;
+        Dnew = mp.D;
+        failed = mp.failed != 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { s.sdh[k * N + i] = sdh[k]; s.sdl[k * N + i] = sdl[k]; }
+    Dnext[i] = Dnew;
 
     float A[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
-    if (mp.failed) {
+    if (failed) {
         s.fail[i] = (int32_t)(c.step_index + 1);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s.sig[6 * i + k] = 0.0;
+        for (int k = 0; k < 6; ++k) s.sigf[k * N + i] = 0.0f;
     } else {
-        const float sh[6] = { (float)(mp.sd[0] + mp.sm), (float)(mp.sd[1] + mp.sm), (float)(mp.sd[2] + mp.sm),
-                              (float)mp.sd[3], (float)mp.sd[4], (float)mp.sd[5] };
+        // sigma = R (sigma_m I + s_hat) R^T ;  P = J sigma F^{-T} ;  A = P L^{-T}
+        const float sh[6] = { sdh[0] + sm, sdh[1] + sm, sdh[2] + sm, sdh[3], sdh[4], sdh[5] };
         float sg[6];
         sym_rotate_f(R, sh, sg);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s.sig[6 * i + k] = (double)sg[k];
+        for (int k = 0; k < 6; ++k) s.sigf[k * N + i] = sg[k];
         float S[9] = { sg[0], sg[3], sg[5], sg[3], sg[1], sg[4], sg[5], sg[4], sg[2] }, P[9];
         mul3f_bt(S, Fi, P);
-        const float Jf = (float)J;
 #pragma unroll
         for (int k = 0; k < 9; ++k) P[k] *= Jf;
         mul3f_bt(P, Li, A);
@@ -271,13 +395,13 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
         for (int k = 0; k < 9; ++k) fin &= isfinite(A[k]);
         if (!fin) st |= TLSPH_ST_NONFINITE;
     }
-    const double omd = 1.0 - mp.D;
+    const float omd = 1.0f - (float)Dnew;
     r2[i] = make_float4(A[0], A[1], A[2], A[3]);
     r2[N + i] = make_float4(A[4], A[5], A[6], A[7]);
-    r2[2 * N + i] = make_float4(A[8], (float)(Vi * omd), (float)Vi, (float)un[3 * i]);
-    r2[3 * N + i] = make_float4((float)un[3 * i + 1], (float)un[3 * i + 2], (float)(Fn[0] - 1.0), (float)Fn[1]);
-    r2[4 * N + i] = make_float4((float)Fn[2], (float)Fn[3], (float)(Fn[4] - 1.0), (float)Fn[5]);
-    r2[5 * N + i] = make_float4((float)Fn[6], (float)Fn[7], (float)(Fn[8] - 1.0), (float)(s.sqrtE[i] * Vi * omd));
+    r2[2 * N + i] = make_float4(A[8], Vf * omd, Vf, u0);
+    r2[3 * N + i] = make_float4(u1, u2, G[0], G[1]);
+    r2[4 * N + i] = make_float4(G[2], G[3], G[4], G[5]);
+    r2[5 * N + i] = make_float4(G[6], G[7], G[8], (float)s.sqrtE[i] * Vf * omd);
     if (st) atomicOr(s.status, st);
 }
 
@@ -422,7 +546,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         f[1] += hc * (double)keep[7];
         f[2] += hc * (double)keep[8];
     }
-    const double im = 1.0 / s.mass[i];
+    const double im = s.inv_mass[i];
     const int fail = s.fail[i];
     double vn[3], v2[3];
 #pragma unroll
@@ -710,7 +834,61 @@ __global__ void k_mixed_export_A(DevState s)
     for (int k = 0; k < 9; ++k) s.A[9 * i + k] = (double)A[k];
 }
 
+// compensated F, stress deviator and FP32 stress -> FP64 arrays (which = bit
+// set of 1 F, 2 stress deviator, 4 Cauchy stress)
+__global__ void k_mixed_export(DevState s, int which)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = s.N;
+    if (i >= N) return;
+    if (which & 1)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s.F[9 * i + k] = df_value(s.Fh[k * N + i], s.Fl[k * N + i]);
+    if (which & 2)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s.sd[6 * i + k] = df_value(s.sdh[k * N + i], s.sdl[k * N + i]);
+    if (which & 4)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s.sig[6 * i + k] = (double)s.sigf[k * N + i];
+}
+
+// FP64 arrays -> compensated state (same bit set)
+__global__ void k_mixed_import(DevState s, int which)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = s.N;
+    if (i >= N) return;
+    if (which & 1)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) df_split(s.F[9 * i + k], s.Fh[k * N + i], s.Fl[k * N + i]);
+    if (which & 2)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) df_split(s.sd[6 * i + k], s.sdh[k * N + i], s.sdl[k * N + i]);
+    if (which & 4)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s.sigf[k * N + i] = (float)s.sig[6 * i + k];
+}
+
+static int mixed_field_bits(int field)
+{
+    switch (field) {
+    case -1: return 7;
+    case TLSPH_FIELD_F: return 1;
+    case TLSPH_FIELD_STRESS_DEV: return 2;
+    case TLSPH_FIELD_SIGMA: return 4;
+    default: return 0;
+    }
+}
+
 static unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t mixed_import(const tlsph_ctx &ctx, int field, cudaStream_t st)
+{
+    const int bits = mixed_field_bits(field);
+    if (bits == 0 || ctx.N == 0) return cudaSuccess;
+    k_mixed_import<<<nb(ctx.N, 256), 256, 0, st>>>(ctx.s, bits);
+    return cudaGetLastError();
+}
 
 cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPack &pk, cudaStream_t st)
 {
@@ -792,11 +970,12 @@ int mixed_kernels_per_step(const tlsph_ctx &ctx) { return (ctx.plan[0] >= 2 ? 2 
 
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st)
 {
-    if (field == TLSPH_FIELD_A && ctx.steps > 0) {
+    if (ctx.N == 0) return cudaSuccess;
+    if ((field == TLSPH_FIELD_A || field == -1) && ctx.steps > 0)
         k_mixed_export_A<<<nb(ctx.N, 256), 256, 0, st>>>(ctx.s);
-        return cudaGetLastError();
-    }
-    return cudaSuccess;
+    const int bits = mixed_field_bits(field);
+    if (bits) k_mixed_export<<<nb(ctx.N, 256), 256, 0, st>>>(ctx.s, bits);
+    return cudaGetLastError();
 }
 
 void mixed_release(tlsph_ctx &) {}

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass2_fp64(DevState s, StepCon
 #pragma unroll
         for (int k = 0; k < 3; ++k) f[k] += hc * keep[6 + k];
     }
-    const double im = 1.0 / s.mass[i];
+    const double im = s.inv_mass[i];
     const int fail = s.fail[i];
     double vn[3], v2[3];
 #pragma unroll
@@ -355,6 +355,7 @@ __global__ void k_material_fields(DevState s, int mat_id, int dcur, int set_gtn_
     if (i >= s.N || s.mat[i] != mat_id) return;
     const DevMat &m = s.mats[mat_id];
     const_cast<double *>(s.mass)[i] = m.rho0 * s.vol[i];
+    const_cast<double *>(s.inv_mass)[i] = 1.0 / (m.rho0 * s.vol[i]);
     const_cast<double *>(s.sqrtE)[i] = m.sqrtE;
     if (set_gtn_damage && m.damage == TLSPH_DAMAGE_GTN) s.D[dcur][i] = m.q1 * gtn_fstar(m, s.por[i]);
 }
@@ -364,7 +365,7 @@ __global__ void k_predict(DevState s, int ucur, double dt, int wall)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    const double im = 1.0 / s.mass[i];
+    const double im = s.inv_mass[i];
     double v[3], u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) v[k] = s.v[3 * i + k] + 0.5 * dt * (s.force[3 * i + k] * im);

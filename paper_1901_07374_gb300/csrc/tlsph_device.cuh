@@ -354,7 +354,7 @@ __device__ __forceinline__ uint32_t material_update(const DevMat &m, double dt, 
             for (int k = 0; k < 6; ++k) s.sd[k] = sc * tr[k];
         }
         s.ep += dep;
-        s.epdot = dep / dt;
+        s.epdot = dep > 0.0 ? dep / dt : 0.0;
         s.sm = eos_sm(m, J, s.D);
     }
     // damage initiation and evolution (no plastic increment: D_init unchanged)

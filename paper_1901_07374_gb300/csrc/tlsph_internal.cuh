@@ -25,6 +25,8 @@ struct DevMat {
     double q1, q2, q3, fN, eN, sN, fc, fF, komega;
     double nucl_coef;    // fN / (sN sqrt(2 pi))
     double fstar_slope;  // (1/q1 - fc) / (fF - fc)
+    // single-precision copies for the mixed path's elastic fast path
+    float Kf, Gf, Af, Bf, nf, Cf, inv_epsdot0f, rho0c02f, S_alphaf, Gamma0f, sqrtEf;
 };
 
 // Packed cell coordinates of the mixed path: positions travel as the offset
@@ -47,6 +49,7 @@ struct DevState {
     const double *X;        // N*3
     const double *vol;      // N
     const double *mass;     // N   rho0 V
+    const double *inv_mass; // N   1 / (rho0 V)
     const double *sqrtE;    // N   sqrt of the particle's Young modulus (hourglass stiffness)
     const int32_t *mat;     // N
     const uint8_t *bcm;     // N
@@ -74,6 +77,12 @@ struct DevState {
     float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
     float4 *r2;             // 6 x N pass-2 gather record (SoA of float4, see mixed.cu)
     float *fsum;            // 9 x N pass-1 pair sums (split launch plans)
+    // mixed path: F and the stress deviator as compensated FP32 pairs (value =
+    // hi + lo, SoA by component: component k of particle i at k N + i); the
+    // FP64 arrays F, sd and sig are refreshed from these when read
+    float *Fh, *Fl;         // 9 x N deformation gradient
+    float *sdh, *sdl;       // 6 x N unrotated stress deviator
+    float *sigf;            // 6 x N Cauchy stress
     const int32_t *colE;    // sliced-ELL neighbour columns (slices of 32 rows)
     const int64_t *ell_off; // (N + 31) / 32 + 1 slice offsets
     double vref[3];         // bulk reference velocity of the r1 mirror
@@ -188,7 +197,7 @@ void set_last_error_text(const std::string &msg);
 // mixed.cu -- step constants of the mixed path (defined there)
 struct MixConst {
     double dt, half_dt;
-    float inv_h, dw_norm, w_norm, hg_coef, cs;
+    float dt_dw, inv_h, dw_norm, w_norm, hg_coef, cs;   // dt_dw = dt x W' normalisation
     double vref0, vref1, vref2;
     int64_t N;
     int64_t step_index;
@@ -215,7 +224,11 @@ cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPac
 cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st);
 cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st);
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
+// FP64 arrays -> compensated mixed state for one field (TLSPH_FIELD_F,
+// _STRESS_DEV, _SIGMA) or all of them (-1)
+cudaError_t mixed_import(const tlsph_ctx &ctx, int field, cudaStream_t st);
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
+// compensated mixed state -> FP64 arrays for one field or all (-1)
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st);
 int mixed_kernels_per_step(const tlsph_ctx &ctx);
 void mixed_release(tlsph_ctx &ctx);

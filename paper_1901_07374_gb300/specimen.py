@@ -287,6 +287,35 @@ def failure_variant(w: Workload, v_grip: float = 20.0, scale: float = 0.02) -> W
     return dataclasses.replace(w, name=w.name + "_failure", specimen=sp, materials=mats)
 
 
+def plastic_flow_state(w: Workload, strain: float = 0.01) -> dict:
+    """A starting state in which every particle of a tensile bar flows
+    plastically: an affine isochoric stretch F = diag(1 - e/2, 1 - e/2, 1 + e)
+    about the bar's centroid, the matching affine velocity field of the grip
+    rate (strain rate 2 v_grip / length), and an uniaxial unrotated stress
+    deviator diag(-1, -1, 2) A / 3 whose von Mises value is the yield stress A
+    of the first material.  Returned as caller-order fields (U, V, F,
+    STRESS_DEV; tensors as 9 row-major components per particle) to load
+    with set_state before stepping."""
+    sp = w.specimen
+    X = sp.X
+    c = X.mean(axis=0)
+    length = float(X[:, 2].max() - X[:, 2].min())
+    vz = float(np.abs(sp.bc_vel[:, 2]).max())
+    rate = 2.0 * vz / length if length > 0 else 0.0
+    shape = np.array([-0.5, -0.5, 1.0])
+    N = sp.N
+    F = np.zeros((N, 3, 3))
+    F[:, [0, 1, 2], [0, 1, 2]] = 1.0 + strain * shape
+    U = (X - c) * (strain * shape)
+    V = (X - c) * (rate * shape)
+    bc = sp.bc_mask.astype(bool)
+    V[bc] = sp.bc_vel[bc]
+    A = float(w.materials[0]["A"])
+    S = np.zeros((N, 3, 3))
+    S[:, [0, 1, 2], [0, 1, 2]] = np.array([-1.0, -1.0, 2.0]) * (A / 3.0)
+    return {"U": U, "V": V, "F": F.reshape(N, 9), "STRESS_DEV": S.reshape(N, 9)}
+
+
 def taylor_impact(n_particles: int = 12000, spacing: float = 0.5e-3, v_impact: float = 200.0, seed: int = 0,
                   steps: int = 1000, scale: float = 1.0, hg_alpha: float = HG_ALPHA) -> Workload:
     """Taylor impact: a cylinder (length/diameter 3.2, about n_particles

@@ -143,6 +143,31 @@ def test_one_step_from_plastic_state_jc_gtn(make):
     compare_state(gs, os_, w)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("mixed", 2e-4)])
+def test_plastic_flow_window(precision, tol):
+    """Every particle flowing plastically (the plastic-flow starting state):
+    ten steps through the radial return and Johnson-Cook damage accumulation,
+    against the oracle from the same state.  In the mixed path every particle
+    takes the FP64 constitutive branch here."""
+    w = S.tensile_bar_jc(nx=9, ny=9, nz=20, steps=10)
+    st = S.plastic_flow_state(w)
+    g = gpu_sim(w, precision)
+    for k, v in st.items():
+        g.set(k, v)
+    o = oracle.Simulation.from_workload(w)
+    o["u"][:] = st["U"]
+    o["v"][:] = st["V"]
+    o["F"][:] = st["F"].reshape(-1, 9)
+    o["sd"][:] = st["STRESS_DEV"].reshape(-1, 9)
+    g.step(10)
+    o.step(10)
+    assert g.status_bits() == 0
+    got = g.state()
+    assert np.mean(got["EPSP"] > 0) > 0.5
+    compare_state(got, o.state(), w, tol=tol,
+                  fields=("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "DINIT", "FORCE", "A"))
+
+
 def test_gtn_notched_bar_small():
     """GTN porous plasticity on a small notched round bar (f0 from the seed)."""
     w = S.notched_bar_gtn(radius=2.0e-3, height=6e-3, spacing=0.3e-3, notch_radius=0.6e-3, v_grip=20.0, steps=300)

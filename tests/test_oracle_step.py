@@ -206,3 +206,26 @@ def test_body_resting_on_the_wall_stays_at_rest():
     o = oracle.Simulation.from_workload(w)
     o.step(30)
     assert np.abs(o["v"]).max() == 0.0 and np.abs(o["sigma"]).max() == 0.0
+
+
+def test_plastic_flow_state_yields_everywhere():
+    """The plastic-flow starting state puts every particle of a tensile bar on
+    the yield surface (von Mises of the deviator = A) with a stretching
+    velocity field, so one oracle step gives a plastic increment to each
+    particle whose neighbourhood is a full sphere."""
+    w = S.tensile_bar_jc(nx=9, ny=9, nz=20, steps=10)
+    st = S.plastic_flow_state(w)
+    sd = st["STRESS_DEV"].reshape(-1, 9)
+    vm = np.sqrt(1.5 * np.sum(sd * sd, axis=1))
+    assert np.allclose(vm, w.materials[0]["A"], rtol=1e-14)
+    o = oracle.Simulation.from_workload(w)
+    o["u"][:] = st["U"]
+    o["v"][:] = st["V"]
+    o["F"][:] = st["F"].reshape(-1, 9)
+    o["sd"][:] = sd
+    o.step(1)
+    X = w.specimen.X
+    lo, hi = X.min(0) + 3 * w.specimen.spacing, X.max(0) - 3 * w.specimen.spacing
+    inner = np.all((X > lo) & (X < hi), axis=1)
+    assert inner.sum() > 50
+    assert np.all(o["ep"][inner] > 0.0)
