@@ -216,6 +216,19 @@ int tlsph_destroy(tlsph_ctx *ctx);
 int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);
 int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
 
+/* Form of the mixed path's sliced neighbour lists (the thread-per-row plans
+ * read the fixed neighbour sets of Sec. 2.2 through them; the paper has no
+ * counterpart of the layout).  A slice is the 32 consecutive rows of one warp.
+ * An "aligned" slice stores the union of its rows' neighbour index offsets
+ * j - i once plus one bit per row and offset; an "explicit" slice stores
+ * every row's neighbour indices, padded to the slice's longest row.  Writes
+ * the number of slices, of aligned slices, of slots (32 x slice width,
+ * summed) and of 4-byte words the lists occupy; each pointer may be NULL.
+ * TLSPH_ERR_STATE if the context has no sliced lists (FP64 precision, or
+ * a caller arena too small for them). */
+int tlsph_neighbor_layout(const tlsph_ctx *ctx, int64_t *slices, int64_t *aligned_slices, int64_t *slots,
+                          int64_t *words);
+
 /* ---- Batched stepping (many specimens advanced together) ----------------
  * A batch advances every member context with one launch per kernel kind and
  * step over all members (a persistent grid striding over every member's

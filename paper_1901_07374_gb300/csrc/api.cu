@@ -26,7 +26,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 struct Layout {
     size_t X, vol, mass, inv_mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
-    size_t xo, s0, linv32, r1, r2, fsum, ell_off;
+    size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
     size_t perm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order + staged caller-order inputs
@@ -88,6 +88,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
         L.xo = c.take(n * 16);
         L.s0 = c.take(n * 16);
         L.ell_off = c.take(((n + 31) / 32 + 1) * sizeof(int64_t));
+        L.ell_w = c.take(((n + 31) / 32) * sizeof(int32_t));
         L.linv32 = c.take(9 * n * sizeof(float));
         L.r1 = c.take(n * 16);
         L.r2 = c.take(6 * n * 16);
@@ -165,6 +166,7 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.xo = at<float4>(base, L.xo);
         s.s0 = at<float4>(base, L.s0);
         s.ell_off = at<int64_t>(base, L.ell_off);
+        s.ell_w = at<int32_t>(base, L.ell_w);
         s.linv32 = at<float>(base, L.linv32);
         s.r1 = at<float4>(base, L.r1);
         s.r2 = at<float4>(base, L.r2);
@@ -176,6 +178,7 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.fsum = nullptr;
         s.xo = s.s0 = s.r1 = s.r2 = nullptr;
         s.ell_off = nullptr;
+        s.ell_w = nullptr;
         s.colE = nullptr;
         s.linv32 = nullptr;
     }
@@ -474,15 +477,24 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         pk.m2 = (1 << bits[2]) - 1;
         s.pack = pk;
         CK(mixed_init_static(s, s.force, pk, st));
-        // sliced-ELL columns for the thread-per-row plans
+        // sliced neighbour lists for the thread-per-row plans
         const int64_t ng = (N + 31) / 32;
         int64_t *ell_off = const_cast<int64_t *>(s.ell_off);
         CK(cudaMemsetAsync(ell_off + ng, 0, sizeof(int64_t), st));
         CK(mixed_ell_widths(s, ell_off, st));
         CK(scan_exclusive_i64(ell_off, ng + 1, sc.scan_tmp, st));
         int64_t ell_n = 0;
+        std::vector<int32_t> ell_w_host((size_t)ng);
         CK(cudaMemcpyAsync(&ell_n, ell_off + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        if (ng > 0)
+            CK(cudaMemcpyAsync(ell_w_host.data(), s.ell_w, (size_t)ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        ctx->ell_stats[0] = ng;
+        ctx->ell_stats[3] = ell_n;
+        for (int32_t wv : ell_w_host) {
+            ctx->ell_stats[1] += wv < 0;
+            ctx->ell_stats[2] += 32 * (int64_t)(wv < 0 ? ~wv : wv);
+        }
         int32_t *colE = nullptr;
         if (arena) {
             if (ell_n <= ell_capacity(N, nnz_cap)) colE = at<int32_t>(base, L.ell);
@@ -602,6 +614,18 @@ int tlsph_sync(tlsph_ctx *ctx)
         ctx->err = "device status bits " + std::to_string(bits);
         return TLSPH_ERR_NUMERICS;
     }
+    return TLSPH_OK;
+}
+
+int tlsph_neighbor_layout(const tlsph_ctx *ctx, int64_t *slices, int64_t *aligned_slices, int64_t *slots,
+                          int64_t *words)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (!ctx->ell_ok) return TLSPH_ERR_STATE;
+    if (slices) *slices = ctx->ell_stats[0];
+    if (aligned_slices) *aligned_slices = ctx->ell_stats[1];
+    if (slots) *slots = ctx->ell_stats[2];
+    if (words) *words = ctx->ell_stats[3];
     return TLSPH_OK;
 }
 

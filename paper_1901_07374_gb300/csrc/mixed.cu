@@ -163,6 +163,154 @@ __device__ __forceinline__ float3 xdiff(const MixConst &c, const float4 oj, cons
 
 __device__ __forceinline__ int row_bias(const MixConst &c, const float4 oi) { return c.bias - __float_as_int(oi.w); }
 
+// ------------------------------------------------------------------ sliced neighbour lists
+// The thread-per-row kernels read neighbours slice by slice, a slice being the
+// 32 consecutive rows of one warp.  A slice is stored in one of two forms:
+//
+//  explicit: ell_w[g] = W >= 0 slots; entry k of lane l at ell_off[g] + 32 k + l
+//            holds the neighbour index j, or ~p for a padding slot (p a valid
+//            particle index other than the row's, weight 0);
+//  aligned:  ell_w[g] = ~W < 0.  Slot k stands for the same index offset o_k
+//            in every row of the slice (j = i + o_k); the slice's union of
+//            offsets is stored once (o_k at ell_off[g] + k, padded with 0 to
+//            T = 32 ceil(W / 32) words) followed by one mask word per row and
+//            32 slots (bit k % 32 of the word at ell_off[g] + T + 32 (k / 32) + l
+//            says whether row l has j = i + o_k as a neighbour).
+//
+// Rows are sorted by j, so slots run in ascending j in both forms: the sums
+// over j are taken in CSR order either way.  Particles laid out with a regular
+// index structure (lattice rows) have nearly the same neighbour offsets in
+// all rows of a slice, so the aligned form replaces 4 bytes per pair with a
+// few bits, and the 32 lanes' k-th neighbours are consecutive particles (one
+// contiguous 512-byte record load per warp).  A slice whose offset union is
+// much wider than its longest row keeps the explicit form.
+
+// union width of the slice's offsets, cut off once it exceeds `limit`
+__device__ __forceinline__ int slice_union(const int64_t *row_ptr, const int32_t *col, int64_t i, int64_t N, int limit,
+                                          int32_t *table, uint32_t *masks, int lane, int T)
+{
+    int64_t p = 0, e = 0;
+    if (i < N) { p = row_ptr[i]; e = row_ptr[i + 1]; }
+    int h = p < e ? (int)(col[p] - i) : INT_MAX;
+    int cnt = 0;
+    int myoff = 0;
+    uint32_t mword = 0;
+    while (true) {
+        const int m = __reduce_min_sync(0xffffffffu, h);
+        if (m == INT_MAX || cnt >= limit) break;
+        if (table) {
+            if (lane == (cnt & 31)) myoff = m;
+            if (h == m) mword |= 1u << (cnt & 31);
+            if ((cnt & 31) == 31) {
+                table[32 * (cnt >> 5) + lane] = myoff;
+                masks[T + 32 * (cnt >> 5) + lane] = mword;
+                myoff = 0;
+                mword = 0;
+            }
+        }
+        ++cnt;
+        if (h == m) {
+            ++p;
+            h = p < e ? (int)(col[p] - i) : INT_MAX;
+        }
+    }
+    if (table && (cnt & 31)) {
+        table[32 * (cnt >> 5) + lane] = myoff;
+        masks[T + 32 * (cnt >> 5) + lane] = mword;
+    }
+    return cnt;
+}
+
+// per slice: the form, its width and its word count (into ell_off, scanned later)
+__global__ void k_ell_plan(const int64_t *row_ptr, const int32_t *col, int64_t N, int32_t *ell_w, int64_t *ell_off)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = i >> 5;
+    if (g >= (N + 31) / 32) return;       // whole warps: N rounded up to 32 rows
+    const int lane = threadIdx.x & 31;
+    const int len = i < N ? (int)(row_ptr[i + 1] - row_ptr[i]) : 0;
+    const int wp = __reduce_max_sync(0xffffffffu, len);
+    // aligned only when its slots stay within 5/4 of the explicit form's and its words fit in the explicit form's
+    const int limit = (5 * wp) / 4 + 4;
+    const int wu = slice_union(row_ptr, col, i, N, limit + 1, nullptr, nullptr, lane, 0);
+    const int64_t words_u = 64 * (int64_t)((wu + 31) / 32);
+    const bool aligned = wp > 0 && wu <= limit && words_u <= 32 * (int64_t)wp;
+    if (lane == 0) {
+        ell_w[g] = aligned ? ~wu : wp;
+        ell_off[g] = aligned ? words_u : 32 * (int64_t)wp;
+    }
+}
+
+__global__ void k_ell_fill(const int64_t *row_ptr, const int32_t *col, int64_t N, const int32_t *ell_w,
+                           const int64_t *ell_off, int32_t *colE)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = i >> 5;
+    if (g >= (N + 31) / 32) return;
+    const int lane = threadIdx.x & 31;
+    const int wv = ell_w[g];
+    int32_t *o = colE + ell_off[g];
+    if (wv < 0) {
+        const int W = ~wv;
+        const int T = 32 * ((W + 31) / 32);
+        slice_union(row_ptr, col, i, N, W, o, reinterpret_cast<uint32_t *>(o), lane, T);
+        return;
+    }
+    const int64_t b = i < N ? row_ptr[i] : 0, n = i < N ? row_ptr[i + 1] - row_ptr[i] : 0;
+    const int32_t pad = ~(int32_t)(i == 0 ? (N > 1 ? 1 : 0) : (i < N ? i - 1 : 0));
+    for (int k = 0; k < wv; ++k) o[32 * k + lane] = k < n ? col[b + k] : pad;
+}
+
+// Neighbour slots of row i in groups of U (U divides 32): body(j[U], w[U]) for
+// each group, w = 1 for a neighbour and 0 for a padding slot (whose j is a
+// valid particle other than i, so its terms are finite).
+template <int U, class Body>
+__device__ __forceinline__ void for_slots(const DevState &s, int64_t i, Body &&body)
+{
+    const int64_t g = i >> 5;
+    const int lane = (int)(i & 31);
+    const int wv = s.ell_w[g];
+    const int32_t *__restrict__ base = s.colE + s.ell_off[g];
+    const int64_t N = s.N;
+    const int alt = i == 0 ? 1 : (int)i - 1;
+    if (wv < 0) {
+        const int W = ~wv;
+        const int T = 32 * ((W + 31) / 32);
+        const uint32_t *__restrict__ mk = reinterpret_cast<const uint32_t *>(base) + T + lane;
+        uint32_t bits = 0;
+        for (int k = 0; k < W; k += U) {
+            if ((k & 31) == 0) bits = mk[k];
+            int j[U];
+            float w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int kk = k + u;
+                int jj = (int)i + base[kk];            // padding entries of the table are 0: jj = i
+                const bool on = kk < W && ((bits >> (kk & 31)) & 1u);
+                if (jj == (int)i || (unsigned)jj >= (unsigned)N) jj = alt;
+                j[u] = jj;
+                w[u] = on ? 1.0f : 0.0f;
+            }
+            body(j, w);
+        }
+    } else {
+        const int32_t *__restrict__ cp = base + lane;
+        for (int k = 0; k < wv; k += U) {
+            int j[U];
+            float w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int kk = k + u;
+                const int jj = kk < wv ? cp[32 * kk] : ~alt;
+                j[u] = jj >= 0 ? jj : ~jj;
+                w[u] = jj >= 0 ? 1.0f : 0.0f;
+            }
+            body(j, w);
+        }
+    }
+}
+
+
 // ------------------------------------------------------------------ compensated FP32
 // A value carried as an unevaluated sum hi + lo of two floats keeps about 46
 // significant bits, enough for quantities that accumulate small increments
@@ -419,24 +567,21 @@ __device__ __forceinline__ void pair1(const MixConst &c, const float4 oi, int ti
     m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
 }
 
-// thread per row over the sliced-ELL columns, two pairs in flight
+// thread per row over the sliced neighbour lists, U pairs in flight
+template <int U>
 __device__ __forceinline__ void gather1_row(const DevState &s, const MixConst &c, int64_t i, float *m)
 {
     const float4 oi = s.xo[i], vi = s.r1[i];
     const int ti = row_bias(c, oi);
-    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
-    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = 0.0f;
-    for (int k = 0; k < n; k += 2) {
-        const bool two = k + 1 < n;
-        const int j0 = cp[32 * k];
-        const int j1 = two ? cp[32 * (k + 1)] : j0;
-        const float4 o0 = s.xo[j0], v0 = s.r1[j0];
-        const float4 o1 = s.xo[j1], v1 = s.r1[j1];
-        pair1(c, oi, ti, vi, o0, v0, 1.0f, m);
-        pair1(c, oi, ti, vi, o1, v1, two ? 1.0f : 0.0f, m);
-    }
+    for_slots<U>(s, i, [&](const int *j, const float *w) {
+        float4 o[U], v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { o[u] = s.xo[j[u]]; v[u] = s.r1[j[u]]; }
+#pragma unroll
+        for (int u = 0; u < U; ++u) pair1(c, oi, ti, vi, o[u], v[u], w[u], m);
+    });
 }
 
 // warp per 32 consecutive rows over the CSR (lanes stride a row)
@@ -482,7 +627,7 @@ __global__ void __launch_bounds__(256) k_pass1_mixed_t(DevState s, MixConst c)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
     float m[9];
-    gather1_row(s, c, i, m);
+    gather1_row<2>(s, c, i, m);
     epi1_mixed(s, c, i, m);
 }
 
@@ -493,7 +638,7 @@ __global__ void __launch_bounds__(256) k_gather1_mixed_t(DevState s, MixConst c)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
     float m[9];
-    gather1_row(s, c, i, m);
+    gather1_row<2>(s, c, i, m);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = m[k];
 }
@@ -670,54 +815,27 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixCons
     epi2_mixed<HG>(s, c, row0 + lane, keep);
 }
 
+// pass-2 pair sums of row i over its slots, U pairs in flight
+template <bool HG, int U>
+__device__ __forceinline__ void gather2_row(const DevState &s, const MixConst &c, int64_t i, float *acc)
+{
+    const Row2 w = load_row2<HG>(s, c, i);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+    for_slots<U>(s, i, [&](const int *j, const float *wm) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) pair2<HG>(s, c, w, j[u], wm[u], acc);
+    });
+}
+
 template <bool HG>
 __global__ void __launch_bounds__(256) k_pass2_mixed_t(DevState s, MixConst c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    const Row2 w = load_row2<HG>(s, c, i);
-    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
-    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
     float acc[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-    for (int k = 0; k < n; k += 2) {
-        const bool two = k + 1 < n;
-        const int j0 = cp[32 * k];
-        const int j1 = two ? cp[32 * (k + 1)] : j0;
-        pair2<HG>(s, c, w, j0, 1.0f, acc);
-        pair2<HG>(s, c, w, j1, two ? 1.0f : 0.0f, acc);
-    }
+    gather2_row<HG, 2>(s, c, i, acc);
     epi2_mixed<HG>(s, c, i, acc);
-}
-
-// four pairs in flight per thread (pass 1)
-__device__ __forceinline__ void gather1_row4(const DevState &s, const MixConst &c, int64_t i, float *m)
-{
-    const float4 oi = s.xo[i], vi = s.r1[i];
-    const int ti = row_bias(c, oi);
-    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
-    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) m[k] = 0.0f;
-    for (int k = 0; k < n; k += 4) {
-        // a padded slot repeats the first (real) neighbour with weight 0
-        int j[4];
-        float w[4];
-        j[0] = cp[32 * k];
-        w[0] = 1.0f;
-#pragma unroll
-        for (int u = 1; u < 4; ++u) {
-            const bool ok = k + u < n;
-            j[u] = ok ? cp[32 * (k + u)] : j[0];
-            w[u] = ok ? 1.0f : 0.0f;
-        }
-        float4 o[4], v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { o[u] = s.xo[j[u]]; v[u] = s.r1[j[u]]; }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) pair1(c, oi, ti, vi, o[u], v[u], w[u], m);
-    }
 }
 
 __global__ void __launch_bounds__(256) k_gather1_mixed_t4(DevState s, MixConst c)
@@ -725,7 +843,7 @@ __global__ void __launch_bounds__(256) k_gather1_mixed_t4(DevState s, MixConst c
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
     float m[9];
-    gather1_row4(s, c, i, m);
+    gather1_row<4>(s, c, i, m);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = m[k];
 }
@@ -737,19 +855,8 @@ __global__ void __launch_bounds__(256) k_gather2_mixed_t(DevState s, MixConst c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    const Row2 w = load_row2<HG>(s, c, i);
-    const int n = (int)(s.row_ptr[i + 1] - s.row_ptr[i]);
-    const int32_t *__restrict__ cp = s.colE + s.ell_off[i >> 5] + (i & 31);
     float acc[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-    for (int k = 0; k < n; k += 2) {
-        const bool two = k + 1 < n;
-        const int j0 = cp[32 * k];
-        const int j1 = two ? cp[32 * (k + 1)] : j0;
-        pair2<HG>(s, c, w, j0, 1.0f, acc);
-        pair2<HG>(s, c, w, j1, two ? 1.0f : 0.0f, acc);
-    }
+    gather2_row<HG, 2>(s, c, i, acc);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = acc[k];
 }
@@ -763,32 +870,6 @@ __global__ void __launch_bounds__(128) k_epi2_mixed(DevState s, MixConst c)
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = s.fsum[k * s.N + i];
     epi2_mixed<HG>(s, c, i, m);
-}
-
-// ------------------------------------------------------------------ sliced ELL
-// slice g = rows 32g .. 32g+31; its width is the longest row; entry k of
-// lane l sits at ell_off[g] + 32 k + l
-__global__ void k_ell_width(const int64_t *row_ptr, int64_t N, int64_t *ell_off)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const long long len = i < N ? (long long)(row_ptr[i + 1] - row_ptr[i]) : 0;
-    long long m = len;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0 && (i >> 5) < (N + 31) / 32) ell_off[i >> 5] = 32 * (int64_t)m;
-}
-
-__global__ void k_ell_fill(const int64_t *row_ptr, const int32_t *col, int64_t N, const int64_t *ell_off, int32_t *colE)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t g = i >> 5;
-    if (g >= (N + 31) / 32) return;
-    const int lane = (int)(i & 31);
-    const int64_t width = (ell_off[g + 1] - ell_off[g]) / 32;
-    const int64_t b = i < N ? row_ptr[i] : 0, n = i < N ? row_ptr[i + 1] - row_ptr[i] : 0;
-    int32_t *o = colE + ell_off[g] + lane;
-    for (int64_t k = 0; k < width; ++k) o[32 * k] = k < n ? col[b + k] : (int32_t)(i < N ? i : 0);
 }
 
 // ------------------------------------------------------------------ mirrors
@@ -899,14 +980,14 @@ cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPac
 cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st)
 {
     const int64_t rows = (s.N + 31) / 32 * 32;
-    k_ell_width<<<nb(rows, 256), 256, 0, st>>>(s.row_ptr, s.N, ell_off);
+    k_ell_plan<<<nb(rows, 256), 256, 0, st>>>(s.row_ptr, s.col, s.N, const_cast<int32_t *>(s.ell_w), ell_off);
     return cudaGetLastError();
 }
 
 cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st)
 {
     const int64_t rows = (s.N + 31) / 32 * 32;
-    k_ell_fill<<<nb(rows, 256), 256, 0, st>>>(s.row_ptr, s.col, s.N, ell_off, colE);
+    k_ell_fill<<<nb(rows, 256), 256, 0, st>>>(s.row_ptr, s.col, s.N, s.ell_w, ell_off, colE);
     return cudaGetLastError();
 }
 
@@ -1019,7 +1100,7 @@ __global__ void __launch_bounds__(128) k_batch(const BatchHdr *hdr, BatchSlot *s
         if (i < sl.s.N) {
             if (KIND == 0) {            // pass-1 gather
                 float m[9];
-                gather1_row4(sl.s, sl.c, i, m);
+                gather1_row<4>(sl.s, sl.c, i, m);
 #pragma unroll
                 for (int k = 0; k < 9; ++k) sl.s.fsum[k * sl.s.N + i] = m[k];
             } else if (KIND == 1) {     // pass-1 per-particle update
@@ -1028,19 +1109,8 @@ __global__ void __launch_bounds__(128) k_batch(const BatchHdr *hdr, BatchSlot *s
                 for (int k = 0; k < 9; ++k) m[k] = sl.s.fsum[k * sl.s.N + i];
                 epi1_mixed(sl.s, sl.c, i, m);
             } else {                    // pass 2
-                const Row2 r = load_row2<HG>(sl.s, sl.c, i);
-                const int n = (int)(sl.s.row_ptr[i + 1] - sl.s.row_ptr[i]);
-                const int32_t *__restrict__ cp = sl.s.colE + sl.s.ell_off[i >> 5] + (i & 31);
                 float acc[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-                for (int k = 0; k < n; k += 2) {
-                    const bool two = k + 1 < n;
-                    const int j0 = cp[32 * k];
-                    const int j1 = two ? cp[32 * (k + 1)] : j0;
-                    pair2<HG>(sl.s, sl.c, r, j0, 1.0f, acc);
-                    pair2<HG>(sl.s, sl.c, r, j1, two ? 1.0f : 0.0f, acc);
-                }
+                gather2_row<HG, 2>(sl.s, sl.c, i, acc);
                 epi2_mixed<HG>(sl.s, sl.c, i, acc);
             }
         }

@@ -83,8 +83,9 @@ struct DevState {
     float *Fh, *Fl;         // 9 x N deformation gradient
     float *sdh, *sdl;       // 6 x N unrotated stress deviator
     float *sigf;            // 6 x N Cauchy stress
-    const int32_t *colE;    // sliced-ELL neighbour columns (slices of 32 rows)
-    const int64_t *ell_off; // (N + 31) / 32 + 1 slice offsets
+    const int32_t *colE;    // sliced neighbour lists (slices of 32 rows, explicit or aligned form)
+    const int64_t *ell_off; // (N + 31) / 32 + 1 slice word offsets
+    const int32_t *ell_w;   // (N + 31) / 32 slice widths: W (explicit) or ~W (aligned)
     double vref[3];         // bulk reference velocity of the r1 mirror
     CellPack pack;
 };
@@ -128,7 +129,8 @@ struct tlsph_ctx {
     std::string err;
     // internal order: perm[k] = caller index of internal particle k, inv its inverse
     bool reordered = false;
-    bool ell_ok = false;        // sliced-ELL columns built (thread-per-row plans allowed)
+    bool ell_ok = false;        // sliced neighbour lists built (thread-per-row plans allowed)
+    int64_t ell_stats[4] = { 0, 0, 0, 0 };   // slices, aligned slices, slots, words
     void *ell_mem = nullptr;    // library-owned sliced-ELL columns
     int32_t *perm_dev = nullptr;
     std::vector<int32_t> perm, inv;

@@ -77,7 +77,7 @@ EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph
            "tlsph_status_bits", "tlsph_info", "tlsph_get_state", "tlsph_set_state", "tlsph_last_error",
            "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
            "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
-           "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy")
+           "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_neighbor_layout")
 
 _lib = None
 _lock = threading.Lock()
@@ -131,6 +131,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_set_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
         L.tlsph_get_plan.restype = i32
         L.tlsph_get_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
+        L.tlsph_neighbor_layout.restype = i32
+        L.tlsph_neighbor_layout.argtypes = [vp] + [ctypes.POINTER(i64)] * 4
         L.tlsph_batch_create.restype = i32
         L.tlsph_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
         L.tlsph_batch_set.restype = i32
@@ -286,6 +288,13 @@ class Simulation:
         N, nnz, steps = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(load().tlsph_info(self.ctx, ctypes.byref(N), ctypes.byref(nnz), ctypes.byref(steps)), self.ctx)
         return N.value, nnz.value, steps.value
+
+    def neighbor_layout(self) -> dict:
+        """Form of the sliced neighbour lists of a mixed-precision context:
+        slices, aligned slices, slots and 4-byte words."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(load().tlsph_neighbor_layout(self.ctx, *[ctypes.byref(x) for x in v]), self.ctx)
+        return dict(zip(("slices", "aligned_slices", "slots", "words"), (x.value for x in v)))
 
     @property
     def nnz(self) -> int:

@@ -101,6 +101,54 @@ def test_every_launch_plan_computes_the_same_step():
             assert np.max(np.abs(a - b)) <= 1e-5 * max(np.max(np.abs(b)), 1e-30), k
 
 
+def _reordered(w, perm):
+    import dataclasses
+    sp = w.specimen
+    sp2 = dataclasses.replace(sp, X=sp.X[perm].copy(), vol=sp.vol[perm].copy(), mat_id=sp.mat_id[perm].copy(),
+                              bc_mask=sp.bc_mask[perm].copy(), bc_vel=sp.bc_vel[perm].copy(), f0=sp.f0[perm].copy())
+    return dataclasses.replace(w, specimen=sp2)
+
+
+@pytest.mark.parametrize("shuffle", ["all", "second_half"])
+def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
+    """Lattice order gives aligned slices (one shared offset table per 32
+    rows); a shuffled caller order leaves the index offsets irregular, so its
+    slices keep the explicit form (shuffling half the particles mixes both
+    forms in one context).  The thread-per-row plans then compute the same
+    step in both layouts to FP32 rounding, within MIXED_TOL of the oracle."""
+    w = S.failure_variant(S.tensile_bar_cl(nx=8, ny=8, nz=24), v_grip=10.0, scale=0.05)
+    N = w.specimen.N
+    perm = np.arange(N)
+    rng = np.random.default_rng(3)
+    if shuffle == "all":
+        perm = rng.permutation(N)
+    else:
+        perm[N // 2:] = N // 2 + rng.permutation(N - N // 2)
+    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    b = tlsph.Simulation.from_workload(_reordered(w, perm), precision="mixed")
+    la, lb = a.neighbor_layout(), b.neighbor_layout()
+    assert la["slices"] == lb["slices"] == (N + 31) // 32
+    assert la["aligned_slices"] >= 0.9 * la["slices"]
+    if shuffle == "all":
+        assert lb["aligned_slices"] <= 0.1 * lb["slices"]
+    else:
+        assert 0.3 * lb["slices"] <= lb["aligned_slices"] <= 0.7 * lb["slices"]
+    assert la["words"] < lb["words"]
+    for plan in [(4, 128, 1, 128), (1, 64, 2, 256)]:
+        a = tlsph.Simulation.from_workload(w, precision="mixed")
+        b = tlsph.Simulation.from_workload(_reordered(w, perm), precision="mixed")
+        a.set_plan(plan)
+        b.set_plan(plan)
+        a.step(30)
+        b.step(30)
+        for k in ("U", "V", "F", "SIGMA"):
+            x, y = a.get(k)[perm], b.get(k)
+            assert np.max(np.abs(x - y)) <= 1e-5 * max(np.max(np.abs(x)), 1e-30), (plan, k)
+    o = oracle.Simulation.from_workload(w)
+    o.step(30)
+    compare_state(a.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
+
+
 def test_autotune_restores_the_state_bitwise(tmp_path, monkeypatch):
     from paper_1901_07374_gb300 import autotune
     monkeypatch.setenv("TLSPH_PLAN_CACHE", str(tmp_path / "plans.json"))
