@@ -50,11 +50,12 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def algorithmic_bytes(N: int, nnz: int, precision: str) -> dict:
-    """Bytes each pass must move between HBM and the SMs per step: the CSR
-    column index of every pair plus every particle's own state read and
-    written once (gathered neighbour data counts as on-chip reuse).  Per-pass
-    per-particle figures follow the state layout of the library."""
+def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None = None) -> dict:
+    """Bytes each pass must move between HBM and the SMs per step: the
+    neighbour lists (the CSR column index of every pair, or the mixed path's
+    sliced lists: `list_words` 4-byte words) plus every particle's own state
+    read and written once (gathered neighbour data counts as on-chip reuse).
+    Per-pass per-particle figures follow the state layout of the library."""
     if precision == "fp64":
         p1 = 4 * nnz + 592 * N     # row_ptr 8, X 24, v 24, Linv 72, F rw 144, sd rw 96, scalars rw 64,
         #                            D r+w 16, fail 4, mat 4, sigma w 48, A w 72, vol 16 (gathered only)
@@ -62,8 +63,14 @@ def algorithmic_bytes(N: int, nnz: int, precision: str) -> dict:
         #                            vh rw 48, v w 24, force w 24, u' w 24, fail 4, bc 1
     else:
         from paper_1901_07374_gb300 import tlsph
-        p1, p2 = tlsph.mixed_algorithmic_bytes(N, nnz)
+        p1, p2 = tlsph.mixed_algorithmic_bytes(N, nnz if list_words is None else list_words)
     return {"pass1": p1, "pass2": p2}
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the same kernel build, keyed by (workload, precision, kernel);
+# absent when the kernel changed after the capture
+TRAFFIC = {}
 
 
 # ---------------------------------------------------------------- clocks
@@ -181,14 +188,31 @@ def field_scales(w) -> dict:
     return dict(U=L, V=v, F=1.0, SIGMA=s, STRESS_DEV=s, EPSP=1e-3, DINIT=1e-3, DAMAGE=1e-3, FORCE=s * L * L)
 
 
-def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None):
+def launches_per_step(plan) -> int:
+    """Kernels one step launches: FP64 path 2; mixed plans 1 or 2 per pass."""
+    if not plan:
+        return 2
+    return (2 if plan[0] >= 2 else 1) + (2 if plan[2] == 2 else 1)
+
+
+def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, plan=None, state=None):
     """Create, warm up, then time `steps` steps with CUDA events on the
-    library's stream; per-kernel times from the library's own events."""
+    library's stream; per-kernel times from the library's own events.  A
+    mixed context takes `plan`, else the autotuner's; `state` (caller-order
+    fields) is loaded before the warm-up."""
     sim = tlsph.Simulation.from_workload(w, precision=precision, stream=stream)
     N, nnz, _ = sim.info()
+    words = None
     if precision == "mixed":
         from paper_1901_07374_gb300 import autotune
-        autotune.tune(sim)
+        if plan:
+            sim.set_plan(plan)
+        else:
+            autotune.tune(sim)
+        pl, lw = sim.get_plan(), sim.neighbor_layout()["words"]
+        words = (lw if pl[0] in (1, 2, 4) else nnz, lw if pl[2] != 0 else nnz)
+    for k, v in (state or {}).items():
+        sim.set(k, v)
     sim.step(warmup)
     torch.cuda.synchronize()
     if clocks:
@@ -206,7 +230,8 @@ def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None):
     clk = clocks.stop() if clocks else None
     sim.sync()
     return sim, dict(ms=ms, p1=p1 / max(1, nprof), p2=p2 / max(1, nprof), N=N, nnz=nnz, clocks=clk,
-                     plan=sim.get_plan() if precision == "mixed" else None)
+                     plan=sim.get_plan() if precision == "mixed" else None, words=words,
+                     layout=sim.neighbor_layout() if precision == "mixed" else None)
 
 
 def run_ours(args, rank: int, world: int, dist):
@@ -230,7 +255,7 @@ def run_ours(args, rank: int, world: int, dist):
     if args.precision != "fp64" and not args.skip_fp64:
         ref_sim, ref = timed_run(tlsph, torch, w, "fp64", args.steps, args.warmup, stream)
     sim, r = timed_run(tlsph, torch, w, args.precision, args.steps, args.warmup, stream,
-                       clocks=ClockSampler(torch.cuda.current_device()))
+                       clocks=ClockSampler(torch.cuda.current_device()), plan=args.plan)
     N, nnz, ms = r["N"], r["nnz"], r["ms"]
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -251,8 +276,10 @@ def run_ours(args, rank: int, world: int, dist):
         ref_sim.close()
     sim.close()
 
-    # ---- roofline of the dominant kernel
-    ab = algorithmic_bytes(N, nnz, args.precision)
+    # ---- roofline of the dominant kernel: HBM bytes and FP32 issue
+    words = r.get("words") or (nnz, nnz)
+    ab = {"pass1": algorithmic_bytes(N, nnz, args.precision, words[0])["pass1"],
+          "pass2": algorithmic_bytes(N, nnz, args.precision, words[1])["pass2"]}
     kern = "pass2" if r["p2"] >= r["p1"] else "pass1"
     k_ms = r[{"pass1": "p1", "pass2": "p2"}[kern]]
     peaks = measured_peaks()
@@ -260,41 +287,80 @@ def run_ours(args, rank: int, world: int, dist):
     if not peak:
         peak, src = 6800.0, "fallback"
     achieved = ab[kern] / (k_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": src, "traffic": None,
-                "algorithmic_bytes_per_launch": ab[kern],
-                "ms_per_launch": {"pass1": r["p1"], "pass2": r["p2"]}}
+    hbm = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_source": src, "traffic": TRAFFIC.get((args.workload, args.precision, kern)),
+           "algorithmic_bytes_per_launch": ab[kern]}
+    roofline = hbm
+    if args.precision == "mixed":
+        ops = dict(zip(("pass1", "pass2"), tlsph.mixed_fp32_ops(nnz, w.hg_alpha != 0.0)))
+        peak_alu = tlsph.FP32_LANES * 2070e6 / 1e12
+        ach_alu = ops[kern] / (k_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": kern, "achieved": ach_alu, "peak": peak_alu, "unit": "TFLOP/s",
+                    "frac": ach_alu / peak_alu,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (an FMA counts as one op)",
+                    "traffic": hbm["traffic"], "algorithmic_ops_per_launch": ops[kern],
+                    "fp32_ops_per_pair": tlsph.MIXED_FP32_OPS_PER_PAIR, "hbm_view": hbm}
+    roofline["ms_per_launch"] = {"pass1": r["p1"], "pass2": r["p2"]}
+
+    # ---- the same bar with every particle in plastic flow (FP64 return in both paths)
+    plastic = None
+    if not args.no_plastic and args.workload.startswith("tensile_bar"):
+        from paper_1901_07374_gb300 import specimen as S
+        st = S.plastic_flow_state(w)
+        ps, pr = timed_run(tlsph, torch, w, args.precision, args.plastic_steps, args.warmup, stream,
+                           plan=r.get("plan"), state=st)
+        plastic = {"steps": args.plastic_steps, "ms_per_step": pr["ms"] / args.plastic_steps,
+                   "value": world * nnz * args.plastic_steps / (pr["ms"] * 1e-3),
+                   "ms_per_launch": {"pass1": pr["p1"], "pass2": pr["p2"]},
+                   "plastic_fraction": float(np.mean(ps.get("EPSP") > 0))}
+        if args.precision != "fp64" and not args.skip_fp64:
+            qs, qr = timed_run(tlsph, torch, w, "fp64", args.plastic_steps, args.warmup, stream, state=st)
+            plastic["fp64_value"] = world * nnz * args.plastic_steps / (qr["ms"] * 1e-3)
+            sc = field_scales(w)
+            acc = {}
+            for f in FIELDS:
+                a, b = ps.get(f), qs.get(f)
+                acc[f] = float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), sc[f]))
+            d = np.abs(ps.get("EPSP") - qs.get("EPSP"))
+            acc["particles_epsp_diff_above_1e-8"] = int((d > 1e-8).sum())
+            plastic["accuracy_vs_fp64"] = acc
+            qs.close()
+        ps.close()
 
     # ---- end to end through the C ABI from pinned host buffers
-    def pinned(a):
-        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        return t, t.numpy()
-    keep = [pinned(a) for a in (sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0)]
-    X, vol, mat, bcm, bcv, f0 = (k[1] for k in keep)
-    outs = {k: pinned(np.empty((N, c))) for k, c in (("U", 3), ("V", 3), ("SIGMA", 9), ("DAMAGE", 1))}
-    h2d = sum(k[1].nbytes for k in keep)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    s2 = tlsph.Simulation(X, vol, mat, bcm, bcv, f0, w.materials, w.h, w.rc, w.dt, w.hg_alpha,
-                          precision=args.precision, stream=stream)
-    s2.step(args.steps)
-    d2h = 0
-    L = tlsph.load()
-    for k, (t, a) in outs.items():
-        tlsph._check(L.tlsph_get_state(s2.ctx, tlsph.FIELD[k], a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0),
-                     s2.ctx)
-        d2h += a.nbytes
-    el = time.perf_counter() - t0
-    s2.close()
-    if dist:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    e2e = {"value": world * nnz * args.steps / el, "unit": UNIT,
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "includes": "create (upload, neighbour build, L^-1) + K steps + download of u, v, sigma, D"}
+    e2e = None
+    if not args.no_e2e:
+        def pinned(a):
+            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            return t, t.numpy()
+        keep = [pinned(a) for a in (sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0)]
+        X, vol, mat, bcm, bcv, f0 = (k[1] for k in keep)
+        outs = {k: pinned(np.empty((N, c))) for k, c in (("U", 3), ("V", 3), ("SIGMA", 9), ("DAMAGE", 1))}
+        h2d = sum(k[1].nbytes for k in keep)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        s2 = tlsph.Simulation(X, vol, mat, bcm, bcv, f0, w.materials, w.h, w.rc, w.dt, w.hg_alpha,
+                              precision=args.precision, stream=stream)
+        if r.get("plan"):
+            s2.set_plan(r["plan"])
+        s2.step(args.steps)
+        d2h = 0
+        L = tlsph.load()
+        for k, (t, a) in outs.items():
+            tlsph._check(L.tlsph_get_state(s2.ctx, tlsph.FIELD[k], a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0),
+                         s2.ctx)
+            d2h += a.nbytes
+        el = time.perf_counter() - t0
+        s2.close()
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * nnz * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "includes": "create (upload, neighbour build, L^-1) + K steps + download of u, v, sigma, D"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -308,6 +374,10 @@ def run_ours(args, rank: int, world: int, dist):
            "particle_steps_per_s": world * N * args.steps / (ms * 1e-3),
            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
            "l2": "inputs larger than L2 (about 1.8 GB per step vs 129 MB)"}
+    if r.get("layout"):
+        cfg["neighbor_lists"] = dict(r["layout"], bytes_per_pair=4.0 * r["layout"]["words"] / nnz)
+    if plastic:
+        cfg["plastic_flow_window"] = plastic
     if ref is not None:
         cfg["plan"] = r.get("plan")
         cfg["fp64_gpu_value"] = world * nnz * args.steps / (ref["ms"] * 1e-3)
@@ -317,7 +387,7 @@ def run_ours(args, rank: int, world: int, dist):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic (seeded jittered lattice)", "config": cfg,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step(r.get("plan")) * args.steps,
             "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
 
@@ -428,9 +498,15 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving workload: arrivals per second")
     ap.add_argument("--chunk", type=int, default=100, help="serving workload: steps per batch chunk")
+    ap.add_argument("--plan", default=None, help="mixed launch plan v1,b1,v2,b2 (default: autotuned)")
+    ap.add_argument("--no-plastic", action="store_true", help="skip the plastic-flow window")
+    ap.add_argument("--plastic-steps", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.plan:
+        args.plan = tuple(int(x) for x in args.plan.split(","))
     if args.precision is None:
         from paper_1901_07374_gb300 import tlsph
         args.precision = tlsph.DEFAULT_PRECISION

@@ -209,10 +209,14 @@ int tlsph_destroy(tlsph_ctx *ctx);
  * 32 rows; 1 thread per row; 2 thread-per-row gather + per-particle kernel;
  * 3 warp-per-32-rows gather + per-particle kernel; 4 as 2 with four pairs in
  * flight per thread), plan[1] its block size, plan[2] pass-2 form (0 warp
- * per 32 rows; 1 thread per row; 2 thread-per-row gather + per-particle
- * kernel), plan[3] its block size (multiples of 32 up to 256).  Every plan computes the same
- * method; sums over a row are grouped differently, so results differ only
- * by FP32 rounding.  n must be 4.  The FP64 path ignores the plan. */
+ * per 32 rows; 1 thread per row, two pairs in flight; 2 thread-per-row
+ * gather + per-particle kernel; 3 thread per row, one pair in flight; 4 as
+ * 1 with registers capped for six resident blocks; 5 as 3 with registers
+ * capped for eight resident blocks; block size at most 128 for 4 and 5),
+ * plan[3] its block size (multiples of 32 up to 256).  Every plan computes
+ * the same method; sums over a row are grouped differently, so results
+ * differ only by FP32 rounding.  n must be 4.  TLSPH_ERR_ARG for a plan out
+ * of range.  The FP64 path ignores the plan. */
 int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);
 int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
 

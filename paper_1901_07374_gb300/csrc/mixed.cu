@@ -172,10 +172,13 @@ __device__ __forceinline__ int row_bias(const MixConst &c, const float4 oi) { re
 //            particle index other than the row's, weight 0);
 //  aligned:  ell_w[g] = ~W < 0.  Slot k stands for the same index offset o_k
 //            in every row of the slice (j = i + o_k); the slice's union of
-//            offsets is stored once (o_k at ell_off[g] + k, padded with 0 to
-//            T = 32 ceil(W / 32) words) followed by one mask word per row and
-//            32 slots (bit k % 32 of the word at ell_off[g] + T + 32 (k / 32) + l
-//            says whether row l has j = i + o_k as a neighbour).
+//            offsets is stored once (o_k at ell_off[g] + k, padded with the
+//            last offset to T = 32 ceil(W / 32) words) followed by one mask
+//            word per row and 32 slots (bit k % 32 of the word at
+//            ell_off[g] + T + 32 (k / 32) + l says whether row l has
+//            j = i + o_k as a neighbour).  A slice is aligned only if i + o_k
+//            is a particle index for every row i < N of the slice and every
+//            offset, so a masked slot still reads a valid particle (j != i).
 //
 // Rows are sorted by j, so slots run in ascending j in both forms: the sums
 // over j are taken in CSR order either way.  Particles laid out with a regular
@@ -185,9 +188,10 @@ __device__ __forceinline__ int row_bias(const MixConst &c, const float4 oi) { re
 // contiguous 512-byte record load per warp).  A slice whose offset union is
 // much wider than its longest row keeps the explicit form.
 
-// union width of the slice's offsets, cut off once it exceeds `limit`
+// union of the slice's offsets (ascending), cut off once it exceeds `limit`;
+// returns its width, the smallest and the largest offset
 __device__ __forceinline__ int slice_union(const int64_t *row_ptr, const int32_t *col, int64_t i, int64_t N, int limit,
-                                          int32_t *table, uint32_t *masks, int lane, int T)
+                                          int32_t *table, uint32_t *masks, int lane, int T, int &omin, int &omax)
 {
     int64_t p = 0, e = 0;
     if (i < N) { p = row_ptr[i]; e = row_ptr[i + 1]; }
@@ -195,9 +199,13 @@ __device__ __forceinline__ int slice_union(const int64_t *row_ptr, const int32_t
     int cnt = 0;
     int myoff = 0;
     uint32_t mword = 0;
+    omin = 0;
+    omax = 0;
     while (true) {
         const int m = __reduce_min_sync(0xffffffffu, h);
         if (m == INT_MAX || cnt >= limit) break;
+        if (cnt == 0) omin = m;
+        omax = m;
         if (table) {
             if (lane == (cnt & 31)) myoff = m;
             if (h == m) mword |= 1u << (cnt & 31);
@@ -215,6 +223,7 @@ __device__ __forceinline__ int slice_union(const int64_t *row_ptr, const int32_t
         }
     }
     if (table && (cnt & 31)) {
+        if (lane >= (cnt & 31)) myoff = omax;      // table padding: a valid offset, its mask bits are 0
         table[32 * (cnt >> 5) + lane] = myoff;
         masks[T + 32 * (cnt >> 5) + lane] = mword;
     }
@@ -230,11 +239,14 @@ __global__ void k_ell_plan(const int64_t *row_ptr, const int32_t *col, int64_t N
     const int lane = threadIdx.x & 31;
     const int len = i < N ? (int)(row_ptr[i + 1] - row_ptr[i]) : 0;
     const int wp = __reduce_max_sync(0xffffffffu, len);
-    // aligned only when its slots stay within 5/4 of the explicit form's and its words fit in the explicit form's
+    // aligned only when its slots stay within 5/4 of the explicit form's, its
+    // words fit in the explicit form's and every row's i + o_k is a particle
     const int limit = (5 * wp) / 4 + 4;
-    const int wu = slice_union(row_ptr, col, i, N, limit + 1, nullptr, nullptr, lane, 0);
+    int omin, omax;
+    const int wu = slice_union(row_ptr, col, i, N, limit + 1, nullptr, nullptr, lane, 0, omin, omax);
     const int64_t words_u = 64 * (int64_t)((wu + 31) / 32);
-    const bool aligned = wp > 0 && wu <= limit && words_u <= 32 * (int64_t)wp;
+    const bool in_range = i >= N || (i + omin >= 0 && i + omax < N);
+    const bool aligned = __all_sync(0xffffffffu, in_range) && wp > 0 && wu <= limit && words_u <= 32 * (int64_t)wp;
     if (lane == 0) {
         ell_w[g] = aligned ? ~wu : wp;
         ell_off[g] = aligned ? words_u : 32 * (int64_t)wp;
@@ -253,7 +265,8 @@ __global__ void k_ell_fill(const int64_t *row_ptr, const int32_t *col, int64_t N
     if (wv < 0) {
         const int W = ~wv;
         const int T = 32 * ((W + 31) / 32);
-        slice_union(row_ptr, col, i, N, W, o, reinterpret_cast<uint32_t *>(o), lane, T);
+        int omin, omax;
+        slice_union(row_ptr, col, i, N, W, o, reinterpret_cast<uint32_t *>(o), lane, T, omin, omax);
         return;
     }
     const int64_t b = i < N ? row_ptr[i] : 0, n = i < N ? row_ptr[i + 1] - row_ptr[i] : 0;
@@ -271,12 +284,13 @@ __device__ __forceinline__ void for_slots(const DevState &s, int64_t i, Body &&b
     const int lane = (int)(i & 31);
     const int wv = s.ell_w[g];
     const int32_t *__restrict__ base = s.colE + s.ell_off[g];
-    const int64_t N = s.N;
     const int alt = i == 0 ? 1 : (int)i - 1;
     if (wv < 0) {
+        // aligned: every slot's j = i + o_k is a particle other than i (see above)
         const int W = ~wv;
         const int T = 32 * ((W + 31) / 32);
         const uint32_t *__restrict__ mk = reinterpret_cast<const uint32_t *>(base) + T + lane;
+        const int ii = (int)i;
         uint32_t bits = 0;
         for (int k = 0; k < W; k += U) {
             if ((k & 31) == 0) bits = mk[k];
@@ -284,12 +298,8 @@ __device__ __forceinline__ void for_slots(const DevState &s, int64_t i, Body &&b
             float w[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int kk = k + u;
-                int jj = (int)i + base[kk];            // padding entries of the table are 0: jj = i
-                const bool on = kk < W && ((bits >> (kk & 31)) & 1u);
-                if (jj == (int)i || (unsigned)jj >= (unsigned)N) jj = alt;
-                j[u] = jj;
-                w[u] = on ? 1.0f : 0.0f;
+                j[u] = ii + base[k + u];
+                w[u] = (float)((bits >> ((k & 31) + u)) & 1u);
             }
             body(j, w);
         }
@@ -838,6 +848,39 @@ __global__ void __launch_bounds__(256) k_pass2_mixed_t(DevState s, MixConst c)
     epi2_mixed<HG>(s, c, i, acc);
 }
 
+// one pair in flight per thread (fewer registers, more resident warps)
+template <bool HG>
+__global__ void __launch_bounds__(256) k_pass2_mixed_t1(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float acc[9];
+    gather2_row<HG, 1>(s, c, i, acc);
+    epi2_mixed<HG>(s, c, i, acc);
+}
+
+// one pair in flight, registers capped so that eight blocks of 128 fit an SM
+template <bool HG>
+__global__ void __launch_bounds__(128, 8) k_pass2_mixed_t1c(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float acc[9];
+    gather2_row<HG, 1>(s, c, i, acc);
+    epi2_mixed<HG>(s, c, i, acc);
+}
+
+// two pairs in flight, registers capped so that six blocks of 128 fit an SM
+template <bool HG>
+__global__ void __launch_bounds__(128, 6) k_pass2_mixed_tc(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float acc[9];
+    gather2_row<HG, 2>(s, c, i, acc);
+    epi2_mixed<HG>(s, c, i, acc);
+}
+
 __global__ void __launch_bounds__(256) k_gather1_mixed_t4(DevState s, MixConst c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1001,8 +1044,10 @@ cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st)
 //   pass 1: 0 = warp per 32 rows, fused;  1 = thread per row, fused;
 //           2 = thread-per-row gather + per-particle kernel;  3 = warp-per-32-rows gather + per-particle kernel;
 //           4 = as 2 with four pairs in flight per thread
-//   pass 2: 0 = warp per 32 rows;  1 = thread per row;  2 = thread-per-row gather + per-particle kernel
-// block sizes are multiples of 32 up to 256 (128 for the fused warp forms).
+//   pass 2: 0 = warp per 32 rows;  1 = thread per row;  2 = thread-per-row gather + per-particle kernel;
+//           3 = thread per row, one pair in flight;  4 = thread per row, registers capped for 6 blocks of 128;
+//           5 = as 3 with registers capped for 8 blocks of 128
+// block sizes are multiples of 32 up to 256 (128 for the fused warp forms and pass-2 forms 4 and 5).
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev)
 {
     const MixConst c = make_mix_const(ctx, step_index);
@@ -1031,6 +1076,15 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
     if (v2 == 1) {
         if (hg) k_pass2_mixed_t<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
         else k_pass2_mixed_t<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+    } else if (v2 == 3) {
+        if (hg) k_pass2_mixed_t1<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+        else k_pass2_mixed_t1<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+    } else if (v2 == 4) {
+        if (hg) k_pass2_mixed_tc<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+        else k_pass2_mixed_tc<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+    } else if (v2 == 5) {
+        if (hg) k_pass2_mixed_t1c<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+        else k_pass2_mixed_t1c<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
     } else if (v2 == 2) {
         if (hg) {
             k_gather2_mixed_t<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);

@@ -157,17 +157,43 @@ def _check(code: int, ctx=None):
         raise TlsphError(code, msg)
 
 
-def mixed_algorithmic_bytes(N: int, nnz: int):
+def mixed_algorithmic_bytes(N: int, list_words: int):
     """HBM bytes per step of (pass 1, pass 2) in the mixed path that the method
-    must move: the 4-byte column index of every pair plus each particle's own
-    records and FP64 state read and written once.
-    pass 1: row_ptr 8, cell offsets 16, v record 16, L^-1 36, F rw 144,
-            deviator rw 96, eps_p / rate / D_init / f rw 64, D r+w 16, fail 4,
-            material 4, u 24, V 8, sqrt E 8, sigma w 48, pass-2 record w 96 = 588
-    pass 2: row_ptr 8, cell offsets 16, own pass-2 record 96, S0 16, V 8, D 8,
-            sqrt E 8, mass 8, v_half rw 48, v w 24, force w 24, u r+w 48,
-            fail 4, bc 1, v record w 16                                   = 333"""
-    return 4 * nnz + 588 * N, 4 * nnz + 333 * N
+    must move with the library's state layout: the neighbour lists once per
+    pass (`list_words` 4-byte words: 4 per pair for the CSR or explicit
+    slices, a few bits per pair for aligned slices) plus each particle's own
+    records and state read and written once (an elastic particle; gathered
+    neighbour records count as on-chip reuse).
+    pass 1: cell offsets 16, v record 16, L^-1 36, F (compensated) rw 144,
+            deviator (compensated) rw 96, eps_p / rate / D_init r 24, D r+w 16,
+            fail 4, material 4, V 8, u 24, sqrt E 8, sigma w 24,
+            pass-2 record w 96                                          = 516
+    pass 2: cell offsets 16, own pass-2 record 96, S0 16, V 8, D 8, sqrt E 8,
+            1/m 8, v_half rw 48, v w 24, force w 24, u r+w 48, fail 4, bc 1,
+            v record w 16                                               = 325"""
+    return 4 * list_words + 516 * N, 4 * list_words + 325 * N
+
+
+# FP32 operations per pair-interaction of the mixed path's pair terms (an FMA,
+# a compare-and-select or a reciprocal square root counts as one), from the
+# formulas as written in the pair functions of the library:
+#  pass 1 (velocity gradient): X_ij from cell offsets 9, r^2 3, 1/r 1, q 2,
+#         W'(q) 9, weight 3, v_ij 6, 9 sums                               = 42
+#  pass 2 (forces): X_ij 9, r^2 3, 1/r 1, q 2, W'(q) 9, weights 5, 3 sums of
+#         the S0 term, (A_j - A_i) X_ij 18, 3 sums                        = 53
+#         hourglass: u_ij 3, x_ij 3, 1/|x_ij| 4, error vector 21, projection 4,
+#         W(q) 11, coefficient 6, 3 sums                                  = 55
+MIXED_FP32_OPS_PER_PAIR = {"pass1": 42, "pass2": 53, "pass2_hourglass": 55}
+
+
+def mixed_fp32_ops(nnz: int, hourglass: bool = True):
+    """Algorithmic FP32 operations per step of (pass 1, pass 2)."""
+    o = MIXED_FP32_OPS_PER_PAIR
+    return o["pass1"] * nnz, (o["pass2"] + (o["pass2_hourglass"] if hourglass else 0)) * nnz
+
+
+# FP32 issue peak of one GB300: 152 SMs x 128 FP32 lanes x clock (Hz)
+FP32_LANES = 152 * 128
 
 
 FLAG_SPATIAL_ORDER = 1

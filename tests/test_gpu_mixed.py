@@ -76,7 +76,8 @@ def test_mixed_resume_is_bitwise():
         assert np.array_equal(v, ref[k]), k
 
 
-PLANS = [(0, 128, 0, 128), (1, 64, 1, 64), (2, 256, 1, 256), (3, 128, 0, 128), (1, 128, 1, 256)]
+PLANS = [(0, 128, 0, 128), (1, 64, 1, 64), (2, 256, 1, 256), (3, 128, 0, 128), (1, 128, 1, 256), (4, 64, 3, 128),
+         (2, 128, 4, 128), (4, 128, 2, 64), (4, 128, 5, 128)]
 
 
 def test_every_launch_plan_computes_the_same_step():
@@ -128,11 +129,13 @@ def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
     b = tlsph.Simulation.from_workload(_reordered(w, perm), precision="mixed")
     la, lb = a.neighbor_layout(), b.neighbor_layout()
     assert la["slices"] == lb["slices"] == (N + 31) // 32
-    assert la["aligned_slices"] >= 0.9 * la["slices"]
+    # lattice order: all slices aligned but those within 3 layers of either end
+    # of the index range (there i + o_k would leave the particle range)
+    assert la["aligned_slices"] >= 0.6 * la["slices"]
     if shuffle == "all":
         assert lb["aligned_slices"] <= 0.1 * lb["slices"]
     else:
-        assert 0.3 * lb["slices"] <= lb["aligned_slices"] <= 0.7 * lb["slices"]
+        assert 0.15 * lb["slices"] <= lb["aligned_slices"] <= 0.7 * lb["slices"]
     assert la["words"] < lb["words"]
     for plan in [(4, 128, 1, 128), (1, 64, 2, 256)]:
         a = tlsph.Simulation.from_workload(w, precision="mixed")
@@ -147,6 +150,14 @@ def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
     o = oracle.Simulation.from_workload(w)
     o.step(30)
     compare_state(a.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
+
+
+def test_plans_out_of_range_are_rejected():
+    g = tlsph.Simulation.from_workload(S.tensile_bar_cl(nx=5, ny=5, nz=8), precision="mixed")
+    for plan in [(5, 128, 1, 128), (1, 128, 6, 128), (1, 100, 1, 128), (1, 128, 4, 256), (1, 128, 5, 256), (1, 512, 1, 128)]:
+        with pytest.raises(tlsph.TlsphError) as e:
+            g.set_plan(plan)
+        assert e.value.code == -1, plan
 
 
 def test_autotune_restores_the_state_bitwise(tmp_path, monkeypatch):
