@@ -11,9 +11,9 @@ full step (both gather passes).  `value` is device-timed with CUDA events on
 the stream the library launches on, inputs resident in HBM; `e2e` is the same
 metric through the C ABI with host buffers: upload of the specimen from
 pinned memory, neighbour build, the K steps and the download of the final
-fields, all inside the timed region.  The working set (about 1.8 GB touched
-per step) is far larger than the 129 MB L2, so no flush is needed between
-steps.
+fields, all inside the timed region.  The state a step reads and writes
+(about 0.9 GB of HBM traffic) is far larger than the 129 MB L2, so no flush is
+needed between steps.
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 prefix of the same bar (same metric and unit).
@@ -295,9 +295,16 @@ def run_ours(args, rank: int, world: int, dist):
         ops = dict(zip(("pass1", "pass2"), tlsph.mixed_fp32_ops(nnz, w.hg_alpha != 0.0)))
         peak_alu = tlsph.FP32_LANES * 2070e6 / 1e12
         ach_alu = ops[kern] / (k_ms * 1e-3) / 1e12
+        try:
+            fma32 = tlsph.fma_peak(False, 4096) / 1e12
+            fma64 = tlsph.fma_peak(True, 128) / 1e12
+        except tlsph.TlsphError:
+            fma32 = fma64 = None
         roofline = {"bound": "alu", "kernel": kern, "achieved": ach_alu, "peak": peak_alu, "unit": "TFLOP/s",
                     "frac": ach_alu / peak_alu,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (an FMA counts as one op)",
+                    "measured_fma_peak": {"fp32": fma32, "fp64": fma64, "unit": "T FMA/s"},
+                    "frac_of_measured_fp32": ach_alu / fma32 if fma32 else None,
                     "traffic": hbm["traffic"], "algorithmic_ops_per_launch": ops[kern],
                     "fp32_ops_per_pair": tlsph.MIXED_FP32_OPS_PER_PAIR, "hbm_view": hbm}
     roofline["ms_per_launch"] = {"pass1": r["p1"], "pass2": r["p2"]}
@@ -373,7 +380,7 @@ def run_ours(args, rank: int, world: int, dist):
     cfg = {"workload": args.workload, "precision": args.precision, "particles": N, "pairs_per_step": nnz,
            "particle_steps_per_s": world * N * args.steps / (ms * 1e-3),
            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-           "l2": "inputs larger than L2 (about 1.8 GB per step vs 129 MB)"}
+           "l2": "inputs larger than L2 (about 0.9 GB of HBM traffic per step vs 129 MB)"}
     if r.get("layout"):
         cfg["neighbor_lists"] = dict(r["layout"], bytes_per_pair=4.0 * r["layout"]["words"] / nnz)
     if plastic:
@@ -452,16 +459,12 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
-    """Poisson stream (rate 20/s) of tensile bars and Taylor-impact cylinders,
-    1000-5000 steps each, served by continuous batching under a 120 GB
-    device-memory cap."""
+def serve_once(args, rate):
     import torch
 
     from paper_1901_07374_gb300 import serve
     from paper_1901_07374_gb300 import specimen as S
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    stream_reqs = S.serving_requests(count=args.requests, rate=args.rate, seed=0)
+    stream_reqs = S.serving_requests(count=args.requests, rate=rate, seed=0)
     reqs = [serve.Request(k, t, w, n) for k, (t, w, n) in enumerate(stream_reqs)]
     srv = serve.Server(mem_cap_bytes=120e9, chunk_steps=args.chunk)
     clk = ClockSampler(torch.cuda.current_device())
@@ -471,15 +474,41 @@ def run_serving(args):
     makespan = time.perf_counter() - t0
     clocks = clk.stop()
     summ = serve.summarize(reqs, makespan)
-    line = {"metric": METRIC, "value": summ["pair_interactions_per_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": int(sum(r.steps for r in reqs)), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+    offered = rate * sum(r.pairs * r.steps for r in reqs) / max(1, len(reqs))
+    summ.update(rate_per_s=rate, offered_pair_interactions_per_s=offered, peak_mem_gb=srv.peak_used / 1e9,
+                max_live=max((n for _, n, _ in srv.timeline), default=0),
+                steps=int(sum(r.steps for r in reqs)), clocks=clocks)
+    return summ
+
+
+def run_serving(args):
+    """Poisson stream of tensile bars and Taylor-impact cylinders, 1000-5000
+    steps each, served by continuous batching under a 120 GB device-memory
+    cap: the configured rate (20/s) and, with --rates, a sweep of arrival rates
+    on the same request seeds (latency knee)."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rates = sorted({float(x) for x in args.rates.split(",")} | {args.rate}) if args.rates else [args.rate]
+    runs = {rate: serve_once(args, rate) for rate in rates}
+    head = runs[args.rate]
+    sweep = None
+    if len(rates) > 1:
+        base = runs[rates[0]]["p99_s"]
+        knee = next((r for r in rates if runs[r]["p99_s"] > 2.0 * base), None)
+        sweep = {"knee_rate_per_s": knee,
+                 "knee_definition": "lowest arrival rate whose p99 latency exceeds twice the p99 at the lowest rate",
+                 "runs": [{k: runs[r][k] for k in ("rate_per_s", "p50_s", "p95_s", "p99_s", "makespan_s",
+                                                  "pair_interactions_per_s", "offered_pair_interactions_per_s",
+                                                  "done", "max_live", "peak_mem_gb")} for r in rates]}
+    line = {"metric": METRIC, "value": head["pair_interactions_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": head["steps"], "warmup": 0, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic request stream",
-            "config": {"workload": "serving", "requests": len(reqs), "rate_per_s": args.rate,
-                       "chunk_steps": args.chunk, "mem_cap_gb": 120, "peak_mem_gb": srv.peak_used / 1e9,
-                       "latency_s": {"p50": summ["p50_s"], "p95": summ["p95_s"], "p99": summ["p99_s"]},
-                       "makespan_s": makespan, "done": summ["done"], "failed": summ["failed"],
-                       "max_live": max((n for _, n, _ in srv.timeline), default=0)},
-            "clocks": clocks}
+            "config": {"workload": "serving", "requests": args.requests, "rate_per_s": args.rate,
+                       "chunk_steps": args.chunk, "mem_cap_gb": 120, "peak_mem_gb": head["peak_mem_gb"],
+                       "latency_s": {"p50": head["p50_s"], "p95": head["p95_s"], "p99": head["p99_s"]},
+                       "makespan_s": head["makespan_s"], "done": head["done"], "failed": head["failed"],
+                       "max_live": head["max_live"], "rate_sweep": sweep},
+            "clocks": head["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -498,6 +527,7 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving workload: arrivals per second")
     ap.add_argument("--chunk", type=int, default=100, help="serving workload: steps per batch chunk")
+    ap.add_argument("--rates", default=None, help="serving workload: comma-separated arrival-rate sweep")
     ap.add_argument("--plan", default=None, help="mixed launch plan v1,b1,v2,b2 (default: autotuned)")
     ap.add_argument("--no-plastic", action="store_true", help="skip the plastic-flow window")
     ap.add_argument("--plastic-steps", type=int, default=10)

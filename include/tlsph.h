@@ -317,6 +317,15 @@ int tlsph_material_point_batch(const tlsph_material *mat, double dt, int64_t n,
 int tlsph_neighbors_noalloc(const double *X, int64_t N, double rc, int64_t *row_ptr, int32_t *col,
                             int64_t nnz_cap, int64_t *nnz_out, void *stream);
 
+/* ---- FMA-rate microbenchmark (no counterpart in the paper) -------------
+ * Measures the current device's fused multiply-add rate, FP32 (fp64 = 0) or
+ * FP64 (fp64 != 0): every resident thread of an SM-filling grid runs 8
+ * independent FMA chains of 64 x iters FMAs (1 <= iters <= 2^20), timed with
+ * CUDA events on a private stream after a warm-up launch.  Writes FMAs per
+ * second to *fma_per_s (host).  It allocates and frees a small device sink.
+ * TLSPH_ERR_ARG for a bad argument, TLSPH_ERR_CUDA if a CUDA call fails. */
+int tlsph_fma_peak(int fp64, int iters, double *fma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

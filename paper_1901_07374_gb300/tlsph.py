@@ -77,7 +77,8 @@ EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph
            "tlsph_status_bits", "tlsph_info", "tlsph_get_state", "tlsph_set_state", "tlsph_last_error",
            "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
            "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
-           "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_neighbor_layout")
+           "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_neighbor_layout",
+           "tlsph_fma_peak")
 
 _lib = None
 _lock = threading.Lock()
@@ -131,6 +132,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_set_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
         L.tlsph_get_plan.restype = i32
         L.tlsph_get_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
+        L.tlsph_fma_peak.restype = i32
+        L.tlsph_fma_peak.argtypes = [i32, i32, ctypes.POINTER(dbl)]
         L.tlsph_neighbor_layout.restype = i32
         L.tlsph_neighbor_layout.argtypes = [vp] + [ctypes.POINTER(i64)] * 4
         L.tlsph_batch_create.restype = i32
@@ -194,6 +197,13 @@ def mixed_fp32_ops(nnz: int, hourglass: bool = True):
 
 # FP32 issue peak of one GB300: 152 SMs x 128 FP32 lanes x clock (Hz)
 FP32_LANES = 152 * 128
+
+
+def fma_peak(fp64: bool = False, iters: int = 4096) -> float:
+    """Measured FMA rate (FMAs per second) of the current device."""
+    v = ctypes.c_double()
+    _check(load().tlsph_fma_peak(1 if fp64 else 0, int(iters), ctypes.byref(v)))
+    return v.value
 
 
 FLAG_SPATIAL_ORDER = 1

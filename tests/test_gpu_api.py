@@ -129,3 +129,15 @@ def test_internal_order_is_invisible():
         c = tlsph.Simulation.from_workload(w, precision=precision, spatial_order=True)
         c.step(60)
         compare_state(c.state(), ref, w, tol=2e-4, fields=("U", "V", "F", "SIGMA", "FORCE"))
+
+
+def test_fma_peak_microbenchmark():
+    """The FMA-rate probe: FP32 well above FP64 on this part, both positive
+    and below the nominal unit counts x 2.2 GHz."""
+    f32 = tlsph.fma_peak(False, 512)
+    f64 = tlsph.fma_peak(True, 16)
+    assert 1e12 < f32 < 152 * 128 * 2.2e9
+    assert 0 < f64 < f32 / 8
+    with pytest.raises(tlsph.TlsphError) as e:
+        tlsph.fma_peak(False, 0)
+    assert e.value.code == -1
