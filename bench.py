@@ -67,10 +67,13 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
     return {"pass1": p1, "pass2": p2}
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the same kernel build, keyed by (workload, precision, kernel);
-# absent when the kernel changed after the capture
-TRAFFIC = {}
+# DRAM bytes (read + write) per step of each pass from one ncu capture of the
+# same kernel build, keyed by (workload, precision, pass, plan form of that
+# pass); absent for other plans and once the kernels change after the capture
+TRAFFIC = {
+    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 554882816,   # k_gather1_mixed_t4 + k_epi1_mixed
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 3): 334029568,   # k_pass2_mixed_t1
+}
 
 
 # ---------------------------------------------------------------- clocks
@@ -288,7 +291,9 @@ def run_ours(args, rank: int, world: int, dist):
         peak, src = 6800.0, "fallback"
     achieved = ab[kern] / (k_ms * 1e-3) / 1e9
     hbm = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-           "frac": achieved / peak, "peak_source": src, "traffic": TRAFFIC.get((args.workload, args.precision, kern)),
+           "frac": achieved / peak, "peak_source": src,
+           "traffic": TRAFFIC.get((args.workload, args.precision, kern,
+                                   (r.get("plan") or (0, 0, 0, 0))[0 if kern == "pass1" else 2])),
            "algorithmic_bytes_per_launch": ab[kern]}
     roofline = hbm
     if args.precision == "mixed":

@@ -7,7 +7,7 @@ stream, keeps the fastest per pass, and restores the simulation state
 bit for bit afterwards (checkpoint of every resumable field, step counter
 included), so tuning never changes a trajectory.  Results are cached per
 (GPU, precision, particle-count bucket, neighbours-per-row bucket, hourglass
-on/off) in a JSON file ($TLSPH_PLAN_CACHE, default
+on/off, candidate set) in a JSON file ($TLSPH_PLAN_CACHE, default
 ~/.cache/tlsph_gb300/plans.json).
 """
 from __future__ import annotations
@@ -16,10 +16,11 @@ import json
 import math
 import os
 import threading
+import zlib
 
 PASS1 = [(0, 128), (1, 128), (2, 64), (2, 128), (2, 256), (3, 256), (4, 64), (4, 128), (4, 256)]
 PASS2 = [(0, 128), (1, 64), (1, 128), (1, 256), (2, 128), (3, 64), (3, 128), (3, 256), (4, 128), (5, 64), (5, 128)]
-DEFAULT = (4, 128, 1, 128)
+DEFAULT = (4, 64, 3, 128)
 
 _lock = threading.Lock()
 
@@ -34,7 +35,11 @@ def _key(sim) -> str:
     N, nnz, _ = sim.info()
     name = torch.cuda.get_device_name()
     hg = "hg" if sim.cfg.hg_alpha != 0 else "nohg"
-    return f"{name}|{sim.precision}|N2^{int(math.log2(max(N, 1)))}|row{int(round(nnz / max(N, 1) / 8.0)) * 8}|{hg}"
+    # the candidate lists are part of the key: a cached plan is only reused by a tuner that would choose among
+    # the same candidates
+    cand = zlib.crc32(repr((PASS1, PASS2, DEFAULT)).encode())
+    return (f"{name}|{sim.precision}|N2^{int(math.log2(max(N, 1)))}|row{int(round(nnz / max(N, 1) / 8.0)) * 8}|{hg}"
+            f"|c{cand:08x}")
 
 
 def _load() -> dict:

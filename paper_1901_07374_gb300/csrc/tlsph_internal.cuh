@@ -115,7 +115,7 @@ struct tlsph_ctx {
     int dcur = 0;   // D[dcur] = D^n
     // mixed launch plan: pass-1 form, block, pass-2 form, block (the fastest on
     // GB300 for the 1M-particle bar; the autotuner may choose another)
-    int32_t plan[4] = { 4, 128, 1, 128 };
+    int32_t plan[4] = { 4, 64, 3, 128 };
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
     bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
     void *mixed = nullptr;      // mixed-precision state (mixed.cu)
@@ -138,7 +138,7 @@ struct tlsph_ctx {
 
 namespace tlsph {
 
-// scan.cu / nbr.cu
+// nbr.cu (scan, neighbour grid, CSR, order, correction matrix)
 size_t scan_tmp_elems(int64_t n);
 cudaError_t scan_exclusive_i64(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t st);
 struct CellGrid {
