@@ -163,7 +163,7 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
 {
     DevState &s = ctx->s;
     if (ctx->cfg.precision == TLSPH_PRECISION_MIXED) {
-        s.xo = at<float4>(base, L.xo);
+        s.xo = at<int4>(base, L.xo);
         s.s0 = at<float4>(base, L.s0);
         s.ell_off = at<int64_t>(base, L.ell_off);
         s.ell_w = at<int32_t>(base, L.ell_w);
@@ -176,7 +176,8 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.sigf = at<float>(base, L.sigf);
     } else {
         s.fsum = nullptr;
-        s.xo = s.s0 = s.r1 = s.r2 = nullptr;
+        s.xo = nullptr;
+        s.s0 = s.r1 = s.r2 = nullptr;
         s.ell_off = nullptr;
         s.ell_w = nullptr;
         s.colE = nullptr;
@@ -458,23 +459,23 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         for (size_t i = 0; i < n; ++i)
             for (int k = 0; k < 3; ++k) vr[k] += bcv_h[3 * i + k];
         for (int k = 0; k < 3; ++k) s.vref[k] = vr[k] / (double)n;
-        // packed cell coordinates: b_k bits hold c + 2 <= nc + 1
-        CellPack pk{};
-        int bits[3];
+        // fixed-point positions about the bounding-box centre, |coordinate| < 2^31 - 2^10 units
+        FixPack pk{};
+        double lo3[3], hi3[3];
+        for (int k = 0; k < 3; ++k) { lo3[k] = INFINITY; hi3[k] = -INFINITY; }
+        for (size_t i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) {
+                lo3[k] = std::min(lo3[k], X[3 * i + k]);
+                hi3[k] = std::max(hi3[k], X[3 * i + k]);
+            }
+        double ext = 0.0;
         for (int k = 0; k < 3; ++k) {
-            pk.lo[k] = grid.xmin[k];
-            pk.nc[k] = grid.nc[k];
-            bits[k] = 1;
-            while ((1 << bits[k]) < grid.nc[k] + 2) ++bits[k];
+            pk.center[k] = 0.5 * (lo3[k] + hi3[k]);
+            ext = std::max(ext, std::max(hi3[k] - pk.center[k], pk.center[k] - lo3[k]));
         }
-        if (bits[0] + bits[1] + bits[2] > 31) return bail(TLSPH_ERR_ARG, "specimen spans too many neighbour cells for the mixed path");
-        pk.cs = (float)grid.cs;
-        pk.inv_cs = 1.0 / (double)pk.cs;
-        pk.sh1 = bits[0];
-        pk.sh2 = bits[0] + bits[1];
-        pk.m0 = (1 << bits[0]) - 1;
-        pk.m1 = (1 << bits[1]) - 1;
-        pk.m2 = (1 << bits[2]) - 1;
+        const int e2 = ext > 0.0 ? (int)std::ceil(std::log2(ext / 2147482624.0)) : 0;
+        pk.unit = std::ldexp(1.0, e2);
+        pk.inv_unit = std::ldexp(1.0, -e2);
         s.pack = pk;
         CK(mixed_init_static(s, s.force, pk, st));
         // sliced neighbour lists for the thread-per-row plans

@@ -1,20 +1,25 @@
-// Mixed-precision time step: FP32 pair gathers and FP32 sums over j, FP64
-// particle state.
+// Mixed-precision time step: FP32 pair gathers and FP32 sums over j.
 //
-// What stays FP64: positions and displacements (u accumulated in FP64), the
-// deformation gradient F and its determinant J, the correction matrix
-// inverse (computed once in FP64, used rounded), the stress deviator and the
-// whole constitutive + damage update (the radial return and the failure
-// threshold decisions), the nodal force handed to the integrator and the
-// velocity-Verlet update.
+// What stays FP64: displacements and velocities (u, v, v^{n+1/2}), the
+// correction matrix inverse (computed once in FP64, used rounded), the nodal
+// force handed to the integrator and the velocity-Verlet update, and the
+// constitutive + damage update of every particle that yields, is near yield,
+// is a GTN particle or has reached damage initiation.
 //
-// What is FP32: every per-pair term of both passes, the sums over j, the
-// polar decomposition, the rotations and P = J sigma F^{-T}, A = P L^{-T}.
+// Compensated FP32 (hi + lo float pairs): F and the unrotated stress deviator,
+// so that small increments accumulate without loss over many steps.
+//
+// What is FP32: every per-pair term of both passes, the sums over j, J - 1
+// (from the invariants of F - I), the polar decomposition, the rotations,
+// P = J sigma F^{-T}, A = P L^{-T}, and the elastic branch of Algorithm 1 for
+// particles whose trial stress is clearly inside the yield surface.
 //
 // The pair terms are arranged so the FP32 sums carry no large cancellation:
-//  - a position travels as its offset from the origin of its neighbour-grid
-//    cell plus the cell's integer coordinates, so X_ij = dc * cs + (o_j - o_i)
-//    with dc in {-1, 0, 1} per axis and offsets no longer than a cell;
+//  - a reference position is an int32 fixed-point triple about the specimen's
+//    centre (unit a power of two, |coordinate| < 2^31), so X_ij is an exact
+//    integer difference rounded once to FP32; every pair length is in those
+//    units (the kernel argument q uses unit / h, the hourglass sums are
+//    rescaled per particle);
 //  - velocities are mirrored relative to a bulk reference velocity;
 //  - the hourglass error vector uses F - I and u, e = (F_i - I) X_ij - u_ij;
 //  - the stress term is written with differences (Sec. 3.1 force, rearranged):
@@ -22,17 +27,16 @@
 //          + V_i A_i [ (2 - D_i) S0_i - sum_j V_j D_j grad W_ij ],
 //    with the static S0_i = sum_j V_j grad W_ij computed once in FP64.
 //
-// Data layout (float4 arrays indexed by particle, "SoA of float4", so a warp
+// Data layout (16-byte records indexed by particle, "SoA of float4", so a warp
 // gathering consecutive particles reads consecutive 16-byte words):
-//   xo   {offset to cell origin, packed cell coordinates}
+//   xo   int4 {fixed-point x, y, z, 0}
 //   r1   {v^{n+1/2} - v_ref, V (1 - D)}                       pass-1 gather record
 //   r2k  k = 0..5 (at r2 + k N):                               pass-2 gather record
 //        {A00 A01 A02 A10} {A11 A12 A20 A21} {A22, V(1-D), V, u_x}
 //        {u_y, u_z, G00, G01} {G02 G10 G11 G12} {G20, G21, G22, sqrt(E) V (1-D)}
-//        with G = F - I.
-// Thread-per-row kernels read their neighbour indices from a sliced-ELL copy
-// of the CSR (slice = one warp of 32 consecutive rows, column-major inside
-// the slice), so the 32 lanes' k-th neighbour indices are one 128-byte line.
+//        with G = F - I and u in fixed-point units.
+// Thread-per-row kernels read their neighbours through the sliced neighbour
+// lists (slices of 32 rows, aligned or explicit form, described below).
 #include <math.h>
 
 #include <algorithm>
@@ -50,12 +54,13 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     const tlsph_config &cfg = ctx.cfg;
     c.dt = cfg.dt;
     c.half_dt = 0.5 * cfg.dt;
-    c.inv_h = (float)(1.0 / cfg.h);
+    c.inv_h = (float)(ctx.s.pack.unit / cfg.h);
     c.dt_dw = (float)(cfg.dt / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
     c.dw_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
     c.w_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h));
     c.hg_coef = (float)(-0.5 * cfg.hg_alpha);
-    c.cs = ctx.s.pack.cs;
+    c.inv_unit = ctx.s.pack.inv_unit;
+    c.inv_unit_f = (float)ctx.s.pack.inv_unit;
     c.vref0 = ctx.s.vref[0];
     c.vref1 = ctx.s.vref[1];
     c.vref2 = ctx.s.vref[2];
@@ -63,12 +68,6 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     c.step_index = step_index;
     c.ucur = ctx.ucur;
     c.dcur = ctx.dcur;
-    c.sh1 = ctx.s.pack.sh1;
-    c.sh2 = ctx.s.pack.sh2;
-    c.m0 = ctx.s.pack.m0;
-    c.m1 = ctx.s.pack.m1;
-    c.m2 = ctx.s.pack.m2;
-    c.bias = 1 | (1 << c.sh1) | (1 << c.sh2);
     c.wall = (cfg.flags & TLSPH_FLAG_WALL) != 0;
     return c;
 }
@@ -150,18 +149,24 @@ __device__ __forceinline__ void sym_rotate_f(const float *Q, const float *s, flo
 #undef QT
 }
 
-// X_j - X_i from cell offsets; t_i = bias - packed_i (per row).  Each biased
-// field of packed_j + t_i is c_j - c_i + 1 in {0, 1, 2}, so no field borrows.
-__device__ __forceinline__ float3 xdiff(const MixConst &c, const float4 oj, const float4 oi, int t_i)
+// X_j - X_i in units of the fixed-point grid: an exact integer difference
+// (modular, so a masked slot between distant particles stays finite), then
+// rounded once to FP32
+__device__ __forceinline__ float3 xdiff(const int4 oj, const int4 oi)
 {
-    const int D = __float_as_int(oj.w) + t_i;
-    const float dx = (float)(D & c.m0) - 1.0f;
-    const float dy = (float)((D >> c.sh1) & c.m1) - 1.0f;
-    const float dz = (float)((D >> c.sh2) & c.m2) - 1.0f;
-    return make_float3(fmaf(dx, c.cs, oj.x - oi.x), fmaf(dy, c.cs, oj.y - oi.y), fmaf(dz, c.cs, oj.z - oi.z));
+    return make_float3((float)(int)((unsigned)oj.x - (unsigned)oi.x), (float)(int)((unsigned)oj.y - (unsigned)oi.y),
+                       (float)(int)((unsigned)oj.z - (unsigned)oi.z));
 }
 
-__device__ __forceinline__ int row_bias(const MixConst &c, const float4 oi) { return c.bias - __float_as_int(oi.w); }
+// M4 spline (normalisation in the step constants) in the branch-free form
+//   W(q) = (2 - q)_+^3 / 4 - (1 - q)_+^3,   W'(q) = 3 (1 - q)_+^2 - 3/4 (2 - q)_+^2
+__device__ __forceinline__ float spline_dw_ab(float q, float &a, float &b)
+{
+    a = fmaxf(2.0f - q, 0.0f);
+    b = fmaxf(1.0f - q, 0.0f);
+    return fmaf(3.0f * b, b, -0.75f * a * a);
+}
+__device__ __forceinline__ float spline_w_ab(float a, float b) { return fmaf(0.25f * a * a, a, -b * b * b); }
 
 // ------------------------------------------------------------------ sliced neighbour lists
 // The thread-per-row kernels read neighbours slice by slice, a slice being the
@@ -412,12 +417,13 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     float4 *__restrict__ r2 = s.r2;
     const int64_t N = c.N;
     const int fail = s.fail[i];
-    const double *un = s.u[c.ucur ^ 1];   // u^{n+1}, mirrored for pass 2's hourglass term
+    const double *un = s.u[c.ucur ^ 1];   // u^{n+1}, mirrored for pass 2's hourglass term (fixed-point units)
     const float Vf = (float)s.vol[i];
     float Fh[9], Fl[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) { Fh[k] = s.Fh[k * N + i]; Fl[k] = s.Fl[k * N + i]; }
-    const float u0 = (float)un[3 * i], u1 = (float)un[3 * i + 1], u2 = (float)un[3 * i + 2];
+    const float u0 = (float)un[3 * i] * c.inv_unit_f, u1 = (float)un[3 * i + 1] * c.inv_unit_f,
+                u2 = (float)un[3 * i + 2] * c.inv_unit_f;
     if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
         Dnext[i] = Dn[i];
         r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -564,13 +570,14 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
 }
 
 // ------------------------------------------------------------------ pass 1 pair terms
-__device__ __forceinline__ void pair1(const MixConst &c, const float4 oi, int ti, const float4 vi, const float4 oj,
+__device__ __forceinline__ void pair1(const MixConst &c, const int4 oi, const float4 vi, const int4 oj,
                                       const float4 vj, float wmask, float *m)
 {
-    const float3 d = xdiff(c, oj, oi, ti);
+    const float3 d = xdiff(oj, oi);
     const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
     const float rinv = rsqrtf(r2);
-    const float cw = wmask * vj.w * spline_dw(r2 * rinv * c.inv_h) * rinv;   // V_j (1 - D_j) W'/r
+    float a, b;
+    const float cw = wmask * vj.w * spline_dw_ab(r2 * rinv * c.inv_h, a, b) * rinv;   // V_j (1 - D_j) W'/r
     const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
     m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
     m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
@@ -581,16 +588,17 @@ __device__ __forceinline__ void pair1(const MixConst &c, const float4 oi, int ti
 template <int U>
 __device__ __forceinline__ void gather1_row(const DevState &s, const MixConst &c, int64_t i, float *m)
 {
-    const float4 oi = s.xo[i], vi = s.r1[i];
-    const int ti = row_bias(c, oi);
+    const int4 oi = s.xo[i];
+    const float4 vi = s.r1[i];
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = 0.0f;
     for_slots<U>(s, i, [&](const int *j, const float *w) {
-        float4 o[U], v[U];
+        int4 o[U];
+        float4 v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) { o[u] = s.xo[j[u]]; v[u] = s.r1[j[u]]; }
 #pragma unroll
-        for (int u = 0; u < U; ++u) pair1(c, oi, ti, vi, o[u], v[u], w[u], m);
+        for (int u = 0; u < U; ++u) pair1(c, oi, vi, o[u], v[u], w[u], m);
     });
 }
 
@@ -602,15 +610,15 @@ __device__ __forceinline__ void gather1_w32(const DevState &s, const MixConst &c
     for (int k = 0; k < 9; ++k) keep[k] = 0.0f;
     for (int r = 0; r < nrows; ++r) {
         const int64_t i = row0 + r;
-        const float4 oi = s.xo[i], vi = s.r1[i];
-        const int ti = row_bias(c, oi);
+        const int4 oi = s.xo[i];
+        const float4 vi = s.r1[i];
         const int64_t p0 = s.row_ptr[i], p1 = s.row_ptr[i + 1];
         float m[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) m[k] = 0.0f;
         for (int64_t p = p0 + lane; p < p1; p += 32) {
             const int j = s.col[p];
-            pair1(c, oi, ti, vi, s.xo[j], s.r1[j], 1.0f, m);
+            pair1(c, oi, vi, s.xo[j], s.r1[j], 1.0f, m);
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -696,7 +704,8 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
     f[1] = Vi * (double)c.dw_norm * ((double)(Ai[3] * bx + Ai[4] * by + Ai[5] * bz) + omdi * (double)keep[4]);
     f[2] = Vi * (double)c.dw_norm * ((double)(Ai[6] * bx + Ai[7] * by + Ai[8] * bz) + omdi * (double)keep[5]);
     if (HG) {
-        const double hc = (double)c.hg_coef * s.sqrtE[i] * omdi * Vi * (double)c.w_norm;
+        // the pair sums are in fixed-point units: X_ij, u_ij and x_ij scaled by 1/unit
+        const double hc = (double)c.hg_coef * s.sqrtE[i] * omdi * Vi * (double)c.w_norm * c.inv_unit;
         f[0] += hc * (double)keep[6];
         f[1] += hc * (double)keep[7];
         f[2] += hc * (double)keep[8];
@@ -739,8 +748,8 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
 }
 
 struct Row2 {   // row i's own pass-2 record
-    float4 o, a0, a1, a2, a3, a4, a5;
-    int t;
+    int4 o;
+    float4 a0, a1, a2, a3, a4, a5;
 };
 
 template <bool HG>
@@ -749,7 +758,6 @@ __device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, 
     const int64_t N = c.N;
     Row2 w;
     w.o = s.xo[i];
-    w.t = row_bias(c, w.o);
     w.a0 = s.r2[i];
     w.a1 = s.r2[N + i];
     w.a2 = s.r2[2 * N + i];
@@ -767,13 +775,14 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
                                       float *acc)
 {
     const int64_t N = c.N;
-    const float4 oj = s.xo[j];
+    const int4 oj = s.xo[j];
     const float4 b0 = s.r2[j], b1 = s.r2[N + j], b2 = s.r2[2 * N + j];
-    const float3 d = xdiff(c, oj, w.o, w.t);
+    const float3 d = xdiff(oj, w.o);
     const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
     const float rinv = rsqrtf(r2v);
     const float q = r2v * rinv * c.inv_h;
-    const float g0 = wmask * spline_dw(q) * rinv;
+    float a, b;
+    const float g0 = wmask * spline_dw_ab(q, a, b) * rinv;
     const float g = b2.z * g0;                     // V_j W'/r
     const float gd = (b2.z - b2.y) * g0;           // V_j D_j W'/r
     acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
@@ -791,7 +800,7 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
         const float ey = (w.a4.y + b4.y) * d.x + (w.a4.z + b4.z) * d.y + (w.a4.w + b4.w) * d.z - 2.0f * uy;
         const float ez = (w.a5.x + b5.x) * d.x + (w.a5.y + b5.y) * d.y + (w.a5.z + b5.z) * d.z - 2.0f * uz;
         const float delta = (ex * xx + ey * xy + ez * xz) * lxi;
-        const float ch = wmask * b5.w * spline_w(q) * rinv * rinv * delta * lxi;   // sqrt(E_j) V_j (1 - D_j) ...
+        const float ch = wmask * b5.w * spline_w_ab(a, b) * rinv * rinv * delta * lxi;   // sqrt(E_j) V_j (1 - D_j) ...
         acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
     }
 }
@@ -916,23 +925,15 @@ __global__ void __launch_bounds__(128) k_epi2_mixed(DevState s, MixConst c)
 }
 
 // ------------------------------------------------------------------ mirrors
-// static records from the FP64 inputs: cell offsets, S0, L^{-1}
-__global__ void k_mixed_static(DevState s, const double *S0, CellPack pk)
+// static records from the FP64 inputs: fixed-point positions, S0, L^{-1}
+__global__ void k_mixed_static(DevState s, const double *S0, FixPack pk)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    int cc[3];
-    float off[3];
+    int x[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const double x = s.X[3 * i + k] - pk.lo[k];
-        int ck = (int)floor(x * pk.inv_cs);
-        ck = ck < 0 ? 0 : (ck > pk.nc[k] - 1 ? pk.nc[k] - 1 : ck);
-        cc[k] = ck;
-        off[k] = (float)(x - (double)ck * (double)pk.cs);
-    }
-    const int packed = (cc[0] + 1) | ((cc[1] + 1) << pk.sh1) | ((cc[2] + 1) << pk.sh2);
-    s.xo[i] = make_float4(off[0], off[1], off[2], __int_as_float(packed));
+    for (int k = 0; k < 3; ++k) x[k] = (int)llrint((s.X[3 * i + k] - pk.center[k]) * pk.inv_unit);
+    s.xo[i] = make_int4(x[0], x[1], x[2], 0);
     s.s0[i] = make_float4((float)S0[3 * i], (float)S0[3 * i + 1], (float)S0[3 * i + 2], 0.0f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.linv32[9 * i + k] = (float)s.Linv[9 * i + k];
@@ -1014,7 +1015,7 @@ cudaError_t mixed_import(const tlsph_ctx &ctx, int field, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPack &pk, cudaStream_t st)
+cudaError_t mixed_init_static(const DevState &s, const double *S0, const FixPack &pk, cudaStream_t st)
 {
     k_mixed_static<<<nb(s.N, 256), 256, 0, st>>>(s, S0, pk);
     return cudaGetLastError();

@@ -29,16 +29,13 @@ struct DevMat {
     float Kf, Gf, Af, Bf, nf, Cf, inv_epsdot0f, rho0c02f, S_alphaf, Gamma0f, sqrtEf;
 };
 
-// Packed cell coordinates of the mixed path: positions travel as the offset
-// from the origin of a neighbour-grid cell (size cs >= rc) plus the cell's
-// coordinates packed in one int32 (fields of m_k = 2^b_k - 1 at shifts 0,
-// sh1, sh2).
-struct CellPack {
-    double lo[3];
-    double inv_cs;
-    float cs;
-    int32_t nc[3];
-    int32_t sh1, sh2, m0, m1, m2;
+// Fixed-point reference positions of the mixed path: X = center + unit * (x, y, z)
+// with int32 x, y, z and unit a power of two chosen so that |x|, |y|, |z| < 2^31.
+// A neighbour offset X_ij is then an exact integer difference, converted to
+// FP32 in units of `unit`.
+struct FixPack {
+    double center[3];
+    double unit, inv_unit;
 };
 
 // Device arrays of one context.  SoA per quantity; vectors and tensors of a
@@ -71,7 +68,7 @@ struct DevState {
     uint32_t *status;       // 1
     const DevMat *mats;     // TLSPH_MAX_MATERIALS
     // mixed-precision records (null in the FP64 path)
-    float4 *xo;             // N   {offset to cell origin, packed cell coordinates}
+    int4 *xo;               // N   {fixed-point position x, y, z (FixPack), 0}
     float4 *s0;             // N   {sum_j V_j W'(r)/r (X_j - X_i), 0}  (static, FP64-accurate)
     float *linv32;          // N*9 L^{-1} rounded
     float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
@@ -87,7 +84,7 @@ struct DevState {
     const int64_t *ell_off; // (N + 31) / 32 + 1 slice word offsets
     const int32_t *ell_w;   // (N + 31) / 32 slice widths: W (explicit) or ~W (aligned)
     double vref[3];         // bulk reference velocity of the r1 mirror
-    CellPack pack;
+    FixPack pack;
 };
 
 struct Scratch {            // neighbour-build scratch (set-up only)
@@ -199,12 +196,13 @@ void set_last_error_text(const std::string &msg);
 // mixed.cu -- step constants of the mixed path (defined there)
 struct MixConst {
     double dt, half_dt;
-    float dt_dw, inv_h, dw_norm, w_norm, hg_coef, cs;   // dt_dw = dt x W' normalisation
+    float dt_dw, inv_h, dw_norm, w_norm, hg_coef;   // dt_dw = dt x W' normalisation; inv_h = unit / h
+    float inv_unit_f;                               // 1 / unit (a power of two)
+    double inv_unit;
     double vref0, vref1, vref2;
     int64_t N;
     int64_t step_index;
     int ucur, dcur;
-    int sh1, sh2, m0, m1, m2, bias;   // packed cell coordinates
     int wall;
 };
 
@@ -222,7 +220,7 @@ BatchSlot make_batch_slot(const tlsph_ctx &ctx);
 cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, int grid, cudaStream_t st);
 int batch_grid(bool hg);
 
-cudaError_t mixed_init_static(const DevState &s, const double *S0, const CellPack &pk, cudaStream_t st);
+cudaError_t mixed_init_static(const DevState &s, const double *S0, const FixPack &pk, cudaStream_t st);
 cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st);
 cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st);
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
