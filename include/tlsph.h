@@ -76,7 +76,7 @@ typedef struct {
     double dt;         /* time step [s], fixed for the run */
     double hg_alpha;   /* hourglass-control coefficient (0 disables it) */
     int32_t precision; /* TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED */
-    int32_t flags;     /* 0 or TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_WALL */
+    int32_t flags;     /* 0 or an OR of TLSPH_FLAG_SPATIAL_ORDER or TLSPH_FLAG_LINE_ORDER, TLSPH_FLAG_WALL */
 } tlsph_config;
 
 /* Store particles in a spatially compact internal order (cells of the
@@ -87,6 +87,19 @@ typedef struct {
  * consecutive particles and a warp's gathers coalesce; the brick order helps
  * inputs in arbitrary order. */
 #define TLSPH_FLAG_SPATIAL_ORDER 1
+
+/* Store particles in lattice-line order along the specimen's longest
+ * bounding-box axis L: sorted by (round((X_a - min_a) / d),
+ * round((X_b - min_b) / d), X_L) with a, b the two shorter axes and d the
+ * cube root of the median particle volume.  For particles on a (jittered)
+ * simple cubic lattice of spacing d every lattice line along L becomes
+ * contiguous, so the 32 rows of a warp share their neighbourhood shape and
+ * their neighbour index offsets: the mixed path's neighbour lists are then
+ * aligned slices with almost no padding slots.  Every field crossing the ABI
+ * stays in the caller's order; results differ from the caller's order only by
+ * the order of the sums over j.  Not combinable with TLSPH_FLAG_SPATIAL_ORDER
+ * (TLSPH_ERR_ARG). */
+#define TLSPH_FLAG_LINE_ORDER 4
 
 /* A rigid frictionless wall on the plane z = 0 (current configuration): a
  * particle that would drift below it is put back on the plane and its
@@ -216,7 +229,7 @@ int tlsph_destroy(tlsph_ctx *ctx);
  * plan[3] its block size (multiples of 32 up to 256).  Every plan computes
  * the same method; sums over a row are grouped differently, so results
  * differ only by FP32 rounding.  n must be 4.  TLSPH_ERR_ARG for a plan out
- * of range.  A new mixed context starts with (4, 64, 3, 128).  The FP64 path
+ * of range.  A new mixed context starts with (2, 128, 4, 128).  The FP64 path
  * ignores the plan. */
 int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);
 int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);

@@ -27,7 +27,7 @@ struct Layout {
     size_t X, vol, mass, inv_mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
     size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
-    size_t Fh, Fl, sdh, sdl, sigf;
+    size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
     size_t perm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order + staged caller-order inputs
     size_t overlay_end, ell;
@@ -52,6 +52,47 @@ struct Carver {
 int64_t ell_capacity(int64_t N, int64_t nnz_cap)
 {
     return std::max<int64_t>(nnz_cap + nnz_cap / 2 + 128 * ((N + 31) / 32), 32);
+}
+
+// Lattice-line order (TLSPH_FLAG_LINE_ORDER): perm[k] = caller index of
+// internal particle k, sorted by the rounded lattice coordinates of the two
+// shorter bounding-box axes, then by the coordinate along the longest axis
+// (ties by caller index).
+std::vector<int32_t> line_order_perm(const double *X, const double *vol, int64_t N)
+{
+    std::vector<int32_t> perm((size_t)N);
+    for (int64_t i = 0; i < N; ++i) perm[(size_t)i] = (int32_t)i;
+    if (N < 2) return perm;
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+    for (int64_t i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], X[3 * i + k]);
+            hi[k] = std::max(hi[k], X[3 * i + k]);
+        }
+    int L = 0;
+    for (int k = 1; k < 3; ++k)
+        if (hi[k] - lo[k] > hi[L] - lo[L]) L = k;
+    const int a = (L + 1) % 3, b = (L + 2) % 3;
+    std::vector<double> v(vol, vol + N);
+    std::nth_element(v.begin(), v.begin() + N / 2, v.end());
+    const double d = std::cbrt(std::max(v[(size_t)(N / 2)], 0.0));
+    const double inv = d > 0.0 ? 1.0 / d : 0.0;
+    struct Key { int64_t ab; double xl; int32_t i; };
+    std::vector<Key> key((size_t)N);
+    const int64_t nb = (int64_t)std::llround((hi[b] - lo[b]) * inv) + 1;
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t ka = (int64_t)std::llround((X[3 * i + a] - lo[a]) * inv);
+        const int64_t kb = (int64_t)std::llround((X[3 * i + b] - lo[b]) * inv);
+        key[(size_t)i] = Key{ ka * nb + kb, X[3 * i + L], (int32_t)i };
+    }
+    std::sort(key.begin(), key.end(), [](const Key &p, const Key &q) {
+        if (p.ab != q.ab) return p.ab < q.ab;
+        if (p.xl != q.xl) return p.xl < q.xl;
+        return p.i < q.i;
+    });
+    for (int64_t k = 0; k < N; ++k) perm[(size_t)k] = key[(size_t)k].i;
+    return perm;
 }
 
 Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
@@ -97,6 +138,8 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
         L.Fh = c.take(9 * n * f); L.Fl = c.take(9 * n * f);
         L.sdh = c.take(6 * n * f); L.sdl = c.take(6 * n * f);
         L.sigf = c.take(6 * n * f);
+        L.slowq = c.take(n * sizeof(int32_t));
+        L.slowq_n = c.take(2 * sizeof(uint32_t));
     }
     // overlay block: F, sd, sig, A  |  neighbour-build scratch
     const size_t ov = c.off;
@@ -155,7 +198,11 @@ bool valid_config(const tlsph_config *c, std::string &why)
         why = "precision must be TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED";
         return false;
     }
-    if ((c->flags & ~(TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_WALL)) != 0) { why = "unknown flags"; return false; }
+    if ((c->flags & ~(TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_LINE_ORDER | TLSPH_FLAG_WALL)) != 0) { why = "unknown flags"; return false; }
+    if ((c->flags & TLSPH_FLAG_SPATIAL_ORDER) && (c->flags & TLSPH_FLAG_LINE_ORDER)) {
+        why = "TLSPH_FLAG_SPATIAL_ORDER and TLSPH_FLAG_LINE_ORDER exclude each other";
+        return false;
+    }
     return true;
 }
 
@@ -174,6 +221,8 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.Fh = at<float>(base, L.Fh); s.Fl = at<float>(base, L.Fl);
         s.sdh = at<float>(base, L.sdh); s.sdl = at<float>(base, L.sdl);
         s.sigf = at<float>(base, L.sigf);
+        s.slowq = at<int32_t>(base, L.slowq);
+        s.slowq_n = at<uint32_t>(base, L.slowq_n);
     } else {
         s.fsum = nullptr;
         s.xo = nullptr;
@@ -400,9 +449,16 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     Scratch sc{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
                 at<int64_t>(base, L.scan_tmp), L.scan_elems };
     // ---- internal order (brick-major cells, caller index inside a cell) and the gather into it
-    ctx->reordered = (cfg->flags & TLSPH_FLAG_SPATIAL_ORDER) != 0;
+    const bool line_order = (cfg->flags & TLSPH_FLAG_LINE_ORDER) != 0;
+    ctx->reordered = (cfg->flags & (TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_LINE_ORDER)) != 0;
     ctx->perm_dev = at<int32_t>(base, L.perm);
-    CK(build_order(stX, N, grid, sc, !ctx->reordered, ctx->perm_dev, st));
+    if (line_order) {
+        const std::vector<int32_t> lp = line_order_perm(X, vol, N);
+        CK(cudaMemcpyAsync(ctx->perm_dev, lp.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        CK(build_order(stX, N, grid, sc, !ctx->reordered, ctx->perm_dev, st));
+    }
     CK(launch_gather_inputs(ctx->perm_dev, N, stX, stvol, stmat, stbcm, stbcv, stf0, s, st));
     ctx->perm.resize(n);
     ctx->inv.resize(n);
@@ -494,7 +550,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         ctx->ell_stats[3] = ell_n;
         for (int32_t wv : ell_w_host) {
             ctx->ell_stats[1] += wv < 0;
-            ctx->ell_stats[2] += 32 * (int64_t)(wv < 0 ? ~wv : wv);
+            ctx->ell_stats[2] += 32 * (int64_t)(wv < 0 ? ((~wv) & 0xffffff) : wv);
         }
         int32_t *colE = nullptr;
         if (arena) {
@@ -516,7 +572,10 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
 
     // ---- initial state (overwrites the scratch overlay)
     CK(launch_init_state(s, st));
-    if (mixed) CK(mixed_import(*ctx, -1, st));
+    if (mixed) {
+        CK(mixed_import(*ctx, -1, st));
+        CK(cudaMemsetAsync(s.slowq_n, 0, 2 * sizeof(uint32_t), st));
+    }
     CK(cudaStreamSynchronize(st));
 #undef CK
     ctx->need_predict = true;

@@ -24,7 +24,7 @@ struct tlsph_batch {
     std::vector<tlsph_ctx *> members;
     std::vector<int64_t> steps_at;  // each member's step count the table was built for
     int hg = -1;                    // hourglass on/off shared by the members
-    int grid = 0;
+    int grid[2][4] = { { 0, 0, 0, 0 }, { 0, 0, 0, 0 } };   // persistent grids per kernel kind, without / with hourglass
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_hg = -1;
@@ -141,7 +141,8 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph)
             return batch_fail(b, TLSPH_ERR_STATE, "a member was changed outside the batch: call tlsph_batch_set again");
     }
     const bool hg = b->hg == 1;
-    if (b->grid == 0) b->grid = batch_grid(hg);
+    int *grid = b->grid[hg ? 1 : 0];
+    if (grid[0] == 0) batch_grid(hg, grid);
     // the batch's work follows everything already queued on the caller's stream
     cudaError_t e = cudaEventRecord(b->start, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->own, b->start, 0);
@@ -152,7 +153,7 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph)
             if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
             e = cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t le = launch_batch_step(b->hdr, b->slots, b->capacity, hg, b->grid, b->own);
+                cudaError_t le = launch_batch_step(b->hdr, b->slots, b->capacity, hg, grid, b->own);
                 e = cudaStreamEndCapture(b->own, &b->graph);
                 if (le != cudaSuccess) e = le;
             }
@@ -166,7 +167,7 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph)
         for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->exec, b->own);
     } else {
         for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
-            e = launch_batch_step(b->hdr, b->slots, b->capacity, hg, b->grid, b->own);
+            e = launch_batch_step(b->hdr, b->slots, b->capacity, hg, grid, b->own);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->done, b->own);
     // later work on the caller's stream and on each member's own stream is ordered after the batch

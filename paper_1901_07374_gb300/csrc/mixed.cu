@@ -175,15 +175,17 @@ __device__ __forceinline__ float spline_w_ab(float a, float b) { return fmaf(0.2
 //  explicit: ell_w[g] = W >= 0 slots; entry k of lane l at ell_off[g] + 32 k + l
 //            holds the neighbour index j, or ~p for a padding slot (p a valid
 //            particle index other than the row's, weight 0);
-//  aligned:  ell_w[g] = ~W < 0.  Slot k stands for the same index offset o_k
-//            in every row of the slice (j = i + o_k); the slice's union of
-//            offsets is stored once (o_k at ell_off[g] + k, padded with the
-//            last offset to T = 32 ceil(W / 32) words) followed by one mask
-//            word per row and 32 slots (bit k % 32 of the word at
-//            ell_off[g] + T + 32 (k / 32) + l says whether row l has
-//            j = i + o_k as a neighbour).  A slice is aligned only if i + o_k
-//            is a particle index for every row i < N of the slice and every
-//            offset, so a masked slot still reads a valid particle (j != i).
+//  aligned:  ell_w[g] = ~(W | clamp << 24) < 0.  Slot k stands for the same
+//            index offset o_k in every row of the slice (j = i + o_k); the
+//            slice's union of offsets is stored once (o_k at ell_off[g] + k,
+//            padded with the last offset to T = 32 ceil(W / 32) words)
+//            followed by one mask word per row and 32 slots (bit k % 32 of
+//            the word at ell_off[g] + T + 32 (k / 32) + l says whether row l
+//            has j = i + o_k as a neighbour).  clamp = 0 when i + o_k is a
+//            particle index for every row i < N of the slice and every
+//            offset, so a masked slot reads a valid particle (j != i) as it
+//            stands; slices near either end of the index range have clamp = 1
+//            and their masked slots that would leave the range read i -+ 1.
 //
 // Rows are sorted by j, so slots run in ascending j in both forms: the sums
 // over j are taken in CSR order either way.  Particles laid out with a regular
@@ -251,9 +253,10 @@ __global__ void k_ell_plan(const int64_t *row_ptr, const int32_t *col, int64_t N
     const int wu = slice_union(row_ptr, col, i, N, limit + 1, nullptr, nullptr, lane, 0, omin, omax);
     const int64_t words_u = 64 * (int64_t)((wu + 31) / 32);
     const bool in_range = i >= N || (i + omin >= 0 && i + omax < N);
-    const bool aligned = __all_sync(0xffffffffu, in_range) && wp > 0 && wu <= limit && words_u <= 32 * (int64_t)wp;
+    const int clamp = __all_sync(0xffffffffu, in_range) ? 0 : 1;
+    const bool aligned = wp > 0 && wu <= limit && words_u <= 32 * (int64_t)wp;
     if (lane == 0) {
-        ell_w[g] = aligned ? ~wu : wp;
+        ell_w[g] = aligned ? ~(wu | (clamp << 24)) : wp;
         ell_off[g] = aligned ? words_u : 32 * (int64_t)wp;
     }
 }
@@ -268,7 +271,7 @@ __global__ void k_ell_fill(const int64_t *row_ptr, const int32_t *col, int64_t N
     const int wv = ell_w[g];
     int32_t *o = colE + ell_off[g];
     if (wv < 0) {
-        const int W = ~wv;
+        const int W = (~wv) & 0xffffff;
         const int T = 32 * ((W + 31) / 32);
         int omin, omax;
         slice_union(row_ptr, col, i, N, W, o, reinterpret_cast<uint32_t *>(o), lane, T, omin, omax);
@@ -277,6 +280,29 @@ __global__ void k_ell_fill(const int64_t *row_ptr, const int32_t *col, int64_t N
     const int64_t b = i < N ? row_ptr[i] : 0, n = i < N ? row_ptr[i + 1] - row_ptr[i] : 0;
     const int32_t pad = ~(int32_t)(i == 0 ? (N > 1 ? 1 : 0) : (i < N ? i - 1 : 0));
     for (int k = 0; k < wv; ++k) o[32 * k + lane] = k < n ? col[b + k] : pad;
+}
+
+// aligned slice: slots in groups of U; CLAMP replaces an index outside the
+// particle range (only ever a masked slot) by alt
+template <int U, bool CLAMP, class Body>
+__device__ __forceinline__ void aligned_slots(const int32_t *__restrict__ base, int W, int lane, int ii, int alt,
+                                              int N, Body &&body)
+{
+    const int T = 32 * ((W + 31) / 32);
+    const uint32_t *__restrict__ mk = reinterpret_cast<const uint32_t *>(base) + T + lane;
+    uint32_t bits = 0;
+    for (int k = 0; k < W; k += U) {
+        if ((k & 31) == 0) bits = mk[k];
+        int j[U];
+        float w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned ju = (unsigned)ii + (unsigned)base[k + u];   // modular: a negative index wraps high
+            j[u] = (CLAMP && ju >= (unsigned)N) ? alt : (int)ju;
+            w[u] = (float)((bits >> ((k & 31) + u)) & 1u);
+        }
+        body(j, w);
+    }
 }
 
 // Neighbour slots of row i in groups of U (U divides 32): body(j[U], w[U]) for
@@ -291,23 +317,9 @@ __device__ __forceinline__ void for_slots(const DevState &s, int64_t i, Body &&b
     const int32_t *__restrict__ base = s.colE + s.ell_off[g];
     const int alt = i == 0 ? 1 : (int)i - 1;
     if (wv < 0) {
-        // aligned: every slot's j = i + o_k is a particle other than i (see above)
-        const int W = ~wv;
-        const int T = 32 * ((W + 31) / 32);
-        const uint32_t *__restrict__ mk = reinterpret_cast<const uint32_t *>(base) + T + lane;
-        const int ii = (int)i;
-        uint32_t bits = 0;
-        for (int k = 0; k < W; k += U) {
-            if ((k & 31) == 0) bits = mk[k];
-            int j[U];
-            float w[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                j[u] = ii + base[k + u];
-                w[u] = (float)((bits >> ((k & 31) + u)) & 1u);
-            }
-            body(j, w);
-        }
+        const int W = (~wv) & 0xffffff;
+        if ((~wv) >> 24) aligned_slots<U, true>(base, W, lane, (int)i, alt, (int)s.N, body);
+        else aligned_slots<U, false>(base, W, lane, (int)i, alt, (int)s.N, body);
     } else {
         const int32_t *__restrict__ cp = base + lane;
         for (int k = 0; k < wv; k += U) {
@@ -408,23 +420,102 @@ static constexpr float YIELD_GUARD = 1.0f - 1e-5f;
 // to FP32 rounding of J - 1 itself.  A particle whose FP32 trial stress lies
 // inside the yield surface by more than the guard band takes the elastic
 // branch of Algorithm 1 in FP32 (no plastic increment, so no damage
-// increment); every other particle (yielding, near yield, GTN, damage at or
-// past initiation) runs the FP64 material update.
+// increment) in this kernel; every other particle (yielding, near yield,
+// GTN, damage at or past initiation) is queued with its strain increment and
+// finished by the FP64 material update in a separate kernel, so this kernel
+// carries no FP64 return-mapping code (fewer registers, more resident warps).
+
+// kinematics at F^{n+1}: G = F - I, J - 1, F^{-1} and the rotation R
+struct Kin1 {
+    float G[9], Fi[9], R[9];
+    float Jm1, Jf;
+};
+
+__device__ __forceinline__ bool kin_from_F(const float *Fh, const float *Fl, Kin1 &k, uint32_t &st)
+{
+    // G = F - I (the diagonal's hi - 1 is exact for hi in [0.5, 2])
+#pragma unroll
+    for (int q = 0; q < 9; ++q) k.G[q] = ((q % 4 == 0) ? Fh[q] - 1.0f : Fh[q]) + Fl[q];
+    const float *G = k.G;
+    const float m2 = (G[0] * G[4] - G[1] * G[3]) + (G[4] * G[8] - G[5] * G[7]) + (G[0] * G[8] - G[2] * G[6]);
+    const float m3 = G[0] * (G[4] * G[8] - G[5] * G[7]) + G[1] * (G[5] * G[6] - G[3] * G[8])
+                   + G[2] * (G[3] * G[7] - G[4] * G[6]);
+    k.Jm1 = (G[0] + G[4] + G[8]) + (m2 + m3);
+    k.Jf = 1.0f + k.Jm1;
+    if (!(k.Jf > 0.0f) || !isfinite(k.Jm1)) return false;
+    float cf[9];
+    cof3f(Fh, cf);
+    const float iJ = 1.0f / k.Jf;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) k.Fi[3 * a + b] = cf[3 * b + a] * iJ;
+    if (!polar_rotation_f(Fh, k.R)) st |= TLSPH_ST_POLAR_CAP;
+    return true;
+}
+
+// stress, A and the pass-2 record of a particle after its constitutive update
+__device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c, int64_t i, const Kin1 &k,
+                                            const float *Li, const float *sd, float sm, double Dnew, bool failed,
+                                            float Vf, float u0, float u1, float u2, uint32_t st)
+{
+    const int64_t N = c.N;
+    float4 *__restrict__ r2 = s.r2;
+    float A[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
+    if (failed) {
+        s.fail[i] = (int32_t)(c.step_index + 1);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s.sigf[q * N + i] = 0.0f;
+    } else {
+        // sigma = R (sigma_m I + s_hat) R^T ;  P = J sigma F^{-T} ;  A = P L^{-T}
+        const float sh[6] = { sd[0] + sm, sd[1] + sm, sd[2] + sm, sd[3], sd[4], sd[5] };
+        float sg[6];
+        sym_rotate_f(k.R, sh, sg);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s.sigf[q * N + i] = sg[q];
+        float S[9] = { sg[0], sg[3], sg[5], sg[3], sg[1], sg[4], sg[5], sg[4], sg[2] }, P[9];
+        mul3f_bt(S, k.Fi, P);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) P[q] *= k.Jf;
+        mul3f_bt(P, Li, A);
+        bool fin = true;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fin &= isfinite(A[q]);
+        if (!fin) st |= TLSPH_ST_NONFINITE;
+    }
+    const float omd = 1.0f - (float)Dnew;
+    const float *G = k.G;
+    r2[i] = make_float4(A[0], A[1], A[2], A[3]);
+    r2[N + i] = make_float4(A[4], A[5], A[6], A[7]);
+    r2[2 * N + i] = make_float4(A[8], Vf * omd, Vf, u0);
+    r2[3 * N + i] = make_float4(u1, u2, G[0], G[1]);
+    r2[4 * N + i] = make_float4(G[2], G[3], G[4], G[5]);
+    r2[5 * N + i] = make_float4(G[6], G[7], G[8], (float)s.sqrtE[i] * Vf * omd);
+    if (st) atomicOr(s.status, st);
+}
+
+__device__ __forceinline__ void load_u1(const DevState &s, const MixConst &c, int64_t i, float &u0, float &u1, float &u2)
+{
+    const double *un = s.u[c.ucur ^ 1];   // u^{n+1}, mirrored for pass 2's hourglass term (fixed-point units)
+    u0 = (float)un[3 * i] * c.inv_unit_f;
+    u1 = (float)un[3 * i + 1] * c.inv_unit_f;
+    u2 = (float)un[3 * i + 2] * c.inv_unit_f;
+}
+
 __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
     const double *__restrict__ Dn = s.D[c.dcur];
     double *__restrict__ Dnext = s.D[c.dcur ^ 1];
-    float4 *__restrict__ r2 = s.r2;
     const int64_t N = c.N;
     const int fail = s.fail[i];
-    const double *un = s.u[c.ucur ^ 1];   // u^{n+1}, mirrored for pass 2's hourglass term (fixed-point units)
     const float Vf = (float)s.vol[i];
     float Fh[9], Fl[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) { Fh[k] = s.Fh[k * N + i]; Fl[k] = s.Fl[k * N + i]; }
-    const float u0 = (float)un[3 * i] * c.inv_unit_f, u1 = (float)un[3 * i + 1] * c.inv_unit_f,
-                u2 = (float)un[3 * i + 2] * c.inv_unit_f;
+    float u0, u1, u2;
+    load_u1(s, c, i, u0, u1, u2);
     if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
+        float4 *__restrict__ r2 = s.r2;
         Dnext[i] = Dn[i];
         r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         r2[N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -450,35 +541,19 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
         s.Fh[k * N + i] = Fh[k];
         s.Fl[k * N + i] = Fl[k];
     }
-    // G = F - I (the diagonal's hi - 1 is exact for hi in [0.5, 2])
-    float G[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? Fh[k] - 1.0f : Fh[k]) + Fl[k];
-    const float m2 = (G[0] * G[4] - G[1] * G[3]) + (G[4] * G[8] - G[5] * G[7]) + (G[0] * G[8] - G[2] * G[6]);
-    const float m3 = G[0] * (G[4] * G[8] - G[5] * G[7]) + G[1] * (G[5] * G[6] - G[3] * G[8])
-                   + G[2] * (G[3] * G[7] - G[4] * G[6]);
-    const float Jm1 = (G[0] + G[4] + G[8]) + (m2 + m3);
-    const float Jf = 1.0f + Jm1;
-    if (!(Jf > 0.0f) || !isfinite(Jm1)) {
+    Kin1 kin;
+    uint32_t st = 0;
+    if (!kin_from_F(Fh, Fl, kin, st)) {
         atomicOr(s.status, TLSPH_ST_BAD_J);
         Dnext[i] = Dn[i];
         return;
     }
-    // kinematics: F^{-1} = cof^T / J, dt L_v = dF F^{-1}, rotation R of F^{n+1},
-    // unrotated strain increment dh = R^T sym(dt L_v) R
-    float cf[9], Fi[9], Lv[9];
-    cof3f(Fh, cf);
-    const float iJ = 1.0f / Jf;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int l = 0; l < 3; ++l) Fi[3 * k + l] = cf[3 * l + k] * iJ;
-    mul3f(dF, Fi, Lv);
+    // unrotated strain increment dh = R^T sym(dt L_v) R with dt L_v = dF F^{-1}
+    float Lv[9];
+    mul3f(dF, kin.Fi, Lv);
     const float d[6] = { Lv[0], Lv[4], Lv[8], 0.5f * (Lv[1] + Lv[3]), 0.5f * (Lv[5] + Lv[7]), 0.5f * (Lv[2] + Lv[6]) };
-    float R[9];
-    uint32_t st = polar_rotation_f(Fh, R) ? 0u : TLSPH_ST_POLAR_CAP;
     float dh[6];
-    sym_rotate_t_f(R, d, dh);
+    sym_rotate_t_f(kin.R, d, dh);
 
     const DevMat &mat = s.mats[s.mat[i]];
     const double Dd = Dn[i];
@@ -499,74 +574,87 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
                              2.0f * (tr[3] * tr[3] + tr[4] * tr[4] + tr[5] * tr[5]));
     const float sf = jc_flow_f(mat, (float)s.ep[i], (float)epdot) * omDf;
     const bool fast = mat.damage != TLSPH_DAMAGE_GTN && dinit < 1.0 && sf > 0.0f && s2 <= sf * sf * YIELD_GUARD;
-    float sm;
-    double Dnew;
-    bool failed = false;
-    if (fast) {
+    if (!fast) {
+        // the FP64 update finishes this particle (k_epi1_slow): hand it the strain increment
 #pragma unroll
-        for (int k = 0; k < 6; ++k) df_add(sdh[k], sdl[k], inc[k]);
-        if (epdot != 0.0) s.epdot[i] = 0.0;
-        sm = eos_sm_f(mat, Jm1, Jf, (float)Dd);
-        Dnew = mat.damage == TLSPH_DAMAGE_NONE ? Dd : 0.0;   // D from D_init < 1
-    } else {
-        MPState mp;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) mp.sd[k] = df_value(sdh[k], sdl[k]);
-        mp.sm = 0.0;
-        mp.ep = s.ep[i];
-        mp.epdot = epdot;
-        mp.dinit = dinit;
-        mp.D = Dd;
-        mp.f = s.por[i];
-        mp.failed = 0;
-        double de[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) de[k] = (double)dh[k];
-        st |= material_update(mat, c.dt, de, 1.0 + (double)Jm1, mp);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) df_split(mp.sd[k], sdh[k], sdl[k]);
-        s.ep[i] = mp.ep;
-        s.epdot[i] = mp.epdot;
-        s.dinit[i] = mp.dinit;
-        s.por[i] = mp.f;
-        sm = (float)mp.sm;
-        Dnew = mp.D;
-        failed = mp.failed != 0;
+        for (int k = 0; k < 6; ++k) s.fsum[k * N + i] = dh[k];
+        const uint32_t q = atomicAdd(&s.slowq_n[c.step_index & 1], 1u);
+        s.slowq[q] = (int32_t)i;
+        if (st) atomicOr(s.status, st);
+        return;
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) { s.sdh[k * N + i] = sdh[k]; s.sdl[k * N + i] = sdl[k]; }
+    for (int k = 0; k < 6; ++k) {
+        df_add(sdh[k], sdl[k], inc[k]);
+        s.sdh[k * N + i] = sdh[k];
+        s.sdl[k * N + i] = sdl[k];
+    }
+    if (epdot != 0.0) s.epdot[i] = 0.0;
+    const float sm = eos_sm_f(mat, kin.Jm1, kin.Jf, (float)Dd);
+    const double Dnew = mat.damage == TLSPH_DAMAGE_NONE ? Dd : 0.0;   // D from D_init < 1
     Dnext[i] = Dnew;
+    epi1_finish(s, c, i, kin, Li, sdh, sm, Dnew, false, Vf, u0, u1, u2, st);
+}
 
-    float A[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
-    if (failed) {
-        s.fail[i] = (int32_t)(c.step_index + 1);
+// FP64 constitutive and damage update of a queued particle (F^{n+1} already
+// stored, its unrotated strain increment in fsum[0..5])
+__device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, int64_t i)
+{
+    const double *__restrict__ Dn = s.D[c.dcur];
+    double *__restrict__ Dnext = s.D[c.dcur ^ 1];
+    const int64_t N = c.N;
+    const float Vf = (float)s.vol[i];
+    float Fh[9], Fl[9], Li[9];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s.sigf[k * N + i] = 0.0f;
-    } else {
-        // sigma = R (sigma_m I + s_hat) R^T ;  P = J sigma F^{-T} ;  A = P L^{-T}
-        const float sh[6] = { sdh[0] + sm, sdh[1] + sm, sdh[2] + sm, sdh[3], sdh[4], sdh[5] };
-        float sg[6];
-        sym_rotate_f(R, sh, sg);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) s.sigf[k * N + i] = sg[k];
-        float S[9] = { sg[0], sg[3], sg[5], sg[3], sg[1], sg[4], sg[5], sg[4], sg[2] }, P[9];
-        mul3f_bt(S, Fi, P);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) P[k] *= Jf;
-        mul3f_bt(P, Li, A);
-        bool fin = true;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) fin &= isfinite(A[k]);
-        if (!fin) st |= TLSPH_ST_NONFINITE;
+    for (int k = 0; k < 9; ++k) {
+        Fh[k] = s.Fh[k * N + i];
+        Fl[k] = s.Fl[k * N + i];
+        Li[k] = s.linv32[9 * i + k];
     }
-    const float omd = 1.0f - (float)Dnew;
-    r2[i] = make_float4(A[0], A[1], A[2], A[3]);
-    r2[N + i] = make_float4(A[4], A[5], A[6], A[7]);
-    r2[2 * N + i] = make_float4(A[8], Vf * omd, Vf, u0);
-    r2[3 * N + i] = make_float4(u1, u2, G[0], G[1]);
-    r2[4 * N + i] = make_float4(G[2], G[3], G[4], G[5]);
-    r2[5 * N + i] = make_float4(G[6], G[7], G[8], (float)s.sqrtE[i] * Vf * omd);
-    if (st) atomicOr(s.status, st);
+    float u0, u1, u2;
+    load_u1(s, c, i, u0, u1, u2);
+    Kin1 kin;
+    uint32_t st = 0;
+    kin_from_F(Fh, Fl, kin, st);     // same inputs and code as the first kernel: J was valid there
+    const DevMat &mat = s.mats[s.mat[i]];
+    MPState mp;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mp.sd[k] = df_value(s.sdh[k * N + i], s.sdl[k * N + i]);
+    mp.sm = 0.0;
+    mp.ep = s.ep[i];
+    mp.epdot = s.epdot[i];
+    mp.dinit = s.dinit[i];
+    mp.D = Dn[i];
+    mp.f = s.por[i];
+    mp.failed = 0;
+    double de[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) de[k] = (double)s.fsum[k * N + i];
+    st |= material_update(mat, c.dt, de, 1.0 + (double)kin.Jm1, mp);
+    float sdh[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float l;
+        df_split(mp.sd[k], sdh[k], l);
+        s.sdh[k * N + i] = sdh[k];
+        s.sdl[k * N + i] = l;
+    }
+    s.ep[i] = mp.ep;
+    s.epdot[i] = mp.epdot;
+    s.dinit[i] = mp.dinit;
+    s.por[i] = mp.f;
+    Dnext[i] = mp.D;
+    epi1_finish(s, c, i, kin, Li, sdh, (float)mp.sm, mp.D, mp.failed != 0, Vf, u0, u1, u2, st);
+}
+
+// persistent grid over the step's queue of FP64 updates; clears the queue
+// counter of the next step (the two counters alternate with the step parity)
+__global__ void __launch_bounds__(128) k_epi1_slow(DevState s, MixConst c)
+{
+    const uint32_t n = s.slowq_n[c.step_index & 1];
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        epi1_slow(s, c, s.slowq[q]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.slowq_n[(c.step_index + 1) & 1] = 0u;
 }
 
 // ------------------------------------------------------------------ pass 1 pair terms
@@ -674,7 +762,7 @@ __global__ void __launch_bounds__(256) k_gather1_mixed_w32(DevState s, MixConst 
     for (int k = 0; k < 9; ++k) s.fsum[k * s.N + row0 + lane] = keep[k];
 }
 
-__global__ void __launch_bounds__(128) k_epi1_mixed(DevState s, MixConst c)
+__global__ void __launch_bounds__(128, 5) k_epi1_mixed(DevState s, MixConst c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
@@ -1038,7 +1126,22 @@ cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *c
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st)
 {
     k_mixed_r1<<<nb(s.N, 256), 256, 0, st>>>(s, dcur);
-    return cudaGetLastError();
+    // the state may have been replaced (set_state, restore): start both step-parity queues empty
+    return cudaMemsetAsync(s.slowq_n, 0, 2 * sizeof(uint32_t), st);
+}
+
+// persistent grid of the FP64-update kernel: SMs x resident blocks of 128
+static int slow_grid()
+{
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_epi1_slow, 128, 0);
+        grid = std::max(1, sms) * std::max(1, per);
+    }
+    return grid;
 }
 
 // Launch plans (chosen per context, e.g. by the autotuner):
@@ -1073,6 +1176,7 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
         break;
     default: k_pass1_mixed<<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c); break;
     }
+    k_epi1_slow<<<slow_grid(), 128, 0, st>>>(s, c);
     if (ev) cudaEventRecord(ev[1], st);
     if (v2 == 1) {
         if (hg) k_pass2_mixed_t<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
@@ -1102,7 +1206,7 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
     return cudaGetLastError();
 }
 
-int mixed_kernels_per_step(const tlsph_ctx &ctx) { return (ctx.plan[0] >= 2 ? 2 : 1) + (ctx.plan[2] == 2 ? 2 : 1); }
+int mixed_kernels_per_step(const tlsph_ctx &ctx) { return (ctx.plan[0] >= 2 ? 2 : 1) + 1 + (ctx.plan[2] == 2 ? 2 : 1); }
 
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st)
 {
@@ -1141,8 +1245,8 @@ __device__ __forceinline__ int batch_find(const BatchSlot *slots, int n, int64_t
     return lo;
 }
 
-template <int KIND, bool HG>
-__global__ void __launch_bounds__(128) k_batch(const BatchHdr *hdr, BatchSlot *slots)
+template <int KIND, bool HG, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_batch(const BatchHdr *hdr, BatchSlot *slots)
 {
     __shared__ int sidx;
     const int nspec = hdr->nspec;
@@ -1173,6 +1277,20 @@ __global__ void __launch_bounds__(128) k_batch(const BatchHdr *hdr, BatchSlot *s
     }
 }
 
+// the FP64 updates queued by every member in this step (persistent grid over
+// the members' queues); clears each member's queue counter of the next step
+__global__ void __launch_bounds__(128) k_batch_slow(const BatchHdr *hdr, BatchSlot *slots)
+{
+    const int nspec = hdr->nspec;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int m = 0; m < nspec; ++m) {
+        const BatchSlot &sl = slots[m];
+        const uint32_t n = sl.s.slowq_n[sl.c.step_index & 1];
+        for (uint32_t q = t; q < n; q += stride) epi1_slow(sl.s, sl.c, sl.s.slowq[q]);
+    }
+    for (uint32_t m = t; m < (uint32_t)nspec; m += stride) slots[m].s.slowq_n[(slots[m].c.step_index + 1) & 1] = 0u;
+}
+
 // end of a step: flip the ping-pong buffers and count the step, per slot
 __global__ void k_batch_advance(const BatchHdr *hdr, BatchSlot *slots)
 {
@@ -1192,32 +1310,46 @@ BatchSlot make_batch_slot(const tlsph_ctx &ctx)
     return b;
 }
 
-// two HG flavours x three kernel kinds; grid is persistent
-cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, int grid, cudaStream_t st)
+// two HG flavours x three kernel kinds, each a persistent grid with its
+// registers capped for 8 (pass-1 gather), 3 (per-particle update) and 6
+// (pass 2, as the single-context plan form 4) blocks of 128 per SM
+template <bool HG>
+static void batch_kernels(const BatchHdr *hdr, BatchSlot *slots, const int *grid, cudaStream_t st)
 {
-    if (hg) {
-        k_batch<0, true><<<grid, 128, 0, st>>>(hdr, slots);
-        k_batch<1, true><<<grid, 128, 0, st>>>(hdr, slots);
-        k_batch<2, true><<<grid, 128, 0, st>>>(hdr, slots);
-    } else {
-        k_batch<0, false><<<grid, 128, 0, st>>>(hdr, slots);
-        k_batch<1, false><<<grid, 128, 0, st>>>(hdr, slots);
-        k_batch<2, false><<<grid, 128, 0, st>>>(hdr, slots);
-    }
+    k_batch<0, HG, 8><<<grid[0], 128, 0, st>>>(hdr, slots);
+    k_batch<1, HG, 3><<<grid[1], 128, 0, st>>>(hdr, slots);
+    k_batch_slow<<<grid[3], 128, 0, st>>>(hdr, slots);
+    k_batch<2, HG, 6><<<grid[2], 128, 0, st>>>(hdr, slots);
+}
+
+cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, const int *grid,
+                              cudaStream_t st)
+{
+    if (hg) batch_kernels<true>(hdr, slots, grid, st);
+    else batch_kernels<false>(hdr, slots, grid, st);
     k_batch_advance<<<(nspec + 127) / 128, 128, 0, st>>>(hdr, slots);
     return cudaGetLastError();
 }
 
-int batch_grid(bool hg)
+template <bool HG>
+static void batch_occupancy(int *per)
 {
-    int dev = 0, sms = 0, per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_batch<0, HG, 8>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_batch<1, HG, 3>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_batch<2, HG, 6>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], k_batch_slow, 128, 0);
+}
+
+// persistent grid of each kernel kind (pass-1 gather, per-particle update,
+// pass 2, FP64 updates): SMs x resident blocks per SM
+void batch_grid(bool hg, int *grid)
+{
+    int dev = 0, sms = 0, per[4] = { 0, 0, 0, 0 };
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (hg)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2, true>, 128, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<2, false>, 128, 0);
-    return std::max(1, sms) * std::max(1, per);
+    if (hg) batch_occupancy<true>(per);
+    else batch_occupancy<false>(per);
+    for (int k = 0; k < 4; ++k) grid[k] = std::max(1, sms) * std::max(1, per[k]);
 }
 
 }  // namespace tlsph

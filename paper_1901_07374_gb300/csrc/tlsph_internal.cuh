@@ -80,6 +80,8 @@ struct DevState {
     float *Fh, *Fl;         // 9 x N deformation gradient
     float *sdh, *sdl;       // 6 x N unrotated stress deviator
     float *sigf;            // 6 x N Cauchy stress
+    int32_t *slowq;         // N     particles queued for the FP64 constitutive update this step
+    uint32_t *slowq_n;      // 2     queue lengths, used alternately by even and odd steps
     const int32_t *colE;    // sliced neighbour lists (slices of 32 rows, explicit or aligned form)
     const int64_t *ell_off; // (N + 31) / 32 + 1 slice word offsets
     const int32_t *ell_w;   // (N + 31) / 32 slice widths: W (explicit) or ~W (aligned)
@@ -112,7 +114,7 @@ struct tlsph_ctx {
     int dcur = 0;   // D[dcur] = D^n
     // mixed launch plan: pass-1 form, block, pass-2 form, block (the fastest on
     // GB300 for the 1M-particle bar; the autotuner may choose another)
-    int32_t plan[4] = { 4, 64, 3, 128 };
+    int32_t plan[4] = { 2, 128, 4, 128 };
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
     bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
     void *mixed = nullptr;      // mixed-precision state (mixed.cu)
@@ -217,8 +219,10 @@ struct BatchHdr {
     int64_t total_blk;
 };
 BatchSlot make_batch_slot(const tlsph_ctx &ctx);
-cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, int grid, cudaStream_t st);
-int batch_grid(bool hg);
+// grid: the persistent grid of each of the four kernel kinds (batch_grid)
+cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, const int *grid,
+                              cudaStream_t st);
+void batch_grid(bool hg, int *grid);
 
 cudaError_t mixed_init_static(const DevState &s, const double *S0, const FixPack &pk, cudaStream_t st);
 cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st);

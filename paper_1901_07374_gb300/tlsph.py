@@ -209,6 +209,7 @@ def fma_peak(fp64: bool = False, iters: int = 4096) -> float:
 
 FLAG_SPATIAL_ORDER = 1
 FLAG_WALL = 2
+FLAG_LINE_ORDER = 4
 
 
 def make_config(h, rc, dt, hg_alpha, precision="fp64", flags=0) -> Config:
@@ -251,7 +252,8 @@ class Simulation:
     stream: torch.cuda.Stream or raw handle; default the current stream."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
-                 precision="fp64", arena=None, nnz_cap=0, stream=None, spatial_order=False, wall=False):
+                 precision="fp64", arena=None, nnz_cap=0, stream=None, spatial_order=False, wall=False,
+                 line_order=False):
         L = load()
         X = _host(X, np.float64)
         self.N = N = X.shape[0]
@@ -262,7 +264,8 @@ class Simulation:
         bc_vel = _host(bc_vel, np.float64, (N, 3))
         f0 = _host(f0, np.float64)
         self.cfg = make_config(h, rc, dt, hg_alpha, precision,
-                               (FLAG_SPATIAL_ORDER if spatial_order else 0) | (FLAG_WALL if wall else 0))
+                               (FLAG_SPATIAL_ORDER if spatial_order else 0) | (FLAG_WALL if wall else 0) |
+                               (FLAG_LINE_ORDER if line_order else 0))
         self.precision = precision
         self.arena = arena
         self.stream = _stream_handle(stream)

@@ -109,13 +109,15 @@ def test_step_counter_is_part_of_the_checkpoint():
     assert g.get("STEP")[0] == 43
 
 
-def test_internal_order_is_invisible():
-    """A spatially reordered context and one keeping the caller's order
-    return the same neighbour CSR bit for bit and the same fields to FP64
-    rounding (only the order of the sums over j differs)."""
+@pytest.mark.parametrize("order", ["spatial_order", "line_order"])
+def test_internal_order_is_invisible(order):
+    """A reordered context (brick order, or lattice lines along the longest
+    axis) and one keeping the caller's order return the same neighbour CSR bit
+    for bit and the same fields to FP64 rounding (only the order of the sums
+    over j differs)."""
     from parity import ORACLE_KEY, compare_state
     w = S.failure_variant(S.tensile_bar_jc(nx=9, ny=7, nz=30, seed=2, steps=60))
-    a = tlsph.Simulation.from_workload(w, spatial_order=True)
+    a = tlsph.Simulation.from_workload(w, **{order: True})
     b = tlsph.Simulation.from_workload(w)
     assert np.array_equal(a.get("NBR_ROWPTR"), b.get("NBR_ROWPTR"))
     assert np.array_equal(a.get("NBR_COL"), b.get("NBR_COL"))
@@ -125,8 +127,12 @@ def test_internal_order_is_invisible():
     ref = {ORACLE_KEY[k]: v for k, v in b.state().items()}
     compare_state(a.state(), ref, w, tol=1e-9)
     assert np.array_equal(a.get("FAIL_STEP"), b.get("FAIL_STEP"))
+    if order == "line_order":
+        with pytest.raises(tlsph.TlsphError) as e:
+            tlsph.Simulation.from_workload(w, spatial_order=True, line_order=True)
+        assert e.value.code == -1
     for precision in ("mixed",):
-        c = tlsph.Simulation.from_workload(w, precision=precision, spatial_order=True)
+        c = tlsph.Simulation.from_workload(w, precision=precision, **{order: True})
         c.step(60)
         compare_state(c.state(), ref, w, tol=2e-4, fields=("U", "V", "F", "SIGMA", "FORCE"))
 
