@@ -249,11 +249,14 @@ class Simulation:
     materials: list of material dicts (index = material id).
     arena: optional torch.uint8 CUDA tensor the library carves (with
     nnz_cap); otherwise the library owns its memory.
-    stream: torch.cuda.Stream or raw handle; default the current stream."""
+    stream: torch.cuda.Stream or raw handle; default the current stream.
+    spatial_order / line_order: internal particle order (TLSPH_FLAG_SPATIAL_ORDER
+    / TLSPH_FLAG_LINE_ORDER); line_order defaults to on for the mixed path.
+    wall: the rigid wall on z = 0 (TLSPH_FLAG_WALL)."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
                  precision="fp64", arena=None, nnz_cap=0, stream=None, spatial_order=False, wall=False,
-                 line_order=False):
+                 line_order=None):
         L = load()
         X = _host(X, np.float64)
         self.N = N = X.shape[0]
@@ -263,6 +266,8 @@ class Simulation:
         bc_mask = _host(bc_mask, np.uint8)
         bc_vel = _host(bc_vel, np.float64, (N, 3))
         f0 = _host(f0, np.float64)
+        if line_order is None:      # lattice-line order by default for the mixed path (fewer padding slots)
+            line_order = precision == "mixed" and not spatial_order
         self.cfg = make_config(h, rc, dt, hg_alpha, precision,
                                (FLAG_SPATIAL_ORDER if spatial_order else 0) | (FLAG_WALL if wall else 0) |
                                (FLAG_LINE_ORDER if line_order else 0))

@@ -112,10 +112,10 @@ def _reordered(w, perm):
 
 @pytest.mark.parametrize("shuffle", ["all", "second_half"])
 def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
-    """Lattice order gives aligned slices (one shared offset table per 32
-    rows); a shuffled caller order leaves the index offsets irregular, so its
-    slices keep the explicit form (shuffling half the particles mixes both
-    forms in one context).  The thread-per-row plans then compute the same
+    """Caller order kept (no internal reordering): lattice order gives aligned
+    slices (one shared offset table per 32 rows); a shuffled caller order
+    leaves the index offsets irregular, so its slices keep the explicit form
+    (shuffling half the particles mixes both forms in one context).  The thread-per-row plans then compute the same
     step in both layouts to FP32 rounding, within MIXED_TOL of the oracle."""
     w = S.failure_variant(S.tensile_bar_cl(nx=8, ny=8, nz=24), v_grip=10.0, scale=0.05)
     N = w.specimen.N
@@ -125,8 +125,8 @@ def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
         perm = rng.permutation(N)
     else:
         perm[N // 2:] = N // 2 + rng.permutation(N - N // 2)
-    a = tlsph.Simulation.from_workload(w, precision="mixed")
-    b = tlsph.Simulation.from_workload(_reordered(w, perm), precision="mixed")
+    a = tlsph.Simulation.from_workload(w, precision="mixed", line_order=False)
+    b = tlsph.Simulation.from_workload(_reordered(w, perm), precision="mixed", line_order=False)
     la, lb = a.neighbor_layout(), b.neighbor_layout()
     assert la["slices"] == lb["slices"] == (N + 31) // 32
     # lattice order: all slices aligned but those within 3 layers of either end
@@ -138,8 +138,8 @@ def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
         assert 0.15 * lb["slices"] <= lb["aligned_slices"] <= 0.7 * lb["slices"]
     assert la["words"] < lb["words"]
     for plan in [(4, 128, 1, 128), (1, 64, 2, 256)]:
-        a = tlsph.Simulation.from_workload(w, precision="mixed")
-        b = tlsph.Simulation.from_workload(_reordered(w, perm), precision="mixed")
+        a = tlsph.Simulation.from_workload(w, precision="mixed", line_order=False)
+        b = tlsph.Simulation.from_workload(_reordered(w, perm), precision="mixed", line_order=False)
         a.set_plan(plan)
         b.set_plan(plan)
         a.step(30)
@@ -194,7 +194,7 @@ def test_line_order_removes_padding_slots():
     surface and interior rows), and the step agrees with the caller-order
     context to FP32 rounding."""
     w = S.failure_variant(S.tensile_bar_cl(nx=6, ny=6, nz=64), v_grip=10.0, scale=0.05)
-    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    a = tlsph.Simulation.from_workload(w, precision="mixed", line_order=False)
     b = tlsph.Simulation.from_workload(w, precision="mixed", line_order=True)
     la, lb = a.neighbor_layout(), b.neighbor_layout()
     nnz = a.nnz
