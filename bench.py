@@ -71,8 +71,8 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # same kernel build, keyed by (workload, precision, pass, plan form of that
 # pass); absent for other plans and once the kernels change after the capture
 TRAFFIC = {
-    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 554882816,   # k_gather1_mixed_t4 + k_epi1_mixed
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 3): 334029568,   # k_pass2_mixed_t1
+    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 2): 566840832,   # k_gather1_mixed_t + k_epi1_mixed + k_epi1_slow
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 335525632,   # k_pass2_mixed_tc
 }
 
 

@@ -57,7 +57,8 @@ int64_t ell_capacity(int64_t N, int64_t nnz_cap)
 // Lattice-line order (TLSPH_FLAG_LINE_ORDER): perm[k] = caller index of
 // internal particle k, sorted by the rounded lattice coordinates of the two
 // shorter bounding-box axes, then by the coordinate along the longest axis
-// (ties by caller index).
+// (quantised to 32 bits over its extent; ties keep the caller order).  A
+// least-significant-digit radix sort (four 16-bit digits) of 64-bit keys.
 std::vector<int32_t> line_order_perm(const double *X, const double *vol, int64_t N)
 {
     std::vector<int32_t> perm((size_t)N);
@@ -78,20 +79,32 @@ std::vector<int32_t> line_order_perm(const double *X, const double *vol, int64_t
     std::nth_element(v.begin(), v.begin() + N / 2, v.end());
     const double d = std::cbrt(std::max(v[(size_t)(N / 2)], 0.0));
     const double inv = d > 0.0 ? 1.0 / d : 0.0;
-    struct Key { int64_t ab; double xl; int32_t i; };
-    std::vector<Key> key((size_t)N);
-    const int64_t nb = (int64_t)std::llround((hi[b] - lo[b]) * inv) + 1;
+    const uint64_t nb = (uint64_t)std::llround((hi[b] - lo[b]) * inv) + 1;
+    const double extL = hi[L] - lo[L];
+    const double qL = extL > 0.0 ? 4294967295.0 / extL : 0.0;
+    std::vector<uint64_t> key((size_t)N), key2((size_t)N);
+    std::vector<int32_t> idx2((size_t)N);
     for (int64_t i = 0; i < N; ++i) {
-        const int64_t ka = (int64_t)std::llround((X[3 * i + a] - lo[a]) * inv);
-        const int64_t kb = (int64_t)std::llround((X[3 * i + b] - lo[b]) * inv);
-        key[(size_t)i] = Key{ ka * nb + kb, X[3 * i + L], (int32_t)i };
+        const uint64_t ka = (uint64_t)std::llround((X[3 * i + a] - lo[a]) * inv);
+        const uint64_t kb = (uint64_t)std::llround((X[3 * i + b] - lo[b]) * inv);
+        const double t = std::min(4294967295.0, std::max(0.0, std::floor((X[3 * i + L] - lo[L]) * qL)));
+        key[(size_t)i] = ((ka * nb + kb) << 32) | (uint64_t)t;
     }
-    std::sort(key.begin(), key.end(), [](const Key &p, const Key &q) {
-        if (p.ab != q.ab) return p.ab < q.ab;
-        if (p.xl != q.xl) return p.xl < q.xl;
-        return p.i < q.i;
-    });
-    for (int64_t k = 0; k < N; ++k) perm[(size_t)k] = key[(size_t)k].i;
+    std::vector<int64_t> count(65536);
+    for (int pass = 0; pass < 4; ++pass) {
+        const int sh = 16 * pass;
+        std::fill(count.begin(), count.end(), 0);
+        for (int64_t i = 0; i < N; ++i) ++count[(key[(size_t)i] >> sh) & 0xffff];
+        int64_t sum = 0;
+        for (auto &c : count) { const int64_t t = c; c = sum; sum += t; }
+        for (int64_t i = 0; i < N; ++i) {     // stable: equal digits keep their order
+            const int64_t dst = count[(key[(size_t)i] >> sh) & 0xffff]++;
+            key2[(size_t)dst] = key[(size_t)i];
+            idx2[(size_t)dst] = perm[(size_t)i];
+        }
+        key.swap(key2);
+        perm.swap(idx2);
+    }
     return perm;
 }
 
