@@ -229,7 +229,7 @@ int tlsph_destroy(tlsph_ctx *ctx);
  * plan[3] its block size (multiples of 32 up to 256).  Every plan computes
  * the same method; sums over a row are grouped differently, so results
  * differ only by FP32 rounding.  n must be 4.  TLSPH_ERR_ARG for a plan out
- * of range.  A new mixed context starts with (2, 128, 4, 128).  The FP64 path
+ * of range.  A new mixed context starts with (4, 64, 4, 128).  The FP64 path
  * ignores the plan. */
 int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);
 int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);

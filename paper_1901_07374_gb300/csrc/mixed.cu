@@ -32,7 +32,7 @@
 //   xo   int4 {fixed-point x, y, z, 0}
 //   r1   {v^{n+1/2} - v_ref, V (1 - D)}                       pass-1 gather record
 //   r2k  k = 0..5 (at r2 + k N):                               pass-2 gather record
-//        {A00 A01 A02 A10} {A11 A12 A20 A21} {A22, V(1-D), V, u_x}
+//        {A00 A01 A02 A10} {A11 A12 A20 A21} {A22, V D, V, u_x}
 //        {u_y, u_z, G00, G01} {G02 G10 G11 G12} {G20, G21, G22, sqrt(E) V (1-D)}
 //        with G = F - I and u in fixed-point units.
 // Thread-per-row kernels read their neighbours through the sliced neighbour
@@ -293,14 +293,31 @@ __device__ __forceinline__ void aligned_slots(const int32_t *__restrict__ base, 
     uint32_t bits = 0;
     for (int k = 0; k < W; k += U) {
         if ((k & 31) == 0) bits = mk[k];
+        int o[U];
+        // the table is 128-byte aligned and k a multiple of U: one 8- or 16-byte load for the group
+        if (U == 2) {
+            const int2 t = *reinterpret_cast<const int2 *>(base + k);
+            o[0] = t.x;
+            o[U - 1] = t.y;
+        } else if (U == 4) {
+            const int4 t = *reinterpret_cast<const int4 *>(base + k);
+            o[0] = t.x;
+            o[1 % U] = t.y;
+            o[2 % U] = t.z;
+            o[3 % U] = t.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) o[u] = base[k + u];
+        }
         int j[U];
         float w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const unsigned ju = (unsigned)ii + (unsigned)base[k + u];   // modular: a negative index wraps high
+            const unsigned ju = (unsigned)ii + (unsigned)o[u];   // modular: a negative index wraps high
             j[u] = (CLAMP && ju >= (unsigned)N) ? alt : (int)ju;
-            w[u] = (float)((bits >> ((k & 31) + u)) & 1u);
+            w[u] = (bits & (1u << u)) ? 1.0f : 0.0f;
         }
+        bits >>= U;
         body(j, w);
     }
 }
@@ -487,7 +504,7 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
     const float *G = k.G;
     r2[i] = make_float4(A[0], A[1], A[2], A[3]);
     r2[N + i] = make_float4(A[4], A[5], A[6], A[7]);
-    r2[2 * N + i] = make_float4(A[8], Vf * omd, Vf, u0);
+    r2[2 * N + i] = make_float4(A[8], Vf * (float)Dnew, Vf, u0);
     r2[3 * N + i] = make_float4(u1, u2, G[0], G[1]);
     r2[4 * N + i] = make_float4(G[2], G[3], G[4], G[5]);
     r2[5 * N + i] = make_float4(G[6], G[7], G[8], (float)s.sqrtE[i] * Vf * omd);
@@ -519,7 +536,7 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
         Dnext[i] = Dn[i];
         r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         r2[N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2[2 * N + i] = make_float4(0.f, 0.f, Vf, u0);
+        r2[2 * N + i] = make_float4(0.f, Vf, Vf, u0);     // V D with D = 1
         r2[3 * N + i] = make_float4(u1, u2, (Fh[0] - 1.0f) + Fl[0], Fh[1] + Fl[1]);
         r2[4 * N + i] = make_float4(Fh[2] + Fl[2], Fh[3] + Fl[3], (Fh[4] - 1.0f) + Fl[4], Fh[5] + Fl[5]);
         r2[5 * N + i] = make_float4(Fh[6] + Fl[6], Fh[7] + Fl[7], (Fh[8] - 1.0f) + Fl[8], 0.f);
@@ -872,7 +889,7 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
     float a, b;
     const float g0 = wmask * spline_dw_ab(q, a, b) * rinv;
     const float g = b2.z * g0;                     // V_j W'/r
-    const float gd = (b2.z - b2.y) * g0;           // V_j D_j W'/r
+    const float gd = b2.y * g0;                    // V_j D_j W'/r
     acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
     const float t0 = (b0.x - w.a0.x) * d.x + (b0.y - w.a0.y) * d.y + (b0.z - w.a0.z) * d.z;
     const float t1 = (b0.w - w.a0.w) * d.x + (b1.x - w.a1.x) * d.y + (b1.y - w.a1.y) * d.z;

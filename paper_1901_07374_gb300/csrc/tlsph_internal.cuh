@@ -114,7 +114,7 @@ struct tlsph_ctx {
     int dcur = 0;   // D[dcur] = D^n
     // mixed launch plan: pass-1 form, block, pass-2 form, block (the fastest on
     // GB300 for the 1M-particle bar; the autotuner may choose another)
-    int32_t plan[4] = { 2, 128, 4, 128 };
+    int32_t plan[4] = { 4, 64, 4, 128 };
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
     bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
     void *mixed = nullptr;      // mixed-precision state (mixed.cu)
