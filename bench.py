@@ -70,10 +70,7 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # DRAM bytes (read + write) per step of each pass from one ncu capture of the
 # same kernel build, keyed by (workload, precision, pass, plan form of that
 # pass); absent for other plans and once the kernels change after the capture
-TRAFFIC = {
-    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 2): 566840832,   # k_gather1_mixed_t + k_epi1_mixed + k_epi1_slow
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 335525632,   # k_pass2_mixed_tc
-}
+TRAFFIC = {}
 
 
 # ---------------------------------------------------------------- clocks
