@@ -196,7 +196,20 @@ def launches_per_step(plan) -> int:
     return (2 if plan[0] >= 2 else 1) + 1 + (2 if plan[2] == 2 else 1)
 
 
-def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, plan=None, state=None):
+def field_errors(sim, ref: dict, sc: dict) -> dict:
+    """Normwise relative error of each field of `sim` against the state dict
+    `ref` (floors `sc`), and the size of the symmetric difference of the
+    failure sets."""
+    import numpy as np
+    out = {}
+    for f in FIELDS:
+        a, b = sim.get(f), ref[f]
+        out[f] = float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), sc[f]))
+    out["failure_set_symdiff"] = int(((sim.get("FAIL_STEP") >= 0) ^ (ref["FAIL_STEP"] >= 0)).sum())
+    return out
+
+
+def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, plan=None, state=None, guard=None):
     """Create, warm up, then time `steps` steps with CUDA events on the
     library's stream; per-kernel times from the library's own events.  A
     mixed context takes `plan`, else the autotuner's; `state` (caller-order
@@ -212,6 +225,8 @@ def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, pl
             autotune.tune(sim)
         pl, lw = sim.get_plan(), sim.neighbor_layout()["words"]
         words = (lw if pl[0] in (1, 2, 4) else nnz, lw if pl[2] != 0 else nnz)
+        if guard is not None:
+            sim.set_guard(guard)
     for k, v in (state or {}).items():
         sim.set(k, v)
     sim.step(warmup)
@@ -266,16 +281,34 @@ def run_ours(args, rank: int, world: int, dist):
 
     # ---- accuracy of the headline path against the FP64 GPU path (same steps)
     accuracy = None
+    ref_state = None
     if ref_sim is not None:
         sc = field_scales(w)
-        accuracy = {"steps": args.warmup + args.steps}
-        for f in FIELDS:
-            a, b = sim.get(f), ref_sim.get(f)
-            accuracy[f] = float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), sc[f]))
-        fa, fb = sim.get("FAIL_STEP") >= 0, ref_sim.get("FAIL_STEP") >= 0
-        accuracy["failure_set_symdiff"] = int((fa ^ fb).sum())
+        ref_state = {f: ref_sim.get(f) for f in FIELDS + ("FAIL_STEP",)}
+        accuracy = field_errors(sim, ref_state, sc)
+        accuracy["steps"] = args.warmup + args.steps
         ref_sim.close()
     sim.close()
+
+    # ---- guard band of the FP32 elastic screen: throughput and accuracy per band
+    guard = None
+    if args.guard_sweep and args.precision == "mixed" and ref_state is not None:
+        from paper_1901_07374_gb300 import specimen as S
+        st = S.plastic_flow_state(w) if args.workload.startswith("tensile_bar") else None
+        guard = []
+        for band in (1e-5, 1e-3, 1e-1, 1.0):
+            gs, gr = timed_run(tlsph, torch, w, "mixed", args.steps, args.warmup, stream, plan=r.get("plan"),
+                               guard=band)
+            row = {"band": band, "ms_per_step": gr["ms"] / args.steps,
+                   "max_error_vs_fp64": max(v for k, v in field_errors(gs, ref_state, field_scales(w)).items()
+                                            if k != "failure_set_symdiff")}
+            gs.close()
+            if st is not None:
+                ps, pr = timed_run(tlsph, torch, w, "mixed", args.plastic_steps, args.warmup, stream,
+                                   plan=r.get("plan"), state=st, guard=band)
+                row["plastic_ms_per_step"] = pr["ms"] / args.plastic_steps
+                ps.close()
+            guard.append(row)
 
     # ---- roofline of the dominant kernel: HBM bytes and FP32 issue
     words = r.get("words") or (nnz, nnz)
@@ -388,6 +421,8 @@ def run_ours(args, rank: int, world: int, dist):
         cfg["neighbor_lists"] = dict(r["layout"], bytes_per_pair=4.0 * r["layout"]["words"] / nnz)
     if plastic:
         cfg["plastic_flow_window"] = plastic
+    if guard:
+        cfg["guard_sweep"] = guard
     if ref is not None:
         cfg["plan"] = r.get("plan")
         cfg["fp64_gpu_value"] = world * nnz * args.steps / (ref["ms"] * 1e-3)
@@ -535,6 +570,8 @@ def main():
     ap.add_argument("--no-plastic", action="store_true", help="skip the plastic-flow window")
     ap.add_argument("--plastic-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--guard-sweep", action="store_true",
+                    help="time the mixed path at several guard bands of its FP32 elastic screen")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

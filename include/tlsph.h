@@ -234,6 +234,17 @@ int tlsph_destroy(tlsph_ctx *ctx);
 int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n);
 int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
 
+/* Guard band of the mixed path's FP32 elastic screen (Algorithm 1, Sec. 4:
+ * the decision sigma_eq <= sigma_f; the band has no counterpart in the
+ * paper).  A particle takes the FP32 elastic branch only when, in FP32,
+ * sigma_eq^2 <= sigma_f^2 (1 - band); every other particle runs the FP64
+ * constitutive update.  band >= 1e-5 (default 1e-5) keeps the screen
+ * conservative; band >= 1 sends every particle through the FP64 update.
+ * TLSPH_ERR_ARG for band < 1e-5 or non-finite.  Applies to the context's
+ * own steps and, through the batch table, to batched steps after the next
+ * tlsph_batch_set.  The FP64 path ignores it. */
+int tlsph_set_guard(tlsph_ctx *ctx, double band);
+
 /* Form of the mixed path's sliced neighbour lists (the thread-per-row plans
  * read the fixed neighbour sets of Sec. 2.2 through them; the paper has no
  * counterpart of the layout).  A slice is the 32 consecutive rows of one warp.

@@ -690,6 +690,20 @@ int tlsph_sync(tlsph_ctx *ctx)
     return TLSPH_OK;
 }
 
+int tlsph_set_guard(tlsph_ctx *ctx, double band)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    if (!(band >= 1e-5) || !std::isfinite(band)) {
+        ctx->err = "guard band must be finite and >= 1e-5 (below it the FP32 screen is not conservative)";
+        return TLSPH_ERR_ARG;
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_guard sync");
+    ctx->guard = band;
+    return TLSPH_OK;
+}
+
 int tlsph_neighbor_layout(const tlsph_ctx *ctx, int64_t *slices, int64_t *aligned_slices, int64_t *slots,
                           int64_t *words)
 {

@@ -60,6 +60,7 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     c.w_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h));
     c.hg_coef = (float)(-0.5 * cfg.hg_alpha);
     c.inv_unit = ctx.s.pack.inv_unit;
+    c.yield_keep = ctx.guard >= 1.0 ? -1.0f : (float)(1.0 - ctx.guard);
     c.inv_unit_f = (float)ctx.s.pack.inv_unit;
     c.vref0 = ctx.s.vref[0];
     c.vref1 = ctx.s.vref[1];
@@ -423,10 +424,11 @@ __device__ __forceinline__ float eos_sm_f(const DevMat &m, float Jm1, float J, f
     return sm > 0.0f ? sm * (1.0f - D) : sm;
 }
 
-// relative guard band of the single-precision yield screen: the FP32 values
-// of sigma_eq^2 and sigma_f^2 are within 2e-6 of their FP64 counterparts, so
-// sigma_eq^2 <= sigma_f^2 (1 - 1e-5) in FP32 implies the FP64 test passes
-static constexpr float YIELD_GUARD = 1.0f - 1e-5f;
+// The single-precision yield screen passes a particle when sigma_eq^2 <=
+// sigma_f^2 (1 - band) in FP32.  The FP32 values of sigma_eq^2 and sigma_f^2
+// are within 2e-6 of their FP64 counterparts, so any band >= 1e-5 (the
+// default; tlsph_set_guard) implies the FP64 test passes; band >= 1 sends
+// every particle to the FP64 update.
 
 // ------------------------------------------------------------------ pass 1, per particle
 // F^{n+1}, J, kinematics, constitutive and damage update, stress, A and the
@@ -590,7 +592,7 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     const float s2 = 1.5f * ((tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]) +
                              2.0f * (tr[3] * tr[3] + tr[4] * tr[4] + tr[5] * tr[5]));
     const float sf = jc_flow_f(mat, (float)s.ep[i], (float)epdot) * omDf;
-    const bool fast = mat.damage != TLSPH_DAMAGE_GTN && dinit < 1.0 && sf > 0.0f && s2 <= sf * sf * YIELD_GUARD;
+    const bool fast = mat.damage != TLSPH_DAMAGE_GTN && dinit < 1.0 && sf > 0.0f && s2 <= sf * sf * c.yield_keep;
     if (!fast) {
         // the FP64 update finishes this particle (k_epi1_slow): hand it the strain increment
 #pragma unroll

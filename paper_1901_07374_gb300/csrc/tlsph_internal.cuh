@@ -115,6 +115,7 @@ struct tlsph_ctx {
     // mixed launch plan: pass-1 form, block, pass-2 form, block (the fastest on
     // GB300 for the 1M-particle bar; the autotuner may choose another)
     int32_t plan[4] = { 4, 64, 4, 128 };
+    double guard = 1e-5;        // relative guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
     bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
     void *mixed = nullptr;      // mixed-precision state (mixed.cu)
@@ -200,6 +201,7 @@ struct MixConst {
     double dt, half_dt;
     float dt_dw, inv_h, dw_norm, w_norm, hg_coef;   // dt_dw = dt x W' normalisation; inv_h = unit / h
     float inv_unit_f;                               // 1 / unit (a power of two)
+    float yield_keep;                               // 1 - guard band of the FP32 elastic screen
     double inv_unit;
     double vref0, vref1, vref2;
     int64_t N;

@@ -78,7 +78,7 @@ EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph
            "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
            "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
            "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_neighbor_layout",
-           "tlsph_fma_peak")
+           "tlsph_fma_peak", "tlsph_set_guard")
 
 _lib = None
 _lock = threading.Lock()
@@ -132,6 +132,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_set_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
         L.tlsph_get_plan.restype = i32
         L.tlsph_get_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
+        L.tlsph_set_guard.restype = i32
+        L.tlsph_set_guard.argtypes = [vp, dbl]
         L.tlsph_fma_peak.restype = i32
         L.tlsph_fma_peak.argtypes = [i32, i32, ctypes.POINTER(dbl)]
         L.tlsph_neighbor_layout.restype = i32
@@ -333,6 +335,10 @@ class Simulation:
         N, nnz, steps = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(load().tlsph_info(self.ctx, ctypes.byref(N), ctypes.byref(nnz), ctypes.byref(steps)), self.ctx)
         return N.value, nnz.value, steps.value
+
+    def set_guard(self, band: float) -> None:
+        """Guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)."""
+        _check(load().tlsph_set_guard(self.ctx, float(band)), self.ctx)
 
     def neighbor_layout(self) -> dict:
         """Form of the sliced neighbour lists of a mixed-precision context:

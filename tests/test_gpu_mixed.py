@@ -208,3 +208,37 @@ def test_line_order_removes_padding_slots():
     for k in ("U", "V", "F", "SIGMA"):
         x, y = a.get(k), b.get(k)
         assert np.max(np.abs(x - y)) <= 1e-5 * max(np.max(np.abs(x)), 1e-30), k
+
+
+def test_guard_band_changes_only_which_kernel_updates():
+    """The FP32 elastic screen's guard band only moves particles between the
+    FP32 elastic branch and the FP64 update: band 1 (every particle in FP64)
+    agrees with the default band to FP32 rounding through plastic flow with
+    elastic unloading near the free surfaces, and bands below the
+    conservative 1e-5 are refused."""
+    w = S.tensile_bar_jc(nx=9, ny=9, nz=20, steps=20)
+    st = S.plastic_flow_state(w)
+    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    b = tlsph.Simulation.from_workload(w, precision="mixed")
+    for g in (a, b):
+        for k, v in st.items():
+            g.set(k, v)
+    b.set_guard(1.0)
+    for bad in (0.0, 1e-6, float("nan"), float("inf")):
+        with pytest.raises(tlsph.TlsphError) as e:
+            a.set_guard(bad)
+        assert e.value.code == -1
+    a.step(20)
+    b.step(20)
+    assert a.status_bits() == 0 and b.status_bits() == 0
+    assert np.mean(a.get("EPSP") > 0) > 0.5
+    for k in ("U", "V", "F", "SIGMA", "STRESS_DEV"):
+        x, y = a.get(k), b.get(k)
+        assert np.max(np.abs(x - y)) <= 1e-5 * max(np.max(np.abs(x)), 1e-30), k
+    o = oracle.Simulation.from_workload(w)
+    o["u"][:] = st["U"]
+    o["v"][:] = st["V"]
+    o["F"][:] = st["F"]
+    o["sd"][:] = st["STRESS_DEV"]
+    o.step(20)
+    compare_state(b.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
