@@ -122,6 +122,9 @@ def lib():
             L.orc_forces.argtypes = [_P(System), _P(Config)]
             L.orc_step.restype = None
             L.orc_step.argtypes = [_P(System), _P(Config), ctypes.c_int64]
+            for name in ("orc_step_predict", "orc_step_pass1", "orc_step_pass2"):
+                getattr(L, name).restype = None
+                getattr(L, name).argtypes = [_P(System), _P(Config)]
             L.orc_init_state.restype = None
             L.orc_init_state.argtypes = [_P(System)]
             L.orc_mat_det.restype = ctypes.c_double
@@ -336,6 +339,18 @@ class Simulation:
 
     def step(self, n: int = 1) -> None:
         lib().orc_step(ctypes.byref(self.sys), ctypes.byref(self.cfg), int(n))
+
+    def step_phase(self, phase: str) -> None:
+        """One phase of a step: "predict" (half kick, drift, constraints),
+        "pass1" (velocity gradients and the per-particle update) or "pass2"
+        (forces and the second half kick); the three in order are one step."""
+        fn = {"predict": lib().orc_step_predict, "pass1": lib().orc_step_pass1, "pass2": lib().orc_step_pass2}[phase]
+        fn(ctypes.byref(self.sys), ctypes.byref(self.cfg))
+
+    @property
+    def vh(self) -> np.ndarray:
+        """The half-step velocity v^{n+1/2} (N x 3, live view)."""
+        return self._vh
 
     def forces(self) -> np.ndarray:
         """Recompute the nodal forces from the current A, D, F, u (no step)."""

@@ -828,37 +828,59 @@ static void apply_bc(const orc_system *s, int64_t i, double *vi)
  *   constitutive update, damage -> D^{n+1}, P^{n+1}
  *   f^{n+1} from P^{n+1}, D^{n+1}, F^{n+1}, u^{n+1}
  *   v^{n+1}   = v^{n+1/2} + dt/2 f^{n+1}/m (BCs applied)                */
-void orc_step(orc_system *s, const orc_config *c, int64_t nsteps)
+/* One time step in three phases (the whole step is the three in order):
+ *  predict: half-step kick v^{n+1/2} = v^n + dt/2 f^n/m (constraints applied)
+ *           and drift u^{n+1} = u^n + dt v^{n+1/2} (rigid wall applied);
+ *  pass 1:  velocity gradients of every row from v^{n+1/2} and D^n, then the
+ *           per-particle update (F, kinematics, constitutive, damage, A);
+ *  pass 2:  forces from A, D^{n+1}, F, u^{n+1}, then the second half kick. */
+void orc_step_predict(orc_system *s, const orc_config *c)
 {
     int64_t N = s->N;
+    for (int64_t i = 0; i < N; ++i) {
+        double m = particle_mass(s, i);
+        for (int k = 0; k < 3; ++k)
+            s->vh[3 * i + k] = s->v[3 * i + k] + 0.5 * c->dt * s->force[3 * i + k] / m;
+        apply_bc(s, i, s->vh + 3 * i);
+    }
+    for (int64_t i = 0; i < 3 * N; ++i) s->u[i] += c->dt * s->vh[i];
+    /* Reading (rigid wall; the paper has no contact): a kinematic plane
+     * z = 0 -- a particle that drifted below it is put back on it and its
+     * velocity may not point into it */
+    if (c->wall)
+        for (int64_t i = 0; i < N; ++i)
+            if (s->X[3 * i + 2] + s->u[3 * i + 2] < 0.0) {
+                s->u[3 * i + 2] = -s->X[3 * i + 2];
+                if (s->vh[3 * i + 2] < 0.0) s->vh[3 * i + 2] = 0.0;
+            }
+}
+
+void orc_step_pass1(orc_system *s, const orc_config *c)
+{
+    int64_t N = s->N;
+    orc_velocity_gradient(N, s->X, s->vol, s->vh, s->D, s->Linv, s->row_ptr, s->col, c->h, s->Fdot);
+    for (int64_t i = 0; i < N; ++i) particle_update(s, c, i);
+}
+
+void orc_step_pass2(orc_system *s, const orc_config *c)
+{
+    int64_t N = s->N;
+    orc_forces(s, c);
+    for (int64_t i = 0; i < N; ++i) {
+        double m = particle_mass(s, i);
+        for (int k = 0; k < 3; ++k)
+            s->v[3 * i + k] = s->vh[3 * i + k] + 0.5 * c->dt * s->force[3 * i + k] / m;
+        apply_bc(s, i, s->v + 3 * i);
+    }
+    s->step += 1;
+}
+
+void orc_step(orc_system *s, const orc_config *c, int64_t nsteps)
+{
     for (int64_t it = 0; it < nsteps; ++it) {
-        for (int64_t i = 0; i < N; ++i) {
-            double m = particle_mass(s, i);
-            for (int k = 0; k < 3; ++k)
-                s->vh[3 * i + k] = s->v[3 * i + k] + 0.5 * c->dt * s->force[3 * i + k] / m;
-            apply_bc(s, i, s->vh + 3 * i);
-        }
-        for (int64_t i = 0; i < 3 * N; ++i) s->u[i] += c->dt * s->vh[i];
-        /* Reading (rigid wall; the paper has no contact): a kinematic plane
-         * z = 0 -- a particle that drifted below it is put back on it and its
-         * velocity may not point into it */
-        if (c->wall)
-            for (int64_t i = 0; i < N; ++i)
-                if (s->X[3 * i + 2] + s->u[3 * i + 2] < 0.0) {
-                    s->u[3 * i + 2] = -s->X[3 * i + 2];
-                    if (s->vh[3 * i + 2] < 0.0) s->vh[3 * i + 2] = 0.0;
-                }
-        orc_velocity_gradient(N, s->X, s->vol, s->vh, s->D, s->Linv, s->row_ptr, s->col,
-                              c->h, s->Fdot);
-        for (int64_t i = 0; i < N; ++i) particle_update(s, c, i);
-        orc_forces(s, c);
-        for (int64_t i = 0; i < N; ++i) {
-            double m = particle_mass(s, i);
-            for (int k = 0; k < 3; ++k)
-                s->v[3 * i + k] = s->vh[3 * i + k] + 0.5 * c->dt * s->force[3 * i + k] / m;
-            apply_bc(s, i, s->v + 3 * i);
-        }
-        s->step += 1;
+        orc_step_predict(s, c);
+        orc_step_pass1(s, c);
+        orc_step_pass2(s, c);
     }
 }
 

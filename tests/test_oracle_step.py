@@ -229,3 +229,19 @@ def test_plastic_flow_state_yields_everywhere():
     inner = np.all((X > lo) & (X < hi), axis=1)
     assert inner.sum() > 50
     assert np.all(o["ep"][inner] > 0.0)
+
+
+def test_step_is_its_three_phases():
+    """predict, pass 1, pass 2 in order are one step, bit for bit (the phases
+    the sharded stepper exchanges halo rows between)."""
+    w = S.failure_variant(S.tensile_bar_cl(nx=5, ny=5, nz=12, steps=20))
+    a = oracle.Simulation.from_workload(w)
+    b = oracle.Simulation.from_workload(w)
+    a.step(15)
+    for _ in range(15):
+        for phase in ("predict", "pass1", "pass2"):
+            b.step_phase(phase)
+    assert a.step_count == b.step_count == 15
+    for k, v in a.state().items():
+        assert np.array_equal(v, b.state()[k]), k
+    assert np.array_equal(a.vh, b.vh)
