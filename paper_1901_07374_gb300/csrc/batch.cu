@@ -20,6 +20,8 @@ struct tlsph_batch {
     void *mem = nullptr;          // BatchHdr followed by capacity BatchSlots
     BatchHdr *hdr = nullptr;
     BatchSlot *slots = nullptr;
+    int64_t *blk0 = nullptr;        // capacity first work blocks (device), after the slots
+    std::vector<int64_t> blk0_host;
     std::vector<BatchSlot> host;
     std::vector<tlsph_ctx *> members;
     std::vector<int64_t> steps_at;  // each member's step count the table was built for
@@ -52,7 +54,7 @@ int tlsph_batch_create(int capacity, void *stream, tlsph_batch **out)
     if (!b) return TLSPH_ERR_NOMEM;
     b->capacity = capacity;
     b->stream = static_cast<cudaStream_t>(stream);
-    const size_t bytes = 256 + (size_t)capacity * sizeof(BatchSlot);
+    const size_t bytes = 256 + (size_t)capacity * sizeof(BatchSlot) + (size_t)capacity * sizeof(int64_t);
     if (cudaMalloc(&b->mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -60,7 +62,8 @@ int tlsph_batch_create(int capacity, void *stream, tlsph_batch **out)
     }
     b->hdr = static_cast<BatchHdr *>(b->mem);
     b->slots = reinterpret_cast<BatchSlot *>(static_cast<char *>(b->mem) + 256);
-    BatchHdr h{ 0, 0 };
+    b->blk0 = reinterpret_cast<int64_t *>(b->slots + capacity);
+    BatchHdr h{ 0, 0, b->blk0 };
     if (cudaMemcpy(b->hdr, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) != cudaSuccess ||
@@ -112,16 +115,20 @@ int tlsph_batch_set(tlsph_batch *b, tlsph_ctx *const *ctxs, int n)
     b->members.assign(ctxs, ctxs + n);
     b->steps_at.resize(n);
     int64_t blk = 0;
+    b->blk0_host.resize(n);
     for (int k = 0; k < n; ++k) {
         b->host[k] = make_batch_slot(*ctxs[k]);
         b->host[k].blk0 = blk;
+        b->blk0_host[k] = blk;
         blk += (ctxs[k]->N + 127) / 128;
         b->steps_at[k] = ctxs[k]->steps;
     }
-    BatchHdr h{ n, blk };
+    BatchHdr h{ n, blk, b->blk0 };
     e = cudaStreamSynchronize(b->own);
     if (e == cudaSuccess && n > 0)
         e = cudaMemcpyAsync(b->slots, b->host.data(), (size_t)n * sizeof(BatchSlot), cudaMemcpyHostToDevice, b->own);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(b->blk0, b->blk0_host.data(), (size_t)n * sizeof(int64_t), cudaMemcpyHostToDevice, b->own);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->hdr, &h, sizeof h, cudaMemcpyHostToDevice, b->own);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->own);
     if (e != cudaSuccess) return batch_fail(b, TLSPH_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));

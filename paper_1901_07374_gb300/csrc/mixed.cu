@@ -1254,42 +1254,59 @@ void mixed_release(tlsph_ctx &) {}
 // depend on the company it keeps.
 namespace tlsph {
 
-__device__ __forceinline__ int batch_find(const BatchSlot *slots, int n, int64_t w)
+// member of work block w: binary search over the members' first blocks (a
+// contiguous array next to the table)
+__device__ __forceinline__ int batch_find(const int64_t *blk0, int n, int64_t w)
 {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (slots[mid].blk0 <= w) lo = mid; else hi = mid - 1;
+        if (blk0[mid] <= w) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
+// A block keeps its current member's slot in shared memory (copied when the
+// block's work moves to another member), so the kernels read the member's
+// arrays and constants from registers and shared memory rather than through
+// global loads that stores into the state could alias.
 template <int KIND, bool HG, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_batch(const BatchHdr *hdr, BatchSlot *slots)
+__global__ void __launch_bounds__(128, MINB) k_batch(const BatchHdr *hdr, const BatchSlot *slots)
 {
     __shared__ int sidx;
+    __shared__ uint64_t slot_words[(sizeof(BatchSlot) + 7) / 8];
+    const BatchSlot &sl = *reinterpret_cast<const BatchSlot *>(slot_words);
     const int nspec = hdr->nspec;
     const int64_t total = hdr->total_blk;
+    int cur = -1;
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
-        if (threadIdx.x == 0) sidx = batch_find(slots, nspec, w);
+        if (threadIdx.x == 0) sidx = batch_find(hdr->blk0, nspec, w);
         __syncthreads();
-        const BatchSlot &sl = slots[sidx];
+        const int m = sidx;
+        if (m != cur) {
+            const uint64_t *src = reinterpret_cast<const uint64_t *>(slots + m);
+            for (int k = threadIdx.x; k < (int)((sizeof(BatchSlot) + 7) / 8); k += blockDim.x) slot_words[k] = src[k];
+            cur = m;
+            __syncthreads();
+        }
+        const DevState &st = sl.s;
+        const MixConst &c = sl.c;
         const int64_t i = (w - sl.blk0) * blockDim.x + threadIdx.x;
-        if (i < sl.s.N) {
+        if (i < st.N) {
             if (KIND == 0) {            // pass-1 gather
-                float m[9];
-                gather1_row<4>(sl.s, sl.c, i, m);
+                float mm[9];
+                gather1_row<4>(st, c, i, mm);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) sl.s.fsum[k * sl.s.N + i] = m[k];
+                for (int k = 0; k < 9; ++k) st.fsum[k * st.N + i] = mm[k];
             } else if (KIND == 1) {     // pass-1 per-particle update
-                float m[9];
+                float mm[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) m[k] = sl.s.fsum[k * sl.s.N + i];
-                epi1_mixed(sl.s, sl.c, i, m);
+                for (int k = 0; k < 9; ++k) mm[k] = st.fsum[k * st.N + i];
+                epi1_mixed(st, c, i, mm);
             } else {                    // pass 2
                 float acc[9];
-                gather2_row<HG, 2>(sl.s, sl.c, i, acc);
-                epi2_mixed<HG>(sl.s, sl.c, i, acc);
+                gather2_row<HG, 2>(st, c, i, acc);
+                epi2_mixed<HG>(st, c, i, acc);
             }
         }
         __syncthreads();

@@ -219,6 +219,7 @@ struct BatchSlot {
 struct BatchHdr {
     int nspec;
     int64_t total_blk;
+    const int64_t *blk0;    // nspec first work blocks, ascending (device, after the slots)
 };
 BatchSlot make_batch_slot(const tlsph_ctx &ctx);
 // grid: the persistent grid of each of the four kernel kinds (batch_grid)
