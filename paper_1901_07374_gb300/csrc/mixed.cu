@@ -59,6 +59,7 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     c.dw_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
     c.w_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h));
     c.hg_coef = (float)(-0.5 * cfg.hg_alpha);
+    c.hg_w = (float)(-0.5 * cfg.hg_alpha / (M_PI * cfg.h * cfg.h * cfg.h) * ctx.s.pack.inv_unit);
     c.inv_unit = ctx.s.pack.inv_unit;
     c.yield_keep = ctx.guard >= 1.0 ? -1.0f : (float)(1.0 - ctx.guard);
     c.inv_unit_f = (float)ctx.s.pack.inv_unit;
@@ -798,32 +799,38 @@ template <bool HG>
 __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
     const int64_t N = c.N;
-    const double Vi = s.vol[i];
-    const double Di = s.D[c.dcur ^ 1][i];
-    const double omdi = 1.0 - Di;
     const float4 a0 = s.r2[i], a1 = s.r2[N + i], a2 = s.r2[2 * N + i];
     const float Ai[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
+    const float Vf = a2.z;                           // V_i
+    const float Df = (float)s.D[c.dcur ^ 1][i];      // D_i^{n+1}
+    const float omdf = 1.0f - Df;
     const float4 s0 = s.s0[i];
-    const float w2 = (float)(2.0 - Di);
+    const float w2 = 2.0f - Df;
     const float bx = w2 * s0.x - keep[0], by = w2 * s0.y - keep[1], bz = w2 * s0.z - keep[2];
-    double f[3];
-    f[0] = Vi * (double)c.dw_norm * ((double)(Ai[0] * bx + Ai[1] * by + Ai[2] * bz) + omdi * (double)keep[3]);
-    f[1] = Vi * (double)c.dw_norm * ((double)(Ai[3] * bx + Ai[4] * by + Ai[5] * bz) + omdi * (double)keep[4]);
-    f[2] = Vi * (double)c.dw_norm * ((double)(Ai[6] * bx + Ai[7] * by + Ai[8] * bz) + omdi * (double)keep[5]);
+    const float vdw = Vf * c.dw_norm;
+    float f[3];
+    f[0] = vdw * ((Ai[0] * bx + Ai[1] * by + Ai[2] * bz) + omdf * keep[3]);
+    f[1] = vdw * ((Ai[3] * bx + Ai[4] * by + Ai[5] * bz) + omdf * keep[4]);
+    f[2] = vdw * ((Ai[6] * bx + Ai[7] * by + Ai[8] * bz) + omdf * keep[5]);
     if (HG) {
-        // the pair sums are in fixed-point units: X_ij, u_ij and x_ij scaled by 1/unit
-        const double hc = (double)c.hg_coef * s.sqrtE[i] * omdi * Vi * (double)c.w_norm * c.inv_unit;
-        f[0] += hc * (double)keep[6];
-        f[1] += hc * (double)keep[7];
-        f[2] += hc * (double)keep[8];
+        // the pair sums are in fixed-point units (X_ij, u_ij and x_ij scaled by 1/unit): hg_w folds 1/unit in;
+        // r2 record 5 .w holds sqrt(E_i) V_i (1 - D_i)
+        const float hc = c.hg_w * s.r2[5 * N + i].w;
+        f[0] += hc * keep[6];
+        f[1] += hc * keep[7];
+        f[2] += hc * keep[8];
     }
+    // the integrator in FP64 from the FP32 force; the half kick is the
+    // predictor's expression (v + dt/2 (f / m)), so a state reloaded from a
+    // checkpoint predicts exactly the v^{n+1/2} of the uninterrupted run
     const double im = s.inv_mass[i];
     const int fail = s.fail[i];
-    double vn[3], v2[3];
+    double fd[3], vn[3], v2[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        s.force[3 * i + k] = f[k];
-        vn[k] = s.vh[3 * i + k] + c.half_dt * (f[k] * im);
+        fd[k] = (double)f[k] * im;
+        s.force[3 * i + k] = (double)f[k];
+        vn[k] = s.vh[3 * i + k] + c.half_dt * fd[k];
     }
     if (fail >= 0) {
         vn[0] = vn[1] = vn[2] = 0.0;
@@ -831,7 +838,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         vn[0] = s.bcv[3 * i]; vn[1] = s.bcv[3 * i + 1]; vn[2] = s.bcv[3 * i + 2];
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * (f[k] * im);
+    for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * fd[k];
     if (fail >= 0) {
         v2[0] = v2[1] = v2[2] = 0.0;
     } else if (s.bcm[i]) {
@@ -849,8 +856,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         s.vh[3 * i + k] = v2[k];
         unext[3 * i + k] = un2[k];
     }
-    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2),
-                          (float)(Vi * omdi));
+    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2), Vf * omdf);
     if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
 }
 

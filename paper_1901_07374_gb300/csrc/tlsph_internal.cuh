@@ -202,6 +202,7 @@ struct MixConst {
     float dt_dw, inv_h, dw_norm, w_norm, hg_coef;   // dt_dw = dt x W' normalisation; inv_h = unit / h
     float inv_unit_f;                               // 1 / unit (a power of two)
     float yield_keep;                               // 1 - guard band of the FP32 elastic screen
+    float hg_w;                                     // -alpha/2 x W normalisation / unit (hourglass force factor)
     double inv_unit;
     double vref0, vref1, vref2;
     int64_t N;
