@@ -47,6 +47,8 @@ def workload(name: str):
         return S.tensile_bar_cl()
     if name == "notched_bar_gtn":
         return S.notched_bar_gtn()
+    if name == "taylor_impact_500k":
+        return S.taylor_impact(500000, v_impact=200.0)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -209,7 +211,8 @@ def field_errors(sim, ref: dict, sc: dict) -> dict:
     return out
 
 
-def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, plan=None, state=None, guard=None):
+def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, plan=None, state=None, guard=None,
+              prestep=0):
     """Create, warm up, then time `steps` steps with CUDA events on the
     library's stream; per-kernel times from the library's own events.  A
     mixed context takes `plan`, else the autotuner's; `state` (caller-order
@@ -229,6 +232,8 @@ def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, pl
             sim.set_guard(guard)
     for k, v in (state or {}).items():
         sim.set(k, v)
+    if prestep:
+        sim.step(prestep)       # untimed: move the run to the window of interest (e.g. after an impact)
     sim.step(warmup)
     torch.cuda.synchronize()
     if clocks:
@@ -269,9 +274,9 @@ def run_ours(args, rank: int, world: int, dist):
     # ---- FP64 GPU path (the comparison) and the headline precision
     ref_sim, ref = (None, None)
     if args.precision != "fp64" and not args.skip_fp64:
-        ref_sim, ref = timed_run(tlsph, torch, w, "fp64", args.steps, args.warmup, stream)
+        ref_sim, ref = timed_run(tlsph, torch, w, "fp64", args.steps, args.warmup, stream, prestep=args.prestep)
     sim, r = timed_run(tlsph, torch, w, args.precision, args.steps, args.warmup, stream,
-                       clocks=ClockSampler(torch.cuda.current_device()), plan=args.plan)
+                       clocks=ClockSampler(torch.cuda.current_device()), plan=args.plan, prestep=args.prestep)
     N, nnz, ms = r["N"], r["nnz"], r["ms"]
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -286,7 +291,7 @@ def run_ours(args, rank: int, world: int, dist):
         sc = field_scales(w)
         ref_state = {f: ref_sim.get(f) for f in FIELDS + ("FAIL_STEP",)}
         accuracy = field_errors(sim, ref_state, sc)
-        accuracy["steps"] = args.warmup + args.steps
+        accuracy["steps"] = args.prestep + args.warmup + args.steps
         ref_sim.close()
     sim.close()
 
@@ -414,6 +419,7 @@ def run_ours(args, rank: int, world: int, dist):
     if rank != 0:
         return
     cfg = {"workload": args.workload, "precision": args.precision, "particles": N, "pairs_per_step": nnz,
+           "prestep": args.prestep,
            "particle_steps_per_s": world * N * args.steps / (ms * 1e-3),
            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
            "l2": "inputs larger than L2 (about 0.9 GB of HBM traffic per step vs 129 MB)"}
@@ -569,6 +575,7 @@ def main():
     ap.add_argument("--plan", default=None, help="mixed launch plan v1,b1,v2,b2 (default: autotuned)")
     ap.add_argument("--no-plastic", action="store_true", help="skip the plastic-flow window")
     ap.add_argument("--plastic-steps", type=int, default=10)
+    ap.add_argument("--prestep", type=int, default=0, help="untimed steps before the warm-up (both paths)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--guard-sweep", action="store_true",
                     help="time the mixed path at several guard bands of its FP32 elastic screen")
