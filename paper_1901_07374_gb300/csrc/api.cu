@@ -359,6 +359,8 @@ DevMat make_dev_mat(const tlsph_material &m)
     d.Kf = (float)d.K; d.Gf = (float)d.G; d.Af = (float)d.A; d.Bf = (float)d.B; d.nf = (float)d.n;
     d.Cf = (float)d.C; d.inv_epsdot0f = (float)d.inv_epsdot0; d.rho0c02f = (float)d.rho0c02;
     d.S_alphaf = (float)d.S_alpha; d.Gamma0f = (float)d.Gamma0; d.sqrtEf = (float)d.sqrtE;
+    d.q1f = (float)d.q1; d.q2f = (float)d.q2; d.q3f = (float)d.q3; d.fcf = (float)d.fc; d.fFf = (float)d.fF;
+    d.fstar_slopef = (float)d.fstar_slope;
     return d;
 }
 

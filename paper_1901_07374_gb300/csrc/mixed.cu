@@ -425,6 +425,27 @@ __device__ __forceinline__ float eos_sm_f(const DevMat &m, float Jm1, float J, f
     return sm > 0.0f ? sm * (1.0f - D) : sm;
 }
 
+// Single-precision elastic screen of the GTN return (Algorithm 2, Eq.
+// yield_GTN): the trial state is inside the yield surface when
+// Phi = x^2 + 2 q1 f* cosh(3/2 q2 T x) - (1 + q3 f*^2) <= 0 with x = sigma_eq / sigma_M
+// and T = sigma_m / sigma_eq (elastic as well when sigma_eq < 1e-12 K).  In
+// FP32 the terms of Phi are O(1) with rounding below 1e-6, so Phi <= -10 band
+// (1 + q3 f*^2) implies the FP64 test passes; s2 = sigma_eq^2 of the trial.
+__device__ __forceinline__ bool gtn_elastic_f(const DevMat &m, float s2, float sm, float ep, float epdot, float f,
+                                              float keep)
+{
+    const float tiny = 1e-12f * m.Kf;
+    if (s2 <= tiny * tiny * keep) return true;
+    const float sM = jc_flow_f(m, ep, epdot);
+    if (!(sM > 0.0f)) return false;
+    const float fs = f <= m.fcf ? f : (f >= m.fFf ? 1.0f / m.q1f : m.fcf + m.fstar_slopef * (f - m.fcf));
+    const float seq = sqrtf(s2);
+    const float x = seq / sM, tri = sm / seq;
+    const float c0 = 1.0f + m.q3f * fs * fs;
+    const float phi = x * x + 2.0f * m.q1f * fs * coshf(1.5f * m.q2f * tri * x) - c0;
+    return phi <= -10.0f * (1.0f - keep) * c0;
+}
+
 // The single-precision yield screen passes a particle when sigma_eq^2 <=
 // sigma_f^2 (1 - band) in FP32.  The FP32 values of sigma_eq^2 and sigma_f^2
 // are within 2e-6 of their FP64 counterparts, so any band >= 1e-5 (the
@@ -592,8 +613,16 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     for (int k = 0; k < 6; ++k) tr[k] = sdh[k] + inc[k];
     const float s2 = 1.5f * ((tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]) +
                              2.0f * (tr[3] * tr[3] + tr[4] * tr[4] + tr[5] * tr[5]));
-    const float sf = jc_flow_f(mat, (float)s.ep[i], (float)epdot) * omDf;
-    const bool fast = mat.damage != TLSPH_DAMAGE_GTN && dinit < 1.0 && sf > 0.0f && s2 <= sf * sf * c.yield_keep;
+    const float sm = eos_sm_f(mat, kin.Jm1, kin.Jf, (float)Dd);
+    double por = 0.0;
+    bool fast;
+    if (mat.damage == TLSPH_DAMAGE_GTN) {
+        por = s.por[i];
+        fast = por < mat.fF && gtn_elastic_f(mat, s2, sm, (float)s.ep[i], (float)epdot, (float)por, c.yield_keep);
+    } else {
+        const float sf = jc_flow_f(mat, (float)s.ep[i], (float)epdot) * omDf;
+        fast = dinit < 1.0 && sf > 0.0f && s2 <= sf * sf * c.yield_keep;
+    }
     if (!fast) {
         // the FP64 update finishes this particle (k_epi1_slow): hand it the strain increment
 #pragma unroll
@@ -610,8 +639,9 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
         s.sdl[k * N + i] = sdl[k];
     }
     if (epdot != 0.0) s.epdot[i] = 0.0;
-    const float sm = eos_sm_f(mat, kin.Jm1, kin.Jf, (float)Dd);
-    const double Dnew = mat.damage == TLSPH_DAMAGE_NONE ? Dd : 0.0;   // D from D_init < 1
+    // D of the unchanged damage variables: Sec. 5.3 with D_init < 1 (CL, JC), q1 f*(f) (GTN), unchanged (none)
+    const double Dnew = mat.damage == TLSPH_DAMAGE_NONE ? Dd
+                      : (mat.damage == TLSPH_DAMAGE_GTN ? mat.q1 * gtn_fstar(mat, por) : 0.0);
     Dnext[i] = Dnew;
     epi1_finish(s, c, i, kin, Li, sdh, sm, Dnew, false, Vf, u0, u1, u2, st);
 }

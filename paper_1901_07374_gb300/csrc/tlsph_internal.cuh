@@ -27,6 +27,7 @@ struct DevMat {
     double fstar_slope;  // (1/q1 - fc) / (fF - fc)
     // single-precision copies for the mixed path's elastic fast path
     float Kf, Gf, Af, Bf, nf, Cf, inv_epsdot0f, rho0c02f, S_alphaf, Gamma0f, sqrtEf;
+    float q1f, q2f, q3f, fcf, fFf, fstar_slopef;
 };
 
 // Fixed-point reference positions of the mixed path: X = center + unit * (x, y, z)

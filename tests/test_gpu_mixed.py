@@ -242,3 +242,26 @@ def test_guard_band_changes_only_which_kernel_updates():
     o["sd"][:] = st["STRESS_DEV"]
     o.step(20)
     compare_state(b.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
+
+
+def test_gtn_mixed_screen_against_fp64_update_and_oracle():
+    """GTN porous plasticity in the mixed path: particles clearly inside the
+    GTN yield surface take the FP32 elastic branch, the others the FP64
+    return.  Through 300 steps of a small notched bar (plastic flow near the
+    notch, elastic elsewhere) it agrees with every particle in the FP64 update
+    (guard band 1) to FP32 rounding and with the oracle within MIXED_TOL."""
+    w = S.notched_bar_gtn(radius=2.0e-3, height=6e-3, spacing=0.3e-3, notch_radius=0.6e-3, v_grip=20.0, steps=300)
+    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    b = tlsph.Simulation.from_workload(w, precision="mixed")
+    b.set_guard(1.0)
+    a.step(300)
+    b.step(300)
+    assert a.status_bits() == 0 and b.status_bits() == 0
+    ep = a.get("EPSP")
+    assert (ep > 0).any() and (ep == 0).any()
+    for k in ("U", "V", "F", "SIGMA", "POROSITY"):
+        x, y = a.get(k), b.get(k)
+        assert np.max(np.abs(x - y)) <= 1e-4 * max(np.max(np.abs(x)), 1e-30), k
+    o = oracle.Simulation.from_workload(w)
+    o.step(300)
+    compare_state(a.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
