@@ -215,6 +215,17 @@ int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, in
  * next call on ctx. */
 const char *tlsph_last_error(const tlsph_ctx *ctx);
 
+/* Diagnostics of the state at the current step boundary (no counterpart in
+ * the paper; conservation checks and monitoring): out[0..2] momentum
+ * sum_i m_i v_i, out[3..5] force sum sum_i f_i, out[6] kinetic energy
+ * sum_i m_i |v_i|^2 / 2, out[7] number of failed particles, out[8] largest D,
+ * out[9] largest equivalent plastic strain; SI units, FP64, host array of n =
+ * TLSPH_DIAG_COUNT doubles.  The sums are deterministic (fixed blocking and
+ * order).  Synchronises the context's stream.  TLSPH_ERR_ARG for n !=
+ * TLSPH_DIAG_COUNT or NULL out. */
+#define TLSPH_DIAG_COUNT 10
+int tlsph_diagnostics(tlsph_ctx *ctx, double *out, int n);
+
 /* Release the context (and its device memory when the library owns it). */
 int tlsph_destroy(tlsph_ctx *ctx);
 

@@ -25,7 +25,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 // F / sd / sig / A block, which is only initialised after the build.
 struct Layout {
     size_t X, vol, mass, inv_mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
-    size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col;
+    size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col, diag;
     size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
@@ -136,6 +136,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.force = c.take(3 * n * d);
     L.fail = c.take(n * sizeof(int32_t));
     L.status = c.take(sizeof(uint32_t));
+    L.diag = c.take(DIAG_BLOCKS * TLSPH_DIAG_COUNT * sizeof(double));
     L.perm = c.take(n * sizeof(int32_t));
     L.mats = c.take(TLSPH_MAX_MATERIALS * sizeof(DevMat));
     if (mixed) {
@@ -273,6 +274,7 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
     s.force = at<double>(base, L.force);
     s.fail = at<int32_t>(base, L.fail);
     s.status = at<uint32_t>(base, L.status);
+    ctx->diag = at<double>(base, L.diag);
     s.mats = at<DevMat>(base, L.mats);
 }
 
@@ -675,6 +677,18 @@ int tlsph_status_bits(tlsph_ctx *ctx, uint32_t *bits)
     cudaError_t e = cudaMemcpyAsync(bits, ctx->s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    return TLSPH_OK;
+}
+
+int tlsph_diagnostics(tlsph_ctx *ctx, double *out, int n)
+{
+    if (!ctx || !out || n != TLSPH_DIAG_COUNT) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    cudaError_t e = launch_diagnostics(ctx->s, ctx->dcur, ctx->diag, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, ctx->diag, TLSPH_DIAG_COUNT * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics");
     return TLSPH_OK;
 }
 

@@ -499,6 +499,63 @@ cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ diagnostics
+// Block b reduces particles [b N / B, (b + 1) N / B) in a fixed order (thread
+// stride, then a shared-memory tree); a second one-block kernel reduces the
+// block partials in block order: the same N gives the same bits every time.
+constexpr int DIAG_THREADS = 256;
+
+__device__ __forceinline__ void diag_combine(double *a, const double *b)
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += b[k];      // momentum, force sum, kinetic energy, failed count
+#pragma unroll
+    for (int k = 8; k < TLSPH_DIAG_COUNT; ++k) a[k] = fmax(a[k], b[k]);
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_blocks(DevState s, int dcur, double *partials)
+{
+    __shared__ double sh[DIAG_THREADS][TLSPH_DIAG_COUNT];
+    const int64_t N = s.N;
+    const int64_t lo = (int64_t)blockIdx.x * N / gridDim.x, hi = (int64_t)(blockIdx.x + 1) * N / gridDim.x;
+    double a[TLSPH_DIAG_COUNT];
+#pragma unroll
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double m = s.mass[i];
+        const double v0 = s.v[3 * i], v1 = s.v[3 * i + 1], v2 = s.v[3 * i + 2];
+        double b[TLSPH_DIAG_COUNT] = { m * v0, m * v1, m * v2, s.force[3 * i], s.force[3 * i + 1], s.force[3 * i + 2],
+                                       0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2), s.fail[i] >= 0 ? 1.0 : 0.0,
+                                       s.D[dcur][i], s.ep[i] };
+        diag_combine(a, b);
+    }
+#pragma unroll
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) sh[threadIdx.x][k] = a[k];
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) diag_combine(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) partials[(int64_t)blockIdx.x * TLSPH_DIAG_COUNT + k] = sh[0][k];
+}
+
+__global__ void k_diag_final(double *partials, int nblocks)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a[TLSPH_DIAG_COUNT];
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = partials[k];
+    for (int b = 1; b < nblocks; ++b) diag_combine(a, partials + (int64_t)b * TLSPH_DIAG_COUNT);
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) partials[k] = a[k];
+}
+
+cudaError_t launch_diagnostics(const DevState &s, int dcur, double *partials, cudaStream_t st)
+{
+    k_diag_blocks<<<DIAG_BLOCKS, DIAG_THREADS, 0, st>>>(s, dcur, partials);
+    k_diag_final<<<1, 32, 0, st>>>(partials, DIAG_BLOCKS);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, cudaStream_t st)
 {
     k_predict<<<nblk(s.N, 256), 256, 0, st>>>(s, ucur, dt, wall ? 1 : 0);

@@ -132,6 +132,7 @@ struct tlsph_ctx {
     bool reordered = false;
     bool ell_ok = false;        // sliced neighbour lists built (thread-per-row plans allowed)
     int64_t ell_stats[4] = { 0, 0, 0, 0 };   // slices, aligned slices, slots, words
+    double *diag = nullptr;     // DIAG_BLOCKS x TLSPH_DIAG_COUNT partials; the first row holds the result
     void *ell_mem = nullptr;    // library-owned sliced-ELL columns
     int32_t *perm_dev = nullptr;
     std::vector<int32_t> perm, inv;
@@ -162,6 +163,10 @@ cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, 
                          cudaStream_t st);
 
 // step64.cu
+// deterministic reductions of the diagnostics (tlsph_diagnostics) over a
+// fixed grid of DIAG_BLOCKS blocks; the result lands in partials[0 .. TLSPH_DIAG_COUNT)
+constexpr int DIAG_BLOCKS = 152;
+cudaError_t launch_diagnostics(const DevState &s, int dcur, double *partials, cudaStream_t st);
 cudaError_t launch_init_state(const DevState &s, cudaStream_t st);
 cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool gtn_damage, cudaStream_t st);
 cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, cudaStream_t st);

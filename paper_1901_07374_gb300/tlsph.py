@@ -78,7 +78,7 @@ EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph
            "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
            "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
            "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_neighbor_layout",
-           "tlsph_fma_peak", "tlsph_set_guard")
+           "tlsph_fma_peak", "tlsph_set_guard", "tlsph_diagnostics")
 
 _lib = None
 _lock = threading.Lock()
@@ -132,6 +132,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_set_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
         L.tlsph_get_plan.restype = i32
         L.tlsph_get_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
+        L.tlsph_diagnostics.restype = i32
+        L.tlsph_diagnostics.argtypes = [vp, ctypes.POINTER(dbl), i32]
         L.tlsph_set_guard.restype = i32
         L.tlsph_set_guard.argtypes = [vp, dbl]
         L.tlsph_fma_peak.restype = i32
@@ -335,6 +337,14 @@ class Simulation:
         N, nnz, steps = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(load().tlsph_info(self.ctx, ctypes.byref(N), ctypes.byref(nnz), ctypes.byref(steps)), self.ctx)
         return N.value, nnz.value, steps.value
+
+    def diagnostics(self) -> dict:
+        """Momentum, force sum, kinetic energy, failed count, largest D and
+        plastic strain of the current state (tlsph_diagnostics)."""
+        out = (ctypes.c_double * 10)()
+        _check(load().tlsph_diagnostics(self.ctx, out, 10), self.ctx)
+        return {"momentum": tuple(out[0:3]), "force_sum": tuple(out[3:6]), "kinetic_energy": out[6],
+                "failed": int(out[7]), "max_damage": out[8], "max_epsp": out[9]}
 
     def set_guard(self, band: float) -> None:
         """Guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)."""

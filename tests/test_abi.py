@@ -80,3 +80,11 @@ def test_null_context_calls(lib):
     assert lib.tlsph_sync(None) == -1
     assert lib.tlsph_destroy(None) == -1
     assert lib.tlsph_set_material(None, 0, None) == -1
+
+
+def test_diagnostics_argument_errors(lib):
+    import ctypes
+    out = (ctypes.c_double * 10)()
+    lib.tlsph_diagnostics.restype = ctypes.c_int
+    lib.tlsph_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    assert lib.tlsph_diagnostics(None, out, 10) == -1

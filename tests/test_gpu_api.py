@@ -147,3 +147,25 @@ def test_fma_peak_microbenchmark():
     with pytest.raises(tlsph.TlsphError) as e:
         tlsph.fma_peak(False, 0)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_diagnostics_match_the_fields(precision):
+    """Momentum, force sum, kinetic energy, failed count and the largest D and
+    plastic strain equal the same reductions of the fields read back, and the
+    device reduction returns the same bits every time."""
+    w = S.failure_variant(S.tensile_bar_cl(nx=6, ny=6, nz=20))
+    g = tlsph.Simulation.from_workload(w, precision=precision)
+    g.step(300)
+    d = g.diagnostics()
+    assert d == g.diagnostics()
+    m = w.materials[0]["rho0"] * w.specimen.vol
+    v, f = g.get("V"), g.get("FORCE")
+    mom = (m[:, None] * v).sum(0)
+    assert np.allclose(d["momentum"], mom, rtol=1e-12, atol=1e-12 * np.abs(m[:, None] * v).sum())
+    assert np.allclose(d["force_sum"], f.sum(0), rtol=1e-12, atol=1e-12 * np.abs(f).sum())
+    assert d["kinetic_energy"] == pytest.approx(0.5 * (m * (v * v).sum(1)).sum(), rel=1e-12)
+    assert d["failed"] == int((g.get("FAIL_STEP") >= 0).sum())
+    assert d["max_damage"] == g.get("DAMAGE").max()
+    assert d["max_epsp"] == g.get("EPSP").max()
+    assert d["max_epsp"] > 0
