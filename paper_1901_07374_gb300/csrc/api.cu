@@ -28,7 +28,7 @@ struct Layout {
     size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col, diag;
     size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
-    size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp;
+    size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp, xf;
     size_t perm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order + staged caller-order inputs
     size_t overlay_end, ell;
     size_t total;
@@ -177,6 +177,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.cell_cursor = s.take((size_t)L.max_cells * sizeof(int64_t));
     L.cell_items = s.take(n * sizeof(int32_t));
     L.scan_tmp = s.take(L.scan_elems * sizeof(int64_t));
+    L.xf = s.take(n * 16);
     c.off = std::max(state_end, s.off);
     L.overlay_end = c.off;
     L.col = c.take((size_t)std::max<int64_t>(nnz_cap, 1) * sizeof(int32_t));
@@ -464,7 +465,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     const CellGrid grid = make_cell_grid(X, N, cfg->rc);
     if (grid.ncells > L.max_cells) return bail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
     Scratch sc{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
-                at<int64_t>(base, L.scan_tmp), L.scan_elems };
+                at<int64_t>(base, L.scan_tmp), L.scan_elems, at<float4>(base, L.xf) };
     // ---- internal order (brick-major cells, caller index inside a cell) and the gather into it
     const bool line_order = (cfg->flags & TLSPH_FLAG_LINE_ORDER) != 0;
     ctx->reordered = (cfg->flags & (TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_LINE_ORDER)) != 0;
@@ -509,7 +510,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         bind_state(ctx, base, L);
         ctx->perm_dev = at<int32_t>(base, L.perm);
         sc = Scratch{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
-                      at<int64_t>(base, L.scan_tmp), L.scan_elems };
+                      at<int64_t>(base, L.scan_tmp), L.scan_elems, at<float4>(base, L.xf) };
         row_ptr = const_cast<int64_t *>(s.row_ptr);
         s.col = at<int32_t>(base, L.overlay_end);
         ctx->nnz_cap = nnz;

@@ -186,14 +186,33 @@ __device__ __forceinline__ bool within(const double *xi, const double *xj, doubl
     return r2 < rc2;
 }
 
+// Single-precision prefilter of the FP64 predicate: xf holds X - centre
+// rounded once to FP32 (error <= delta per coordinate), so the FP32 r^2 of a
+// pair is within a margin of the exact one that the host bounds; a pair whose
+// FP32 r^2 is below lo is a neighbour, above hi is not, and only the band in
+// between is decided by the FP64 predicate itself, so the result is the FP64
+// predicate's exactly.
+struct Prefilter {
+    double cx, cy, cz;
+    float lo, hi;
+};
+
+__global__ void k_xf(const double *X, int64_t N, Prefilter p, float4 *xf)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    xf[i] = make_float4((float)(X[3 * i] - p.cx), (float)(X[3 * i + 1] - p.cy), (float)(X[3 * i + 2] - p.cz), 0.0f);
+}
+
 // one thread per particle: count (out == nullptr) or write its neighbours
 __global__ void k_nbr(const double *X, int64_t N, GridArgs a, const int64_t *cell_start,
                       const int32_t *items, double rc2, int64_t *count, const int64_t *row_ptr,
-                      int32_t *out)
+                      int32_t *out, const float4 *xf, Prefilter pf)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double xi[3] = { X[3 * i], X[3 * i + 1], X[3 * i + 2] };
+    const float4 fi = xf ? xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     int cx, cy, cz;
     cell_of(a, xi, cx, cy, cz);
     int64_t n = 0;
@@ -207,7 +226,16 @@ __global__ void k_nbr(const double *X, int64_t N, GridArgs a, const int64_t *cel
             for (int64_t k = b; k < e; ++k) {
                 int32_t j = items[k];
                 if (j == i) continue;
-                if (within(xi, X + 3 * (int64_t)j, rc2)) {
+                bool nb;
+                if (xf) {
+                    const float4 fj = xf[j];
+                    const float dx = fj.x - fi.x, dy = fj.y - fi.y, dz = fj.z - fi.z;
+                    const float r2f = dx * dx + dy * dy + dz * dz;
+                    nb = r2f < pf.lo ? true : (r2f > pf.hi ? false : within(xi, X + 3 * (int64_t)j, rc2));
+                } else {
+                    nb = within(xi, X + 3 * (int64_t)j, rc2);
+                }
+                if (nb) {
                     if (out) out[w + n] = j;
                     ++n;
                 }
@@ -216,27 +244,114 @@ __global__ void k_nbr(const double *X, int64_t N, GridArgs a, const int64_t *cel
     if (!out) count[i] = n;
 }
 
-// insertion sort of each row (rows are short; runs once)
+// Rows sorted ascending, one warp per row: a bitonic network over E elements
+// (E / 32 per lane, element e = k * 32 + lane, padded with INT_MAX); rows
+// longer than 256 fall back to an insertion sort by lane 0.
+template <int PER>
+__device__ __forceinline__ void warp_bitonic(int32_t (&v)[PER], int lane)
+{
+    constexpr int E = 32 * PER;
+#pragma unroll
+    for (int size = 2; size <= E; size <<= 1) {
+#pragma unroll
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            if (d >= 32) {
+                const int kd = d >> 5;
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    if (k & kd) continue;
+                    const int e = k * 32 + lane;
+                    const bool asc = (e & size) == 0;
+                    const int32_t a = v[k], b = v[k | kd];
+                    const int32_t lo = min(a, b), hi = max(a, b);
+                    v[k] = asc ? lo : hi;
+                    v[k | kd] = asc ? hi : lo;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int e = k * 32 + lane;
+                    const bool asc = (e & size) == 0;
+                    const int32_t o = __shfl_xor_sync(0xffffffffu, v[k], d);
+                    const bool keep_min = ((lane & d) == 0) == asc;
+                    v[k] = keep_min ? min(v[k], o) : max(v[k], o);
+                }
+            }
+        }
+    }
+}
+
+template <int PER>
+__device__ __forceinline__ void sort_row_warp(int32_t *c, int n, int lane)
+{
+    int32_t v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = k * 32 + lane;
+        v[k] = e < n ? c[e] : INT_MAX;
+    }
+    warp_bitonic<PER>(v, lane);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = k * 32 + lane;
+        if (e < n) c[e] = v[k];
+    }
+}
+
 __global__ void k_sort_rows(const int64_t *row_ptr, int32_t *col, int64_t N)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int64_t b = row_ptr[i], e = row_ptr[i + 1];
-    for (int64_t k = b + 1; k < e; ++k) {
-        int32_t v = col[k];
-        int64_t m = k - 1;
-        while (m >= b && col[m] > v) { col[m + 1] = col[m]; --m; }
-        col[m + 1] = v;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;                       // whole warps: blockDim is a multiple of 32
+    const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+    const int64_t n = e - b;
+    if (n <= 64) sort_row_warp<2>(col + b, (int)n, lane);
+    else if (n <= 128) sort_row_warp<4>(col + b, (int)n, lane);
+    else if (n <= 256) sort_row_warp<8>(col + b, (int)n, lane);
+    else if (lane == 0) {
+        for (int64_t k = b + 1; k < e; ++k) {
+            int32_t v = col[k];
+            int64_t m = k - 1;
+            while (m >= b && col[m] > v) { col[m + 1] = col[m]; --m; }
+            col[m + 1] = v;
+        }
     }
 }
 
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// prefilter thresholds for the grid's box: the FP32 positions are centred on
+// the box, so each coordinate carries at most delta = half extent x 2^-24;
+// |r2f - r2| <= 4 sqrt(3) rc delta + 4 sqrt(3) delta^2 + 4 2^-24 rc^2 for a
+// pair near the cutoff, widened by 4x
+static Prefilter prefilter_for(const CellGrid &g, double rc2)
+{
+    Prefilter p{};
+    double ext = 0.0, c[3];
+    for (int k = 0; k < 3; ++k) {
+        const double span = g.nc[k] * g.cs;
+        c[k] = g.xmin[k] + 0.5 * span;
+        ext = fmax(ext, 0.5 * span);
+    }
+    p.cx = c[0]; p.cy = c[1]; p.cz = c[2];
+    const double rc = sqrt(rc2), delta = ext * 0x1p-24;
+    const double margin = 4.0 * (6.93 * rc * delta + 6.93 * delta * delta + 4.0 * 0x1p-24 * rc2);
+    p.lo = (float)((rc2 - margin) * (1.0 - 1e-6));
+    p.hi = (float)((rc2 + margin) * (1.0 + 1e-6));
+    if (!(p.lo > 0.0f)) p.lo = 0.0f;   // no certain neighbours: every pair below hi goes to FP64
+    return p;
+}
 
 cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
                                   int64_t *row_ptr, cudaStream_t st)
 {
     GridArgs a = grid_args(g);
     cudaError_t e;
+    const Prefilter pf = prefilter_for(g, rc2);
+    if (sc.xf) {
+        k_xf<<<blocks_for(s.N, 256), 256, 0, st>>>(s.X, s.N, pf, sc.xf);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // cell histogram -> cell_start (exclusive scan) -> scatter with a cursor
     if ((e = cudaMemsetAsync(sc.cell_start, 0, (g.ncells + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
     k_cell_count<<<blocks_for(s.N, 256), 256, 0, st>>>(s.X, s.N, a, sc.cell_start);
@@ -247,7 +362,7 @@ cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Sc
                                                          sc.cell_items);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_nbr<<<blocks_for(s.N, 128), 128, 0, st>>>(s.X, s.N, a, sc.cell_start, sc.cell_items, rc2, row_ptr,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, sc.xf, pf);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(row_ptr + s.N, 0, sizeof(int64_t), st)) != cudaSuccess) return e;
     return scan_exclusive_i64(row_ptr, s.N + 1, sc.scan_tmp, st);
@@ -258,10 +373,10 @@ cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scr
 {
     GridArgs a = grid_args(g);
     k_nbr<<<blocks_for(s.N, 128), 128, 0, st>>>(s.X, s.N, a, sc.cell_start, sc.cell_items, rc2, nullptr,
-                                                 row_ptr, col);
+                                                 row_ptr, col, sc.xf, prefilter_for(g, rc2));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sort_rows<<<blocks_for(s.N, 128), 128, 0, st>>>(row_ptr, col, s.N);
+    k_sort_rows<<<blocks_for(s.N * 32, 256), 256, 0, st>>>(row_ptr, col, s.N);
     return cudaGetLastError();
 }
 
@@ -360,8 +475,9 @@ __global__ void k_shape(const double *X, const double *vol, const int64_t *row_p
     for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
         const int64_t j = col[p];
         const double dx = X[3 * j] - xi, dy = X[3 * j + 1] - yi, dz = X[3 * j + 2] - zi;
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        const double c0 = vol[j] * spline_dw(r * inv_h) / r;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double rinv = rsqrt(r2);
+        const double c0 = vol[j] * spline_dw(r2 * rinv * inv_h) * rinv;
         g[0] += c0 * dx; g[1] += c0 * dy; g[2] += c0 * dz;
         const double c = dw_norm * c0;
         l[0] += c * dx * dx; l[1] += c * dy * dy; l[2] += c * dz * dz;

@@ -96,6 +96,7 @@ struct Scratch {            // neighbour-build scratch (set-up only)
     int32_t *cell_items;    // N
     int64_t *scan_tmp;      // scan partial sums
     size_t scan_tmp_elems;
+    float4 *xf = nullptr;   // N single-precision positions for the prefilter of the FP64 predicate (or null)
 };
 
 }  // namespace tlsph

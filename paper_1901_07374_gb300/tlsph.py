@@ -255,7 +255,7 @@ class Simulation:
     nnz_cap); otherwise the library owns its memory.
     stream: torch.cuda.Stream or raw handle; default the current stream.
     spatial_order / line_order: internal particle order (TLSPH_FLAG_SPATIAL_ORDER
-    / TLSPH_FLAG_LINE_ORDER); line_order defaults to on for the mixed path.
+    / TLSPH_FLAG_LINE_ORDER); both off by default (the caller's order).
     wall: the rigid wall on z = 0 (TLSPH_FLAG_WALL)."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
@@ -270,8 +270,8 @@ class Simulation:
         bc_mask = _host(bc_mask, np.uint8)
         bc_vel = _host(bc_vel, np.float64, (N, 3))
         f0 = _host(f0, np.float64)
-        if line_order is None:      # lattice-line order by default for the mixed path (fewer padding slots)
-            line_order = precision == "mixed" and not spatial_order
+        if line_order is None:      # opt-in: fewer padding slots, but a host sort at create and permuted reads
+            line_order = False
         self.cfg = make_config(h, rc, dt, hg_alpha, precision,
                                (FLAG_SPATIAL_ORDER if spatial_order else 0) | (FLAG_WALL if wall else 0) |
                                (FLAG_LINE_ORDER if line_order else 0))
