@@ -456,7 +456,7 @@ def run_batched(args):
     ws = S.batched_specimens(args.specimens, seed=0)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    sims = [tlsph.Simulation.from_workload(w, precision="mixed", stream=stream) for w in ws]
+    sims = [tlsph.Simulation.from_workload(w, precision="mixed", stream=stream, line_order=True) for w in ws]
     setup = time.perf_counter() - t0
     N = sum(s.N for s in sims)
     nnz = sum(s.nnz for s in sims)

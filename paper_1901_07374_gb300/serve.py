@@ -66,7 +66,7 @@ def memory_estimate(w, precision: str = "mixed") -> int:
 class Server:
     def __init__(self, mem_cap_bytes: float = 120e9, max_live: int = 512, chunk_steps: int = 100,
                  precision: str = "mixed", graph: bool = True, fields=("U", "V", "SIGMA", "DAMAGE", "FAIL_STEP"),
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, line_order: bool = True):
         import torch
         self.cap = int(mem_cap_bytes)
         self.max_live = int(max_live)
@@ -74,6 +74,8 @@ class Server:
         self.precision = precision
         self.graph = graph
         self.fields = tuple(fields)
+        # lattice-line internal order: the many small specimens of a request mix carry far fewer padding slots
+        self.line_order = line_order
         self.clock = clock
         self.create_stream = torch.cuda.Stream()
         self.batch = tlsph.Batch(self.max_live, stream=torch.cuda.current_stream())
@@ -92,7 +94,8 @@ class Server:
         if self.used + need > self.cap or len(self.live) >= self.max_live:
             return False
         try:
-            sim = tlsph.Simulation.from_workload(r.workload, precision=self.precision, stream=self.create_stream)
+            sim = tlsph.Simulation.from_workload(r.workload, precision=self.precision, stream=self.create_stream,
+                                                 line_order=self.line_order and self.precision == "mixed")
         except (tlsph.TlsphError, RuntimeError, ValueError) as e:
             r.status, r.error, r.done = "failed", str(e), now
             return True
