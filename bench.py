@@ -72,7 +72,11 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # DRAM bytes (read + write) per step of each pass from one ncu capture of the
 # same kernel build, keyed by (workload, precision, pass, plan form of that
 # pass); absent for other plans and once the kernels change after the capture
-TRAFFIC = {}
+TRAFFIC = {
+    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 551736064,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 1): 319848704,   # k_pass2_mixed_t
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 319711744,   # k_pass2_mixed_tc
+}
 
 
 # ---------------------------------------------------------------- clocks
