@@ -10,8 +10,9 @@ A pair-interaction is one directed pair (i, j in S_i) advanced through one
 full step (both gather passes).  `value` is device-timed with CUDA events on
 the stream the library launches on, inputs resident in HBM; `e2e` is the same
 metric through the C ABI with host buffers: upload of the specimen from
-pinned memory, neighbour build, the K steps and the download of the final
-fields, all inside the timed region.  The state a step reads and writes
+pinned memory, neighbour build, the K steps (each followed by a read-back of
+its diagnostics: momentum, force sum, kinetic energy, failures) and the
+download of the final fields, all inside the timed region.  The state a step reads and writes
 (about 0.9 GB of HBM traffic) is far larger than the 129 MB L2, so no flush is
 needed between steps.
 
@@ -77,6 +78,17 @@ TRAFFIC = {
     ("tensile_bar_jc_40x40x640", "mixed", "pass2", 1): 319848704,   # k_pass2_mixed_t
     ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 319711744,   # k_pass2_mixed_tc
 }
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The largest value over all ranks (a timing: the job ends with its
+    slowest rank); identity on one process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------- clocks
@@ -163,6 +175,29 @@ def oracle_rate(seconds: float, max_steps: int | None = None, nz: int = 24):
         if el >= seconds or (max_steps and steps >= max_steps):
             break
     return sim.nnz * steps / el, steps, sim.nnz, sim.N, el
+
+
+def _oracle_replica(seconds: float, q) -> None:
+    q.put(oracle_rate(seconds)[0])
+
+
+def oracle_rate_all_cores(seconds: float, cores: int | None = None):
+    """Aggregate pair-interactions/s of `cores` independent single-thread
+    oracle replicas (spawned processes, one per host core) stepping the same
+    bounded sample side by side: the host's all-core oracle throughput.  The
+    oracle sums each row sequentially, so every replica computes the same
+    bits as the single-thread run."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica, args=(seconds, q)) for _ in range(cores)]
+    for p in procs:
+        p.start()
+    rates = [q.get() for _ in procs]
+    for p in procs:
+        p.join()
+    return sum(rates), cores
 
 
 def run_reference(args, rank: int, world: int):
@@ -282,10 +317,7 @@ def run_ours(args, rank: int, world: int, dist):
     sim, r = timed_run(tlsph, torch, w, args.precision, args.steps, args.warmup, stream,
                        clocks=ClockSampler(torch.cuda.current_device()), plan=args.plan, prestep=args.prestep)
     N, nnz, ms = r["N"], r["nnz"], r["ms"]
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     value = world * nnz * args.steps / (ms * 1e-3)
 
     # ---- accuracy of the headline path against the FP64 GPU path (same steps)
@@ -397,8 +429,12 @@ def run_ours(args, rank: int, world: int, dist):
                               precision=args.precision, stream=stream)
         if r.get("plan"):
             s2.set_plan(r["plan"])
-        s2.step(args.steps)
         d2h = 0
+        diag = None
+        for _ in range(args.steps):      # each step's result read back: the step's diagnostics (10 doubles)
+            s2.step(1)
+            diag = s2.diagnostics()
+            d2h += 10 * 8
         L = tlsph.load()
         for k, (t, a) in outs.items():
             tlsph._check(L.tlsph_get_state(s2.ctx, tlsph.FIELD[k], a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0),
@@ -406,13 +442,13 @@ def run_ours(args, rank: int, world: int, dist):
             d2h += a.nbytes
         el = time.perf_counter() - t0
         s2.close()
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, dist, "cuda")
         e2e = {"value": world * nnz * args.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "includes": "create (upload, neighbour build, L^-1) + K steps + download of u, v, sigma, D"}
+               "includes": "create (upload of the specimen from pinned memory, neighbour build, L^-1) + K steps, each "
+                           "followed by a read-back of its diagnostics (momentum, force sum, kinetic energy, failures) "
+                           "+ download of u, v, sigma, D",
+               "final_kinetic_energy": diag["kinetic_energy"] if diag else None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -420,6 +456,10 @@ def run_ours(args, rank: int, world: int, dist):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first 24 of 640 layers of the bar ({oN} particles, {onnz} pairs), "
                          f"{steps} steps in {oel:.1f} s, single thread"}
+        if args.cpu_all_cores:
+            agg, cores = oracle_rate_all_cores(args.cpu_seconds / 2)
+            cpu["all_cores"] = {"value": agg, "unit": UNIT, "cores": cores,
+                                "how": "independent single-thread replicas of the same sample, one per core"}
     if rank != 0:
         return
     cfg = {"workload": args.workload, "precision": args.precision, "particles": N, "pairs_per_step": nnz,
@@ -570,6 +610,8 @@ def main():
     ap.add_argument("--workload", default="tensile_bar_jc_40x40x640")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
+                    help="skip the all-core oracle figure (one replica per host core)")
     ap.add_argument("--skip-fp64", action="store_true", help="do not run the FP64 comparison path")
     ap.add_argument("--specimens", type=int, default=256, help="batched workload: number of specimens")
     ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
