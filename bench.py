@@ -74,9 +74,9 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # same kernel build, keyed by (workload, precision, pass, plan form of that
 # pass); absent for other plans and once the kernels change after the capture
 TRAFFIC = {
-    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 551736064,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 1): 319848704,   # k_pass2_mixed_t
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 319711744,   # k_pass2_mixed_tc
+    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 551018496,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 1): 317005056,   # k_pass2_mixed_t
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 317319424,   # k_pass2_mixed_tc
 }
 
 
@@ -488,6 +488,73 @@ def run_ours(args, rank: int, world: int, dist):
 
 
 # ---------------------------------------------------------------- batched and served forms
+# ---------------------------------------------------------------- accuracy trajectories
+ACCURACY_CHECKPOINTS = (1, 10, 100, 500, 2000)
+
+
+def accuracy_cases():
+    """Workloads of the mixed-vs-FP64 trajectory report: the two
+    failure-exercising 8x8x32 bars (Cockcroft-Latham and Johnson-Cook damage),
+    the 1.02M-particle Johnson-Cook bar as specified, and the GTN notched bar."""
+    from paper_1901_07374_gb300 import specimen as S
+    return {
+        "tensile_bar_cl_8x8x32_failure": lambda: S.failure_variant(S.tensile_bar_cl(steps=2000)),
+        "tensile_bar_jc_8x8x32_failure": lambda: S.failure_variant(S.tensile_bar_jc(nx=8, ny=8, nz=32, steps=2000)),
+        "tensile_bar_jc_40x40x640": lambda: S.tensile_bar_jc(),
+        "notched_bar_gtn": lambda: S.notched_bar_gtn(steps=2000),
+    }
+
+
+def trajectory_errors(a, b, sc: dict) -> dict:
+    """Max and RMS normwise relative error of every field of `a` (mixed)
+    against `b` (FP64), the symmetric difference of the failure sets and the
+    distribution of the failure-step differences of particles failed in both."""
+    import numpy as np
+    out = {}
+    fa, fb = a.get("FAIL_STEP"), b.get("FAIL_STEP")
+    live = (fa < 0) & (fb < 0)
+    for f in FIELDS:
+        x, y = a.get(f), b.get(f)
+        out[f] = {"max": float(np.max(np.abs(x - y)) / max(float(np.max(np.abs(y))), sc[f])),
+                  "rms": float(np.sqrt(np.mean((x - y) ** 2)) / max(float(np.sqrt(np.mean(y ** 2))), sc[f]))}
+        if not live.all() and live.any():   # the particles that have not failed in either path
+            xl, yl = x[live], y[live]
+            out[f]["max_live"] = float(np.max(np.abs(xl - yl)) / max(float(np.max(np.abs(yl))), sc[f]))
+    both = (fa >= 0) & (fb >= 0)
+    d = (fa[both] - fb[both]).astype(np.int64)
+    out["failed"] = {"fp64": int((fb >= 0).sum()), "mixed": int((fa >= 0).sum()),
+                     "symdiff": int(((fa >= 0) ^ (fb >= 0)).sum())}
+    out["fail_step_delta"] = ({"n": int(d.size), "nonzero": int((d != 0).sum()), "min": int(d.min()),
+                               "max": int(d.max()), "mean_abs": float(np.abs(d).mean())} if d.size else {"n": 0})
+    return out
+
+
+def run_accuracy(args):
+    """Mixed against the FP64 GPU path along whole trajectories, reported at
+    fixed step counts (not gated: the tests gate the FP64 path against the
+    oracle and the mixed path over short windows).  One JSON line per
+    workload."""
+    from paper_1901_07374_gb300 import tlsph
+    cases = accuracy_cases()
+    names = args.accuracy_cases.split(",") if args.accuracy_cases else list(cases)
+    for name in names:
+        w = cases[name]()
+        sc = field_scales(w)
+        a = tlsph.Simulation.from_workload(w, precision="mixed")
+        b = tlsph.Simulation.from_workload(w, precision="fp64")
+        N, nnz, _ = b.info()
+        rows, done, t0 = {}, 0, time.perf_counter()
+        for k in ACCURACY_CHECKPOINTS:
+            a.step(k - done)
+            b.step(k - done)
+            done = k
+            rows[str(k)] = trajectory_errors(a, b, sc)
+        print(json.dumps({"accuracy": name, "particles": N, "pairs": nnz, "checkpoints": rows,
+                          "seconds": time.perf_counter() - t0}), flush=True)
+        a.close()
+        b.close()
+
+
 def run_batched(args):
     """256 independent bars (log-uniform 2k..200k particles, JC constants
     +-20%) advanced together: one persistent launch per kernel kind and step
@@ -609,6 +676,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--workload", default="tensile_bar_jc_40x40x640")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--accuracy", action="store_true",
+                    help="report mixed vs FP64 along whole trajectories (steps 1, 10, 100, 500, 2000) and exit")
+    ap.add_argument("--accuracy-cases", default="", help="comma-separated subset of the accuracy workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
                     help="skip the all-core oracle figure (one replica per host core)")
@@ -638,6 +708,9 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.accuracy:
+        run_accuracy(args)
         return
     if args.workload.startswith("batched"):
         run_batched(args)

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <numeric>
 #include <vector>
 
 #include "tlsph_internal.cuh"
@@ -29,7 +30,7 @@ struct Layout {
     size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp, xf;
-    size_t perm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order + staged caller-order inputs
+    size_t perm, iperm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order, its inverse + staged caller-order inputs
     size_t overlay_end, ell;
     size_t total;
     int64_t max_cells;
@@ -138,6 +139,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.status = c.take(sizeof(uint32_t));
     L.diag = c.take(DIAG_BLOCKS * TLSPH_DIAG_COUNT * sizeof(double));
     L.perm = c.take(n * sizeof(int32_t));
+    L.iperm = c.take(n * sizeof(int32_t));
     L.mats = c.take(TLSPH_MAX_MATERIALS * sizeof(DevMat));
     if (mixed) {
         L.xo = c.take(n * 16);
@@ -146,7 +148,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
         L.ell_w = c.take(((n + 31) / 32) * sizeof(int32_t));
         L.linv32 = c.take(9 * n * sizeof(float));
         L.r1 = c.take(n * 16);
-        L.r2 = c.take(6 * n * 16);
+        L.r2 = c.take(6 * ((n + 31) / 32 * 32) * 16);   // tiles of 32 particles
         L.fsum = c.take(9 * n * sizeof(float));
         const size_t f = sizeof(float);
         L.Fh = c.take(9 * n * f); L.Fl = c.take(9 * n * f);
@@ -390,14 +392,25 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     if (!valid_config(cfg, why)) { g_create_error = why; return TLSPH_ERR_ARG; }
     if (N <= 0 || N > INT32_MAX) { g_create_error = "N must be in [1, 2^31)"; return TLSPH_ERR_ARG; }
     if (!X || !vol) { g_create_error = "X and vol are required"; return TLSPH_ERR_ARG; }
+    // one pass over the inputs: validation, bounding box, materials in use and
+    // the sum of the initial velocities (the bulk reference of the mixed path)
+    double lo3[3] = { X[0], X[1], X[2] }, hi3[3] = { X[0], X[1], X[2] }, vsum[3] = { 0.0, 0.0, 0.0 };
+    bool mat_used[TLSPH_MAX_MATERIALS] = {};
+    if (!mat_id) mat_used[0] = true;
     for (int64_t i = 0; i < N; ++i) {
         if (!(vol[i] > 0.0) || !isfinite(vol[i])) { g_create_error = "vol must be positive and finite"; return TLSPH_ERR_ARG; }
-        if (!isfinite(X[3 * i]) || !isfinite(X[3 * i + 1]) || !isfinite(X[3 * i + 2])) {
-            g_create_error = "X must be finite"; return TLSPH_ERR_ARG;
+        const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) { g_create_error = "X must be finite"; return TLSPH_ERR_ARG; }
+        lo3[0] = std::min(lo3[0], x); hi3[0] = std::max(hi3[0], x);
+        lo3[1] = std::min(lo3[1], y); hi3[1] = std::max(hi3[1], y);
+        lo3[2] = std::min(lo3[2], z); hi3[2] = std::max(hi3[2], z);
+        if (mat_id) {
+            if (mat_id[i] < 0 || mat_id[i] >= TLSPH_MAX_MATERIALS) {
+                g_create_error = "mat_id out of range"; return TLSPH_ERR_ARG;
+            }
+            mat_used[mat_id[i]] = true;
         }
-        if (mat_id && (mat_id[i] < 0 || mat_id[i] >= TLSPH_MAX_MATERIALS)) {
-            g_create_error = "mat_id out of range"; return TLSPH_ERR_ARG;
-        }
+        if (bc_vel) { vsum[0] += bc_vel[3 * i]; vsum[1] += bc_vel[3 * i + 1]; vsum[2] += bc_vel[3 * i + 2]; }
     }
     if (arena && ((uintptr_t)arena % ALIGN) != 0) { g_create_error = "arena must be 256-byte aligned"; return TLSPH_ERR_ARG; }
     if (arena && nnz_cap <= 0) { g_create_error = "nnz_cap is required with an arena"; return TLSPH_ERR_ARG; }
@@ -434,16 +447,9 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     bind_state(ctx, base, L);
     DevState &s = ctx->s;
 
-    // ---- copy inputs
+    // ---- copy inputs (straight from the caller's arrays; absent ones are zero)
     const size_t n = (size_t)N;
-    std::vector<int32_t> mat_h(n, 0);
-    std::vector<uint8_t> bcm_h(n, 0);
-    std::vector<double> bcv_h(3 * n, 0.0), f0_h(n, 0.0);
-    if (mat_id) memcpy(mat_h.data(), mat_id, n * sizeof(int32_t));
-    if (bc_mask) memcpy(bcm_h.data(), bc_mask, n);
-    if (bc_vel) memcpy(bcv_h.data(), bc_vel, 3 * n * sizeof(double));
-    if (f0) memcpy(f0_h.data(), f0, n * sizeof(double));
-    for (size_t i = 0; i < n; ++i) ctx->mat_used[mat_h[i]] = true;
+    for (int k = 0; k < TLSPH_MAX_MATERIALS; ++k) ctx->mat_used[k] = mat_used[k];
     cudaError_t e = cudaSuccess;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e)); } } while (0)
     double *stX = at<double>(base, L.stX), *stvol = at<double>(base, L.stvol), *stbcv = at<double>(base, L.stbcv);
@@ -452,17 +458,21 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     uint8_t *stbcm = at<uint8_t>(base, L.stbcm);
     CK(cudaMemcpyAsync(stX, X, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(stvol, vol, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(stmat, mat_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(stbcm, bcm_h.data(), n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(stbcv, bcv_h.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(stf0, f0_h.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (mat_id) CK(cudaMemcpyAsync(stmat, mat_id, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(stmat, 0, n * sizeof(int32_t), st));
+    if (bc_mask) CK(cudaMemcpyAsync(stbcm, bc_mask, n, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(stbcm, 0, n, st));
+    if (bc_vel) CK(cudaMemcpyAsync(stbcv, bc_vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(stbcv, 0, 3 * n * sizeof(double), st));
+    if (f0) CK(cudaMemcpyAsync(stf0, f0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(stf0, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
     CK(cudaMemsetAsync((void *)s.mass, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync((void *)s.inv_mass, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync((void *)s.sqrtE, 0, n * sizeof(double), st));
 
     // ---- neighbour CSR
-    const CellGrid grid = make_cell_grid(X, N, cfg->rc);
+    const CellGrid grid = cell_grid_from_bounds(lo3, hi3, N, cfg->rc);
     if (grid.ncells > L.max_cells) return bail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
     Scratch sc{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
                 at<int64_t>(base, L.scan_tmp), L.scan_elems, at<float4>(base, L.xf) };
@@ -480,9 +490,14 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     CK(launch_gather_inputs(ctx->perm_dev, N, stX, stvol, stmat, stbcm, stbcv, stf0, s, st));
     ctx->perm.resize(n);
     ctx->inv.resize(n);
-    CK(cudaMemcpyAsync(ctx->perm.data(), ctx->perm_dev, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    for (size_t k = 0; k < n; ++k) ctx->inv[ctx->perm[k]] = (int32_t)k;
+    if (ctx->reordered) {
+        CK(cudaMemcpyAsync(ctx->perm.data(), ctx->perm_dev, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t k = 0; k < n; ++k) ctx->inv[ctx->perm[k]] = (int32_t)k;
+    } else {   // caller order: the identity
+        std::iota(ctx->perm.begin(), ctx->perm.end(), 0);
+        std::iota(ctx->inv.begin(), ctx->inv.end(), 0);
+    }
 
     const double rc2 = cfg->rc * cfg->rc;
     int64_t *row_ptr = const_cast<int64_t *>(s.row_ptr);
@@ -516,12 +531,18 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         ctx->nnz_cap = nnz;
     }
     ctx->nnz = nnz;
+    // inverse order on the device (caller index -> internal index) for the caller-order reads
+    ctx->inv_dev = nullptr;
+    if (ctx->reordered) {
+        ctx->inv_dev = at<int32_t>(base, L.iperm);
+        CK(cudaMemcpyAsync(ctx->inv_dev, ctx->inv.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
     CK(build_neighbors_fill(s, grid, sc, rc2, row_ptr, const_cast<int32_t *>(s.col), st));
 
     // ---- correction matrices
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
     // S0 (mixed only) goes to the force array, which init_state clears afterwards
-    CK(shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), mixed ? s.force : nullptr, s.status, st));
+    CK(shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), mixed ? s.force : nullptr, s.status, mixed, st));
     uint32_t n_sing = 0;
     CK(cudaMemcpyAsync(&n_sing, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -529,19 +550,9 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
     if (mixed) {
         // bulk reference velocity of the FP32 velocity mirror: the mean initial velocity
-        double vr[3] = { 0, 0, 0 };
-        for (size_t i = 0; i < n; ++i)
-            for (int k = 0; k < 3; ++k) vr[k] += bcv_h[3 * i + k];
-        for (int k = 0; k < 3; ++k) s.vref[k] = vr[k] / (double)n;
+        for (int k = 0; k < 3; ++k) s.vref[k] = vsum[k] / (double)n;
         // fixed-point positions about the bounding-box centre, |coordinate| < 2^31 - 2^10 units
         FixPack pk{};
-        double lo3[3], hi3[3];
-        for (int k = 0; k < 3; ++k) { lo3[k] = INFINITY; hi3[k] = -INFINITY; }
-        for (size_t i = 0; i < n; ++i)
-            for (int k = 0; k < 3; ++k) {
-                lo3[k] = std::min(lo3[k], X[3 * i + k]);
-                hi3[k] = std::max(hi3[k], X[3 * i + k]);
-            }
         double ext = 0.0;
         for (int k = 0; k < 3; ++k) {
             pk.center[k] = 0.5 * (lo3[k] + hi3[k]);
@@ -810,11 +821,26 @@ int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_
     const int comps = (int)(f.count / (size_t)N);
     const int scomps = f.sym ? 6 : comps;
     const size_t sbytes = (size_t)N * scomps * f.elem;
-    if (dst_on_device) {
-        if (f.sym || ctx->reordered)
-            e = launch_permute(f.ptr, dst, ctx->perm_dev, N, scomps, (int)f.elem, true, f.sym, st);
+    // a page-locked host destination is mapped into the device's address space:
+    // the device writes the caller-order array there itself
+    void *mapped = nullptr;
+    if (!dst_on_device) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, dst) == cudaSuccess) {
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer) mapped = pa.devicePointer;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    const bool plain = !f.sym && !ctx->reordered;
+    if (dst_on_device || mapped) {
+        void *d = dst_on_device ? dst : mapped;
+        if (plain)
+            e = cudaMemcpyAsync(d, f.ptr, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
         else
-            e = cudaMemcpyAsync(dst, f.ptr, bytes, cudaMemcpyDeviceToDevice, st);
+            e = launch_to_caller(f.ptr, d, ctx->inv_dev, N, comps, scomps, (int)f.elem, f.sym, st);
+    } else if (plain) {
+        e = cudaMemcpyAsync(dst, f.ptr, bytes, cudaMemcpyDeviceToHost, st);
     } else {
         std::vector<unsigned char> tmp(sbytes);
         e = cudaMemcpyAsync(tmp.data(), f.ptr, sbytes, cudaMemcpyDeviceToHost, st);

@@ -501,7 +501,7 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
                                             float Vf, float u0, float u1, float u2, uint32_t st)
 {
     const int64_t N = c.N;
-    float4 *__restrict__ r2 = s.r2;
+    float4 *__restrict__ r2 = s.r2 + r2_tile(i);
     float A[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
     if (failed) {
         s.fail[i] = (int32_t)(c.step_index + 1);
@@ -526,12 +526,12 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
     }
     const float omd = 1.0f - (float)Dnew;
     const float *G = k.G;
-    r2[i] = make_float4(A[0], A[1], A[2], A[3]);
-    r2[N + i] = make_float4(A[4], A[5], A[6], A[7]);
-    r2[2 * N + i] = make_float4(A[8], Vf * (float)Dnew, Vf, u0);
-    r2[3 * N + i] = make_float4(u1, u2, G[0], G[1]);
-    r2[4 * N + i] = make_float4(G[2], G[3], G[4], G[5]);
-    r2[5 * N + i] = make_float4(G[6], G[7], G[8], (float)s.sqrtE[i] * Vf * omd);
+    r2[0] = make_float4(A[0], A[1], A[2], A[3]);
+    r2[R2_STRIDE] = make_float4(A[4], A[5], A[6], A[7]);
+    r2[2 * R2_STRIDE] = make_float4(A[8], Vf * (float)Dnew, Vf, u0);
+    r2[3 * R2_STRIDE] = make_float4(u1, u2, G[0], G[1]);
+    r2[4 * R2_STRIDE] = make_float4(G[2], G[3], G[4], G[5]);
+    r2[5 * R2_STRIDE] = make_float4(G[6], G[7], G[8], (float)s.sqrtE[i] * Vf * omd);
     if (st) atomicOr(s.status, st);
 }
 
@@ -556,14 +556,14 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     float u0, u1, u2;
     load_u1(s, c, i, u0, u1, u2);
     if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
-        float4 *__restrict__ r2 = s.r2;
+        float4 *__restrict__ r2 = s.r2 + r2_tile(i);
         Dnext[i] = Dn[i];
-        r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2[N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2[2 * N + i] = make_float4(0.f, Vf, Vf, u0);     // V D with D = 1
-        r2[3 * N + i] = make_float4(u1, u2, (Fh[0] - 1.0f) + Fl[0], Fh[1] + Fl[1]);
-        r2[4 * N + i] = make_float4(Fh[2] + Fl[2], Fh[3] + Fl[3], (Fh[4] - 1.0f) + Fl[4], Fh[5] + Fl[5]);
-        r2[5 * N + i] = make_float4(Fh[6] + Fl[6], Fh[7] + Fl[7], (Fh[8] - 1.0f) + Fl[8], 0.f);
+        r2[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2[R2_STRIDE] = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2[2 * R2_STRIDE] = make_float4(0.f, Vf, Vf, u0);     // V D with D = 1
+        r2[3 * R2_STRIDE] = make_float4(u1, u2, (Fh[0] - 1.0f) + Fl[0], Fh[1] + Fl[1]);
+        r2[4 * R2_STRIDE] = make_float4(Fh[2] + Fl[2], Fh[3] + Fl[3], (Fh[4] - 1.0f) + Fl[4], Fh[5] + Fl[5]);
+        r2[5 * R2_STRIDE] = make_float4(Fh[6] + Fl[6], Fh[7] + Fl[7], (Fh[8] - 1.0f) + Fl[8], 0.f);
         return;
     }
     float Li[9];
@@ -829,7 +829,8 @@ template <bool HG>
 __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
     const int64_t N = c.N;
-    const float4 a0 = s.r2[i], a1 = s.r2[N + i], a2 = s.r2[2 * N + i];
+    const float4 *ri = s.r2 + r2_tile(i);
+    const float4 a0 = ri[0], a1 = ri[R2_STRIDE], a2 = ri[2 * R2_STRIDE];
     const float Ai[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
     const float Vf = a2.z;                           // V_i
     const float Df = (float)s.D[c.dcur ^ 1][i];      // D_i^{n+1}
@@ -845,7 +846,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
     if (HG) {
         // the pair sums are in fixed-point units (X_ij, u_ij and x_ij scaled by 1/unit): hg_w folds 1/unit in;
         // r2 record 5 .w holds sqrt(E_i) V_i (1 - D_i)
-        const float hc = c.hg_w * s.r2[5 * N + i].w;
+        const float hc = c.hg_w * ri[5 * R2_STRIDE].w;
         f[0] += hc * keep[6];
         f[1] += hc * keep[7];
         f[2] += hc * keep[8];
@@ -898,17 +899,17 @@ struct Row2 {   // row i's own pass-2 record
 template <bool HG>
 __device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, int64_t i)
 {
-    const int64_t N = c.N;
+    const float4 *ri = s.r2 + r2_tile(i);
     Row2 w;
     w.o = s.xo[i];
-    w.a0 = s.r2[i];
-    w.a1 = s.r2[N + i];
-    w.a2 = s.r2[2 * N + i];
+    w.a0 = ri[0];
+    w.a1 = ri[R2_STRIDE];
+    w.a2 = ri[2 * R2_STRIDE];
     w.a3 = w.a4 = w.a5 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (HG) {
-        w.a3 = s.r2[3 * N + i];
-        w.a4 = s.r2[4 * N + i];
-        w.a5 = s.r2[5 * N + i];
+        w.a3 = ri[3 * R2_STRIDE];
+        w.a4 = ri[4 * R2_STRIDE];
+        w.a5 = ri[5 * R2_STRIDE];
     }
     return w;
 }
@@ -917,9 +918,9 @@ template <bool HG>
 __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, const Row2 &w, int j, float wmask,
                                       float *acc)
 {
-    const int64_t N = c.N;
     const int4 oj = s.xo[j];
-    const float4 b0 = s.r2[j], b1 = s.r2[N + j], b2 = s.r2[2 * N + j];
+    const float4 *rj = s.r2 + r2_tile(j);
+    const float4 b0 = rj[0], b1 = rj[R2_STRIDE], b2 = rj[2 * R2_STRIDE];
     const float3 d = xdiff(oj, w.o);
     const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
     const float rinv = rsqrtf(r2v);
@@ -934,7 +935,7 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
     const float t2 = (b1.z - w.a1.z) * d.x + (b1.w - w.a1.w) * d.y + (b2.x - w.a2.x) * d.z;
     acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
     if (HG) {
-        const float4 b3 = s.r2[3 * N + j], b4 = s.r2[4 * N + j], b5 = s.r2[5 * N + j];
+        const float4 b3 = rj[3 * R2_STRIDE], b4 = rj[4 * R2_STRIDE], b5 = rj[5 * R2_STRIDE];
         // u_ij, x_ij = X_ij + u_ij, e = ((F_i - I) + (F_j - I)) X_ij - 2 u_ij
         const float ux = b2.w - w.a2.w, uy = b3.x - w.a3.x, uz = b3.y - w.a3.y;
         const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
@@ -1107,7 +1108,8 @@ __global__ void k_mixed_export_A(DevState s)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    const float4 a0 = s.r2[i], a1 = s.r2[s.N + i], a2 = s.r2[2 * s.N + i];
+    const float4 *ri = s.r2 + r2_tile(i);
+    const float4 a0 = ri[0], a1 = ri[R2_STRIDE], a2 = ri[2 * R2_STRIDE];
     const float A[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.A[9 * i + k] = (double)A[k];

@@ -106,30 +106,13 @@ cudaError_t scan_exclusive_i64(int64_t *data, int64_t n, int64_t *tmp, cudaStrea
 // ---------------------------------------------------------------- cell grid
 CellGrid make_cell_grid(const double *X, int64_t N, double rc)
 {
-    CellGrid g{};
     double lo[3] = { X[0], X[1], X[2] }, hi[3] = { X[0], X[1], X[2] };
     for (int64_t i = 1; i < N; ++i)
         for (int k = 0; k < 3; ++k) {
             lo[k] = std::min(lo[k], X[3 * i + k]);
             hi[k] = std::max(hi[k], X[3 * i + k]);
         }
-    // a little wider than rc so rounding in the cell coordinate can never put
-    // two particles closer than rc two cells apart
-    double cs = rc * (1.0 + 1e-6);
-    const double cap = 2.0 * (double)N + 4096.0;
-    for (;;) {
-        double cells = 1.0;
-        for (int k = 0; k < 3; ++k) cells *= floor((hi[k] - lo[k]) / cs) + 1.0;
-        if (cells <= cap) break;
-        cs *= 1.25;
-    }
-    for (int k = 0; k < 3; ++k) {
-        g.xmin[k] = lo[k];
-        g.nc[k] = (int32_t)(floor((hi[k] - lo[k]) / cs) + 1.0);
-    }
-    g.cs = cs;
-    g.ncells = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
-    return g;
+    return cell_grid_from_bounds(lo, hi, N, rc);
 }
 
 __device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc)
@@ -506,12 +489,64 @@ __global__ void k_shape(const double *X, const double *vol, const int64_t *row_p
     }
 }
 
+// The same sums for a mixed-precision context, whose pair terms are FP32 in
+// every step: X_ij is the FP64 difference rounded once to FP32, the kernel
+// weight is formed in FP32, each lane sums its few pairs in FP32 and the lane
+// sums meet in FP64; the 3x3 inversion stays FP64.  L and S0 come out with
+// FP32 rounding of the pair terms (the mixed path keeps L^{-1} and S0 as FP32
+// copies), at about a tenth of the FP64 cost.
+__global__ void k_shape_f32(const double *X, const double *vol, const int64_t *row_ptr, const int32_t *col,
+                            int64_t N, float inv_h, double dw_norm, double *Linv, double *S0, uint32_t *n_singular)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
+    float lf[6] = { 0, 0, 0, 0, 0, 0 };
+    float gf[3] = { 0, 0, 0 };
+    for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
+        const int64_t j = col[p];
+        const float dx = (float)(X[3 * j] - xi), dy = (float)(X[3 * j + 1] - yi), dz = (float)(X[3 * j + 2] - zi);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float rinv = rsqrtf(r2);
+        const float c0 = (float)vol[j] * spline_dw(r2 * rinv * inv_h) * rinv;
+        gf[0] += c0 * dx; gf[1] += c0 * dy; gf[2] += c0 * dz;
+        lf[0] += c0 * dx * dx; lf[1] += c0 * dy * dy; lf[2] += c0 * dz * dz;
+        lf[3] += c0 * dx * dy; lf[4] += c0 * dy * dz; lf[5] += c0 * dz * dx;
+    }
+    double l[6], g[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) l[k] = dw_norm * warp_allsum((double)lf[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = warp_allsum((double)gf[k]);
+    if (lane == 0 && S0) {
+        S0[3 * i] = g[0]; S0[3 * i + 1] = g[1]; S0[3 * i + 2] = g[2];
+    }
+    if (lane == 0) {
+        double L[9], c[9];
+        sym_to_full(l, L);
+        cof3(L, c);
+        const double det = L[0] * c[0] + L[1] * c[1] + L[2] * c[2];
+        double fn2 = 0.0;
+        for (int k = 0; k < 9; ++k) fn2 += L[k] * L[k];
+        const double fn = sqrt(fn2);
+        const bool ok = isfinite(det) && fabs(det) > 1e-12 * fn * fn * fn;
+        for (int k = 0; k < 3; ++k)
+            for (int m = 0; m < 3; ++m) Linv[9 * i + 3 * k + m] = ok ? c[3 * m + k] / det : 0.0;
+        if (!ok) atomicAdd(n_singular, 1u);
+    }
+}
+
 cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
-                         cudaStream_t st)
+                         bool fp32_terms, cudaStream_t st)
 {
     const double dw_norm = 1.0 / (M_PI * h * h * h * h);
-    k_shape<<<blocks_for(s.N * 32, 256), 256, 0, st>>>(s.X, s.vol, s.row_ptr, s.col, s.N, 1.0 / h, dw_norm, Linv,
-                                                       S0, n_singular);
+    if (fp32_terms)
+        k_shape_f32<<<blocks_for(s.N * 32, 256), 256, 0, st>>>(s.X, s.vol, s.row_ptr, s.col, s.N, (float)(1.0 / h),
+                                                               dw_norm, Linv, S0, n_singular);
+    else
+        k_shape<<<blocks_for(s.N * 32, 256), 256, 0, st>>>(s.X, s.vol, s.row_ptr, s.col, s.N, 1.0 / h, dw_norm, Linv,
+                                                           S0, n_singular);
     return cudaGetLastError();
 }
 
@@ -549,8 +584,10 @@ __global__ void k_bounds(const double *X, int64_t N, double *out6)
         for (int k = 0; k < 3; ++k) { out6[k] = lo[k][0]; out6[3 + k] = hi[k][0]; }
 }
 
-// the cell grid of make_cell_grid, from a bounding box instead of host positions
-static CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc)
+// the cell grid over a bounding box: cells a little wider than rc so rounding
+// in the cell coordinate can never put two particles closer than rc two cells
+// apart, widened until there are at most 2N + 4096 cells
+CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc)
 {
     CellGrid g{};
     double cs = rc * (1.0 + 1e-6);

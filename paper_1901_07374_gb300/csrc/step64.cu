@@ -21,6 +21,8 @@
 // rounding.
 #include <math.h>
 
+#include <algorithm>
+
 #include "tlsph_device.cuh"
 #include "tlsph_internal.cuh"
 
@@ -461,6 +463,39 @@ __global__ void k_permute_sym(const double *src, double *dst, const int32_t *per
 
 static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+template <class T>
+__global__ void k_to_caller(const T *__restrict__ src, T *__restrict__ dst, const int32_t *__restrict__ inv,
+                            int64_t N, int comps, int scomps, bool sym)
+{
+    // row-major 3x3 index -> stored symmetric component (xx, yy, zz, xy, yz, zx)
+    const int smap[9] = { 0, 3, 5, 3, 1, 4, 5, 4, 2 };
+    const int64_t total = N * comps;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / comps;
+        const int c = (int)(e - i * comps);
+        const int64_t k = inv ? (int64_t)inv[i] : i;
+        dst[e] = src[k * scomps + (sym ? smap[c] : c)];
+    }
+}
+
+cudaError_t launch_to_caller(const void *src, void *dst, const int32_t *inv, int64_t N, int comps, int scomps,
+                             int elem, bool sym, cudaStream_t st)
+{
+    const int64_t total = N * comps;
+    const unsigned g = (unsigned)std::min<int64_t>(nblk(total, 256), 152 * 16);
+    if (total <= 0) return cudaSuccess;
+    if (elem == 8)
+        k_to_caller<double><<<g, 256, 0, st>>>(static_cast<const double *>(src), static_cast<double *>(dst), inv, N,
+                                               comps, scomps, sym);
+    else if (elem == 4)
+        k_to_caller<int32_t><<<g, 256, 0, st>>>(static_cast<const int32_t *>(src), static_cast<int32_t *>(dst), inv,
+                                                N, comps, scomps, false);
+    else
+        k_to_caller<uint8_t><<<g, 256, 0, st>>>(static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst), inv,
+                                                N, comps, scomps, false);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_inputs(const int32_t *perm, int64_t N, const double *X, const double *vol,
                                  const int32_t *mat, const uint8_t *bcm, const double *bcv, const double *f0,
                                  const DevState &s, cudaStream_t st)
@@ -503,7 +538,7 @@ cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool
 // Block b reduces particles [b N / B, (b + 1) N / B) in a fixed order (thread
 // stride, then a shared-memory tree); a second one-block kernel reduces the
 // block partials in block order: the same N gives the same bits every time.
-constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_THREADS = 512;
 
 __device__ __forceinline__ void diag_combine(double *a, const double *b)
 {
@@ -513,14 +548,47 @@ __device__ __forceinline__ void diag_combine(double *a, const double *b)
     for (int k = 8; k < TLSPH_DIAG_COUNT; ++k) a[k] = fmax(a[k], b[k]);
 }
 
+// a[] of lane 0 becomes the combination over the warp (fixed butterfly order)
+__device__ __forceinline__ void diag_warp(double *a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double b[TLSPH_DIAG_COUNT];
+#pragma unroll
+        for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) b[k] = __shfl_down_sync(0xffffffffu, a[k], o);
+        diag_combine(a, b);
+    }
+}
+
+// combination over the block into sh[0][.]; every thread passes its a[]
+__device__ __forceinline__ void diag_block(double *a, double (*sh)[TLSPH_DIAG_COUNT])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    diag_warp(a);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) sh[wid][k] = a[k];
+    __syncthreads();
+    if (wid == 0) {
+        double b[TLSPH_DIAG_COUNT];
+#pragma unroll
+        for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) b[k] = lane < nw ? sh[lane][k] : (k < 8 ? 0.0 : -INFINITY);
+        diag_warp(b);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) sh[0][k] = b[k];
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag_blocks(DevState s, int dcur, double *partials)
 {
-    __shared__ double sh[DIAG_THREADS][TLSPH_DIAG_COUNT];
+    __shared__ double sh[32][TLSPH_DIAG_COUNT];
     const int64_t N = s.N;
     const int64_t lo = (int64_t)blockIdx.x * N / gridDim.x, hi = (int64_t)(blockIdx.x + 1) * N / gridDim.x;
     double a[TLSPH_DIAG_COUNT];
 #pragma unroll
-    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = 0.0;
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = k < 8 ? 0.0 : -INFINITY;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double m = s.mass[i];
         const double v0 = s.v[3 * i], v1 = s.v[3 * i + 1], v2 = s.v[3 * i + 2];
@@ -529,30 +597,30 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_blocks(DevState s, int dc
                                        s.D[dcur][i], s.ep[i] };
         diag_combine(a, b);
     }
-#pragma unroll
-    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) sh[threadIdx.x][k] = a[k];
-    __syncthreads();
-    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) diag_combine(sh[threadIdx.x], sh[threadIdx.x + w]);
-        __syncthreads();
-    }
+    diag_block(a, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) partials[(int64_t)blockIdx.x * TLSPH_DIAG_COUNT + k] = sh[0][k];
 }
 
+// one block over the per-block partials (nblocks <= blockDim.x)
 __global__ void k_diag_final(double *partials, int nblocks)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sh[32][TLSPH_DIAG_COUNT];
     double a[TLSPH_DIAG_COUNT];
-    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = partials[k];
-    for (int b = 1; b < nblocks; ++b) diag_combine(a, partials + (int64_t)b * TLSPH_DIAG_COUNT);
-    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) partials[k] = a[k];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k)
+        a[k] = t < nblocks ? partials[(int64_t)t * TLSPH_DIAG_COUNT + k] : (k < 8 ? 0.0 : -INFINITY);
+    diag_block(a, sh);
+    if (t == 0)
+        for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) partials[k] = sh[0][k];
 }
 
 cudaError_t launch_diagnostics(const DevState &s, int dcur, double *partials, cudaStream_t st)
 {
+    static_assert(DIAG_BLOCKS <= 256, "the final reduction takes one block of 256 threads");
     k_diag_blocks<<<DIAG_BLOCKS, DIAG_THREADS, 0, st>>>(s, dcur, partials);
-    k_diag_final<<<1, 32, 0, st>>>(partials, DIAG_BLOCKS);
+    k_diag_final<<<1, 256, 0, st>>>(partials, DIAG_BLOCKS);
     return cudaGetLastError();
 }
 

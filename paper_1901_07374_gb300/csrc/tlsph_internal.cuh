@@ -73,7 +73,7 @@ struct DevState {
     float4 *s0;             // N   {sum_j V_j W'(r)/r (X_j - X_i), 0}  (static, FP64-accurate)
     float *linv32;          // N*9 L^{-1} rounded
     float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
-    float4 *r2;             // 6 x N pass-2 gather record (SoA of float4, see mixed.cu)
+    float4 *r2;             // pass-2 gather record: 6 float4 per particle in tiles of 32 particles (r2_tile)
     float *fsum;            // 9 x N pass-1 pair sums (split launch plans)
     // mixed path: F and the stress deviator as compensated FP32 pairs (value =
     // hi + lo, SoA by component: component k of particle i at k N + i); the
@@ -89,6 +89,13 @@ struct DevState {
     double vref[3];         // bulk reference velocity of the r1 mirror
     FixPack pack;
 };
+
+// The pass-2 record is tiled by 32 particles: component k (0..5) of particle j
+// sits at r2[r2_tile(j) + 32 k].  A warp reading 32 consecutive particles
+// still reads 512 contiguous bytes per component, and one address reaches all
+// six components of a neighbour (the others are constant offsets from it).
+__host__ __device__ __forceinline__ int64_t r2_tile(int64_t j) { return (j >> 5) * (6 * 32) + (j & 31); }
+constexpr int R2_STRIDE = 32;
 
 struct Scratch {            // neighbour-build scratch (set-up only)
     int64_t *cell_start;    // ncells + 1
@@ -136,6 +143,7 @@ struct tlsph_ctx {
     double *diag = nullptr;     // DIAG_BLOCKS x TLSPH_DIAG_COUNT partials; the first row holds the result
     void *ell_mem = nullptr;    // library-owned sliced-ELL columns
     int32_t *perm_dev = nullptr;
+    int32_t *inv_dev = nullptr;   // device copy of inv when reordered, else null (identity)
     std::vector<int32_t> perm, inv;
 };
 
@@ -151,6 +159,7 @@ struct CellGrid {
     int64_t ncells;
 };
 CellGrid make_cell_grid(const double *X_host, int64_t N, double rc);
+CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc);
 cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
                                   int64_t *row_ptr, cudaStream_t st);
 cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
@@ -160,8 +169,9 @@ cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scr
 // keep = identity
 cudaError_t build_order(const double *X_user, int64_t N, const CellGrid &g, const Scratch &sc, bool keep,
                         int32_t *perm, cudaStream_t st);
+// fp32_terms: FP32 pair terms summed in FP64 across lanes (mixed contexts)
 cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
-                         cudaStream_t st);
+                         bool fp32_terms, cudaStream_t st);
 
 // step64.cu
 // deterministic reductions of the diagnostics (tlsph_diagnostics) over a
@@ -195,6 +205,12 @@ cudaError_t launch_gather_inputs(const int32_t *perm, int64_t N, const double *X
 // per-particle field transfer between internal and caller order on the device:
 // out: dst[perm[k]] = src[k]; in: dst[k] = src[perm[k]] (comps per particle,
 // elem bytes 1/4/8; sym = 6 stored <-> 9 exchanged)
+// caller-order copy of a per-particle field: dst element e (caller particle
+// i = e / comps) from internal particle inv[i] (inv null: identity); sym
+// expands the 6 stored components of a symmetric tensor to 9; coalesced
+// writes, so dst may be device memory or mapped page-locked host memory
+cudaError_t launch_to_caller(const void *src, void *dst, const int32_t *inv, int64_t N, int comps, int scomps,
+                             int elem, bool sym, cudaStream_t st);
 cudaError_t launch_permute(const void *src, void *dst, const int32_t *perm, int64_t N, int comps, int elem,
                            bool out, bool sym, cudaStream_t st);
 
