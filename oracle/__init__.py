@@ -58,7 +58,7 @@ class Material(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("rc", ctypes.c_double), ("dt", ctypes.c_double),
-                ("hg_alpha", ctypes.c_double), ("wall", ctypes.c_int32)]
+                ("hg_alpha", ctypes.c_double), ("wall", ctypes.c_int32), ("grip_ramp", ctypes.c_double)]
 
 
 _P = ctypes.POINTER
@@ -127,6 +127,8 @@ def lib():
                 getattr(L, name).argtypes = [_P(System), _P(Config)]
             L.orc_init_state.restype = None
             L.orc_init_state.argtypes = [_P(System)]
+            L.orc_apply_grip_ramp.restype = None
+            L.orc_apply_grip_ramp.argtypes = [_P(System), _P(Config)]
             L.orc_mat_det.restype = ctypes.c_double
             L.orc_mat_det.argtypes = [vp]
             _lib = L
@@ -280,14 +282,16 @@ class Simulation:
     matrices computed on construction (Sec. 2.2: both fixed for the run)."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
-                 neighbors_csr=None, wall=False):
+                 neighbors_csr=None, wall=False, grip_ramp=0.0):
         self.N = N = int(np.asarray(X).shape[0])
         self.X = np.ascontiguousarray(X, np.float64).reshape(N, 3).copy()
         self.vol = np.ascontiguousarray(vol, np.float64).copy()
         self.mat_id = np.ascontiguousarray(mat_id, np.int32).copy()
         self.bc_mask = np.ascontiguousarray(bc_mask, np.uint8).copy()
         self.bc_vel = np.ascontiguousarray(bc_vel, np.float64).reshape(N, 3).copy()
-        self.cfg = Config(float(h), float(rc), float(dt), float(hg_alpha), 1 if wall else 0)
+        if not (grip_ramp >= 0.0 and np.isfinite(grip_ramp)):
+            raise ValueError("grip_ramp must be finite and >= 0")
+        self.cfg = Config(float(h), float(rc), float(dt), float(hg_alpha), 1 if wall else 0, float(grip_ramp))
         mats = [make_material(m) for m in materials]
         self._mats = (Material * len(mats))(*mats)
         if neighbors_csr is None:
@@ -317,11 +321,14 @@ class Simulation:
         s.Fdot = self._Fdot.ctypes.data_as(_d)
         self.sys = s
         lib().orc_init_state(ctypes.byref(self.sys))
+        if grip_ramp > 0.0:
+            lib().orc_apply_grip_ramp(ctypes.byref(self.sys), ctypes.byref(self.cfg))
 
     @classmethod
     def from_workload(cls, w, **kw):
         sp = w.specimen
         kw.setdefault("wall", getattr(w, "wall", False))
+        kw.setdefault("grip_ramp", getattr(w, "grip_ramp", 0.0))
         return cls(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, w.materials,
                    w.h, w.rc, w.dt, w.hg_alpha, **kw)
 

@@ -35,6 +35,7 @@
  *   GTN yield, f*, D = q1 f*                       Sec. 5.4, Eqs. (yield_GTN), (void_fraction_function), (yield_GTN_2)
  *   GTN nucleation, growth, omega                  Sec. 5.4, Eqs. (GTN_damage_nucleation), (GTN_damage_growth), (omega)
  *   GTN return with two Newton solves              Sec. 5.4, Algorithm 2 and the derivation after it
+ *   grip velocity ramp v_max (1 - e^{-t})          Sec. 6 (specimens and loading)
  *
  * Where the paper is silent or garbled the oracle takes the readings listed
  * in the design notes (kernel form, integrator, frame, EOS sign, lagged rate,
@@ -64,6 +65,7 @@ typedef struct {
 typedef struct {
     double h, rc, dt, hg_alpha;
     int32_t wall;             /* 1: rigid frictionless wall on the plane z = 0 */
+    double grip_ramp;         /* tau > 0: prescribed velocities ramp up as 1 - exp(-t / tau); 0: constant */
 } orc_config;
 
 /* status bits */
@@ -810,12 +812,34 @@ static double particle_mass(const orc_system *s, int64_t i)
     return s->mats[s->mat_id[i]].rho0 * s->vol[i];
 }
 
-/* velocity boundary conditions: prescribed particles move with their
- * prescribed velocity; fully damaged particles are held at rest (Sec. 3.1) */
-static void apply_bc(const orc_system *s, int64_t i, double *vi)
+/* Sec. 6 drives the grips with v_max (1 - e^{-t}) (v_max in mm/ms, so t in
+ * ms).  Reading: the prescribed velocity v_bc is scaled by
+ * 1 - exp(-t / tau) = -expm1(-t / tau), t the time at which the velocity
+ * holds (t_n + dt/2 for the half-step velocity, t_{n+1} for the full step);
+ * tau = 0 keeps v_bc constant. */
+static double grip_factor(const orc_config *c, double t)
+{
+    return c->grip_ramp > 0.0 ? -expm1(-t / c->grip_ramp) : 1.0;
+}
+
+/* velocity boundary conditions at time t: prescribed particles move with
+ * their (ramped) prescribed velocity; fully damaged particles are held at
+ * rest (Sec. 3.1) */
+static void apply_bc(const orc_system *s, const orc_config *c, int64_t i, double t, double *vi)
 {
     if (s->fail_step[i] >= 0) { vi[0] = vi[1] = vi[2] = 0.0; return; }
-    if (s->bc_mask[i]) for (int k = 0; k < 3; ++k) vi[k] = s->bc_vel[3 * i + k];
+    if (s->bc_mask[i]) {
+        const double r = grip_factor(c, t);
+        for (int k = 0; k < 3; ++k) vi[k] = s->bc_vel[3 * i + k] * r;
+    }
+}
+
+/* the velocities of the prescribed particles at the current time (step * dt),
+ * e.g. zero at t = 0 under a ramp; called when the ramp is switched on */
+void orc_apply_grip_ramp(orc_system *s, const orc_config *c)
+{
+    const double t = (double)s->step * c->dt;
+    for (int64_t i = 0; i < s->N; ++i) apply_bc(s, c, i, t, s->v + 3 * i);
 }
 
 /* One velocity-Verlet step (Reading: the paper does not state its
@@ -837,11 +861,12 @@ static void apply_bc(const orc_system *s, int64_t i, double *vi)
 void orc_step_predict(orc_system *s, const orc_config *c)
 {
     int64_t N = s->N;
+    const double t_half = ((double)s->step + 0.5) * c->dt;
     for (int64_t i = 0; i < N; ++i) {
         double m = particle_mass(s, i);
         for (int k = 0; k < 3; ++k)
             s->vh[3 * i + k] = s->v[3 * i + k] + 0.5 * c->dt * s->force[3 * i + k] / m;
-        apply_bc(s, i, s->vh + 3 * i);
+        apply_bc(s, c, i, t_half, s->vh + 3 * i);
     }
     for (int64_t i = 0; i < 3 * N; ++i) s->u[i] += c->dt * s->vh[i];
     /* Reading (rigid wall; the paper has no contact): a kinematic plane
@@ -866,11 +891,12 @@ void orc_step_pass2(orc_system *s, const orc_config *c)
 {
     int64_t N = s->N;
     orc_forces(s, c);
+    const double t_full = ((double)s->step + 1.0) * c->dt;
     for (int64_t i = 0; i < N; ++i) {
         double m = particle_mass(s, i);
         for (int k = 0; k < 3; ++k)
             s->v[3 * i + k] = s->vh[3 * i + k] + 0.5 * c->dt * s->force[3 * i + k] / m;
-        apply_bc(s, i, s->v + 3 * i);
+        apply_bc(s, c, i, t_full, s->v + 3 * i);
     }
     s->step += 1;
 }

@@ -233,6 +233,7 @@ class Workload:
     hg_alpha: float
     steps: int
     wall: bool = False     # rigid frictionless wall on the plane z = 0
+    grip_ramp: float = 0.0  # tau (s): prescribed velocities ramp up as 1 - exp(-t / tau) (Sec. 6); 0: constant
 
     def sim_params(self) -> dict:
         return dict(h=self.h, rc=self.rc, dt=self.dt, hg_alpha=self.hg_alpha)
@@ -270,6 +271,15 @@ def notched_bar_gtn(radius=5e-3, height=20e-3, spacing=0.15e-3, notch_radius=1e-
     in [0.0008, 0.0012]; 3000 steps."""
     sp = notched_round_bar(radius, height, spacing, notch_radius, seed, v_grip=v_grip)
     return _workload("notched_bar_gtn", sp, [aluminium_gtn()], steps, hg_alpha)
+
+
+def paper_loading(w: Workload, v_max: float = 10.0, tau: float = 1e-3) -> Workload:
+    """The grip loading of the paper's tensile simulations (Sec. 6): the end
+    layers move apart at +-v_max (1 - exp(-t / tau)) along the bar axis, with
+    v_max = 10 mm/ms and t in ms, i.e. tau = 1 ms."""
+    sp = dataclasses.replace(w.specimen)
+    sp.bc_vel = np.where(sp.bc_vel > 0, v_max, np.where(sp.bc_vel < 0, -v_max, 0.0))
+    return dataclasses.replace(w, specimen=sp, grip_ramp=tau, name=w.name + "_ramp")
 
 
 def failure_variant(w: Workload, v_grip: float = 20.0, scale: float = 0.02) -> Workload:

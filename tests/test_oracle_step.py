@@ -245,3 +245,65 @@ def test_step_is_its_three_phases():
     for k, v in a.state().items():
         assert np.array_equal(v, b.state()[k]), k
     assert np.array_equal(a.vh, b.vh)
+
+
+def _ramped_bar(tau_steps, steps=60):
+    import dataclasses
+    w = S.tensile_bar_cl(nx=4, ny=4, nz=12, steps=steps)
+    return dataclasses.replace(w, grip_ramp=tau_steps * w.dt)
+
+
+def test_grip_ramp_displacement_is_the_integral_of_the_ramp():
+    """Sec. 6 grip loading v_bc (1 - exp(-t / tau)): a gripped particle starts
+    at rest, its velocity after n steps is v_bc (1 - exp(-n dt / tau)), and its
+    displacement is the midpoint-rule integral of the ramp, within the rule's
+    error bound t dt^2 max|v''| / 24 = t dt^2 |v_bc| / (24 tau^2) of the exact
+    v_bc (t - tau (1 - exp(-t / tau)))."""
+    w = _ramped_bar(tau_steps=15.0)
+    tau, dt = w.grip_ramp, w.dt
+    o = oracle.Simulation.from_workload(w)
+    g = np.nonzero(w.specimen.bc_mask)[0]
+    vbc = w.specimen.bc_vel[g]
+    assert np.all(o["v"][g] == 0.0)
+    for n in (1, 7, 30, 60):
+        o.step(n - o.step_count)
+        t = n * dt
+        assert np.allclose(o["v"][g], vbc * (1.0 - np.exp(-t / tau)), rtol=1e-14, atol=0.0)
+        exact = vbc * (t - tau * (1.0 - np.exp(-t / tau)))
+        bound = t * dt * dt * np.abs(vbc) / (24.0 * tau * tau)
+        assert np.all(np.abs(o["u"][g] - exact) <= 1.01 * bound + 1e-18)
+        # and not trivially: the constant-velocity displacement is far away
+        assert np.all(np.abs(o["u"][g, 2] - vbc[:, 2] * t) > 10 * bound[:, 2])
+
+
+def test_grip_ramp_limits():
+    """tau -> 0 is the constant grip velocity: bit for bit the same trajectory
+    from the first step on (only the initial grip velocity differs, and the
+    first half kick overwrites it); tau = 0 is exactly the unramped run."""
+    import dataclasses
+    base = S.failure_variant(S.tensile_bar_cl(nx=4, ny=4, nz=12, steps=40))
+    ref = oracle.Simulation.from_workload(base)
+    ref.step(40)
+    zero = oracle.Simulation.from_workload(dataclasses.replace(base, grip_ramp=0.0))
+    zero.step(40)
+    tiny = oracle.Simulation.from_workload(dataclasses.replace(base, grip_ramp=1e-300))
+    g = np.nonzero(base.specimen.bc_mask)[0]
+    assert np.all(tiny["v"][g] == 0.0)
+    tiny.step(40)
+    for k in ("u", "v", "F", "sigma", "ep", "D", "force"):
+        assert np.array_equal(zero[k], ref[k]), k
+        assert np.array_equal(tiny[k], ref[k]), k
+    with pytest.raises(ValueError):
+        oracle.Simulation.from_workload(dataclasses.replace(base, grip_ramp=-1.0))
+
+
+def test_paper_loading_drives_the_grips_apart():
+    w = S.paper_loading(S.tensile_bar_cl(nx=4, ny=4, nz=12, steps=20))
+    assert w.grip_ramp == 1e-3
+    v = w.specimen.bc_vel[w.specimen.bc_mask.astype(bool)][:, 2]
+    assert set(np.unique(v)) == {-10.0, 10.0}
+    o = oracle.Simulation.from_workload(w)
+    o.step(20)
+    top = w.specimen.bc_mask.astype(bool) & (w.specimen.bc_vel[:, 2] > 0)
+    t = 20 * w.dt
+    assert np.allclose(o["v"][top, 2], 10.0 * -np.expm1(-t / 1e-3), rtol=1e-14)
