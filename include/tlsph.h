@@ -257,6 +257,18 @@ int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
  * tlsph_batch_set.  The FP64 path ignores it. */
 int tlsph_set_guard(tlsph_ctx *ctx, double band);
 
+/* Grip velocity ramp (Sec. 6: the end rows move at v_max (1 - e^{-t}), with
+ * v_max in mm/ms and t in ms).  With tau > 0 every prescribed velocity
+ * (bc_mask set) holds as bc_vel (1 - exp(-t / tau)) at the time t of the
+ * velocity it constrains: t_n + dt/2 for the half-step velocity, t_{n+1} for
+ * the step's end, t_n = n dt with n the context's step count.  tau = 0
+ * (default) keeps bc_vel constant.  On the call the prescribed particles'
+ * velocities are set to their ramped value at the current time (zero at
+ * step 0), and the next step starts from them.  Fully damaged particles stay
+ * at rest.  TLSPH_ERR_ARG for tau < 0 or non-finite.  Batches pick the ramp
+ * up at the next tlsph_batch_set. */
+int tlsph_set_grip_ramp(tlsph_ctx *ctx, double tau);
+
 /* Form of the mixed path's sliced neighbour lists (the thread-per-row plans
  * read the fixed neighbour sets of Sec. 2.2 through them; the paper has no
  * counterpart of the layout).  A slice is the 32 consecutive rows of one warp.

@@ -654,7 +654,7 @@ int tlsph_step(tlsph_ctx *ctx, int nsteps)
         }
     cudaError_t e;
     if (ctx->need_predict) {
-        e = launch_predict(ctx->s, ctx->ucur, ctx->cfg.dt, (ctx->cfg.flags & TLSPH_FLAG_WALL) != 0, ctx->stream);
+        e = launch_predict(ctx->s, ctx->ucur, ctx->cfg.dt, (ctx->cfg.flags & TLSPH_FLAG_WALL) != 0, ctx->steps, ctx->stream);
         if (e == cudaSuccess && ctx->cfg.precision == TLSPH_PRECISION_MIXED)
             e = mixed_after_predict(ctx->s, ctx->dcur, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "predict");
@@ -729,6 +729,25 @@ int tlsph_set_guard(tlsph_ctx *ctx, double band)
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_guard sync");
     ctx->guard = band;
+    return TLSPH_OK;
+}
+
+int tlsph_set_grip_ramp(tlsph_ctx *ctx, double tau)
+{
+    if (!ctx) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    if (!(tau >= 0.0) || !std::isfinite(tau)) {
+        ctx->err = "grip ramp tau must be finite and >= 0";
+        return TLSPH_ERR_ARG;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_grip_ramp sync");
+    ctx->s.grip_ramp = tau;
+    e = launch_apply_grip(ctx->s, (double)ctx->steps * ctx->cfg.dt, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_grip_ramp");
+    ctx->need_predict = true;
     return TLSPH_OK;
 }
 

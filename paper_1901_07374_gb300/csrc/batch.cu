@@ -104,7 +104,7 @@ int tlsph_batch_set(tlsph_batch *b, tlsph_ctx *const *ctxs, int n)
         tlsph_ctx *c = ctxs[k];
         e = cudaStreamSynchronize(c->stream);
         if (e == cudaSuccess && c->need_predict) {
-            e = launch_predict(c->s, c->ucur, c->cfg.dt, (c->cfg.flags & TLSPH_FLAG_WALL) != 0, c->stream);
+            e = launch_predict(c->s, c->ucur, c->cfg.dt, (c->cfg.flags & TLSPH_FLAG_WALL) != 0, c->steps, c->stream);
             if (e == cudaSuccess) e = mixed_after_predict(c->s, c->dcur, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e == cudaSuccess) c->need_predict = false;

@@ -863,17 +863,20 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         s.force[3 * i + k] = (double)f[k];
         vn[k] = s.vh[3 * i + k] + c.half_dt * fd[k];
     }
+    // velocity constraints (Sec. 3.1; grip ramp of Sec. 6 at t_{n+1} and at t_{n+3/2})
     if (fail >= 0) {
         vn[0] = vn[1] = vn[2] = 0.0;
     } else if (s.bcm[i]) {
-        vn[0] = s.bcv[3 * i]; vn[1] = s.bcv[3 * i + 1]; vn[2] = s.bcv[3 * i + 2];
+        const double r = grip_factor(s.grip_ramp, ((double)c.step_index + 1.0) * c.dt);
+        vn[0] = s.bcv[3 * i] * r; vn[1] = s.bcv[3 * i + 1] * r; vn[2] = s.bcv[3 * i + 2] * r;
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * fd[k];
     if (fail >= 0) {
         v2[0] = v2[1] = v2[2] = 0.0;
     } else if (s.bcm[i]) {
-        v2[0] = s.bcv[3 * i]; v2[1] = s.bcv[3 * i + 1]; v2[2] = s.bcv[3 * i + 2];
+        const double r = grip_factor(s.grip_ramp, ((double)(c.step_index + 1) + 0.5) * c.dt);
+        v2[0] = s.bcv[3 * i] * r; v2[1] = s.bcv[3 * i + 1] * r; v2[2] = s.bcv[3 * i + 2] * r;
     }
     const double *un = s.u[c.ucur ^ 1];
     double *unext = s.u[c.ucur];

@@ -52,12 +52,16 @@ static StepConst make_const(const tlsph_config &cfg, int ucur, int dcur, int64_t
     return c;
 }
 
-__device__ __forceinline__ void apply_bc(const DevState &s, int64_t i, int fail, double *v)
+// velocity constraints at time t: a fully damaged particle is held at rest
+// (Sec. 3.1); a prescribed particle moves with v_bc, ramped as
+// v_bc (1 - exp(-t / tau)) when the context has a grip ramp (Sec. 6)
+__device__ __forceinline__ void apply_bc(const DevState &s, int64_t i, int fail, double t, double *v)
 {
     if (fail >= 0) {
         v[0] = v[1] = v[2] = 0.0;
     } else if (s.bcm[i]) {
-        v[0] = s.bcv[3 * i]; v[1] = s.bcv[3 * i + 1]; v[2] = s.bcv[3 * i + 2];
+        const double r = grip_factor(s.grip_ramp, t);
+        v[0] = s.bcv[3 * i] * r; v[1] = s.bcv[3 * i + 1] * r; v[2] = s.bcv[3 * i + 2] * r;
     }
 }
 
@@ -300,10 +304,10 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass2_fp64(DevState s, StepCon
         s.force[3 * i + k] = f[k];
         vn[k] = s.vh[3 * i + k] + c.half_dt * (f[k] * im);
     }
-    apply_bc(s, i, fail, vn);
+    apply_bc(s, i, fail, ((double)c.step_index + 1.0) * c.dt, vn);
 #pragma unroll
     for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * (f[k] * im);
-    apply_bc(s, i, fail, v2);
+    apply_bc(s, i, fail, ((double)(c.step_index + 1) + 0.5) * c.dt, v2);
     double *__restrict__ unext = s.u[c.ucur];
     double un2[3];
 #pragma unroll
@@ -363,7 +367,7 @@ __global__ void k_material_fields(DevState s, int mat_id, int dcur, int set_gtn_
 }
 
 // v^{n+1/2} = v^n + dt/2 f^n / m and u^{n+1} = u^n + dt v^{n+1/2} (constraints applied)
-__global__ void k_predict(DevState s, int ucur, double dt, int wall)
+__global__ void k_predict(DevState s, int ucur, double dt, int wall, double t_half)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
@@ -371,7 +375,7 @@ __global__ void k_predict(DevState s, int ucur, double dt, int wall)
     double v[3], u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) v[k] = s.v[3 * i + k] + 0.5 * dt * (s.force[3 * i + k] * im);
-    apply_bc(s, i, s.fail[i], v);
+    apply_bc(s, i, s.fail[i], t_half, v);
 #pragma unroll
     for (int k = 0; k < 3; ++k) u[k] = s.u[ucur][3 * i + k] + dt * v[k];
     if (wall) wall_contact(s.X[3 * i + 2], u[2], v[2]);
@@ -380,6 +384,14 @@ __global__ void k_predict(DevState s, int ucur, double dt, int wall)
         s.vh[3 * i + k] = v[k];
         s.u[ucur ^ 1][3 * i + k] = u[k];
     }
+}
+
+// the velocities of the prescribed particles at time t (a ramp switched on)
+__global__ void k_apply_grip(DevState s, double t)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    apply_bc(s, i, s.fail[i], t, s.v + 3 * i);
 }
 
 __global__ void k_material_point(const DevMat m, double dt, int64_t n, const double *deps, const double *J,
@@ -624,9 +636,15 @@ cudaError_t launch_diagnostics(const DevState &s, int dcur, double *partials, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, cudaStream_t st)
+cudaError_t launch_apply_grip(const DevState &s, double t, cudaStream_t st)
 {
-    k_predict<<<nblk(s.N, 256), 256, 0, st>>>(s, ucur, dt, wall ? 1 : 0);
+    k_apply_grip<<<nblk(s.N, 256), 256, 0, st>>>(s, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, int64_t steps, cudaStream_t st)
+{
+    k_predict<<<nblk(s.N, 256), 256, 0, st>>>(s, ucur, dt, wall ? 1 : 0, ((double)steps + 0.5) * dt);
     return cudaGetLastError();
 }
 

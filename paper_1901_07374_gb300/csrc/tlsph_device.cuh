@@ -48,6 +48,10 @@ __device__ __forceinline__ float spline_dw(float q)
     return 0.0f;
 }
 
+// grip ramp of Sec. 6: a prescribed velocity v_bc holds as v_bc (1 - exp(-t / tau))
+// at time t; tau = 0 keeps it constant
+__device__ __forceinline__ double grip_factor(double tau, double t) { return tau > 0.0 ? -expm1(-t / tau) : 1.0; }
+
 // ---------------------------------------------------------------- 3x3 algebra
 struct M3 { double a[9]; };
 

@@ -88,6 +88,7 @@ struct DevState {
     const int32_t *ell_w;   // (N + 31) / 32 slice widths: W (explicit) or ~W (aligned)
     double vref[3];         // bulk reference velocity of the r1 mirror
     FixPack pack;
+    double grip_ramp = 0.0;  // tau of the grip velocity ramp (Sec. 6); 0: constant prescribed velocities
 };
 
 // The pass-2 record is tiled by 32 particles: component k (0..5) of particle j
@@ -180,7 +181,11 @@ constexpr int DIAG_BLOCKS = 152;
 cudaError_t launch_diagnostics(const DevState &s, int dcur, double *partials, cudaStream_t st);
 cudaError_t launch_init_state(const DevState &s, cudaStream_t st);
 cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool gtn_damage, cudaStream_t st);
-cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, cudaStream_t st);
+// half kick and drift of the first step after a state change; steps = steps done (the
+// half-step velocity holds at (steps + 1/2) dt)
+cudaError_t launch_predict(const DevState &s, int ucur, double dt, bool wall, int64_t steps, cudaStream_t st);
+// prescribed particles' velocities at time t (grip ramp switched on)
+cudaError_t launch_apply_grip(const DevState &s, double t, cudaStream_t st);
 
 // rigid wall on z = 0: put a particle that drifted below it back on the plane
 // and remove the velocity component into it

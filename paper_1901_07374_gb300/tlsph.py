@@ -78,7 +78,7 @@ EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph
            "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
            "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
            "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_neighbor_layout",
-           "tlsph_fma_peak", "tlsph_set_guard", "tlsph_diagnostics")
+           "tlsph_fma_peak", "tlsph_set_guard", "tlsph_diagnostics", "tlsph_set_grip_ramp")
 
 _lib = None
 _lock = threading.Lock()
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_diagnostics.argtypes = [vp, ctypes.POINTER(dbl), i32]
         L.tlsph_set_guard.restype = i32
         L.tlsph_set_guard.argtypes = [vp, dbl]
+        L.tlsph_set_grip_ramp.restype = i32
+        L.tlsph_set_grip_ramp.argtypes = [vp, dbl]
         L.tlsph_fma_peak.restype = i32
         L.tlsph_fma_peak.argtypes = [i32, i32, ctypes.POINTER(dbl)]
         L.tlsph_neighbor_layout.restype = i32
@@ -298,8 +300,11 @@ class Simulation:
     def from_workload(cls, w, precision="fp64", **kw):
         sp = w.specimen
         kw.setdefault("wall", getattr(w, "wall", False))
-        return cls(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, w.materials, w.h, w.rc, w.dt,
-                   w.hg_alpha, precision=precision, **kw)
+        sim = cls(sp.X, sp.vol, sp.mat_id, sp.bc_mask, sp.bc_vel, sp.f0, w.materials, w.h, w.rc, w.dt,
+                  w.hg_alpha, precision=precision, **kw)
+        if getattr(w, "grip_ramp", 0.0):
+            sim.set_grip_ramp(w.grip_ramp)
+        return sim
 
     # ---------------------------------------------------------------- stepping
     def step(self, n: int = 1) -> None:
@@ -349,6 +354,11 @@ class Simulation:
     def set_guard(self, band: float) -> None:
         """Guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)."""
         _check(load().tlsph_set_guard(self.ctx, float(band)), self.ctx)
+
+    def set_grip_ramp(self, tau: float) -> None:
+        """Prescribed velocities ramp up as bc_vel (1 - exp(-t / tau)) (Sec. 6
+        grip loading; tlsph_set_grip_ramp); 0 keeps them constant."""
+        _check(load().tlsph_set_grip_ramp(self.ctx, float(tau)), self.ctx)
 
     def neighbor_layout(self) -> dict:
         """Form of the sliced neighbour lists of a mixed-precision context:

@@ -21,7 +21,8 @@ def _specimens():
             S.failure_variant(S.tensile_bar_cl(nx=8, ny=8, nz=24)),
             S.tensile_bar_jc(nx=13, ny=11, nz=40, seed=2, scale=0.8),
             S.notched_bar_gtn(radius=1.5e-3, height=5e-3, spacing=0.3e-3, notch_radius=0.5e-3, v_grip=20.0),
-            S.failure_variant(S.tensile_bar_jc(nx=6, ny=6, nz=20, seed=4))]
+            S.failure_variant(S.tensile_bar_jc(nx=6, ny=6, nz=20, seed=4)),
+            S.paper_loading(S.tensile_bar_cl(nx=7, ny=6, nz=22, seed=5), v_max=20.0, tau=5e-7)]
 
 
 def _make(ws):

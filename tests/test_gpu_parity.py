@@ -93,6 +93,24 @@ def test_failure_variant_sets_bit_exact():
     compare_state(gs, os_, w, tol=TRAJ_TOL)
 
 
+@pytest.mark.parametrize("tau_steps", [60, 39385])
+def test_grip_ramp_vs_oracle(tau_steps):
+    """Sec. 6 grip loading, v_max (1 - exp(-t / tau)) on the end layers: a
+    ramp that completes within the run (tau = 60 steps, through yield, damage
+    and failure) and the paper's tau = 1 ms (39385 steps).  FP64: fields
+    within the trajectory tolerance, failure set and steps exact; mixed: the
+    first 60 steps within the mixed tolerance."""
+    base = S.failure_variant(S.tensile_bar_cl(steps=300))
+    w = S.paper_loading(base, v_max=20.0, tau=tau_steps * base.dt)
+    gs, os_ = _run_both(w, 300)
+    if tau_steps == 60:
+        assert (os_["fail_step"] >= 0).sum() > 20
+    assert np.array_equal(gs["FAIL_STEP"], os_["fail_step"])
+    compare_state(gs, os_, w, tol=TRAJ_TOL)
+    gm, om = _run_both(w, 60, precision="mixed")
+    compare_state(gm, om, w, tol=2e-4, fields=("U", "V", "F", "SIGMA", "STRESS_DEV", "FORCE"))
+
+
 def test_failure_variant_jc_sets_bit_exact():
     w = S.failure_variant(S.tensile_bar_jc(nx=8, ny=8, nz=32, steps=400))
     gs, os_ = _run_both(w, 400)
