@@ -539,15 +539,8 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     }
     CK(build_neighbors_fill(s, grid, sc, rc2, row_ptr, const_cast<int32_t *>(s.col), st));
 
-    // ---- correction matrices
-    CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
-    // S0 (mixed only) goes to the force array, which init_state clears afterwards
-    CK(shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), mixed ? s.force : nullptr, s.status, mixed, st));
-    uint32_t n_sing = 0;
-    CK(cudaMemcpyAsync(&n_sing, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (n_sing) return bail(TLSPH_ERR_SINGULAR_L, std::to_string(n_sing) + " particles have a singular correction matrix");
-    CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
+    // ---- mixed: fixed-point positions and the sliced neighbour lists, read by
+    // the correction-matrix kernel of a mixed context as by its steps
     if (mixed) {
         // bulk reference velocity of the FP32 velocity mirror: the mean initial velocity
         for (int k = 0; k < 3; ++k) s.vref[k] = vsum[k] / (double)n;
@@ -562,7 +555,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         pk.unit = std::ldexp(1.0, e2);
         pk.inv_unit = std::ldexp(1.0, -e2);
         s.pack = pk;
-        CK(mixed_init_static(s, s.force, pk, st));
+        CK(mixed_init_positions(s, pk, st));
         // sliced neighbour lists for the thread-per-row plans
         const int64_t ng = (N + 31) / 32;
         int64_t *ell_off = const_cast<int64_t *>(s.ell_off);
@@ -598,6 +591,20 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
             ctx->plan[0] = 3; ctx->plan[1] = 256; ctx->plan[2] = 0; ctx->plan[3] = 128;
         }
     }
+
+    // ---- correction matrices
+    CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
+    // S0 (mixed only) goes to the force array, which init_state clears afterwards
+    if (mixed && ctx->ell_ok)
+        CK(mixed_shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), s.force, s.status, st));
+    else
+        CK(shape_matrix(s, cfg->h, const_cast<double *>(s.Linv), mixed ? s.force : nullptr, s.status, mixed, st));
+    uint32_t n_sing = 0;
+    CK(cudaMemcpyAsync(&n_sing, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_sing) return bail(TLSPH_ERR_SINGULAR_L, std::to_string(n_sing) + " particles have a singular correction matrix");
+    CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
+    if (mixed) CK(mixed_init_static(s, s.force, st));
 
     // ---- initial state (overwrites the scratch overlay)
     CK(launch_init_state(s, st));
@@ -858,13 +865,16 @@ int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_
             e = cudaMemcpyAsync(d, f.ptr, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
         else
             e = launch_to_caller(f.ptr, d, ctx->inv_dev, N, comps, scomps, (int)f.elem, f.sym, st);
-    } else if (plain) {
-        e = cudaMemcpyAsync(dst, f.ptr, bytes, cudaMemcpyDeviceToHost, st);
     } else {
+        // pageable destination: copy into a host staging array, then into the
+        // caller's order on the host (faster here than the driver's own
+        // staging into pages the caller has not touched yet)
         std::vector<unsigned char> tmp(sbytes);
         e = cudaMemcpyAsync(tmp.data(), f.ptr, sbytes, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && plain) {
+            memcpy(dst, tmp.data(), sbytes);
+        } else if (e == cudaSuccess) {
             unsigned char *o = static_cast<unsigned char *>(dst);
             for (int64_t k = 0; k < N; ++k) {
                 const int64_t i = ctx->perm[k];

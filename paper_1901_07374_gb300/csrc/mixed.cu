@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(128) k_epi2_mixed(DevState s, MixConst c)
 
 // ------------------------------------------------------------------ mirrors
 // static records from the FP64 inputs: fixed-point positions, S0, L^{-1}
-__global__ void k_mixed_static(DevState s, const double *S0, FixPack pk)
+__global__ void k_mixed_positions(DevState s, FixPack pk)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
@@ -1092,6 +1092,12 @@ __global__ void k_mixed_static(DevState s, const double *S0, FixPack pk)
 #pragma unroll
     for (int k = 0; k < 3; ++k) x[k] = (int)llrint((s.X[3 * i + k] - pk.center[k]) * pk.inv_unit);
     s.xo[i] = make_int4(x[0], x[1], x[2], 0);
+}
+
+__global__ void k_mixed_static(DevState s, const double *S0)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
     s.s0[i] = make_float4((float)S0[3 * i], (float)S0[3 * i + 1], (float)S0[3 * i + 2], 0.0f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.linv32[9 * i + k] = (float)s.Linv[9 * i + k];
@@ -1174,9 +1180,88 @@ cudaError_t mixed_import(const tlsph_ctx &ctx, int field, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t mixed_init_static(const DevState &s, const double *S0, const FixPack &pk, cudaStream_t st)
+cudaError_t mixed_init_positions(const DevState &s, const FixPack &pk, cudaStream_t st)
 {
-    k_mixed_static<<<nb(s.N, 256), 256, 0, st>>>(s, S0, pk);
+    k_mixed_positions<<<nb(s.N, 256), 256, 0, st>>>(s, pk);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_init_static(const DevState &s, const double *S0, cudaStream_t st)
+{
+    k_mixed_static<<<nb(s.N, 256), 256, 0, st>>>(s, S0);
+    return cudaGetLastError();
+}
+
+// Correction matrix (Sec. 2.2, Eq. correction_matrix) and S0 of a mixed
+// context: thread per row over the sliced lists, with the X_ij the steps use
+// (exact fixed-point differences rounded once to FP32) and FP32 pair terms;
+// each row sum is Kahan-compensated in FP32 and finished in FP64, and the 3x3
+// inversion is FP64 (same singularity test as the FP64 path).  In units u of
+// the fixed-point grid, X_ij (x) X_ij / r = u d (x) d / |d| and X_ij / r = d / |d|.
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
+{
+    const float y = __fsub_rn(x, comp);
+    const float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
+__global__ void __launch_bounds__(256) k_shape_mixed(DevState s, float inv_h, double l_scale, double *Linv,
+                                                     double *S0, uint32_t *n_singular)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    const int4 oi = s.xo[i];
+    float sm[9], cp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sm[k] = cp[k] = 0.0f;
+    for_slots<2>(s, i, [&](const int *j, const float *w) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float3 d = xdiff(s.xo[j[u]], oi);
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            const float rinv = rsqrtf(r2);
+            float a, b;
+            const float c0 = w[u] * (float)s.vol[j[u]] * spline_dw_ab(r2 * rinv * inv_h, a, b) * rinv;
+            kahan_add(sm[0], cp[0], c0 * d.x);
+            kahan_add(sm[1], cp[1], c0 * d.y);
+            kahan_add(sm[2], cp[2], c0 * d.z);
+            kahan_add(sm[3], cp[3], c0 * d.x * d.x);
+            kahan_add(sm[4], cp[4], c0 * d.y * d.y);
+            kahan_add(sm[5], cp[5], c0 * d.z * d.z);
+            kahan_add(sm[6], cp[6], c0 * d.x * d.y);
+            kahan_add(sm[7], cp[7], c0 * d.y * d.z);
+            kahan_add(sm[8], cp[8], c0 * d.z * d.x);
+        }
+    });
+    double v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = (double)sm[k] - (double)cp[k];
+    S0[3 * i] = v[0]; S0[3 * i + 1] = v[1]; S0[3 * i + 2] = v[2];
+    const double l[6] = { l_scale * v[3], l_scale * v[4], l_scale * v[5], l_scale * v[6], l_scale * v[7],
+                          l_scale * v[8] };
+    double L[9], c[9];
+    sym_to_full(l, L);
+    cof3(L, c);
+    const double det = L[0] * c[0] + L[1] * c[1] + L[2] * c[2];
+    double fn2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fn2 += L[k] * L[k];
+    const double fn = sqrt(fn2);
+    const bool ok = isfinite(det) && fabs(det) > 1e-12 * fn * fn * fn;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) Linv[9 * i + 3 * k + m] = ok ? c[3 * m + k] / det : 0.0;
+    if (!ok) atomicAdd(n_singular, 1u);
+}
+
+cudaError_t mixed_shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
+                               cudaStream_t st)
+{
+    const double dw_norm = 1.0 / (M_PI * h * h * h * h);
+    k_shape_mixed<<<nb(s.N, 256), 256, 0, st>>>(s, (float)(s.pack.unit / h), dw_norm * s.pack.unit, Linv, S0,
+                                                  n_singular);
     return cudaGetLastError();
 }
 

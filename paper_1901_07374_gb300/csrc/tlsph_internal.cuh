@@ -256,7 +256,13 @@ cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, 
                               cudaStream_t st);
 void batch_grid(bool hg, int *grid);
 
-cudaError_t mixed_init_static(const DevState &s, const double *S0, const FixPack &pk, cudaStream_t st);
+// fixed-point positions xo (before the sliced lists and the correction matrices)
+cudaError_t mixed_init_positions(const DevState &s, const FixPack &pk, cudaStream_t st);
+// FP32 copies of S0 and L^{-1}
+cudaError_t mixed_init_static(const DevState &s, const double *S0, cudaStream_t st);
+// L^{-1} and S0 of a mixed context over its sliced lists (xo and the lists built)
+cudaError_t mixed_shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
+                               cudaStream_t st);
 cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st);
 cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st);
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
