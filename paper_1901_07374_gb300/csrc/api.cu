@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <thread>
 #include <numeric>
 #include <vector>
 
@@ -107,6 +108,70 @@ std::vector<int32_t> line_order_perm(const double *X, const double *vol, int64_t
         perm.swap(idx2);
     }
     return perm;
+}
+
+// The create-time scan of the caller's inputs over one chunk [a, b).
+struct InputScan {
+    double lo[3], hi[3], vsum[3];
+    uint64_t mats = 0;     // bit m: material m in use
+    bool bad_vol = false, bad_x = false, bad_mat = false;
+};
+
+void scan_chunk(const double *X, const double *vol, const int32_t *mat, const double *bcv, int64_t a, int64_t b,
+                InputScan &r)
+{
+    for (int k = 0; k < 3; ++k) { r.lo[k] = X[3 * a + k]; r.hi[k] = X[3 * a + k]; r.vsum[k] = 0.0; }
+    for (int64_t i = a; i < b; ++i) {
+        const double vv = vol[i];
+        r.bad_vol |= !(vv > 0.0 && vv - vv == 0.0);
+        for (int k = 0; k < 3; ++k) {
+            const double c = X[3 * i + k];
+            r.bad_x |= !(c - c == 0.0);
+            r.lo[k] = c < r.lo[k] ? c : r.lo[k];
+            r.hi[k] = c > r.hi[k] ? c : r.hi[k];
+        }
+        if (mat) {
+            const int32_t m = mat[i];
+            if (m >= 0 && m < TLSPH_MAX_MATERIALS) r.mats |= 1ull << m;
+            else r.bad_mat = true;
+        }
+        if (bcv)
+            for (int k = 0; k < 3; ++k) r.vsum[k] += bcv[3 * i + k];
+    }
+    if (!mat) r.mats = 1;
+}
+
+InputScan scan_inputs(const double *X, const double *vol, const int32_t *mat, const double *bcv, int64_t N)
+{
+    const int chunks = N >= 262144 ? 16 : 1;
+    std::vector<InputScan> part((size_t)chunks);
+    auto range = [&](int c, int64_t &a, int64_t &b) { a = N * c / chunks; b = N * (c + 1) / chunks; };
+    std::vector<std::thread> th;
+    for (int c = 1; c < chunks; ++c) {
+        int64_t a, b;
+        range(c, a, b);
+        try {
+            th.emplace_back(scan_chunk, X, vol, mat, bcv, a, b, std::ref(part[(size_t)c]));
+        } catch (...) {        // no thread to be had: scan this chunk here
+            scan_chunk(X, vol, mat, bcv, a, b, part[(size_t)c]);
+        }
+    }
+    int64_t a0, b0;
+    range(0, a0, b0);
+    scan_chunk(X, vol, mat, bcv, a0, b0, part[0]);
+    for (auto &t : th) t.join();
+    InputScan r = part[0];
+    for (int c = 1; c < chunks; ++c) {
+        const InputScan &p = part[(size_t)c];
+        for (int k = 0; k < 3; ++k) {
+            r.lo[k] = std::min(r.lo[k], p.lo[k]);
+            r.hi[k] = std::max(r.hi[k], p.hi[k]);
+            r.vsum[k] += p.vsum[k];
+        }
+        r.mats |= p.mats;
+        r.bad_vol |= p.bad_vol; r.bad_x |= p.bad_x; r.bad_mat |= p.bad_mat;
+    }
+    return r;
 }
 
 Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
@@ -393,25 +458,18 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     if (N <= 0 || N > INT32_MAX) { g_create_error = "N must be in [1, 2^31)"; return TLSPH_ERR_ARG; }
     if (!X || !vol) { g_create_error = "X and vol are required"; return TLSPH_ERR_ARG; }
     // one pass over the inputs: validation, bounding box, materials in use and
-    // the sum of the initial velocities (the bulk reference of the mixed path)
-    double lo3[3] = { X[0], X[1], X[2] }, hi3[3] = { X[0], X[1], X[2] }, vsum[3] = { 0.0, 0.0, 0.0 };
+    // the sum of the initial velocities (the bulk reference of the mixed path).
+    // Large inputs are split into a fixed number of chunks scanned by host
+    // threads; the chunks are joined in their order, so the result depends on
+    // N only, not on the machine.
+    InputScan scan = scan_inputs(X, vol, mat_id, bc_vel, N);
+    if (scan.bad_vol) { g_create_error = "vol must be positive and finite"; return TLSPH_ERR_ARG; }
+    if (scan.bad_x) { g_create_error = "X must be finite"; return TLSPH_ERR_ARG; }
+    if (scan.bad_mat) { g_create_error = "mat_id out of range"; return TLSPH_ERR_ARG; }
+    double lo3[3], hi3[3], vsum[3];
     bool mat_used[TLSPH_MAX_MATERIALS] = {};
-    if (!mat_id) mat_used[0] = true;
-    for (int64_t i = 0; i < N; ++i) {
-        if (!(vol[i] > 0.0) || !isfinite(vol[i])) { g_create_error = "vol must be positive and finite"; return TLSPH_ERR_ARG; }
-        const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
-        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) { g_create_error = "X must be finite"; return TLSPH_ERR_ARG; }
-        lo3[0] = std::min(lo3[0], x); hi3[0] = std::max(hi3[0], x);
-        lo3[1] = std::min(lo3[1], y); hi3[1] = std::max(hi3[1], y);
-        lo3[2] = std::min(lo3[2], z); hi3[2] = std::max(hi3[2], z);
-        if (mat_id) {
-            if (mat_id[i] < 0 || mat_id[i] >= TLSPH_MAX_MATERIALS) {
-                g_create_error = "mat_id out of range"; return TLSPH_ERR_ARG;
-            }
-            mat_used[mat_id[i]] = true;
-        }
-        if (bc_vel) { vsum[0] += bc_vel[3 * i]; vsum[1] += bc_vel[3 * i + 1]; vsum[2] += bc_vel[3 * i + 2]; }
-    }
+    for (int k = 0; k < 3; ++k) { lo3[k] = scan.lo[k]; hi3[k] = scan.hi[k]; vsum[k] = scan.vsum[k]; }
+    for (int k = 0; k < TLSPH_MAX_MATERIALS; ++k) mat_used[k] = (scan.mats >> k) & 1u;
     if (arena && ((uintptr_t)arena % ALIGN) != 0) { g_create_error = "arena must be 256-byte aligned"; return TLSPH_ERR_ARG; }
     if (arena && nnz_cap <= 0) { g_create_error = "nnz_cap is required with an arena"; return TLSPH_ERR_ARG; }
 
@@ -488,15 +546,13 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         CK(build_order(stX, N, grid, sc, !ctx->reordered, ctx->perm_dev, st));
     }
     CK(launch_gather_inputs(ctx->perm_dev, N, stX, stvol, stmat, stbcm, stbcv, stf0, s, st));
-    ctx->perm.resize(n);
-    ctx->inv.resize(n);
+    // host copies of the order and its inverse (kept empty in caller order: the identity)
     if (ctx->reordered) {
+        ctx->perm.resize(n);
+        ctx->inv.resize(n);
         CK(cudaMemcpyAsync(ctx->perm.data(), ctx->perm_dev, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (size_t k = 0; k < n; ++k) ctx->inv[ctx->perm[k]] = (int32_t)k;
-    } else {   // caller order: the identity
-        std::iota(ctx->perm.begin(), ctx->perm.end(), 0);
-        std::iota(ctx->inv.begin(), ctx->inv.end(), 0);
     }
 
     const double rc2 = cfg->rc * cfg->rc;
@@ -877,7 +933,7 @@ int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_
         } else if (e == cudaSuccess) {
             unsigned char *o = static_cast<unsigned char *>(dst);
             for (int64_t k = 0; k < N; ++k) {
-                const int64_t i = ctx->perm[k];
+                const int64_t i = ctx->reordered ? ctx->perm[k] : k;
                 if (f.sym) {
                     const double *a = reinterpret_cast<const double *>(tmp.data()) + 6 * k;
                     double *m = reinterpret_cast<double *>(o) + 9 * i;
@@ -931,7 +987,7 @@ int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, in
         std::vector<unsigned char> tmp((size_t)N * scomps * f.elem);
         const unsigned char *a = static_cast<const unsigned char *>(src);
         for (int64_t k = 0; k < N; ++k) {
-            const int64_t i = ctx->perm[k];
+            const int64_t i = ctx->reordered ? ctx->perm[k] : k;
             if (f.sym) {
                 const double *m = reinterpret_cast<const double *>(a) + 9 * i;
                 double *o = reinterpret_cast<double *>(tmp.data()) + 6 * k;

@@ -145,7 +145,7 @@ struct tlsph_ctx {
     void *ell_mem = nullptr;    // library-owned sliced-ELL columns
     int32_t *perm_dev = nullptr;
     int32_t *inv_dev = nullptr;   // device copy of inv when reordered, else null (identity)
-    std::vector<int32_t> perm, inv;
+    std::vector<int32_t> perm, inv;   // host copies of the order when reordered (empty in caller order)
 };
 
 namespace tlsph {
@@ -177,7 +177,7 @@ cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, 
 // step64.cu
 // deterministic reductions of the diagnostics (tlsph_diagnostics) over a
 // fixed grid of DIAG_BLOCKS blocks; the result lands in partials[0 .. TLSPH_DIAG_COUNT)
-constexpr int DIAG_BLOCKS = 152;
+constexpr int DIAG_BLOCKS = 256;
 cudaError_t launch_diagnostics(const DevState &s, int dcur, double *partials, cudaStream_t st);
 cudaError_t launch_init_state(const DevState &s, cudaStream_t st);
 cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool gtn_damage, cudaStream_t st);
