@@ -177,7 +177,7 @@ cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, 
 // step64.cu
 // deterministic reductions of the diagnostics (tlsph_diagnostics) over a
 // fixed grid of DIAG_BLOCKS blocks; the result lands in partials[0 .. TLSPH_DIAG_COUNT)
-constexpr int DIAG_BLOCKS = 256;
+constexpr int DIAG_BLOCKS = 152;
 cudaError_t launch_diagnostics(const DevState &s, int dcur, double *partials, cudaStream_t st);
 cudaError_t launch_init_state(const DevState &s, cudaStream_t st);
 cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool gtn_damage, cudaStream_t st);
