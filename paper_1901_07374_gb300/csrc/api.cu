@@ -600,9 +600,11 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     if (mixed) {
         // bulk reference velocity of the FP32 velocity mirror: the mean initial velocity
         for (int k = 0; k < 3; ++k) s.vref[k] = vsum[k] / (double)n;
-        // fixed-point positions about the bounding-box centre, |coordinate| < 2^31 - 2^10 units
+        // fixed-point positions about the bounding-box centre, |coordinate| < 2^31 - 2^10 units; the
+        // unit also keeps every neighbour difference (each component below rc) within int32, which a
+        // body smaller than about two cutoffs would otherwise overflow
         FixPack pk{};
-        double ext = 0.0;
+        double ext = cfg->rc;
         for (int k = 0; k < 3; ++k) {
             pk.center[k] = 0.5 * (lo3[k] + hi3[k]);
             ext = std::max(ext, std::max(hi3[k] - pk.center[k], pk.center[k] - lo3[k]));
@@ -612,6 +614,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         pk.inv_unit = std::ldexp(1.0, -e2);
         s.pack = pk;
         CK(mixed_init_positions(s, pk, st));
+        ctx->slow_grid = mixed_slow_grid();
         // sliced neighbour lists for the thread-per-row plans
         const int64_t ng = (N + 31) / 32;
         int64_t *ell_off = const_cast<int64_t *>(s.ell_off);

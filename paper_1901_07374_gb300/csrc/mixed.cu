@@ -1286,18 +1286,15 @@ cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st)
     return cudaMemsetAsync(s.slowq_n, 0, 2 * sizeof(uint32_t), st);
 }
 
-// persistent grid of the FP64-update kernel: SMs x resident blocks of 128
-static int slow_grid()
+// persistent grid of the FP64-update kernel on the current device: SMs x
+// resident blocks of 128 (each context computes it once, at creation)
+int mixed_slow_grid()
 {
-    static int grid = 0;
-    if (grid == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_epi1_slow, 128, 0);
-        grid = std::max(1, sms) * std::max(1, per);
-    }
-    return grid;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_epi1_slow, 128, 0);
+    return std::max(1, sms) * std::max(1, per);
 }
 
 // Launch plans (chosen per context, e.g. by the autotuner):
@@ -1332,7 +1329,7 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
         break;
     default: k_pass1_mixed<<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c); break;
     }
-    k_epi1_slow<<<slow_grid(), 128, 0, st>>>(s, c);
+    k_epi1_slow<<<ctx.slow_grid, 128, 0, st>>>(s, c);
     if (ev) cudaEventRecord(ev[1], st);
     if (v2 == 1) {
         if (hg) k_pass2_mixed_t<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);

@@ -126,6 +126,7 @@ struct tlsph_ctx {
     // GB300 for the 1M-particle bar; the autotuner may choose another)
     int32_t plan[4] = { 4, 64, 4, 128 };
     double guard = 1e-5;        // relative guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)
+    int slow_grid = 1;          // persistent grid of the mixed path's FP64-update kernel on the context's device
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
     bool mixed_dirty = false;   // FP32 mirrors must be refreshed from the FP64 state
     void *mixed = nullptr;      // mixed-precision state (mixed.cu)
@@ -270,6 +271,8 @@ cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
 // _STRESS_DEV, _SIGMA) or all of them (-1)
 cudaError_t mixed_import(const tlsph_ctx &ctx, int field, cudaStream_t st);
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev);
+// persistent grid of the FP64-update kernel on the current device
+int mixed_slow_grid();
 // compensated mixed state -> FP64 arrays for one field or all (-1)
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st);
 int mixed_kernels_per_step(const tlsph_ctx &ctx);
