@@ -1406,68 +1406,114 @@ __device__ __forceinline__ int batch_find(const int64_t *blk0, int n, int64_t w)
 // A block keeps its current member's slot in shared memory (copied when the
 // block's work moves to another member), so the kernels read the member's
 // arrays and constants from registers and shared memory rather than through
-// global loads that stores into the state could alias.
+// global loads that stores into the state could alias.  Blocks take their work
+// in chunks of BATCH_CHUNK consecutive work blocks from a counter: dynamic
+// balance across members of different cost.  Measured on 256 bars of 2k-200k
+// particles: one work block per grab 9.54 ms per step, 4 per grab 9.78 ms, 16
+// per grab 10.8 ms, and a static strided assignment 11.3 ms.  The member of a
+// chunk is found by a search over the first-block table (a few hundred bytes,
+// cached) and then stepped forward.  Every row is computed independently, so
+// the order in which chunks are taken changes no result.
+#ifndef BATCH_CHUNK
+#define BATCH_CHUNK 1
+#endif
+
+// resident blocks of 128 per SM each batch kernel is compiled for (pass-1
+// gather, per-particle update, pass 2)
+#ifndef BATCH_MINB0
+#define BATCH_MINB0 8
+#endif
+#ifndef BATCH_MINB1
+#define BATCH_MINB1 5
+#endif
+#ifndef BATCH_MINB2
+#define BATCH_MINB2 5
+#endif
+
 template <int KIND, bool HG, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_batch(const BatchHdr *hdr, const BatchSlot *slots)
+__global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchSlot *slots)
 {
-    __shared__ int sidx;
     __shared__ uint64_t slot_words[(sizeof(BatchSlot) + 7) / 8];
+    __shared__ int64_t grab;
     const BatchSlot &sl = *reinterpret_cast<const BatchSlot *>(slot_words);
     const int nspec = hdr->nspec;
     const int64_t total = hdr->total_blk;
+    const int64_t *blk0 = hdr->blk0;
     int cur = -1;
-    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
-        if (threadIdx.x == 0) sidx = batch_find(hdr->blk0, nspec, w);
+    for (;;) {
+        __syncthreads();                // every thread has read the previous chunk's start
+        if (threadIdx.x == 0) grab = (int64_t)atomicAdd(&hdr->next[KIND], (unsigned long long)BATCH_CHUNK);
         __syncthreads();
-        const int m = sidx;
-        if (m != cur) {
-            const uint64_t *src = reinterpret_cast<const uint64_t *>(slots + m);
-            for (int k = threadIdx.x; k < (int)((sizeof(BatchSlot) + 7) / 8); k += blockDim.x) slot_words[k] = src[k];
-            cur = m;
-            __syncthreads();
-        }
-        const DevState &st = sl.s;
-        const MixConst &c = sl.c;
-        const int64_t i = (w - sl.blk0) * blockDim.x + threadIdx.x;
-        if (i < st.N) {
-            if (KIND == 0) {            // pass-1 gather
-                float mm[9];
-                gather1_row<4>(st, c, i, mm);
+        const int64_t wb = grab;
+        if (wb >= total) break;
+        const int64_t we = min(total, wb + (int64_t)BATCH_CHUNK);
+        int m = batch_find(blk0, nspec, wb);
+        for (int64_t w = wb; w < we; ++w) {
+            while (m + 1 < nspec && blk0[m + 1] <= w) ++m;
+            if (m != cur) {             // uniform over the block
+                __syncthreads();        // every thread is done with the previous slot
+                const uint64_t *src = reinterpret_cast<const uint64_t *>(slots + m);
+                for (int k = threadIdx.x; k < (int)((sizeof(BatchSlot) + 7) / 8); k += blockDim.x)
+                    slot_words[k] = src[k];
+                cur = m;
+                __syncthreads();
+            }
+            const DevState &st = sl.s;
+            const MixConst &c = sl.c;
+            const int64_t i = (w - sl.blk0) * blockDim.x + threadIdx.x;
+            if (i < st.N) {
+                if (KIND == 0) {            // pass-1 gather
+                    float mm[9];
+                    gather1_row<4>(st, c, i, mm);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) st.fsum[k * st.N + i] = mm[k];
-            } else if (KIND == 1) {     // pass-1 per-particle update
-                float mm[9];
+                    for (int k = 0; k < 9; ++k) st.fsum[k * st.N + i] = mm[k];
+                } else if (KIND == 1) {     // pass-1 per-particle update
+                    float mm[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) mm[k] = st.fsum[k * st.N + i];
-                epi1_mixed(st, c, i, mm);
-            } else {                    // pass 2
-                float acc[9];
-                gather2_row<HG, 2>(st, c, i, acc);
-                epi2_mixed<HG>(st, c, i, acc);
+                    for (int k = 0; k < 9; ++k) mm[k] = st.fsum[k * st.N + i];
+                    epi1_mixed(st, c, i, mm);
+                } else {                    // pass 2
+                    float acc[9];
+                    gather2_row<HG, 2>(st, c, i, acc);
+                    epi2_mixed<HG>(st, c, i, acc);
+                }
             }
         }
-        __syncthreads();
     }
 }
 
 // the FP64 updates queued by every member in this step (persistent grid over
-// the members' queues); clears each member's queue counter of the next step
+// the members' queues; the members' queue lengths are read in parallel, 1024
+// members at a time, so empty queues cost nothing); clears each member's queue
+// counter of the next step
 __global__ void __launch_bounds__(128) k_batch_slow(const BatchHdr *hdr, BatchSlot *slots)
 {
+    __shared__ uint32_t cnt[1024];
     const int nspec = hdr->nspec;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    for (int m = 0; m < nspec; ++m) {
-        const BatchSlot &sl = slots[m];
-        const uint32_t n = sl.s.slowq_n[sl.c.step_index & 1];
-        for (uint32_t q = t; q < n; q += stride) epi1_slow(sl.s, sl.c, sl.s.slowq[q]);
+    for (int m0 = 0; m0 < nspec; m0 += 1024) {
+        const int mn = min(1024, nspec - m0);
+        for (int k = threadIdx.x; k < mn; k += blockDim.x) {
+            const BatchSlot &sl = slots[m0 + k];
+            cnt[k] = sl.s.slowq_n[sl.c.step_index & 1];
+        }
+        __syncthreads();
+        for (int k = 0; k < mn; ++k) {
+            const uint32_t n = cnt[k];
+            if (n == 0) continue;
+            const BatchSlot &sl = slots[m0 + k];
+            for (uint32_t q = t; q < n; q += stride) epi1_slow(sl.s, sl.c, sl.s.slowq[q]);
+        }
+        __syncthreads();
     }
     for (uint32_t m = t; m < (uint32_t)nspec; m += stride) slots[m].s.slowq_n[(slots[m].c.step_index + 1) & 1] = 0u;
 }
 
 // end of a step: flip the ping-pong buffers and count the step, per slot
-__global__ void k_batch_advance(const BatchHdr *hdr, BatchSlot *slots)
+__global__ void k_batch_advance(BatchHdr *hdr, BatchSlot *slots)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) hdr->next[0] = hdr->next[1] = hdr->next[2] = 0ull;   // the kernels of this step are done
     if (k >= hdr->nspec) return;
     slots[k].c.ucur ^= 1;
     slots[k].c.dcur ^= 1;
@@ -1487,15 +1533,15 @@ BatchSlot make_batch_slot(const tlsph_ctx &ctx)
 // registers capped for 8 (pass-1 gather), 3 (per-particle update) and 6
 // (pass 2, as the single-context plan form 4) blocks of 128 per SM
 template <bool HG>
-static void batch_kernels(const BatchHdr *hdr, BatchSlot *slots, const int *grid, cudaStream_t st)
+static void batch_kernels(BatchHdr *hdr, BatchSlot *slots, const int *grid, cudaStream_t st)
 {
-    k_batch<0, HG, 8><<<grid[0], 128, 0, st>>>(hdr, slots);
-    k_batch<1, HG, 3><<<grid[1], 128, 0, st>>>(hdr, slots);
+    k_batch<0, HG, BATCH_MINB0><<<grid[0], 128, 0, st>>>(hdr, slots);
+    k_batch<1, HG, BATCH_MINB1><<<grid[1], 128, 0, st>>>(hdr, slots);
     k_batch_slow<<<grid[3], 128, 0, st>>>(hdr, slots);
-    k_batch<2, HG, 6><<<grid[2], 128, 0, st>>>(hdr, slots);
+    k_batch<2, HG, BATCH_MINB2><<<grid[2], 128, 0, st>>>(hdr, slots);
 }
 
-cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, const int *grid,
+cudaError_t launch_batch_step(BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, const int *grid,
                               cudaStream_t st)
 {
     if (hg) batch_kernels<true>(hdr, slots, grid, st);
@@ -1507,9 +1553,9 @@ cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, 
 template <bool HG>
 static void batch_occupancy(int *per)
 {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_batch<0, HG, 8>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_batch<1, HG, 3>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_batch<2, HG, 6>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_batch<0, HG, BATCH_MINB0>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_batch<1, HG, BATCH_MINB1>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_batch<2, HG, BATCH_MINB2>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], k_batch_slow, 128, 0);
 }
 

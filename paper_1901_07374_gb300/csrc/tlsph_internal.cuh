@@ -250,10 +250,11 @@ struct BatchHdr {
     int nspec;
     int64_t total_blk;
     const int64_t *blk0;    // nspec first work blocks, ascending (device, after the slots)
+    unsigned long long next[3];   // work-block counters of the three persistent kernels (zero between steps)
 };
 BatchSlot make_batch_slot(const tlsph_ctx &ctx);
 // grid: the persistent grid of each of the four kernel kinds (batch_grid)
-cudaError_t launch_batch_step(const BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, const int *grid,
+cudaError_t launch_batch_step(BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, const int *grid,
                               cudaStream_t st);
 void batch_grid(bool hg, int *grid);
 
