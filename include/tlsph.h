@@ -237,7 +237,7 @@ int tlsph_destroy(tlsph_ctx *ctx);
  * gather + per-particle kernel; 3 thread per row, one pair in flight; 4 as
  * 1 with registers capped for six resident blocks; 5 as 3 with registers
  * capped for eight resident blocks; 6 as 1 capped for seven resident blocks;
- * block size at most 128 for 4 to 6),
+ * 7 as 1 capped for five resident blocks; block size at most 128 for 4 to 7),
  * plan[3] its block size (multiples of 32 up to 256).  Every plan computes
  * the same method; sums over a row are grouped differently, so results
  * differ only by FP32 rounding.  n must be 4.  TLSPH_ERR_ARG for a plan out

@@ -1037,6 +1037,17 @@ __global__ void __launch_bounds__(128, 7) k_pass2_mixed_tc7(DevState s, MixConst
     epi2_mixed<HG>(s, c, i, acc);
 }
 
+// two pairs in flight, registers capped so that five blocks of 128 fit an SM
+template <bool HG>
+__global__ void __launch_bounds__(128, 5) k_pass2_mixed_tc5(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float acc[9];
+    gather2_row<HG, 2>(s, c, i, acc);
+    epi2_mixed<HG>(s, c, i, acc);
+}
+
 // two pairs in flight, registers capped so that six blocks of 128 fit an SM
 template <bool HG>
 __global__ void __launch_bounds__(128, 6) k_pass2_mixed_tc(DevState s, MixConst c)
@@ -1303,8 +1314,9 @@ int mixed_slow_grid()
 //           4 = as 2 with four pairs in flight per thread
 //   pass 2: 0 = warp per 32 rows;  1 = thread per row;  2 = thread-per-row gather + per-particle kernel;
 //           3 = thread per row, one pair in flight;  4 = thread per row, registers capped for 6 blocks of 128;
-//           5 = as 3 with registers capped for 8 blocks of 128;  6 = as 1 with registers capped for 7 blocks of 128
-// block sizes are multiples of 32 up to 256 (128 for the fused warp forms and pass-2 forms 4 to 6).
+//           5 = as 3 with registers capped for 8 blocks of 128;  6 = as 1 with registers capped for 7 blocks of 128;
+//           7 = as 1 with registers capped for 5 blocks of 128
+// block sizes are multiples of 32 up to 256 (128 for the fused warp forms and pass-2 forms 4 to 7).
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev)
 {
     const MixConst c = make_mix_const(ctx, step_index);
@@ -1343,6 +1355,9 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
     } else if (v2 == 6) {
         if (hg) k_pass2_mixed_tc7<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
         else k_pass2_mixed_tc7<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+    } else if (v2 == 7) {
+        if (hg) k_pass2_mixed_tc5<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+        else k_pass2_mixed_tc5<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
     } else if (v2 == 5) {
         if (hg) k_pass2_mixed_t1c<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
         else k_pass2_mixed_t1c<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
