@@ -74,9 +74,6 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # same kernel build, keyed by (workload, precision, pass, plan form of that
 # pass); absent for other plans and once the kernels change after the capture
 TRAFFIC = {
-    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 551708672,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 1): 318416640,   # k_pass2_mixed_t
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 318825984,   # k_pass2_mixed_tc
 }
 
 

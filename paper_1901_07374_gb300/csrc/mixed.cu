@@ -170,6 +170,17 @@ __device__ __forceinline__ float spline_dw_ab(float q, float &a, float &b)
 }
 __device__ __forceinline__ float spline_w_ab(float a, float b) { return fmaf(0.25f * a * a, a, -b * b * b); }
 
+// kernel-argument offset of a padding slot: q >= 2 for any pair distance
+constexpr float SLOT_PAD_Q = 4.0f;
+
+// approximate reciprocal, one MUFU operation (relative error about 1 ulp)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ------------------------------------------------------------------ sliced neighbour lists
 // The thread-per-row kernels read neighbours slice by slice, a slice being the
 // 32 consecutive rows of one warp.  A slice is stored in one of two forms:
@@ -317,16 +328,19 @@ __device__ __forceinline__ void aligned_slots(const int32_t *__restrict__ base, 
         for (int u = 0; u < U; ++u) {
             const unsigned ju = (unsigned)ii + (unsigned)o[u];   // modular: a negative index wraps high
             j[u] = (CLAMP && ju >= (unsigned)N) ? alt : (int)ju;
-            w[u] = (bits & (1u << u)) ? 1.0f : 0.0f;
+            w[u] = (bits & (1u << u)) ? 0.0f : SLOT_PAD_Q;
         }
         bits >>= U;
         body(j, w);
     }
 }
 
-// Neighbour slots of row i in groups of U (U divides 32): body(j[U], w[U]) for
-// each group, w = 1 for a neighbour and 0 for a padding slot (whose j is a
-// valid particle other than i, so its terms are finite).
+// Neighbour slots of row i in groups of U (U divides 32): body(j[U], qpad[U])
+// for each group, qpad = 0 for a neighbour and SLOT_PAD_Q for a padding slot
+// (whose j is a valid particle other than i, so its terms are finite).  The
+// pair terms add qpad to the kernel argument q = r / h: a padding slot lands
+// outside the kernel's support (q >= 2), where W and W' are exactly zero, so
+// its terms vanish without a weight multiply.
 template <int U, class Body>
 __device__ __forceinline__ void for_slots(const DevState &s, int64_t i, Body &&body)
 {
@@ -349,7 +363,7 @@ __device__ __forceinline__ void for_slots(const DevState &s, int64_t i, Body &&b
                 const int kk = k + u;
                 const int jj = kk < wv ? cp[32 * kk] : ~alt;
                 j[u] = jj >= 0 ? jj : ~jj;
-                w[u] = jj >= 0 ? 1.0f : 0.0f;
+                w[u] = jj >= 0 ? 0.0f : SLOT_PAD_Q;
             }
             body(j, w);
         }
@@ -709,13 +723,13 @@ __global__ void __launch_bounds__(128) k_epi1_slow(DevState s, MixConst c)
 
 // ------------------------------------------------------------------ pass 1 pair terms
 __device__ __forceinline__ void pair1(const MixConst &c, const int4 oi, const float4 vi, const int4 oj,
-                                      const float4 vj, float wmask, float *m)
+                                      const float4 vj, float qpad, float *m)
 {
     const float3 d = xdiff(oj, oi);
     const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
     const float rinv = rsqrtf(r2);
     float a, b;
-    const float cw = wmask * vj.w * spline_dw_ab(r2 * rinv * c.inv_h, a, b) * rinv;   // V_j (1 - D_j) W'/r
+    const float cw = vj.w * spline_dw_ab(fmaf(r2 * rinv, c.inv_h, qpad), a, b) * rinv;   // V_j (1 - D_j) W'/r
     const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
     m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
     m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
@@ -756,7 +770,7 @@ __device__ __forceinline__ void gather1_w32(const DevState &s, const MixConst &c
         for (int k = 0; k < 9; ++k) m[k] = 0.0f;
         for (int64_t p = p0 + lane; p < p1; p += 32) {
             const int j = s.col[p];
-            pair1(c, oi, vi, s.xo[j], s.r1[j], 1.0f, m);
+            pair1(c, oi, vi, s.xo[j], s.r1[j], 0.0f, m);
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -918,7 +932,7 @@ __device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, 
 }
 
 template <bool HG>
-__device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, const Row2 &w, int j, float wmask,
+__device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, const Row2 &w, int j, float qpad,
                                       float *acc)
 {
     const int4 oj = s.xo[j];
@@ -927,9 +941,9 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
     const float3 d = xdiff(oj, w.o);
     const float r2v = d.x * d.x + d.y * d.y + d.z * d.z;
     const float rinv = rsqrtf(r2v);
-    const float q = r2v * rinv * c.inv_h;
+    const float q = fmaf(r2v * rinv, c.inv_h, qpad);
     float a, b;
-    const float g0 = wmask * spline_dw_ab(q, a, b) * rinv;
+    const float g0 = spline_dw_ab(q, a, b) * rinv;
     const float g = b2.z * g0;                     // V_j W'/r
     const float gd = b2.y * g0;                    // V_j D_j W'/r
     acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
@@ -942,12 +956,12 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
         // u_ij, x_ij = X_ij + u_ij, e = ((F_i - I) + (F_j - I)) X_ij - 2 u_ij
         const float ux = b2.w - w.a2.w, uy = b3.x - w.a3.x, uz = b3.y - w.a3.y;
         const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
-        const float lxi = rsqrtf(xx * xx + xy * xy + xz * xz);
+        const float lxi2 = rcp_approx(xx * xx + xy * xy + xz * xz);    // 1 / |x_ij|^2
         const float ex = (w.a3.z + b3.z) * d.x + (w.a3.w + b3.w) * d.y + (w.a4.x + b4.x) * d.z - 2.0f * ux;
         const float ey = (w.a4.y + b4.y) * d.x + (w.a4.z + b4.z) * d.y + (w.a4.w + b4.w) * d.z - 2.0f * uy;
         const float ez = (w.a5.x + b5.x) * d.x + (w.a5.y + b5.y) * d.y + (w.a5.z + b5.z) * d.z - 2.0f * uz;
-        const float delta = (ex * xx + ey * xy + ez * xz) * lxi;
-        const float ch = wmask * b5.w * spline_w_ab(a, b) * rinv * rinv * delta * lxi;   // sqrt(E_j) V_j (1 - D_j) ...
+        // sqrt(E_j) V_j (1 - D_j) W / X_ij^2 * delta / |x_ij| with delta = (e . x_ij) / |x_ij|
+        const float ch = b5.w * spline_w_ab(a, b) * rinv * rinv * (ex * xx + ey * xy + ez * xz) * lxi2;
         acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
     }
 }
@@ -969,7 +983,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixCons
         float acc[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-        for (int64_t p = p0 + lane; p < p1; p += 32) pair2<HG>(s, c, w, s.col[p], 1.0f, acc);
+        for (int64_t p = p0 + lane; p < p1; p += 32) pair2<HG>(s, c, w, s.col[p], 0.0f, acc);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             if (!HG && k >= 6) continue;
@@ -1233,7 +1247,7 @@ __global__ void __launch_bounds__(256) k_shape_mixed(DevState s, float inv_h, do
             const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
             const float rinv = rsqrtf(r2);
             float a, b;
-            const float c0 = w[u] * (float)s.vol[j[u]] * spline_dw_ab(r2 * rinv * inv_h, a, b) * rinv;
+            const float c0 = (float)s.vol[j[u]] * spline_dw_ab(fmaf(r2 * rinv, inv_h, w[u]), a, b) * rinv;
             kahan_add(sm[0], cp[0], c0 * d.x);
             kahan_add(sm[1], cp[1], c0 * d.y);
             kahan_add(sm[2], cp[2], c0 * d.z);
