@@ -193,7 +193,7 @@ def mixed_algorithmic_bytes(N: int, list_words: int):
 #         hourglass: u_ij 3, x_ij 3, 1/|x_ij| 4, error vector 21, projection 4,
 #         W(q) from the W' terms 5, coefficient 6, 3 sums                 = 49
 # (an integer-to-float conversion of a position difference counts as one)
-MIXED_FP32_OPS_PER_PAIR = {"pass1": 38, "pass2": 49, "pass2_hourglass": 49}
+MIXED_FP32_OPS_PER_PAIR = {"pass1": 37, "pass2": 48, "pass2_hourglass": 47}
 
 
 def mixed_fp32_ops(nnz: int, hourglass: bool = True):
