@@ -1436,8 +1436,10 @@ __device__ __forceinline__ int batch_find(const int64_t *blk0, int n, int64_t w)
 // block's work moves to another member), so the kernels read the member's
 // arrays and constants from registers and shared memory rather than through
 // global loads that stores into the state could alias.  Blocks take their work
-// in chunks of BATCH_CHUNK consecutive work blocks from a counter: dynamic
-// balance across members of different cost.  Measured on 256 bars of 2k-200k
+// in chunks of BATCH_CHUNK consecutive work blocks: its first chunk by its own
+// index, every later one from a counter (dynamic balance across members of
+// different cost; blocks of a grid larger than the work leave at once, so a
+// batch of a few small members pays no contention on the counter).  Measured on 256 bars of 2k-200k
 // particles: one work block per grab 9.54 ms per step, 4 per grab 9.78 ms, 16
 // per grab 10.8 ms, and a static strided assignment 11.3 ms.  The member of a
 // chunk is found by a search over the first-block table (a few hundred bytes,
@@ -1469,12 +1471,11 @@ __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchS
     const int64_t total = hdr->total_blk;
     const int64_t *blk0 = hdr->blk0;
     int cur = -1;
+    // the first chunk is the block's own (blocks without one leave at once, touching no counter);
+    // later chunks come from the counter, after the grid's first chunks
+    int64_t wb = (int64_t)blockIdx.x * BATCH_CHUNK;
     for (;;) {
-        __syncthreads();                // every thread has read the previous chunk's start
-        if (threadIdx.x == 0) grab = (int64_t)atomicAdd(&hdr->next[KIND], (unsigned long long)BATCH_CHUNK);
-        __syncthreads();
-        const int64_t wb = grab;
-        if (wb >= total) break;
+        if (wb >= total) break;         // uniform over the block
         const int64_t we = min(total, wb + (int64_t)BATCH_CHUNK);
         int m = batch_find(blk0, nspec, wb);
         for (int64_t w = wb; w < we; ++w) {
@@ -1508,6 +1509,12 @@ __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchS
                 }
             }
         }
+        __syncthreads();                // every thread has read the previous chunk's start
+        if (threadIdx.x == 0)
+            grab = (int64_t)gridDim.x * BATCH_CHUNK +
+                   (int64_t)atomicAdd(&hdr->next[KIND], (unsigned long long)BATCH_CHUNK);
+        __syncthreads();
+        wb = grab;
     }
 }
 
