@@ -72,7 +72,7 @@ class System(ctypes.Structure):
                 ("row_ptr", _P(ctypes.c_int64)), ("col", _P(ctypes.c_int32)), ("Linv", _d),
                 ("mats", _P(Material)),
                 ("u", _d), ("v", _d), ("F", _d), ("sd", _d), ("sigma", _d), ("A", _d),
-                ("ep", _d), ("epdot", _d), ("dinit", _d), ("D", _d), ("f", _d),
+                ("ep", _d), ("epdot", _d), ("dinit", _d), ("D", _d), ("f", _d), ("e", _d),
                 ("force", _d), ("fail_step", _P(ctypes.c_int32)),
                 ("step", ctypes.c_int64), ("status", ctypes.c_uint32),
                 ("vh", _d), ("Fdot", _d)]
@@ -101,7 +101,7 @@ def lib():
             L.orc_eig_sym.restype = None
             L.orc_eig_sym.argtypes = [vp, vp]
             L.orc_eos_mean_stress.restype = ctypes.c_double
-            L.orc_eos_mean_stress.argtypes = [_P(Material), ctypes.c_double, ctypes.c_double]
+            L.orc_eos_mean_stress.argtypes = [_P(Material), ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.orc_flow_stress.restype = ctypes.c_double
             L.orc_flow_stress.argtypes = [_P(Material), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double]
@@ -209,9 +209,11 @@ def eig_sym(S: np.ndarray) -> np.ndarray:
     return ev
 
 
-def eos_mean_stress(mat: dict, J: float, D: float = 0.0) -> float:
+def eos_mean_stress(mat: dict, J: float, D: float = 0.0, e: float = 0.0) -> float:
+    """Tension-positive mean stress of Eq. pH at J = det F, damage D and
+    specific internal energy e."""
     m = make_material(mat)
-    return lib().orc_eos_mean_stress(ctypes.byref(m), float(J), float(D))
+    return lib().orc_eos_mean_stress(ctypes.byref(m), float(J), float(D), float(e))
 
 
 def flow_stress(mat: dict, ep: float, epdot: float = 0.0, D: float = 0.0) -> float:
@@ -272,7 +274,7 @@ def mat_det(a: np.ndarray) -> float:
 # ---------------------------------------------------------------- full system
 
 STATE_FIELDS = {"u": 3, "v": 3, "F": 9, "sd": 9, "sigma": 9, "A": 9, "ep": 1, "epdot": 1,
-                "dinit": 1, "D": 1, "f": 1, "force": 3}
+                "dinit": 1, "D": 1, "f": 1, "e": 1, "force": 3}
 
 
 class Simulation:

@@ -36,6 +36,7 @@
  *   GTN nucleation, growth, omega                  Sec. 5.4, Eqs. (GTN_damage_nucleation), (GTN_damage_growth), (omega)
  *   GTN return with two Newton solves              Sec. 5.4, Algorithm 2 and the derivation after it
  *   grip velocity ramp v_max (1 - e^{-t})          Sec. 6 (specimens and loading)
+ *   internal energy de/dt = Fdot : P / rho0        Sec. 2.1, Eq. (conservation3); enters Eq. (pH)
  *
  * Where the paper is silent or garbled the oracle takes the readings listed
  * in the design notes (kernel form, integrator, frame, EOS sign, lagged rate,
@@ -372,7 +373,7 @@ static double shear_modulus(const orc_material *m) { return m->E / (2.0 * (1.0 +
  * With S_alpha = Gamma0 = 0 and rho0 c0^2 = K this is sigma_m = K (J - 1)
  * exactly; the linear EOS (eos = 0) uses K = E / (3 (1 - 2 nu)).
  * Internal energy is not tracked (Gamma0 e term taken as zero). */
-double orc_eos_mean_stress(const orc_material *m, double J, double D)
+double orc_eos_mean_stress(const orc_material *m, double J, double D, double e)
 {
     double sm;
     if (m->eos == 0) {
@@ -381,7 +382,11 @@ double orc_eos_mean_stress(const orc_material *m, double J, double D)
         double eta = 1.0 / J;
         double mu = eta - 1.0;
         double den = eta - m->S_alpha * mu;
-        double p = m->rho0 * m->c0 * m->c0 * mu * (eta - 0.5 * m->Gamma0 * mu) / (den * den);
+        /* Hugoniot part plus the energy term: Eq. pH writes Gamma0 e, which has
+         * the units of a pressure only with e per unit reference volume;
+         * reading: e per unit mass (Eq. conservation3), term Gamma0 rho0 e */
+        double p = m->rho0 * m->c0 * m->c0 * mu * (eta - 0.5 * m->Gamma0 * mu) / (den * den)
+                 + m->Gamma0 * m->rho0 * e;
         sm = -p;
     }
     if (sm > 0.0) sm *= (1.0 - D);
@@ -447,6 +452,7 @@ typedef struct {
     double dinit;      /* damage initiation variable */
     double D;          /* damage */
     double f;          /* void volume fraction (GTN) */
+    double e;          /* specific internal energy at the start of the update (enters the EOS) */
     int32_t failed;
     int32_t newton_its;/* diagnostics: iterations of the last GTN solves */
 } orc_mp_state;
@@ -510,7 +516,7 @@ static double gtn_return(const orc_material *m, double dt, const double *ded, do
     double G = shear_modulus(m), K = bulk_modulus(m);
     double f = st->f;
     double fs = orc_gtn_fstar(m, f);
-    double sm_tr = orc_eos_mean_stress(m, J, D);
+    double sm_tr = orc_eos_mean_stress(m, J, D, st->e);
     double tr_s[9];
     for (int k = 0; k < 9; ++k) tr_s[k] = st->sd[k] + 2.0 * G * (1.0 - D) * ded[k];
     double seq = von_mises(tr_s);
@@ -638,7 +644,7 @@ unsigned orc_constitutive(const orc_material *m, double dt, const double *deps, 
         dep = gtn_return(m, dt, ded, J, D, st, &status);
     } else {
         dep = radial_return_jc(m, dt, ded, D, st);
-        st->sm = orc_eos_mean_stress(m, J, D);
+        st->sm = orc_eos_mean_stress(m, J, D, st->e);
     }
     damage_update(m, dt, dep, st);
     if (st->failed) {
@@ -670,6 +676,7 @@ typedef struct {
     double *sigma;            /* N*9 Cauchy stress (current frame) */
     double *A;                /* N*9 P L^{-T} */
     double *ep, *epdot, *dinit, *D, *f;  /* N each */
+    double *e;                /* N   specific internal energy */
     double *force;            /* N*3 */
     int32_t *fail_step;       /* N, -1 while intact */
     int64_t step;
@@ -778,13 +785,23 @@ static void particle_update(orc_system *s, const orc_config *c, int64_t i)
     memcpy(st.sd, s->sd + 9 * i, sizeof st.sd);
     st.sm = 0.0;
     st.ep = s->ep[i]; st.epdot = s->epdot[i]; st.dinit = s->dinit[i];
-    st.D = s->D[i]; st.f = s->f[i]; st.failed = 0; st.newton_its = 0;
+    st.D = s->D[i]; st.f = s->f[i]; st.e = s->e[i]; st.failed = 0; st.newton_its = 0;
     s->status |= orc_constitutive(m, c->dt, deps, J, &st);
     memcpy(s->sd + 9 * i, st.sd, sizeof st.sd);
     s->ep[i] = st.ep; s->epdot[i] = st.epdot; s->dinit[i] = st.dinit;
     s->f[i] = st.f;
     s->D[i] = st.D;
+    /* internal energy, Eq. (conservation3): de/dt = Fdot : P / rho0 = J sigma : d / rho0.
+     * Reading: trapezoidal in the step (second order, like the velocity-Verlet
+     * kinetic energy), in the current frame with the step's J and d:
+     *   e^{n+1} = e^n + dt J / rho0 * (sigma^n + sigma^{n+1}) / 2 : d
+     * with sigma^n the stress at the start of the step and sigma^{n+1} = 0
+     * for a particle that fails in the step (the EOS of the step used e^n). */
+    const double *sg_n = s->sigma + 9 * i;
     if (st.failed) {
+        double w = 0.0;
+        for (int k = 0; k < 9; ++k) w += 0.5 * sg_n[k] * d[k];
+        s->e[i] += c->dt * J / m->rho0 * w;
         s->fail_step[i] = (int32_t)(s->step + 1);
         memset(s->sigma + 9 * i, 0, 9 * sizeof(double));
         memset(s->A + 9 * i, 0, 9 * sizeof(double));
@@ -797,6 +814,11 @@ static void particle_update(orc_system *s, const orc_config *c, int64_t i)
     sh[0] += st.sm; sh[4] += st.sm; sh[8] += st.sm;
     mat_mul(R, sh, tmp);
     mat_mul(tmp, RT, sg);
+    {
+        double w = 0.0;
+        for (int k = 0; k < 9; ++k) w += 0.5 * (sg_n[k] + sg[k]) * d[k];
+        s->e[i] += c->dt * J / m->rho0 * w;
+    }
     memcpy(s->sigma + 9 * i, sg, sizeof sg);
     mat_transpose(Finv, FiT);
     mat_mul(sg, FiT, P);
@@ -926,7 +948,7 @@ void orc_init_state(orc_system *s)
             s->F[9 * i + k] = (k % 4 == 0) ? 1.0 : 0.0;
             s->sd[9 * i + k] = 0.0; s->sigma[9 * i + k] = 0.0; s->A[9 * i + k] = 0.0;
         }
-        s->ep[i] = 0.0; s->epdot[i] = 0.0; s->dinit[i] = 0.0;
+        s->ep[i] = 0.0; s->epdot[i] = 0.0; s->dinit[i] = 0.0; s->e[i] = 0.0;
         s->D[i] = (m->damage == 3) ? m->q1 * orc_gtn_fstar(m, s->f[i]) : 0.0;
         s->fail_step[i] = -1;
     }
@@ -944,6 +966,7 @@ unsigned orc_material_point(const orc_material *m, double dt, int64_t n, const d
     memcpy(st.sd, init, 9 * sizeof(double));
     st.sm = init[9]; st.ep = init[10]; st.epdot = init[11]; st.dinit = init[12];
     st.D = init[13]; st.f = init[14]; st.failed = (int32_t)init[15]; st.newton_its = 0;
+    st.e = 0.0;        /* the material-point driver holds the internal energy at zero */
     unsigned status = 0;
     for (int64_t k = 0; k < n; ++k) {
         status |= orc_constitutive(m, dt, deps + 9 * k, J[k], &st);

@@ -64,7 +64,8 @@ static int run(int damage)
     s.u = calloc(3 * N, sizeof(double)); s.v = calloc(3 * N, sizeof(double)); s.F = calloc(9 * N, sizeof(double));
     s.sd = calloc(9 * N, sizeof(double)); s.sigma = calloc(9 * N, sizeof(double)); s.A = calloc(9 * N, sizeof(double));
     s.ep = calloc(N, sizeof(double)); s.epdot = calloc(N, sizeof(double)); s.dinit = calloc(N, sizeof(double));
-    s.D = calloc(N, sizeof(double)); s.f = f0; s.force = calloc(3 * N, sizeof(double));
+    s.D = calloc(N, sizeof(double)); s.f = f0; s.e = calloc(N, sizeof(double));
+    s.force = calloc(3 * N, sizeof(double));
     s.fail_step = calloc(N, sizeof(int32_t)); s.vh = calloc(3 * N, sizeof(double)); s.Fdot = calloc(9 * N, sizeof(double));
     orc_init_state(&s);
     orc_config c = { h, rc, 0.3 * d / 5907.6, 10.0, 1 };
@@ -79,7 +80,7 @@ static int run(int damage)
            epmax, (long long)failed, s.status);
     free(X); free(vol); free(mat); free(bcm); free(bcv); free(row_ptr); free(col); free(L); free(Linv); free(f0);
     free(s.u); free(s.v); free(s.F); free(s.sd); free(s.sigma); free(s.A); free(s.ep); free(s.epdot); free(s.dinit);
-    free(s.D); free(s.force); free(s.fail_step); free(s.vh); free(s.Fdot);
+    free(s.D); free(s.e); free(s.force); free(s.fail_step); free(s.vh); free(s.Fdot);
     return epmax > 0.0 ? 0 : 1;
 }
 

@@ -307,3 +307,75 @@ def test_paper_loading_drives_the_grips_apart():
     top = w.specimen.bc_mask.astype(bool) & (w.specimen.bc_vel[:, 2] > 0)
     t = 20 * w.dt
     assert np.allclose(o["v"][top, 2], 10.0 * -np.expm1(-t / 1e-3), rtol=1e-14)
+
+
+@pytest.mark.parametrize("eos", ["linear", "mie_grueneisen"])
+def test_internal_energy_closes_the_energy_balance(eos):
+    """Eq. conservation3, de/dt = Fdot : P / rho0, integrated per particle: in
+    an elastic free vibration without hourglass control the kinetic energy
+    plus sum_i m_i e_i stays constant, the internal energy equals the strain
+    energy (1/2) sum V sigma : eps of the small-strain state, and it never
+    goes negative.  With a Mie-Grueneisen EOS and Gamma0 = 2 the energy term
+    of Eq. pH feeds back into the stress and the balance still closes."""
+    if eos == "linear":
+        mat = S.material(A=1e12, damage=0)
+    else:
+        mat = S.material(A=1e12, damage=0, eos=1, c0=5166.0, S_alpha=1.5, Gamma0=2.0)
+    sim, sp = _free_bar(dims=(5, 5, 12), seed=6, mat=mat)
+    z = sp.X[:, 2] / sp.X[:, 2].max()
+    sim["v"][:, 2] = 0.05 * np.cos(np.pi * z)
+    m = sim.vol * mat["rho0"]
+    e0 = 0.5 * np.sum(m[:, None] * sim["v"] ** 2)
+    worst = 0.0
+    for k in range(20):
+        sim.step(10)
+        ek = 0.5 * np.sum(m[:, None] * sim["v"] ** 2)
+        ei = np.sum(m * sim["e"])
+        worst = max(worst, abs(ek + ei - e0) / e0)
+        _, _, strain = _energy(sim, mat["rho0"])
+        assert ei == pytest.approx(strain, rel=2e-2, abs=2e-3 * e0)
+        assert ei >= -1e-6 * e0
+    assert worst < 3e-3, worst
+
+
+def test_mie_grueneisen_energy_term():
+    """Eq. pH with the energy term read as Gamma0 rho0 e (e per unit mass):
+    at J = 1 the Hugoniot part vanishes and sigma_m = -Gamma0 rho0 e; in
+    tension the (1 - D) factor scales the whole mean stress; the linear EOS
+    ignores e."""
+    mg = S.material(A=1e12, eos=1, c0=5166.0, S_alpha=1.5, Gamma0=2.0)
+    lin = S.material(A=1e12)
+    e = 1234.5
+    assert oracle.eos_mean_stress(mg, 1.0, 0.0, e) == pytest.approx(-2.0 * mg["rho0"] * e, rel=1e-15)
+    assert oracle.eos_mean_stress(mg, 1.0, 0.0, -e) == pytest.approx(2.0 * mg["rho0"] * e * 1.0, rel=1e-15)
+    assert oracle.eos_mean_stress(mg, 1.0, 0.3, -e) == pytest.approx(0.7 * 2.0 * mg["rho0"] * e, rel=1e-15)
+    for J in (0.98, 1.0, 1.02):
+        assert oracle.eos_mean_stress(lin, J, 0.0, e) == oracle.eos_mean_stress(lin, J, 0.0, 0.0)
+        d = oracle.eos_mean_stress(mg, J, 0.0, e) - oracle.eos_mean_stress(mg, J, 0.0, 0.0)
+        if J <= 1.0:       # compression: no damage scaling, the term adds linearly
+            assert d == pytest.approx(-2.0 * mg["rho0"] * e, rel=1e-9)
+
+
+def test_internal_energy_under_uniform_compression_closed_form():
+    """Every particle driven with the affine velocity v = -beta (X - X_c): F =
+    (1 - beta t) I exactly (first-order completeness, Sec. 2.2), sigma =
+    K (J - 1) I (linear EOS, no deviator), and Eq. conservation3 integrates to
+    e = K (J - 1)^2 / (2 rho0).  At J = 0.90 the J factor of
+    Fdot : P = J sigma : d is 10 % of the answer, so this pins it."""
+    mat = S.material(A=1e12, damage=0)
+    sp = S.tensile_bar(4, 4, 5, 0.5e-3, jitter=0.01, seed=2)
+    c = sp.X.mean(0)
+    steps = 400
+    dt = S.cfl_dt(mat, 0.5e-3)
+    beta = (1.0 - 0.9 ** (1.0 / 3.0)) / (steps * dt)
+    sp.bc_mask[:] = 1
+    sp.bc_vel[:] = -beta * (sp.X - c)
+    h = 0.75e-3
+    w = S.Workload("squeeze", sp, [mat], h, 2 * h, dt, 0.0, 0)
+    o = oracle.Simulation.from_workload(w)
+    o.step(steps)
+    J = np.linalg.det(o["F"].reshape(-1, 3, 3))
+    assert np.allclose(J, 0.9, rtol=1e-9)
+    K = mat["E"] / (3.0 * (1.0 - 2.0 * mat["nu"]))
+    exact = K * (J - 1.0) ** 2 / (2.0 * mat["rho0"])
+    assert np.allclose(o["e"], exact, rtol=2e-3), (o["e"][:3], exact[:3])
