@@ -133,7 +133,8 @@ typedef enum {
     TLSPH_FIELD_U = 1,          /* f64 N*3  displacement u^n */
     TLSPH_FIELD_V = 2,          /* f64 N*3  velocity v^n */
     TLSPH_FIELD_F = 3,          /* f64 N*9  deformation gradient F^n */
-    TLSPH_FIELD_SIGMA = 4,      /* f64 N*9  Cauchy stress (current frame, read only) */
+    TLSPH_FIELD_SIGMA = 4,      /* f64 N*9  Cauchy stress (current frame; the next step's internal-energy
+                                                update starts from it) */
     TLSPH_FIELD_STRESS_DEV = 5, /* f64 N*9  unrotated deviatoric stress (the constitutive state) */
     TLSPH_FIELD_EPSP = 6,       /* f64 N    equivalent plastic strain (matrix strain for GTN) */
     TLSPH_FIELD_EPSP_RATE = 7,  /* f64 N    plastic strain rate of the last step */
@@ -147,7 +148,8 @@ typedef enum {
     TLSPH_FIELD_NBR_ROWPTR = 15,/* i64 N+1  neighbour CSR row pointers (read only) */
     TLSPH_FIELD_NBR_COL = 16,   /* i32 nnz  neighbour CSR columns, rows ascending (read only) */
     TLSPH_FIELD_STEP = 17,      /* i64 1    number of completed steps (failure steps count from it) */
-    TLSPH_FIELD_COUNT = 18
+    TLSPH_FIELD_ENERGY = 18,    /* f64 N    specific internal energy e (J/kg; Sec. 2.1, Eq. conservation3) */
+    TLSPH_FIELD_COUNT = 19
 } tlsph_field;
 
 /* Bytes of device memory a context needs for N particles and up to nnz_cap

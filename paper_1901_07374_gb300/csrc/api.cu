@@ -27,7 +27,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 // F / sd / sig / A block, which is only initialised after the build.
 struct Layout {
     size_t X, vol, mass, inv_mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
-    size_t ep, epdot, dinit, por, D0, D1, force, fail, status, mats, col, diag;
+    size_t ep, epdot, dinit, por, e, D0, D1, force, fail, status, mats, col, diag;
     size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp, xf;
@@ -197,6 +197,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.epdot = c.take(n * d);
     L.dinit = c.take(n * d);
     L.por = c.take(n * d);
+    L.e = c.take(n * d);
     L.D0 = c.take(n * d);
     L.D1 = c.take(n * d);
     L.force = c.take(3 * n * d);
@@ -337,6 +338,7 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
     s.epdot = at<double>(base, L.epdot);
     s.dinit = at<double>(base, L.dinit);
     s.por = at<double>(base, L.por);
+    s.e = at<double>(base, L.e);
     s.D[0] = at<double>(base, L.D0);
     s.D[1] = at<double>(base, L.D1);
     s.force = at<double>(base, L.force);
@@ -361,7 +363,7 @@ FieldInfo field_info(tlsph_ctx *ctx, int field)
     case TLSPH_FIELD_U: return { s.u[ctx->ucur], d, 3 * n, true, false };
     case TLSPH_FIELD_V: return { s.v, d, 3 * n, true, false };
     case TLSPH_FIELD_F: return { s.F, d, 9 * n, true, false };
-    case TLSPH_FIELD_SIGMA: return { s.sig, d, 9 * n, false, true };
+    case TLSPH_FIELD_SIGMA: return { s.sig, d, 9 * n, true, true };
     case TLSPH_FIELD_STRESS_DEV: return { s.sd, d, 9 * n, true, true };
     case TLSPH_FIELD_EPSP: return { s.ep, d, n, true, false };
     case TLSPH_FIELD_EPSP_RATE: return { s.epdot, d, n, true, false };
@@ -375,6 +377,7 @@ FieldInfo field_info(tlsph_ctx *ctx, int field)
     case TLSPH_FIELD_NBR_ROWPTR: return { (void *)s.row_ptr, sizeof(int64_t), n + 1, false, false };
     case TLSPH_FIELD_NBR_COL: return { (void *)s.col, sizeof(int32_t), (size_t)ctx->nnz, false, false };
     case TLSPH_FIELD_STEP: return { &ctx->steps, sizeof(int64_t), 1, true, false };
+    case TLSPH_FIELD_ENERGY: return { s.e, d, n, true, false };
     default: return { nullptr, 0, 0, false, false };
     }
 }
@@ -415,6 +418,8 @@ DevMat make_dev_mat(const tlsph_material &m)
     d.rho0c02 = m.rho0 * m.c0 * m.c0;
     d.S_alpha = m.S_alpha;
     d.Gamma0 = m.Gamma0;
+    d.g0rho0 = m.Gamma0 * m.rho0;
+    d.inv_rho0 = 1.0 / m.rho0;
     d.A = m.A;
     d.B = m.B;
     d.n = m.n;
@@ -431,6 +436,8 @@ DevMat make_dev_mat(const tlsph_material &m)
     d.S_alphaf = (float)d.S_alpha; d.Gamma0f = (float)d.Gamma0; d.sqrtEf = (float)d.sqrtE;
     d.q1f = (float)d.q1; d.q2f = (float)d.q2; d.q3f = (float)d.q3; d.fcf = (float)d.fc; d.fFf = (float)d.fF;
     d.fstar_slopef = (float)d.fstar_slope;
+    d.g0rho0f = (float)d.g0rho0;
+    d.inv_rho0f = (float)d.inv_rho0;
     return d;
 }
 

@@ -426,7 +426,7 @@ __device__ __forceinline__ float jc_flow_f(const DevMat &m, float ep, float epdo
     return (ep > 0.0f ? m.Af + m.Bf * powf(ep, m.nf) : m.Af) * r;
 }
 // single-precision mean stress (eos_sm) from J - 1
-__device__ __forceinline__ float eos_sm_f(const DevMat &m, float Jm1, float J, float D)
+__device__ __forceinline__ float eos_sm_f(const DevMat &m, float Jm1, float J, float D, float e)
 {
     float sm;
     if (m.eos == 0) {
@@ -434,7 +434,7 @@ __device__ __forceinline__ float eos_sm_f(const DevMat &m, float Jm1, float J, f
     } else {
         const float eta = 1.0f / J, mu = -Jm1 * eta;
         const float den = eta - m.S_alphaf * mu;
-        sm = -m.rho0c02f * mu * (eta - 0.5f * m.Gamma0f * mu) / (den * den);
+        sm = -(m.rho0c02f * mu * (eta - 0.5f * m.Gamma0f * mu) / (den * den) + m.g0rho0f * e);
     }
     return sm > 0.0f ? sm * (1.0f - D) : sm;
 }
@@ -510,13 +510,25 @@ __device__ __forceinline__ bool kin_from_F(const float *Fh, const float *Fl, Kin
 }
 
 // stress, A and the pass-2 record of a particle after its constitutive update
+// internal-energy increment (Eq. conservation3, de/dt = J sigma : d / rho0), trapezoidal in the step:
+// J / rho0 * (sigma^n + sigma^{n+1}) / 2 : dcur with dcur the step's strain increment in the current frame
+__device__ __forceinline__ float sym_ddot_f(const float *a, const float *b)
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + 2.0f * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
+}
+
 __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c, int64_t i, const Kin1 &k,
                                             const float *Li, const float *sd, float sm, double Dnew, bool failed,
-                                            float Vf, float u0, float u1, float u2, uint32_t st)
+                                            const float *dcur, float Vf, float u0, float u1, float u2, uint32_t st)
 {
     const int64_t N = c.N;
     float4 *__restrict__ r2 = s.r2 + r2_tile(i);
     float A[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
+    float sgn[6];                       // the stress at the start of the step
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sgn[q] = s.sigf[q * N + i];
+    float w = sym_ddot_f(sgn, dcur);
+    const float ejr = 0.5f * k.Jf * s.mats[s.mat[i]].inv_rho0f;
     if (failed) {
         s.fail[i] = (int32_t)(c.step_index + 1);
 #pragma unroll
@@ -526,6 +538,7 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
         const float sh[6] = { sd[0] + sm, sd[1] + sm, sd[2] + sm, sd[3], sd[4], sd[5] };
         float sg[6];
         sym_rotate_f(k.R, sh, sg);
+        w += sym_ddot_f(sg, dcur);
 #pragma unroll
         for (int q = 0; q < 6; ++q) s.sigf[q * N + i] = sg[q];
         float S[9] = { sg[0], sg[3], sg[5], sg[3], sg[1], sg[4], sg[5], sg[4], sg[2] }, P[9];
@@ -538,6 +551,7 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
         for (int q = 0; q < 9; ++q) fin &= isfinite(A[q]);
         if (!fin) st |= TLSPH_ST_NONFINITE;
     }
+    s.e[i] += (double)(ejr * w);
     const float omd = 1.0f - (float)Dnew;
     const float *G = k.G;
     r2[0] = make_float4(A[0], A[1], A[2], A[3]);
@@ -627,7 +641,7 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     for (int k = 0; k < 6; ++k) tr[k] = sdh[k] + inc[k];
     const float s2 = 1.5f * ((tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]) +
                              2.0f * (tr[3] * tr[3] + tr[4] * tr[4] + tr[5] * tr[5]));
-    const float sm = eos_sm_f(mat, kin.Jm1, kin.Jf, (float)Dd);
+    const float sm = eos_sm_f(mat, kin.Jm1, kin.Jf, (float)Dd, (float)s.e[i]);
     double por = 0.0;
     bool fast;
     if (mat.damage == TLSPH_DAMAGE_GTN) {
@@ -657,7 +671,7 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     const double Dnew = mat.damage == TLSPH_DAMAGE_NONE ? Dd
                       : (mat.damage == TLSPH_DAMAGE_GTN ? mat.q1 * gtn_fstar(mat, por) : 0.0);
     Dnext[i] = Dnew;
-    epi1_finish(s, c, i, kin, Li, sdh, sm, Dnew, false, Vf, u0, u1, u2, st);
+    epi1_finish(s, c, i, kin, Li, sdh, sm, Dnew, false, d, Vf, u0, u1, u2, st);
 }
 
 // FP64 constitutive and damage update of a queued particle (F^{n+1} already
@@ -690,10 +704,16 @@ __device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, 
     mp.dinit = s.dinit[i];
     mp.D = Dn[i];
     mp.f = s.por[i];
+    mp.e = s.e[i];
     mp.failed = 0;
     double de[6];
+    float dh[6], dcur[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) de[k] = (double)s.fsum[k * N + i];
+    for (int k = 0; k < 6; ++k) {
+        dh[k] = s.fsum[k * N + i];
+        de[k] = (double)dh[k];
+    }
+    sym_rotate_f(kin.R, dh, dcur);      // the strain increment back in the current frame
     st |= material_update(mat, c.dt, de, 1.0 + (double)kin.Jm1, mp);
     float sdh[6];
 #pragma unroll
@@ -708,7 +728,7 @@ __device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, 
     s.dinit[i] = mp.dinit;
     s.por[i] = mp.f;
     Dnext[i] = mp.D;
-    epi1_finish(s, c, i, kin, Li, sdh, (float)mp.sm, mp.D, mp.failed != 0, Vf, u0, u1, u2, st);
+    epi1_finish(s, c, i, kin, Li, sdh, (float)mp.sm, mp.D, mp.failed != 0, dcur, Vf, u0, u1, u2, st);
 }
 
 // persistent grid over the step's queue of FP64 updates; clears the queue

@@ -164,9 +164,16 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass1_fp64(DevState s, StepCon
     mp.dinit = s.dinit[i];
     mp.D = Dn[i];
     mp.f = s.por[i];
+    mp.e = s.e[i];
     mp.failed = 0;
     const DevMat &mat = s.mats[s.mat[i]];
     st |= material_update(mat, c.dt, de, J, mp);
+    // internal energy (Eq. conservation3, de/dt = J sigma : d / rho0), trapezoidal in the step with the
+    // stress at its start and at its end (zero after a failure), current frame, d scaled by dt below
+    double sgn[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sgn[k] = s.sig[6 * i + k];
+    double e_new = mp.e + c.dt * J * mat.inv_rho0 * (0.5 * sym_ddot(sgn, d));
 
 #pragma unroll
     for (int k = 0; k < 6; ++k) s.sd[6 * i + k] = mp.sd[k];
@@ -177,6 +184,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass1_fp64(DevState s, StepCon
     Dnext[i] = mp.D;
     if (mp.failed) {
         s.fail[i] = (int32_t)(c.step_index + 1);
+        s.e[i] = e_new;
 #pragma unroll
         for (int k = 0; k < 6; ++k) s.sig[6 * i + k] = 0.0;
 #pragma unroll
@@ -186,6 +194,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass1_fp64(DevState s, StepCon
         double sh[6] = { mp.sd[0] + mp.sm, mp.sd[1] + mp.sm, mp.sd[2] + mp.sm, mp.sd[3], mp.sd[4], mp.sd[5] };
         double sg[6];
         sym_rotate(R, sh, sg);
+        s.e[i] = e_new + c.dt * J * mat.inv_rho0 * (0.5 * sym_ddot(sg, d));
 #pragma unroll
         for (int k = 0; k < 6; ++k) s.sig[6 * i + k] = sg[k];
         // P = J sigma F^{-T};  A = P L^{-T}
@@ -348,6 +357,7 @@ __global__ void k_init_state(DevState s)
     s.ep[i] = 0.0;
     s.epdot[i] = 0.0;
     s.dinit[i] = 0.0;
+    s.e[i] = 0.0;
     s.D[0][i] = 0.0;
     s.D[1][i] = 0.0;
     s.fail[i] = -1;
@@ -406,6 +416,7 @@ __global__ void k_material_point(const DevMat m, double dt, int64_t n, const dou
     mp.sd[0] = x[0]; mp.sd[1] = x[4]; mp.sd[2] = x[8];
     mp.sd[3] = 0.5 * (x[1] + x[3]); mp.sd[4] = 0.5 * (x[5] + x[7]); mp.sd[5] = 0.5 * (x[2] + x[6]);
     mp.sm = x[9]; mp.ep = x[10]; mp.epdot = x[11]; mp.dinit = x[12]; mp.D = x[13]; mp.f = x[14];
+    mp.e = 0.0;        // the material-point driver holds the internal energy at zero
     mp.failed = x[15] != 0.0;
     material_update(m, dt, de, J[t], mp);
     sym_to_full(mp.sd, x);

@@ -195,6 +195,7 @@ struct MPState {
     double sd[6];   // unrotated stress deviator
     double sm;      // mean stress
     double ep, epdot, dinit, D, f;
+    double e;       // specific internal energy at the start of the update (enters the EOS)
     int failed;
 };
 
@@ -203,7 +204,7 @@ __device__ __forceinline__ double vm_eq(const double *s) { return sqrt(1.5 * sym
 // tension-positive mean stress from the equation of state (Eq. pH): the
 // Mie-Grueneisen pressure with eta = 1/J, negated; the tensile branch is
 // scaled by (1 - D).  eos 0 is its S_alpha = Gamma0 = 0 case K (J - 1).
-__device__ __forceinline__ double eos_sm(const DevMat &m, double J, double D)
+__device__ __forceinline__ double eos_sm(const DevMat &m, double J, double D, double e)
 {
     double sm;
     if (m.eos == 0) {
@@ -211,7 +212,8 @@ __device__ __forceinline__ double eos_sm(const DevMat &m, double J, double D)
     } else {
         double eta = 1.0 / J, mu = eta - 1.0;
         double den = eta - m.S_alpha * mu;
-        sm = -m.rho0c02 * mu * (eta - 0.5 * m.Gamma0 * mu) / (den * den);
+        // the energy term of Eq. pH read as Gamma0 rho0 e with e per unit mass
+        sm = -(m.rho0c02 * mu * (eta - 0.5 * m.Gamma0 * mu) / (den * den) + m.g0rho0 * e);
     }
     return sm > 0.0 ? sm * (1.0 - D) : sm;
 }
@@ -245,7 +247,7 @@ __device__ __forceinline__ double gtn_update(const DevMat &m, double dt, const d
 {
     const double D = s.D, omD = 1.0 - D, f = s.f;
     const double fs = gtn_fstar(m, f);
-    const double sm_tr = eos_sm(m, J, D);
+    const double sm_tr = eos_sm(m, J, D, s.e);
     double tr[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) tr[k] = s.sd[k] + 2.0 * m.G * omD * ed[k];
@@ -359,7 +361,7 @@ __device__ __forceinline__ uint32_t material_update(const DevMat &m, double dt, 
         }
         s.ep += dep;
         s.epdot = dep > 0.0 ? dep / dt : 0.0;
-        s.sm = eos_sm(m, J, s.D);
+        s.sm = eos_sm(m, J, s.D, s.e);
     }
     // damage initiation and evolution (no plastic increment: D_init unchanged)
     if (dep == 0.0) {

@@ -25,9 +25,12 @@ struct DevMat {
     double q1, q2, q3, fN, eN, sN, fc, fF, komega;
     double nucl_coef;    // fN / (sN sqrt(2 pi))
     double fstar_slope;  // (1/q1 - fc) / (fF - fc)
+    double g0rho0;       // Gamma0 rho0 (energy term of the Mie-Grueneisen EOS)
+    double inv_rho0;
     // single-precision copies for the mixed path's elastic fast path
     float Kf, Gf, Af, Bf, nf, Cf, inv_epsdot0f, rho0c02f, S_alphaf, Gamma0f, sqrtEf;
     float q1f, q2f, q3f, fcf, fFf, fstar_slopef;
+    float g0rho0f, inv_rho0f;
 };
 
 // Fixed-point reference positions of the mixed path: X = center + unit * (x, y, z)
@@ -89,6 +92,7 @@ struct DevState {
     double vref[3];         // bulk reference velocity of the r1 mirror
     FixPack pack;
     double grip_ramp = 0.0;  // tau of the grip velocity ramp (Sec. 6); 0: constant prescribed velocities
+    double *e = nullptr;     // N   specific internal energy (Eq. conservation3)
 };
 
 // The pass-2 record is tiled by 32 particles: component k (0..5) of particle j

@@ -22,18 +22,18 @@ DEFAULT_PRECISION = "mixed"
 SMOKE_PRECISIONS = (("fp64", 1e-10), ("mixed", 1e-4))
 
 FIELD = dict(X=0, U=1, V=2, F=3, SIGMA=4, STRESS_DEV=5, EPSP=6, EPSP_RATE=7, DINIT=8, DAMAGE=9,
-             POROSITY=10, FAIL_STEP=11, FORCE=12, A=13, LINV=14, NBR_ROWPTR=15, NBR_COL=16, STEP=17)
+             POROSITY=10, FAIL_STEP=11, FORCE=12, A=13, LINV=14, NBR_ROWPTR=15, NBR_COL=16, STEP=17, ENERGY=18)
 # (numpy dtype, components per particle); None = special count
 _FIELD_SHAPE = dict(X=(np.float64, 3), U=(np.float64, 3), V=(np.float64, 3), F=(np.float64, 9),
                     SIGMA=(np.float64, 9), STRESS_DEV=(np.float64, 9), EPSP=(np.float64, 1),
                     EPSP_RATE=(np.float64, 1), DINIT=(np.float64, 1), DAMAGE=(np.float64, 1),
                     POROSITY=(np.float64, 1), FAIL_STEP=(np.int32, 1), FORCE=(np.float64, 3),
                     A=(np.float64, 9), LINV=(np.float64, 9), NBR_ROWPTR=(np.int64, None),
-                    NBR_COL=(np.int32, None), STEP=(np.int64, None))
+                    NBR_COL=(np.int32, None), STEP=(np.int64, None), ENERGY=(np.float64, 1))
 
 # fields that together are the resumable state of a context
-CHECKPOINT_FIELDS = ("U", "V", "F", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY",
-                     "FAIL_STEP", "FORCE", "STEP")
+CHECKPOINT_FIELDS = ("U", "V", "F", "STRESS_DEV", "SIGMA", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY",
+                     "ENERGY", "FAIL_STEP", "FORCE", "STEP")
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_SINGULAR_L", -3: "ERR_NUMERICS", -4: "ERR_NOMEM",
           -5: "ERR_CUDA", -6: "ERR_STATE"}
@@ -427,7 +427,7 @@ class Simulation:
 
     def state(self) -> dict:
         names = ("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY",
-                 "FAIL_STEP", "FORCE", "A")
+                 "ENERGY", "FAIL_STEP", "FORCE", "A")
         return {k: self.get(k) for k in names}
 
     def close(self) -> None:

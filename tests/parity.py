@@ -11,7 +11,7 @@ import oracle
 # library field name -> oracle state key
 ORACLE_KEY = {"U": "u", "V": "v", "F": "F", "SIGMA": "sigma", "STRESS_DEV": "sd", "EPSP": "ep",
               "EPSP_RATE": "epdot", "DINIT": "dinit", "DAMAGE": "D", "POROSITY": "f", "FORCE": "force",
-              "A": "A", "FAIL_STEP": "fail_step"}
+              "A": "A", "FAIL_STEP": "fail_step", "ENERGY": "e"}
 
 # FP64 tolerance: normwise relative, per field (the FP64 GPU path reorders
 # the sums over j, nothing else)
@@ -29,7 +29,7 @@ def floors(w) -> dict:
     vref = float(np.abs(sp.bc_vel).max()) or 1.0
     s = max(m["A"], 1e6)
     return dict(U=L, V=vref, F=1.0, SIGMA=s, STRESS_DEV=s, A=s, EPSP=1e-3, EPSP_RATE=1e-3 / w.dt,
-                DINIT=1e-3, DAMAGE=1e-3, POROSITY=1e-3, FORCE=s * L * L)
+                DINIT=1e-3, DAMAGE=1e-3, POROSITY=1e-3, FORCE=s * L * L, ENERGY=1e-3 * s / m["rho0"])
 
 
 def relerr(a, b, floor):
@@ -45,7 +45,7 @@ def compare_state(gpu, orc, w, tol=TOL_FP64, fields=None, idx=None):
     fl = floors(w)
     out = {}
     for f in fields or ("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE",
-                        "POROSITY", "FORCE", "A"):
+                        "POROSITY", "FORCE", "A", "ENERGY"):
         g = gpu[f]
         o = orc[ORACLE_KEY[f]]
         if idx is not None:

@@ -21,6 +21,12 @@ pytestmark = pytest.mark.gpu
 TRAJ_TOL = 1e-7
 
 
+# the library fields that make up a resumable state, with their oracle keys
+RESUMABLE = (("U", "u"), ("V", "v"), ("F", "F"), ("STRESS_DEV", "sd"), ("SIGMA", "sigma"), ("EPSP", "ep"),
+             ("EPSP_RATE", "epdot"), ("DINIT", "dinit"), ("DAMAGE", "D"), ("POROSITY", "f"), ("ENERGY", "e"),
+             ("FORCE", "force"), ("FAIL_STEP", "fail_step"))
+
+
 def gpu_sim(w, precision="fp64", **kw):
     return tlsph.Simulation.from_workload(w, precision=precision, **kw)
 
@@ -128,9 +134,7 @@ def test_one_step_from_plastic_damaged_state():
     st = o.state()
     assert (st["fail_step"] >= 0).sum() > 0 and st["ep"].max() > 0.01
     g = gpu_sim(w)
-    for name, key in (("U", "u"), ("V", "v"), ("F", "F"), ("STRESS_DEV", "sd"), ("EPSP", "ep"),
-                      ("EPSP_RATE", "epdot"), ("DINIT", "dinit"), ("DAMAGE", "D"), ("POROSITY", "f"),
-                      ("FORCE", "force"), ("FAIL_STEP", "fail_step")):
+    for name, key in RESUMABLE:
         g.set(name, st[key])
     g.step(1)
     o.step(1)
@@ -150,9 +154,7 @@ def test_one_step_from_plastic_state_jc_gtn(make):
     st = o.state()
     assert st["ep"].max() > 1e-3
     g = gpu_sim(w)
-    for name, key in (("U", "u"), ("V", "v"), ("F", "F"), ("STRESS_DEV", "sd"), ("EPSP", "ep"),
-                      ("EPSP_RATE", "epdot"), ("DINIT", "dinit"), ("DAMAGE", "D"), ("POROSITY", "f"),
-                      ("FORCE", "force"), ("FAIL_STEP", "fail_step")):
+    for name, key in RESUMABLE:
         g.set(name, st[key])
     g.step(1)
     o.step(1)
@@ -304,3 +306,23 @@ def test_taylor_impact_with_wall():
     gm = gpu_sim(w, "mixed")
     gm.step(120)
     compare_state(gm.state(), os_, w, tol=2e-3, fields=("U", "V", "F"))
+
+
+def test_mie_grueneisen_energy_term_taylor_impact():
+    """Taylor impact at 250 m/s with a Mie-Grueneisen EOS and Gamma0 = 2: the
+    internal energy of Eq. conservation3 grows in the compressed, plastically
+    flowing foot and feeds the Gamma0 rho0 e term of Eq. pH.  FP64 against the
+    oracle within the trajectory tolerance (ENERGY included); the mixed path's
+    energy within its tolerance."""
+    import dataclasses
+    w = S.taylor_impact(3000, v_impact=250.0, steps=120)
+    m = dict(w.materials[0])
+    K = m["E"] / (3.0 * (1.0 - 2.0 * m["nu"]))
+    m.update(eos=1, c0=float(np.sqrt(K / m["rho0"])), S_alpha=1.4, Gamma0=2.0)
+    w = dataclasses.replace(w, materials=[m])
+    gs, os_ = _run_both(w, 120)
+    assert os_["e"].max() > 1e3            # J/kg: the energy term is not negligible (Gamma0 rho0 e ~ 1e7 Pa)
+    compare_state(gs, os_, w, tol=TRAJ_TOL)
+    gm = gpu_sim(w, "mixed")
+    gm.step(120)
+    compare_state(gm.state(), os_, w, tol=2e-3, fields=("U", "V", "F", "ENERGY"))
