@@ -60,8 +60,8 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
     read and written once (gathered neighbour data counts as on-chip reuse).
     Per-pass per-particle figures follow the state layout of the library."""
     if precision == "fp64":
-        p1 = 4 * nnz + 592 * N     # row_ptr 8, X 24, v 24, Linv 72, F rw 144, sd rw 96, scalars rw 64,
-        #                            D r+w 16, fail 4, mat 4, sigma w 48, A w 72, vol 16 (gathered only)
+        p1 = 4 * nnz + 656 * N     # row_ptr 8, X 24, v 24, Linv 72, F rw 144, sd rw 96, scalars rw 64,
+        #                            D r+w 16, fail 4, mat 4, sigma r+w 96, e r+w 16, A w 72, vol 16 (gathered only)
         p2 = 4 * nnz + 357 * N     # row_ptr 8, X 24, u 24, F 72, A 72, D 8, vol 8, sqrtE 8, mass 8,
         #                            vh rw 48, v w 24, force w 24, u' w 24, fail 4, bc 1
     else:

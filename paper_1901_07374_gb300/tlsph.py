@@ -175,12 +175,12 @@ def mixed_algorithmic_bytes(N: int, list_words: int):
     neighbour records count as on-chip reuse).
     pass 1: position 16, v record 16, L^-1 36, F (compensated) rw 144,
             deviator (compensated) rw 96, eps_p / rate / D_init r 24, D r+w 16,
-            fail 4, material 4, V 8, u 24, sqrt E 8, sigma w 24,
-            pass-2 record w 96                                          = 516
+            fail 4, material 4, V 8, u 24, sqrt E 8, sigma r+w 48,
+            internal energy r+w 16, pass-2 record w 96                  = 556
     pass 2: position 16, own pass-2 record 96, S0 16, V 8, D 8, sqrt E 8,
             1/m 8, v_half rw 48, v w 24, force w 24, u r+w 48, fail 4, bc 1,
             v record w 16                                               = 325"""
-    return 4 * list_words + 516 * N, 4 * list_words + 325 * N
+    return 4 * list_words + 556 * N, 4 * list_words + 325 * N
 
 
 # FP32 operations per pair-interaction of the mixed path's pair terms (an FMA,
