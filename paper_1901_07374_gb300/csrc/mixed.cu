@@ -517,18 +517,19 @@ __device__ __forceinline__ float sym_ddot_f(const float *a, const float *b)
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + 2.0f * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
 }
 
+// The caller loads sigma^n and e^n before its first store (later loads could
+// not be moved above stores through the other state pointers and would add
+// two memory round trips per particle) and passes w0 = sigma^n : dcur.
 __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c, int64_t i, const Kin1 &k,
                                             const float *Li, const float *sd, float sm, double Dnew, bool failed,
-                                            const float *dcur, float Vf, float u0, float u1, float u2, uint32_t st)
+                                            const float *dcur, float w0, double e_n, float inv_rho0,
+                                            float Vf, float u0, float u1, float u2, uint32_t st)
 {
     const int64_t N = c.N;
     float4 *__restrict__ r2 = s.r2 + r2_tile(i);
     float A[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
-    float sgn[6];                       // the stress at the start of the step
-#pragma unroll
-    for (int q = 0; q < 6; ++q) sgn[q] = s.sigf[q * N + i];
-    float w = sym_ddot_f(sgn, dcur);
-    const float ejr = 0.5f * k.Jf * s.mats[s.mat[i]].inv_rho0f;
+    float w = w0;
+    const float ejr = 0.5f * k.Jf * inv_rho0;
     if (failed) {
         s.fail[i] = (int32_t)(c.step_index + 1);
 #pragma unroll
@@ -551,7 +552,7 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
         for (int q = 0; q < 9; ++q) fin &= isfinite(A[q]);
         if (!fin) st |= TLSPH_ST_NONFINITE;
     }
-    s.e[i] += (double)(ejr * w);
+    s.e[i] = e_n + (double)(ejr * w);
     const float omd = 1.0f - (float)Dnew;
     const float *G = k.G;
     r2[0] = make_float4(A[0], A[1], A[2], A[3]);
@@ -583,6 +584,11 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     for (int k = 0; k < 9; ++k) { Fh[k] = s.Fh[k * N + i]; Fl[k] = s.Fl[k * N + i]; }
     float u0, u1, u2;
     load_u1(s, c, i, u0, u1, u2);
+    // stress at the start of the step and internal energy, loaded before the first store (epi1_finish)
+    float sgn[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sgn[k] = s.sigf[k * N + i];
+    const double e_n = s.e[i];
     if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
         float4 *__restrict__ r2 = s.r2 + r2_tile(i);
         Dnext[i] = Dn[i];
@@ -641,7 +647,7 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     for (int k = 0; k < 6; ++k) tr[k] = sdh[k] + inc[k];
     const float s2 = 1.5f * ((tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]) +
                              2.0f * (tr[3] * tr[3] + tr[4] * tr[4] + tr[5] * tr[5]));
-    const float sm = eos_sm_f(mat, kin.Jm1, kin.Jf, (float)Dd, (float)s.e[i]);
+    const float sm = eos_sm_f(mat, kin.Jm1, kin.Jf, (float)Dd, (float)e_n);
     double por = 0.0;
     bool fast;
     if (mat.damage == TLSPH_DAMAGE_GTN) {
@@ -671,7 +677,8 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     const double Dnew = mat.damage == TLSPH_DAMAGE_NONE ? Dd
                       : (mat.damage == TLSPH_DAMAGE_GTN ? mat.q1 * gtn_fstar(mat, por) : 0.0);
     Dnext[i] = Dnew;
-    epi1_finish(s, c, i, kin, Li, sdh, sm, Dnew, false, d, Vf, u0, u1, u2, st);
+    epi1_finish(s, c, i, kin, Li, sdh, sm, Dnew, false, d, sym_ddot_f(sgn, d), e_n, mat.inv_rho0f, Vf, u0, u1,
+                u2, st);
 }
 
 // FP64 constitutive and damage update of a queued particle (F^{n+1} already
@@ -682,13 +689,15 @@ __device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, 
     double *__restrict__ Dnext = s.D[c.dcur ^ 1];
     const int64_t N = c.N;
     const float Vf = (float)s.vol[i];
-    float Fh[9], Fl[9], Li[9];
+    float Fh[9], Fl[9], Li[9], sgn[6];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         Fh[k] = s.Fh[k * N + i];
         Fl[k] = s.Fl[k * N + i];
         Li[k] = s.linv32[9 * i + k];
     }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sgn[k] = s.sigf[k * N + i];
     float u0, u1, u2;
     load_u1(s, c, i, u0, u1, u2);
     Kin1 kin;
@@ -704,7 +713,8 @@ __device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, 
     mp.dinit = s.dinit[i];
     mp.D = Dn[i];
     mp.f = s.por[i];
-    mp.e = s.e[i];
+    const double e_n = s.e[i];
+    mp.e = e_n;
     mp.failed = 0;
     double de[6];
     float dh[6], dcur[6];
@@ -728,7 +738,8 @@ __device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, 
     s.dinit[i] = mp.dinit;
     s.por[i] = mp.f;
     Dnext[i] = mp.D;
-    epi1_finish(s, c, i, kin, Li, sdh, (float)mp.sm, mp.D, mp.failed != 0, dcur, Vf, u0, u1, u2, st);
+    epi1_finish(s, c, i, kin, Li, sdh, (float)mp.sm, mp.D, mp.failed != 0, dcur, sym_ddot_f(sgn, dcur), e_n,
+                mat.inv_rho0f, Vf, u0, u1, u2, st);
 }
 
 // persistent grid over the step's queue of FP64 updates; clears the queue
@@ -846,7 +857,10 @@ __global__ void __launch_bounds__(256) k_gather1_mixed_w32(DevState s, MixConst 
     for (int k = 0; k < 9; ++k) s.fsum[k * s.N + row0 + lane] = keep[k];
 }
 
-__global__ void __launch_bounds__(128, 5) k_epi1_mixed(DevState s, MixConst c)
+#ifndef EPI1_MINB
+#define EPI1_MINB 5
+#endif
+__global__ void __launch_bounds__(128, EPI1_MINB) k_epi1_mixed(DevState s, MixConst c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
