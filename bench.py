@@ -74,6 +74,9 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # same kernel build, keyed by (workload, precision, pass, plan form of that
 # pass); absent for other plans and once the kernels change after the capture
 TRAFFIC = {
+    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 597262848,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 319589888,   # k_pass2_mixed_tc
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 7): 319007232,   # k_pass2_mixed_tc5
 }
 
 
