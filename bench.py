@@ -11,7 +11,7 @@ full step (both gather passes).  `value` is device-timed with CUDA events on
 the stream the library launches on, inputs resident in HBM; `e2e` is the same
 metric through the C ABI with host buffers: upload of the specimen from
 pinned memory, neighbour build, the K steps (each followed by a read-back of
-its diagnostics: momentum, force sum, kinetic energy, failures) and the
+its diagnostics: momentum, force sum, kinetic and internal energy, failures) and the
 download of the final fields, all inside the timed region.  The state a step reads and writes
 (about 0.9 GB of HBM traffic) is far larger than the 129 MB L2, so no flush is
 needed between steps.
@@ -431,10 +431,10 @@ def run_ours(args, rank: int, world: int, dist):
             s2.set_plan(r["plan"])
         d2h = 0
         diag = None
-        for _ in range(args.steps):      # each step's result read back: the step's diagnostics (10 doubles)
+        for _ in range(args.steps):      # each step's result read back: the step's diagnostics
             s2.step(1)
             diag = s2.diagnostics()
-            d2h += 10 * 8
+            d2h += tlsph.DIAG_COUNT * 8
         L = tlsph.load()
         for k, (t, a) in outs.items():
             tlsph._check(L.tlsph_get_state(s2.ctx, tlsph.FIELD[k], a.ctypes.data_as(ctypes.c_void_p), a.nbytes, 0),
@@ -446,7 +446,7 @@ def run_ours(args, rank: int, world: int, dist):
         e2e = {"value": world * nnz * args.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "includes": "create (upload of the specimen from pinned memory, neighbour build, L^-1) + K steps, each "
-                           "followed by a read-back of its diagnostics (momentum, force sum, kinetic energy, failures) "
+                           "followed by a read-back of its diagnostics (momentum, force sum, kinetic and internal energy, failures) "
                            "+ download of u, v, sigma, D",
                "final_kinetic_energy": diag["kinetic_energy"] if diag else None}
 

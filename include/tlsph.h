@@ -221,11 +221,12 @@ const char *tlsph_last_error(const tlsph_ctx *ctx);
  * the paper; conservation checks and monitoring): out[0..2] momentum
  * sum_i m_i v_i, out[3..5] force sum sum_i f_i, out[6] kinetic energy
  * sum_i m_i |v_i|^2 / 2, out[7] number of failed particles, out[8] largest D,
- * out[9] largest equivalent plastic strain; SI units, FP64, host array of n =
+ * out[9] largest equivalent plastic strain, out[10] internal energy
+ * sum_i m_i e_i (Eq. conservation3; with out[6] the energy balance); SI units, FP64, host array of n =
  * TLSPH_DIAG_COUNT doubles.  The sums are deterministic (fixed blocking and
  * order).  Synchronises the context's stream.  TLSPH_ERR_ARG for n !=
  * TLSPH_DIAG_COUNT or NULL out. */
-#define TLSPH_DIAG_COUNT 10
+#define TLSPH_DIAG_COUNT 11
 int tlsph_diagnostics(tlsph_ctx *ctx, double *out, int n);
 
 /* Release the context (and its device memory when the library owns it). */

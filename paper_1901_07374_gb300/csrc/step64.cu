@@ -563,12 +563,13 @@ cudaError_t launch_material_fields(const DevState &s, int mat_id, int dcur, bool
 // block partials in block order: the same N gives the same bits every time.
 constexpr int DIAG_THREADS = 512;
 
+// slots 8 and 9 are maxima (largest D, largest plastic strain), every other slot a sum
+__device__ __forceinline__ bool diag_is_max(int k) { return k == 8 || k == 9; }
+
 __device__ __forceinline__ void diag_combine(double *a, const double *b)
 {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] += b[k];      // momentum, force sum, kinetic energy, failed count
-#pragma unroll
-    for (int k = 8; k < TLSPH_DIAG_COUNT; ++k) a[k] = fmax(a[k], b[k]);
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = diag_is_max(k) ? fmax(a[k], b[k]) : a[k] + b[k];
 }
 
 // a[] of lane 0 becomes the combination over the warp (fixed butterfly order)
@@ -595,7 +596,7 @@ __device__ __forceinline__ void diag_block(double *a, double (*sh)[TLSPH_DIAG_CO
     if (wid == 0) {
         double b[TLSPH_DIAG_COUNT];
 #pragma unroll
-        for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) b[k] = lane < nw ? sh[lane][k] : (k < 8 ? 0.0 : -INFINITY);
+        for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) b[k] = lane < nw ? sh[lane][k] : (diag_is_max(k) ? -INFINITY : 0.0);
         diag_warp(b);
         if (lane == 0)
 #pragma unroll
@@ -611,13 +612,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_blocks(DevState s, int dc
     const int64_t lo = (int64_t)blockIdx.x * N / gridDim.x, hi = (int64_t)(blockIdx.x + 1) * N / gridDim.x;
     double a[TLSPH_DIAG_COUNT];
 #pragma unroll
-    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = k < 8 ? 0.0 : -INFINITY;
+    for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) a[k] = diag_is_max(k) ? -INFINITY : 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double m = s.mass[i];
         const double v0 = s.v[3 * i], v1 = s.v[3 * i + 1], v2 = s.v[3 * i + 2];
         double b[TLSPH_DIAG_COUNT] = { m * v0, m * v1, m * v2, s.force[3 * i], s.force[3 * i + 1], s.force[3 * i + 2],
                                        0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2), s.fail[i] >= 0 ? 1.0 : 0.0,
-                                       s.D[dcur][i], s.ep[i] };
+                                       s.D[dcur][i], s.ep[i], m * s.e[i] };
         diag_combine(a, b);
     }
     diag_block(a, sh);
@@ -633,7 +634,7 @@ __global__ void k_diag_final(double *partials, int nblocks)
     const int t = threadIdx.x;
 #pragma unroll
     for (int k = 0; k < TLSPH_DIAG_COUNT; ++k)
-        a[k] = t < nblocks ? partials[(int64_t)t * TLSPH_DIAG_COUNT + k] : (k < 8 ? 0.0 : -INFINITY);
+        a[k] = t < nblocks ? partials[(int64_t)t * TLSPH_DIAG_COUNT + k] : (diag_is_max(k) ? -INFINITY : 0.0);
     diag_block(a, sh);
     if (t == 0)
         for (int k = 0; k < TLSPH_DIAG_COUNT; ++k) partials[k] = sh[0][k];

@@ -35,6 +35,9 @@ _FIELD_SHAPE = dict(X=(np.float64, 3), U=(np.float64, 3), V=(np.float64, 3), F=(
 CHECKPOINT_FIELDS = ("U", "V", "F", "STRESS_DEV", "SIGMA", "EPSP", "EPSP_RATE", "DINIT", "DAMAGE", "POROSITY",
                      "ENERGY", "FAIL_STEP", "FORCE", "STEP")
 
+# doubles returned by tlsph_diagnostics (TLSPH_DIAG_COUNT)
+DIAG_COUNT = 11
+
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_SINGULAR_L", -3: "ERR_NUMERICS", -4: "ERR_NOMEM",
           -5: "ERR_CUDA", -6: "ERR_STATE"}
 ST_POLAR_CAP, ST_NEWTON_CAP, ST_BAD_J, ST_NONFINITE = 1, 2, 4, 8
@@ -345,11 +348,12 @@ class Simulation:
 
     def diagnostics(self) -> dict:
         """Momentum, force sum, kinetic energy, failed count, largest D and
-        plastic strain of the current state (tlsph_diagnostics)."""
-        out = (ctypes.c_double * 10)()
-        _check(load().tlsph_diagnostics(self.ctx, out, 10), self.ctx)
+        plastic strain, and internal energy of the current state
+        (tlsph_diagnostics)."""
+        out = (ctypes.c_double * DIAG_COUNT)()
+        _check(load().tlsph_diagnostics(self.ctx, out, DIAG_COUNT), self.ctx)
         return {"momentum": tuple(out[0:3]), "force_sum": tuple(out[3:6]), "kinetic_energy": out[6],
-                "failed": int(out[7]), "max_damage": out[8], "max_epsp": out[9]}
+                "failed": int(out[7]), "max_damage": out[8], "max_epsp": out[9], "internal_energy": out[10]}
 
     def set_guard(self, band: float) -> None:
         """Guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)."""

@@ -84,7 +84,7 @@ def test_null_context_calls(lib):
 
 def test_diagnostics_argument_errors(lib):
     import ctypes
-    out = (ctypes.c_double * 10)()
+    out = (ctypes.c_double * 11)()
     lib.tlsph_diagnostics.restype = ctypes.c_int
     lib.tlsph_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
-    assert lib.tlsph_diagnostics(None, out, 10) == -1
+    assert lib.tlsph_diagnostics(None, out, 11) == -1

@@ -168,4 +168,6 @@ def test_diagnostics_match_the_fields(precision):
     assert d["failed"] == int((g.get("FAIL_STEP") >= 0).sum())
     assert d["max_damage"] == g.get("DAMAGE").max()
     assert d["max_epsp"] == g.get("EPSP").max()
+    assert d["internal_energy"] == pytest.approx((m * g.get("ENERGY")).sum(), rel=1e-12)
+    assert d["internal_energy"] > 0
     assert d["max_epsp"] > 0
