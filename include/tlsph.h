@@ -203,13 +203,17 @@ int tlsph_info(const tlsph_ctx *ctx, int64_t *N, int64_t *nnz, int64_t *steps);
 
 /* Copy a field (tlsph_field) at the current step boundary into dst (host
  * memory, or device memory if dst_on_device), `bytes` must equal the field's
- * size.  Synchronises the context's stream. */
+ * size.  A page-locked host dst (cudaHostAlloc, cudaHostRegister, a pinned
+ * torch tensor) is written by the device directly; a pageable one through a
+ * host staging copy.  Synchronises the context's stream. */
 int tlsph_get_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_on_device);
 
-/* Overwrite a writable field (U, V, F, STRESS_DEV, EPSP, EPSP_RATE, DINIT,
- * DAMAGE, POROSITY, FAIL_STEP, FORCE, STEP) from src; the half-step velocity and
- * the predicted displacement are recomputed from U, V and FORCE.  Used for
- * checkpoint/resume and for tests that start from a chosen state. */
+/* Overwrite a writable field (U, V, F, SIGMA, STRESS_DEV, EPSP, EPSP_RATE,
+ * DINIT, DAMAGE, POROSITY, ENERGY, FAIL_STEP, FORCE, STEP) from src; the
+ * half-step velocity and the predicted displacement are recomputed from U, V
+ * and FORCE.  Used for checkpoint/resume (all of these fields together are a
+ * resumable state: the internal-energy update of the next step starts from
+ * SIGMA) and for tests that start from a chosen state. */
 int tlsph_set_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, int src_on_device);
 
 /* Last error text of ctx, or of the calling thread's last failed
