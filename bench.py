@@ -53,6 +53,11 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+# bars pulled along z by grips at both ends: their plastic-flow window starts
+# from an affine stretch (specimen.plastic_flow_state)
+GRIPPED_BARS = ("tensile_bar", "notched_bar")
+
+
 def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None = None) -> dict:
     """Bytes each pass must move between HBM and the SMs per step: the
     neighbour lists (the CSR column index of every pair, or the mixed path's
@@ -335,7 +340,7 @@ def run_ours(args, rank: int, world: int, dist):
     guard = None
     if args.guard_sweep and args.precision == "mixed" and ref_state is not None:
         from paper_1901_07374_gb300 import specimen as S
-        st = S.plastic_flow_state(w) if args.workload.startswith("tensile_bar") else None
+        st = S.plastic_flow_state(w) if args.workload.startswith(GRIPPED_BARS) else None
         guard = []
         for band in (1e-5, 1e-3, 1e-1, 1.0):
             gs, gr = timed_run(tlsph, torch, w, "mixed", args.steps, args.warmup, stream, plan=r.get("plan"),
@@ -388,7 +393,7 @@ def run_ours(args, rank: int, world: int, dist):
 
     # ---- the same bar with every particle in plastic flow (FP64 return in both paths)
     plastic = None
-    if not args.no_plastic and args.workload.startswith("tensile_bar"):
+    if not args.no_plastic and args.workload.startswith(GRIPPED_BARS):
         from paper_1901_07374_gb300 import specimen as S
         st = S.plastic_flow_state(w)
         ps, pr = timed_run(tlsph, torch, w, args.precision, args.plastic_steps, args.warmup, stream,

@@ -724,7 +724,7 @@ __device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, 
         de[k] = (double)dh[k];
     }
     sym_rotate_f(kin.R, dh, dcur);      // the strain increment back in the current frame
-    st |= material_update(mat, c.dt, de, 1.0 + (double)kin.Jm1, mp);
+    st |= material_update<true>(mat, c.dt, de, 1.0 + (double)kin.Jm1, mp);
     float sdh[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {

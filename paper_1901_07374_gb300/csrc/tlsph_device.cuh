@@ -241,7 +241,61 @@ __device__ __forceinline__ double gtn_fstar(const DevMat &m, double f)
     return m.fc + m.fstar_slope * (f - m.fc);
 }
 
-// Algorithm 2.  Returns the matrix plastic strain increment.
+// Single-precision starting points for the two Newton solves of Algorithm 2
+// (the mixed path).  Each returns a value <= 0 when its iteration does not
+// settle; the FP64 iteration then starts where it does without a seed.  The
+// FP64 iteration that follows keeps its own convergence test, so a seed only
+// shortens it: from a start within FP32 rounding of the root, Newton's
+// quadratic convergence reaches the FP64 tolerance in one or two steps.
+//
+// First solve: x with x^2 + 2 q1 f* cosh(a1 x) - c0 = 0 (Eq. yield_GTN_2 at
+// fixed triaxiality), convex and increasing on x > 0.
+__device__ __forceinline__ float gtn_x_seed32(float a1, float q1f2, float c0, float x)
+{
+    for (int it = 0; it < 20; ++it) {
+        const float e = expf(a1 * x), ie = 1.0f / e;
+        const float phi = x * x + q1f2 * (0.5f * (e + ie)) - c0;
+        const float dphi = 2.0f * x + q1f2 * a1 * (0.5f * (e - ie));
+        const float dx = -phi / dphi;
+        x += dx;
+        if (!(x > 0.0f) || !isfinite(x)) return -1.0f;
+        if (fabsf(dx) <= 1e-5f * x) return x;
+    }
+    return -1.0f;
+}
+// Second solve: de with de - kf (seq - x rate sigma_hard(ep0 + de)) = 0,
+// written as g(de) = de - r0kf + xrk dH(de) with r0kf = (seq - x rate
+// sigma_hard(ep0)) kf, xrk = x rate kf and the hardening increment
+// dH(de) = sigma_hard(ep0 + de) - sigma_hard(ep0): H0 ((1 + de/ep0)^n - 1)
+// with H0 = B ep0^n, or B de^n at ep0 = 0.  In this form no FP32 sum
+// ep0 + de and no difference of two flow stresses is rounded, so the seed is
+// accurate to FP32 rounding of de itself.  g is increasing with its root in
+// [0, r0kf]; Newton steps that leave the bracket are replaced by bisection.
+__device__ __forceinline__ float gtn_de_seed32(float ep0, float H0, float B, float n, float r0kf, float xrk)
+{
+    float lo = 0.0f, hi = r0kf, de = r0kf;
+    for (int it = 0; it < 40; ++it) {
+        const float dH = ep0 > 0.0f ? H0 * expm1f(n * log1pf(de / ep0)) : (de > 0.0f ? B * powf(de, n) : 0.0f);
+        const float g = de - r0kf + xrk * dH;
+        if (g > 0.0f) hi = de; else lo = de;
+        const float ep = ep0 + de;
+        const float gp = 1.0f + xrk * n * (H0 + dH) / ep;
+        float dn = de - g / gp;
+        if (!(dn > lo && dn < hi)) dn = 0.5f * (lo + hi);
+        const float stp = dn - de;
+        de = dn;
+        if (!isfinite(de)) return -1.0f;
+        if (fabsf(stp) <= 1e-5f * de || hi - lo <= 1e-6f * r0kf) return de;
+    }
+    return -1.0f;
+}
+
+// Algorithm 2.  Returns the matrix plastic strain increment.  SEED32 starts
+// both Newton solves from their single-precision seeds (above), takes cosh
+// and sinh of the first solve from one exponential, and the hardening slope
+// of the second from the identity B n e^(n-1) = n (sigma_hard(e) - A) / e
+// (one pow per step); the FP64 convergence tests are unchanged.
+template <bool SEED32 = false>
 __device__ __forceinline__ double gtn_update(const DevMat &m, double dt, const double *ed, double J,
                                             MPState &s, uint32_t &status)
 {
@@ -254,10 +308,12 @@ __device__ __forceinline__ double gtn_update(const DevMat &m, double dt, const d
     const double seq = vm_eq(tr);
     bool elastic = seq < 1e-12 * m.K;
     double tri = 0.0, rate = 1.0, sM = 0.0;
+    double h0 = 0.0;
     if (!elastic) {
         tri = sm_tr / seq;
         rate = jc_rate(m, s.epdot);
-        sM = jc_hard(m, s.ep) * rate;
+        h0 = jc_hard(m, s.ep);
+        sM = h0 * rate;
         double xt = seq / sM;
         double phi = xt * xt + 2.0 * m.q1 * fs * cosh(1.5 * m.q2 * tri * xt) - (1.0 + m.q3 * fs * fs);
         elastic = phi <= 0.0;
@@ -273,11 +329,21 @@ __device__ __forceinline__ double gtn_update(const DevMat &m, double dt, const d
     const double a1 = 1.5 * m.q2 * tri;
     const double c0 = 1.0 + m.q3 * fs * fs;
     double x = fmin(1.0, seq / sM);
+    if (SEED32) {
+        const float xs = gtn_x_seed32((float)a1, (float)(2.0 * m.q1 * fs), (float)c0, (float)x);
+        if (xs > 0.0f) x = (double)xs;
+    }
     bool conv = false;
     for (int it = 0; it < 50; ++it) {
         double ch, sh;
-        sh = sinh(a1 * x);
-        ch = cosh(a1 * x);
+        if (SEED32) {
+            const double e = exp(a1 * x), ie = 1.0 / e;
+            ch = 0.5 * (e + ie);
+            sh = 0.5 * (e - ie);   // enters the derivative only
+        } else {
+            sh = sinh(a1 * x);
+            ch = cosh(a1 * x);
+        }
         double phi = x * x + 2.0 * m.q1 * fs * ch - c0;
         double dphi = 2.0 * x + 2.0 * m.q1 * fs * a1 * sh;
         double dx = -phi / dphi;
@@ -293,11 +359,19 @@ __device__ __forceinline__ double gtn_update(const DevMat &m, double dt, const d
     double de = (seq - x * sM) * kf;
     double lo = 0.0, hi = fmax(de, 0.0);
     const double tol = 1e-14 * (seq * kf + fabs(de));
+    if (SEED32 && de > 0.0) {
+        const float ds = gtn_de_seed32((float)ep0, (float)(h0 - m.A), (float)m.B, (float)m.n, (float)de,
+                                       (float)(x * rate * kf));
+        if (ds > 0.0f && (double)ds < hi) de = (double)ds;
+    }
     conv = false;
     for (int it = 0; it < 50; ++it) {
-        double g = de - (seq - x * jc_hard(m, ep0 + de) * rate) * kf;
+        const double ep = ep0 + de;
+        const double h = jc_hard(m, ep);
+        double g = de - (seq - x * h * rate) * kf;
         if (g > 0.0) hi = de; else lo = de;
-        double gp = 1.0 + x * jc_hard_slope(m, ep0 + de) * rate * kf;
+        const double slope = SEED32 ? (ep > 0.0 ? m.n * (h - m.A) / ep : INFINITY) : jc_hard_slope(m, ep);
+        double gp = 1.0 + x * slope * rate * kf;
         double dn = de - g / gp;
         if (!(dn > lo && dn < hi)) dn = 0.5 * (lo + hi);
         double stp = dn - de;
@@ -330,6 +404,7 @@ __device__ __forceinline__ double gtn_update(const DevMat &m, double dt, const d
 // Constitutive and damage update of one particle from the symmetric strain
 // increment de (unrotated frame) and J = det F^{n+1}.  D^n enters, D^{n+1}
 // leaves.  Returns status bits.
+template <bool SEED32 = false>
 __device__ __forceinline__ uint32_t material_update(const DevMat &m, double dt, const double *de, double J,
                                                     MPState &s)
 {
@@ -339,7 +414,7 @@ __device__ __forceinline__ uint32_t material_update(const DevMat &m, double dt, 
     const double ed[6] = { de[0] - trc, de[1] - trc, de[2] - trc, de[3], de[4], de[5] };
     double dep;
     if (m.damage == TLSPH_DAMAGE_GTN) {
-        dep = gtn_update(m, dt, ed, J, s, status);
+        dep = gtn_update<SEED32>(m, dt, ed, J, s, status);
     } else {
         // Algorithm 1: elastic trial, von Mises check, radial scale-back
         const double omD = 1.0 - s.D;

@@ -298,8 +298,8 @@ def failure_variant(w: Workload, v_grip: float = 20.0, scale: float = 0.02) -> W
 
 
 def plastic_flow_state(w: Workload, strain: float = 0.01) -> dict:
-    """A starting state in which every particle of a tensile bar flows
-    plastically: an affine isochoric stretch F = diag(1 - e/2, 1 - e/2, 1 + e)
+    """A starting state in which every particle of a bar pulled along z by
+    its grips (tensile or notched round bar) flows plastically: an affine isochoric stretch F = diag(1 - e/2, 1 - e/2, 1 + e)
     about the bar's centroid, the matching affine velocity field of the grip
     rate (strain rate 2 v_grip / length), and an uniaxial unrotated stress
     deviator diag(-1, -1, 2) A / 3 whose von Mises value is the yield stress A

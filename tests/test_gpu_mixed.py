@@ -266,3 +266,33 @@ def test_gtn_mixed_screen_against_fp64_update_and_oracle():
     o = oracle.Simulation.from_workload(w)
     o.step(300)
     compare_state(a.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
+
+
+def test_gtn_plastic_flow_seeded_return():
+    """Every particle of a GTN notched bar in plastic flow, so every update
+    goes through the mixed path's FP64 return, whose two Newton solves
+    (Algorithm 2) start from single-precision seeds.  After 10 steps no solve
+    has hit its iteration cap, and the state agrees with the FP64 GPU path
+    (unseeded solves) to the FP32 rounding of the kinematics and with the
+    oracle within MIXED_TOL."""
+    w = S.notched_bar_gtn(radius=2.0e-3, height=6e-3, spacing=0.3e-3, notch_radius=0.6e-3, steps=10)
+    st = S.plastic_flow_state(w)
+    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    b = tlsph.Simulation.from_workload(w, precision="fp64")
+    for g in (a, b):
+        for k, v in st.items():
+            g.set(k, v)
+    a.step(10)
+    b.step(10)
+    assert a.status_bits() == 0 and b.status_bits() == 0
+    assert np.all(a.get("EPSP") > 0)
+    for k in ("U", "F", "SIGMA", "EPSP", "POROSITY"):
+        x, y = a.get(k), b.get(k)
+        assert np.max(np.abs(x - y)) <= 1e-4 * max(np.max(np.abs(y)), 1e-30), k
+    o = oracle.Simulation.from_workload(w)
+    o["u"][:] = st["U"]
+    o["v"][:] = st["V"]
+    o["F"][:] = st["F"]
+    o["sd"][:] = st["STRESS_DEV"]
+    o.step(10)
+    compare_state(a.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))

@@ -231,6 +231,26 @@ def test_plastic_flow_state_yields_everywhere():
     assert np.all(o["ep"][inner] > 0.0)
 
 
+def test_plastic_flow_state_yields_gtn_notched_bar():
+    """The same starting state on the GTN notched round bar (pulled along z by
+    its grips): the porous yield function of Algorithm 2 is below the von
+    Mises value at f > 0, so one oracle step gives every particle a plastic
+    increment, and the void fraction stays in [0, f_F] (Sec. 5.4, Eqs.
+    (GTN_damage_nucleation), (GTN_damage_growth))."""
+    w = S.notched_bar_gtn(radius=1.2e-3, height=4e-3, spacing=0.3e-3, notch_radius=0.4e-3, steps=10)
+    st = S.plastic_flow_state(w)
+    o = oracle.Simulation.from_workload(w)
+    o["u"][:] = st["U"]
+    o["v"][:] = st["V"]
+    o["F"][:] = st["F"].reshape(-1, 9)
+    o["sd"][:] = st["STRESS_DEV"].reshape(-1, 9)
+    o.step(1)
+    assert np.all(o["ep"] > 0.0)
+    f = o["f"]
+    assert np.all(f >= 0.0) and np.all(f <= w.materials[0]["fF"])
+    assert np.any(f != w.specimen.f0)
+
+
 def test_step_is_its_three_phases():
     """predict, pass 1, pass 2 in order are one step, bit for bit (the phases
     the sharded stepper exchanges halo rows between)."""
