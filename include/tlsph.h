@@ -175,7 +175,8 @@ size_t tlsph_workspace_bytes(const tlsph_config *cfg, int64_t N, int64_t nnz_cap
  * Blocks until the set-up is done.  Returns TLSPH_ERR_SINGULAR_L if some L_i
  * is singular, TLSPH_ERR_NOMEM if the arena or nnz_cap is too small (the
  * needed pair count is in tlsph_last_error(NULL)); no context is created on
- * error. */
+ * error (an arena's contents are then unspecified: the inputs are validated
+ * on the device after their upload). */
 int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const double *vol,
                  const int32_t *mat_id, const uint8_t *bc_mask, const double *bc_vel,
                  const double *f0, void *arena, size_t arena_bytes, int64_t nnz_cap,

@@ -7,7 +7,6 @@
 #include <algorithm>
 #include <new>
 #include <string>
-#include <thread>
 #include <numeric>
 #include <vector>
 
@@ -27,7 +26,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 // F / sd / sig / A block, which is only initialised after the build.
 struct Layout {
     size_t X, vol, mass, inv_mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
-    size_t ep, epdot, dinit, por, e, D0, D1, force, fail, status, mats, col, diag;
+    size_t ep, epdot, dinit, por, e, D0, D1, force, fail, status, mats, col, diag, inscan;
     size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp, xf;
@@ -110,70 +109,6 @@ std::vector<int32_t> line_order_perm(const double *X, const double *vol, int64_t
     return perm;
 }
 
-// The create-time scan of the caller's inputs over one chunk [a, b).
-struct InputScan {
-    double lo[3], hi[3], vsum[3];
-    uint64_t mats = 0;     // bit m: material m in use
-    bool bad_vol = false, bad_x = false, bad_mat = false;
-};
-
-void scan_chunk(const double *X, const double *vol, const int32_t *mat, const double *bcv, int64_t a, int64_t b,
-                InputScan &r)
-{
-    for (int k = 0; k < 3; ++k) { r.lo[k] = X[3 * a + k]; r.hi[k] = X[3 * a + k]; r.vsum[k] = 0.0; }
-    for (int64_t i = a; i < b; ++i) {
-        const double vv = vol[i];
-        r.bad_vol |= !(vv > 0.0 && vv - vv == 0.0);
-        for (int k = 0; k < 3; ++k) {
-            const double c = X[3 * i + k];
-            r.bad_x |= !(c - c == 0.0);
-            r.lo[k] = c < r.lo[k] ? c : r.lo[k];
-            r.hi[k] = c > r.hi[k] ? c : r.hi[k];
-        }
-        if (mat) {
-            const int32_t m = mat[i];
-            if (m >= 0 && m < TLSPH_MAX_MATERIALS) r.mats |= 1ull << m;
-            else r.bad_mat = true;
-        }
-        if (bcv)
-            for (int k = 0; k < 3; ++k) r.vsum[k] += bcv[3 * i + k];
-    }
-    if (!mat) r.mats = 1;
-}
-
-InputScan scan_inputs(const double *X, const double *vol, const int32_t *mat, const double *bcv, int64_t N)
-{
-    const int chunks = N >= 262144 ? 16 : 1;
-    std::vector<InputScan> part((size_t)chunks);
-    auto range = [&](int c, int64_t &a, int64_t &b) { a = N * c / chunks; b = N * (c + 1) / chunks; };
-    std::vector<std::thread> th;
-    for (int c = 1; c < chunks; ++c) {
-        int64_t a, b;
-        range(c, a, b);
-        try {
-            th.emplace_back(scan_chunk, X, vol, mat, bcv, a, b, std::ref(part[(size_t)c]));
-        } catch (...) {        // no thread to be had: scan this chunk here
-            scan_chunk(X, vol, mat, bcv, a, b, part[(size_t)c]);
-        }
-    }
-    int64_t a0, b0;
-    range(0, a0, b0);
-    scan_chunk(X, vol, mat, bcv, a0, b0, part[0]);
-    for (auto &t : th) t.join();
-    InputScan r = part[0];
-    for (int c = 1; c < chunks; ++c) {
-        const InputScan &p = part[(size_t)c];
-        for (int k = 0; k < 3; ++k) {
-            r.lo[k] = std::min(r.lo[k], p.lo[k]);
-            r.hi[k] = std::max(r.hi[k], p.hi[k]);
-            r.vsum[k] += p.vsum[k];
-        }
-        r.mats |= p.mats;
-        r.bad_vol |= p.bad_vol; r.bad_x |= p.bad_x; r.bad_mat |= p.bad_mat;
-    }
-    return r;
-}
-
 Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
 {
     Layout L{};
@@ -204,6 +139,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.fail = c.take(n * sizeof(int32_t));
     L.status = c.take(sizeof(uint32_t));
     L.diag = c.take(DIAG_BLOCKS * TLSPH_DIAG_COUNT * sizeof(double));
+    L.inscan = c.take(INSCAN_BLOCKS * sizeof(InputScanDev));
     L.perm = c.take(n * sizeof(int32_t));
     L.iperm = c.take(n * sizeof(int32_t));
     L.mats = c.take(TLSPH_MAX_MATERIALS * sizeof(DevMat));
@@ -464,19 +400,6 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     if (!valid_config(cfg, why)) { g_create_error = why; return TLSPH_ERR_ARG; }
     if (N <= 0 || N > INT32_MAX) { g_create_error = "N must be in [1, 2^31)"; return TLSPH_ERR_ARG; }
     if (!X || !vol) { g_create_error = "X and vol are required"; return TLSPH_ERR_ARG; }
-    // one pass over the inputs: validation, bounding box, materials in use and
-    // the sum of the initial velocities (the bulk reference of the mixed path).
-    // Large inputs are split into a fixed number of chunks scanned by host
-    // threads; the chunks are joined in their order, so the result depends on
-    // N only, not on the machine.
-    InputScan scan = scan_inputs(X, vol, mat_id, bc_vel, N);
-    if (scan.bad_vol) { g_create_error = "vol must be positive and finite"; return TLSPH_ERR_ARG; }
-    if (scan.bad_x) { g_create_error = "X must be finite"; return TLSPH_ERR_ARG; }
-    if (scan.bad_mat) { g_create_error = "mat_id out of range"; return TLSPH_ERR_ARG; }
-    double lo3[3], hi3[3], vsum[3];
-    bool mat_used[TLSPH_MAX_MATERIALS] = {};
-    for (int k = 0; k < 3; ++k) { lo3[k] = scan.lo[k]; hi3[k] = scan.hi[k]; vsum[k] = scan.vsum[k]; }
-    for (int k = 0; k < TLSPH_MAX_MATERIALS; ++k) mat_used[k] = (scan.mats >> k) & 1u;
     if (arena && ((uintptr_t)arena % ALIGN) != 0) { g_create_error = "arena must be 256-byte aligned"; return TLSPH_ERR_ARG; }
     if (arena && nnz_cap <= 0) { g_create_error = "nnz_cap is required with an arena"; return TLSPH_ERR_ARG; }
 
@@ -490,6 +413,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         g_create_error = msg;
         if (ctx->owns_mem && ctx->mem) cudaFree(ctx->mem);
         if (ctx->ell_mem) cudaFree(ctx->ell_mem);
+        if (ctx->col_mem) cudaFree(ctx->col_mem);
         delete ctx;
         return code;
     };
@@ -514,7 +438,6 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
 
     // ---- copy inputs (straight from the caller's arrays; absent ones are zero)
     const size_t n = (size_t)N;
-    for (int k = 0; k < TLSPH_MAX_MATERIALS; ++k) ctx->mat_used[k] = mat_used[k];
     cudaError_t e = cudaSuccess;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e)); } } while (0)
     double *stX = at<double>(base, L.stX), *stvol = at<double>(base, L.stvol), *stbcv = at<double>(base, L.stbcv);
@@ -535,6 +458,21 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     CK(cudaMemsetAsync((void *)s.mass, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync((void *)s.inv_mass, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync((void *)s.sqrtE, 0, n * sizeof(double), st));
+
+    // ---- one pass over the staged inputs: validation, bounding box, materials
+    // in use and the sum of the initial velocities (the bulk reference of the
+    // mixed path), reduced on the device in a fixed order (depends on N only)
+    InputScanDev scan{};
+    InputScanDev *scan_dev = at<InputScanDev>(base, L.inscan);
+    CK(launch_scan_inputs(stX, stvol, stmat, stbcv, N, scan_dev, st));
+    CK(cudaMemcpyAsync(&scan, scan_dev, sizeof(scan), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (scan.bad & INSCAN_BAD_VOL) return bail(TLSPH_ERR_ARG, "vol must be positive and finite");
+    if (scan.bad & INSCAN_BAD_X) return bail(TLSPH_ERR_ARG, "X must be finite");
+    if (scan.bad & INSCAN_BAD_MAT) return bail(TLSPH_ERR_ARG, "mat_id out of range");
+    double lo3[3], hi3[3], vsum[3];
+    for (int k = 0; k < 3; ++k) { lo3[k] = scan.lo[k]; hi3[k] = scan.hi[k]; vsum[k] = scan.vsum[k]; }
+    for (int k = 0; k < TLSPH_MAX_MATERIALS; ++k) ctx->mat_used[k] = (scan.mats >> k) & 1u;
 
     // ---- neighbour CSR
     const CellGrid grid = cell_grid_from_bounds(lo3, hi3, N, cfg->rc);
@@ -574,23 +512,10 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
             return bail(TLSPH_ERR_NOMEM, "neighbour capacity too small: need nnz_cap >= " + std::to_string(nnz));
         s.col = at<int32_t>(base, L.col);
     } else {
-        // grow the library-owned block to hold the columns after the overlay
-        void *nb = nullptr;
-        const size_t need = L.overlay_end + align_up((size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t));
-        e = cudaMalloc(&nb, need);
+        // the columns in an allocation of their own, now that their count is known
+        e = cudaMalloc(&ctx->col_mem, (size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t));
         if (e != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
-        CK(cudaMemcpyAsync(nb, base, L.overlay_end, cudaMemcpyDeviceToDevice, st));
-        CK(cudaStreamSynchronize(st));
-        cudaFree(base);
-        base = nb;
-        ctx->mem = nb;
-        ctx->mem_bytes = need;
-        bind_state(ctx, base, L);
-        ctx->perm_dev = at<int32_t>(base, L.perm);
-        sc = Scratch{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
-                      at<int64_t>(base, L.scan_tmp), L.scan_elems, at<float4>(base, L.xf) };
-        row_ptr = const_cast<int64_t *>(s.row_ptr);
-        s.col = at<int32_t>(base, L.overlay_end);
+        s.col = static_cast<int32_t *>(ctx->col_mem);
         ctx->nnz_cap = nnz;
     }
     ctx->nnz = nnz;
@@ -1030,6 +955,7 @@ int tlsph_destroy(tlsph_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     if (ctx->owns_mem && ctx->mem) cudaFree(ctx->mem);
     if (ctx->ell_mem) cudaFree(ctx->ell_mem);
+    if (ctx->col_mem) cudaFree(ctx->col_mem);
     for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
     mixed_release(*ctx);
     delete ctx;

@@ -421,6 +421,100 @@ __global__ void k_identity(int32_t *perm, int64_t N)
     if (i < N) perm[i] = (int32_t)i;
 }
 
+// ---------------------------------------------------------------- input scan
+// Every block takes a contiguous range of particles, every thread a strided
+// part of it; the block reduction and the final one run in a fixed order, so
+// the FP64 velocity sum depends on N only.
+__device__ __forceinline__ void inscan_init(InputScanDev &a)
+{
+    for (int k = 0; k < 3; ++k) { a.lo[k] = INFINITY; a.hi[k] = -INFINITY; a.vsum[k] = 0.0; }
+    a.mats = 0ull;
+    a.bad = 0u;
+    a.pad = 0u;
+}
+__device__ __forceinline__ void inscan_merge(InputScanDev &a, const InputScanDev &b)
+{
+    for (int k = 0; k < 3; ++k) {
+        a.lo[k] = fmin(a.lo[k], b.lo[k]);
+        a.hi[k] = fmax(a.hi[k], b.hi[k]);
+        a.vsum[k] += b.vsum[k];
+    }
+    a.mats |= b.mats;
+    a.bad |= b.bad;
+}
+__device__ __forceinline__ void inscan_warp(InputScanDev &a)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        InputScanDev b;
+        for (int k = 0; k < 3; ++k) {
+            b.lo[k] = __shfl_xor_sync(0xffffffffu, a.lo[k], o);
+            b.hi[k] = __shfl_xor_sync(0xffffffffu, a.hi[k], o);
+            b.vsum[k] = __shfl_xor_sync(0xffffffffu, a.vsum[k], o);
+        }
+        b.mats = __shfl_xor_sync(0xffffffffu, a.mats, o);
+        b.bad = __shfl_xor_sync(0xffffffffu, a.bad, o);
+        inscan_merge(a, b);
+    }
+}
+// block of 256 threads: the result in thread 0's a
+__device__ __forceinline__ void inscan_block(InputScanDev &a, InputScanDev *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    inscan_warp(a);
+    if (lane == 0) sh[wid] = a;
+    __syncthreads();
+    if (wid == 0) {
+        if (lane < (int)(blockDim.x >> 5)) a = sh[lane];
+        else inscan_init(a);
+        inscan_warp(a);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_inputs(const double *X, const double *vol, const int32_t *mat,
+                                                     const double *bcv, int64_t N, InputScanDev *parts)
+{
+    __shared__ InputScanDev sh[8];
+    const int64_t lo = (int64_t)blockIdx.x * N / gridDim.x, hi = (int64_t)(blockIdx.x + 1) * N / gridDim.x;
+    InputScanDev a;
+    inscan_init(a);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double vv = vol[i];
+        if (!(vv > 0.0 && isfinite(vv))) a.bad |= INSCAN_BAD_VOL;
+        for (int k = 0; k < 3; ++k) {
+            const double c = X[3 * i + k];
+            if (!isfinite(c)) a.bad |= INSCAN_BAD_X;
+            a.lo[k] = fmin(a.lo[k], c);
+            a.hi[k] = fmax(a.hi[k], c);
+            a.vsum[k] += bcv[3 * i + k];
+        }
+        const int32_t m = mat[i];
+        if (m >= 0 && m < TLSPH_MAX_MATERIALS) a.mats |= 1ull << m;
+        else a.bad |= INSCAN_BAD_MAT;
+    }
+    inscan_block(a, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = a;
+}
+
+// one block of 256 threads over the per-block results, in their order
+__global__ void __launch_bounds__(256) k_scan_inputs_final(InputScanDev *parts, int nblocks)
+{
+    __shared__ InputScanDev sh[8];
+    InputScanDev a;
+    if ((int)threadIdx.x < nblocks) a = parts[threadIdx.x];
+    else inscan_init(a);
+    inscan_block(a, sh);
+    if (threadIdx.x == 0) parts[0] = a;
+}
+
+cudaError_t launch_scan_inputs(const double *X, const double *vol, const int32_t *mat, const double *bcv, int64_t N,
+                               InputScanDev *parts, cudaStream_t st)
+{
+    static_assert(INSCAN_BLOCKS <= 256, "the final reduction takes one block of 256 threads");
+    k_scan_inputs<<<INSCAN_BLOCKS, 256, 0, st>>>(X, vol, mat, bcv, N, parts);
+    k_scan_inputs_final<<<1, 256, 0, st>>>(parts, INSCAN_BLOCKS);
+    return cudaGetLastError();
+}
+
 cudaError_t build_order(const double *X_user, int64_t N, const CellGrid &g, const Scratch &sc, bool keep,
                         int32_t *perm, cudaStream_t st)
 {

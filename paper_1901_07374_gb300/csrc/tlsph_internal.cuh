@@ -148,6 +148,7 @@ struct tlsph_ctx {
     int64_t ell_stats[4] = { 0, 0, 0, 0 };   // slices, aligned slices, slots, words
     double *diag = nullptr;     // DIAG_BLOCKS x TLSPH_DIAG_COUNT partials; the first row holds the result
     void *ell_mem = nullptr;    // library-owned sliced-ELL columns
+    void *col_mem = nullptr;    // library-owned CSR columns
     int32_t *perm_dev = nullptr;
     int32_t *inv_dev = nullptr;   // device copy of inv when reordered, else null (identity)
     std::vector<int32_t> perm, inv;   // host copies of the order when reordered (empty in caller order)
@@ -175,6 +176,20 @@ cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scr
 // keep = identity
 cudaError_t build_order(const double *X_user, int64_t N, const CellGrid &g, const Scratch &sc, bool keep,
                         int32_t *perm, cudaStream_t st);
+// create-time scan of the staged caller-order inputs: bounding box, the
+// materials in use, the sum of the initial velocities and validity flags;
+// a deterministic reduction over INSCAN_BLOCKS blocks whose result lands in
+// parts[0]
+struct InputScanDev {
+    double lo[3], hi[3], vsum[3];
+    unsigned long long mats;   // bit m: material m in use
+    unsigned int bad;          // INSCAN_BAD_* bits
+    unsigned int pad;
+};
+constexpr unsigned INSCAN_BAD_VOL = 1u, INSCAN_BAD_X = 2u, INSCAN_BAD_MAT = 4u;
+constexpr int INSCAN_BLOCKS = 152;
+cudaError_t launch_scan_inputs(const double *X, const double *vol, const int32_t *mat, const double *bcv, int64_t N,
+                               InputScanDev *parts, cudaStream_t st);
 // fp32_terms: FP32 pair terms summed in FP64 across lanes (mixed contexts)
 cudaError_t shape_matrix(const DevState &s, double h, double *Linv, double *S0, uint32_t *n_singular,
                          bool fp32_terms, cudaStream_t st);

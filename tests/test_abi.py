@@ -56,17 +56,15 @@ def _create(lib, cfg, N, X, vol, mat=None):
 
 
 def test_create_rejects_bad_arguments_on_host(lib):
+    """Missing arrays, N and the configuration are checked on the host before
+    any device call (the array contents are validated on the device after
+    their upload: test_gpu_api.py)."""
     cfg = tlsph.make_config(0.75e-3, 1.5e-3, 2e-8, 10.0)
     X = np.zeros((4, 3))
     vol = np.ones(4)
     assert _create(lib, cfg, 4, None, vol) == -1
     assert b"required" in lib.tlsph_last_error(None)
-    assert _create(lib, cfg, 4, X, -vol) == -1
-    assert b"vol" in lib.tlsph_last_error(None)
-    Xn = X.copy()
-    Xn[1, 2] = np.nan
-    assert _create(lib, cfg, 4, Xn, vol) == -1
-    assert _create(lib, cfg, 4, X, vol, np.array([0, 1, 99, 0], np.int32)) == -1
+    assert _create(lib, cfg, 4, X, None) == -1
     assert _create(lib, cfg, 0, X, vol) == -1
     bad = tlsph.make_config(0.75e-3, 1.5e-3, 0.0, 10.0)
     assert _create(lib, bad, 4, X, vol) == -1

@@ -60,6 +60,45 @@ def test_arena_too_small_and_capacity_errors():
     assert e.value.code == -4
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_create_validates_inputs_on_device(precision):
+    """The array contents are validated on the device after their upload, in
+    the pass that also forms the bounding box, the materials in use and the
+    bulk velocity: a non-positive or non-finite volume, a non-finite position
+    and a material index out of range are argument errors with their
+    messages, with library memory or a caller arena, and a valid create
+    afterwards works."""
+    import torch
+    w = S.tensile_bar_cl(nx=4, ny=4, nz=6)
+    sp = w.specimen
+    N = sp.N
+    mats = [S.aluminium_cl()]
+
+    def make(X=sp.X, vol=sp.vol, mat=sp.mat_id, **kw):
+        return tlsph.Simulation(X, vol, mat, sp.bc_mask, sp.bc_vel, sp.f0, mats, w.h, w.rc, w.dt, w.hg_alpha,
+                                precision=precision, **kw)
+
+    Xn = sp.X.copy()
+    Xn[N - 1, 2] = np.nan
+    vinf = sp.vol.copy()
+    vinf[5] = np.inf
+    mbad = sp.mat_id.copy()
+    mbad[N // 2] = 99
+    cases = [(dict(vol=-sp.vol), "vol"), (dict(vol=vinf), "vol"), (dict(X=Xn), "X must be finite"),
+             (dict(mat=mbad), "mat_id")]
+    cfg = tlsph.make_config(w.h, w.rc, w.dt, w.hg_alpha, precision)
+    arena = torch.empty(tlsph.workspace_bytes(cfg, N, 200 * N), dtype=torch.uint8, device="cuda")
+    for extra in ({}, dict(arena=arena, nnz_cap=200 * N)):
+        for kw, msg in cases:
+            with pytest.raises(tlsph.TlsphError) as e:
+                make(**kw, **extra)
+            assert e.value.code == -1 and msg in str(e.value), (kw.keys(), str(e.value))
+        g = make(**extra)
+        g.step(2)
+        assert g.status_bits() == 0 and np.all(np.isfinite(g.get("V")))
+        g.close()
+
+
 def test_isolated_particle_is_singular():
     sp = S.tensile_bar(4, 4, 6, 1e-3, jitter=0.0)
     X = np.vstack([sp.X, [[1.0, 1.0, 1.0]]])
