@@ -285,6 +285,8 @@ int tlsph_set_grip_ramp(tlsph_ctx *ctx, double tau);
  * every row's neighbour indices, padded to the slice's longest row.  Writes
  * the number of slices, of aligned slices, of slots (32 x slice width,
  * summed) and of 4-byte words the lists occupy; each pointer may be NULL.
+ * Reads the slice widths back from the device (synchronises the context's
+ * stream).
  * TLSPH_ERR_STATE if the context has no sliced lists (FP64 precision, or
  * a caller arena too small for them). */
 int tlsph_neighbor_layout(const tlsph_ctx *ctx, int64_t *slices, int64_t *aligned_slices, int64_t *slots,

@@ -554,17 +554,9 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         CK(mixed_ell_widths(s, ell_off, st));
         CK(scan_exclusive_i64(ell_off, ng + 1, sc.scan_tmp, st));
         int64_t ell_n = 0;
-        std::vector<int32_t> ell_w_host((size_t)ng);
         CK(cudaMemcpyAsync(&ell_n, ell_off + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        if (ng > 0)
-            CK(cudaMemcpyAsync(ell_w_host.data(), s.ell_w, (size_t)ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        ctx->ell_stats[0] = ng;
-        ctx->ell_stats[3] = ell_n;
-        for (int32_t wv : ell_w_host) {
-            ctx->ell_stats[1] += wv < 0;
-            ctx->ell_stats[2] += 32 * (int64_t)(wv < 0 ? ((~wv) & 0xffffff) : wv);
-        }
+        ctx->ell_words = ell_n;
         int32_t *colE = nullptr;
         if (arena) {
             if (ell_n <= ell_capacity(N, nnz_cap)) colE = at<int32_t>(base, L.ell);
@@ -754,10 +746,22 @@ int tlsph_neighbor_layout(const tlsph_ctx *ctx, int64_t *slices, int64_t *aligne
 {
     if (!ctx) return TLSPH_ERR_ARG;
     if (!ctx->ell_ok) return TLSPH_ERR_STATE;
-    if (slices) *slices = ctx->ell_stats[0];
-    if (aligned_slices) *aligned_slices = ctx->ell_stats[1];
-    if (slots) *slots = ctx->ell_stats[2];
-    if (words) *words = ctx->ell_stats[3];
+    // the per-slice widths, read back and counted here (not at creation)
+    const int64_t ng = (ctx->N + 31) / 32;
+    std::vector<int32_t> w((size_t)ng);
+    cudaError_t e = cudaMemcpyAsync(w.data(), ctx->s.ell_w, (size_t)ng * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { cudaGetLastError(); return TLSPH_ERR_CUDA; }
+    int64_t aligned = 0, nslots = 0;
+    for (int32_t wv : w) {
+        aligned += wv < 0;
+        nslots += 32 * (int64_t)(wv < 0 ? ((~wv) & 0xffffff) : wv);
+    }
+    if (slices) *slices = ng;
+    if (aligned_slices) *aligned_slices = aligned;
+    if (slots) *slots = nslots;
+    if (words) *words = ctx->ell_words;
     return TLSPH_OK;
 }
 

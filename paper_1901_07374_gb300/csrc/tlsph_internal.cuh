@@ -145,7 +145,7 @@ struct tlsph_ctx {
     // internal order: perm[k] = caller index of internal particle k, inv its inverse
     bool reordered = false;
     bool ell_ok = false;        // sliced neighbour lists built (thread-per-row plans allowed)
-    int64_t ell_stats[4] = { 0, 0, 0, 0 };   // slices, aligned slices, slots, words
+    int64_t ell_words = 0;      // 4-byte words of the sliced lists
     double *diag = nullptr;     // DIAG_BLOCKS x TLSPH_DIAG_COUNT partials; the first row holds the result
     void *ell_mem = nullptr;    // library-owned sliced-ELL columns
     void *col_mem = nullptr;    // library-owned CSR columns
