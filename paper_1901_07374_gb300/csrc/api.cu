@@ -475,8 +475,9 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     for (int k = 0; k < TLSPH_MAX_MATERIALS; ++k) ctx->mat_used[k] = (scan.mats >> k) & 1u;
 
     // ---- neighbour CSR
-    const CellGrid grid = cell_grid_from_bounds(lo3, hi3, N, cfg->rc);
-    if (grid.ncells > L.max_cells) return bail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
+    const CellGrid grid = cell_grid_from_bounds(lo3, hi3, N, cfg->rc);         // internal order
+    const CellGrid sgrid = cell_grid_from_bounds(lo3, hi3, N, cfg->rc, 2);     // neighbour search
+    if (grid.ncells > L.max_cells || sgrid.ncells > L.max_cells) return bail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
     Scratch sc{ at<int64_t>(base, L.cell_start), at<int64_t>(base, L.cell_cursor), at<int32_t>(base, L.cell_items),
                 at<int64_t>(base, L.scan_tmp), L.scan_elems, at<float4>(base, L.xf) };
     // ---- internal order (brick-major cells, caller index inside a cell) and the gather into it
@@ -502,7 +503,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
 
     const double rc2 = cfg->rc * cfg->rc;
     int64_t *row_ptr = const_cast<int64_t *>(s.row_ptr);
-    CK(build_neighbors_count(s, grid, sc, rc2, row_ptr, st));
+    CK(build_neighbors_count(s, sgrid, sc, rc2, row_ptr, st));
     int64_t nnz = 0;
     CK(cudaMemcpyAsync(&nnz, row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -525,7 +526,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         ctx->inv_dev = at<int32_t>(base, L.iperm);
         CK(cudaMemcpyAsync(ctx->inv_dev, ctx->inv.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
-    CK(build_neighbors_fill(s, grid, sc, rc2, row_ptr, const_cast<int32_t *>(s.col), st));
+    CK(build_neighbors_fill(s, sgrid, sc, rc2, row_ptr, const_cast<int32_t *>(s.col), st));
 
     // ---- mixed: fixed-point positions and the sliced neighbour lists, read by
     // the correction-matrix kernel of a mixed context as by its steps

@@ -104,31 +104,32 @@ cudaError_t scan_exclusive_i64(int64_t *data, int64_t n, int64_t *tmp, cudaStrea
 }
 
 // ---------------------------------------------------------------- cell grid
-CellGrid make_cell_grid(const double *X, int64_t N, double rc)
-{
-    double lo[3] = { X[0], X[1], X[2] }, hi[3] = { X[0], X[1], X[2] };
-    for (int64_t i = 1; i < N; ++i)
-        for (int k = 0; k < 3; ++k) {
-            lo[k] = std::min(lo[k], X[3 * i + k]);
-            hi[k] = std::max(hi[k], X[3 * i + k]);
-        }
-    return cell_grid_from_bounds(lo, hi, N, rc);
-}
-
 __device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc)
 {
     int c = (int)floor((x - lo) * inv_cs);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// The search visits the cells within `reach` of a particle's cell.  With the
+// single-precision coordinates of the prefilter it also clips them to the
+// ball of radius rcm about the particle (rc plus a margin that covers the
+// FP32 rounding of the coordinates and of the cell boundaries): a (y, z) line
+// of cells is skipped when its distance exceeds rcm, and the cells of a line
+// are cut to those that meet the ball.  A pair within rc always lies in a
+// visited cell, and each visited candidate still goes through the prefilter
+// and the FP64 predicate, so the result is that of the unclipped search.
 struct GridArgs {
     double lo0, lo1, lo2, inv_cs;
-    int nc0, nc1, nc2;
+    int nc0, nc1, nc2, reach;
+    float flo0, flo1, flo2, fcs, finv_cs, rcm2;   // the grid in the prefilter's centred FP32 frame
 };
 
 static GridArgs grid_args(const CellGrid &g)
 {
-    return GridArgs{ g.xmin[0], g.xmin[1], g.xmin[2], 1.0 / g.cs, g.nc[0], g.nc[1], g.nc[2] };
+    GridArgs a{ g.xmin[0], g.xmin[1], g.xmin[2], 1.0 / g.cs, g.nc[0], g.nc[1], g.nc[2], g.reach };
+    a.flo0 = a.flo1 = a.flo2 = 0.0f;
+    a.fcs = a.finv_cs = a.rcm2 = 0.0f;
+    return a;
 }
 
 __device__ __forceinline__ void cell_of(const GridArgs &a, const double *x, int &cx, int &cy, int &cz)
@@ -187,6 +188,9 @@ __global__ void k_xf(const double *X, int64_t N, Prefilter p, float4 *xf)
     xf[i] = make_float4((float)(X[3 * i] - p.cx), (float)(X[3 * i + 1] - p.cy), (float)(X[3 * i + 2] - p.cz), 0.0f);
 }
 
+// distance from c to the interval [lo, lo + w] (0 inside)
+__device__ __forceinline__ float gap(float c, float lo, float w) { return fmaxf(fmaxf(lo - c, c - (lo + w)), 0.0f); }
+
 // one thread per particle: count (out == nullptr) or write its neighbours
 __global__ void k_nbr(const double *X, int64_t N, GridArgs a, const int64_t *cell_start,
                       const int32_t *items, double rc2, int64_t *count, const int64_t *row_ptr,
@@ -200,10 +204,26 @@ __global__ void k_nbr(const double *X, int64_t N, GridArgs a, const int64_t *cel
     cell_of(a, xi, cx, cy, cz);
     int64_t n = 0;
     int64_t w = out ? row_ptr[i] : 0;
-    for (int z = max(cz - 1, 0); z <= min(cz + 1, a.nc2 - 1); ++z)
-        for (int y = max(cy - 1, 0); y <= min(cy + 1, a.nc1 - 1); ++y) {
+    const int R = a.reach;
+    for (int z = max(cz - R, 0); z <= min(cz + R, a.nc2 - 1); ++z) {
+        float dz2 = 0.0f;
+        if (xf) {
+            const float dz = gap(fi.z, fmaf((float)z, a.fcs, a.flo2), a.fcs);
+            dz2 = dz * dz;
+            if (dz2 > a.rcm2) continue;
+        }
+        for (int y = max(cy - R, 0); y <= min(cy + R, a.nc1 - 1); ++y) {
             int64_t rowc = ((int64_t)z * a.nc1 + y) * a.nc0;
-            int x0 = max(cx - 1, 0), x1 = min(cx + 1, a.nc0 - 1);
+            int x0 = max(cx - R, 0), x1 = min(cx + R, a.nc0 - 1);
+            if (xf) {
+                const float dy = gap(fi.y, fmaf((float)y, a.fcs, a.flo1), a.fcs);
+                const float dyz2 = dz2 + dy * dy;
+                if (dyz2 > a.rcm2) continue;
+                const float rx = sqrtf(a.rcm2 - dyz2);
+                x0 = max(x0, (int)floorf((fi.x - rx - a.flo0) * a.finv_cs));
+                x1 = min(x1, (int)floorf((fi.x + rx - a.flo0) * a.finv_cs));
+                if (x0 > x1) continue;
+            }
             // cells x0..x1 of this (y, z) line are contiguous in the cell order
             int64_t b = cell_start[rowc + x0], e = cell_start[rowc + x1 + 1];
             for (int64_t k = b; k < e; ++k) {
@@ -224,6 +244,7 @@ __global__ void k_nbr(const double *X, int64_t N, GridArgs a, const int64_t *cel
                 }
             }
         }
+    }
     if (!out) count[i] = n;
 }
 
@@ -325,12 +346,31 @@ static Prefilter prefilter_for(const CellGrid &g, double rc2)
     return p;
 }
 
+// the grid in the prefilter's frame, with the clipping radius: rc enlarged by
+// 1e-4 of itself plus 32 units of FP32 rounding at the grid's extent (the
+// coordinates, the cell boundaries and the clipped range are each within a
+// few of those)
+static GridArgs clip_args(const CellGrid &g, const Prefilter &p, double rc2)
+{
+    GridArgs a = grid_args(g);
+    double ext = 0.0;
+    for (int k = 0; k < 3; ++k) ext = fmax(ext, g.nc[k] * g.cs);
+    const double rcm = sqrt(rc2) * (1.0 + 1e-4) + 32.0 * ext * 0x1p-24;
+    a.flo0 = (float)(g.xmin[0] - p.cx);
+    a.flo1 = (float)(g.xmin[1] - p.cy);
+    a.flo2 = (float)(g.xmin[2] - p.cz);
+    a.fcs = (float)g.cs;
+    a.finv_cs = (float)(1.0 / g.cs);
+    a.rcm2 = (float)(rcm * rcm);
+    return a;
+}
+
 cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
                                   int64_t *row_ptr, cudaStream_t st)
 {
-    GridArgs a = grid_args(g);
     cudaError_t e;
     const Prefilter pf = prefilter_for(g, rc2);
+    const GridArgs a = clip_args(g, pf, rc2);
     if (sc.xf) {
         k_xf<<<blocks_for(s.N, 256), 256, 0, st>>>(s.X, s.N, pf, sc.xf);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -354,9 +394,10 @@ cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Sc
 cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
                                  const int64_t *row_ptr, int32_t *col, cudaStream_t st)
 {
-    GridArgs a = grid_args(g);
+    const Prefilter pf = prefilter_for(g, rc2);
+    const GridArgs a = clip_args(g, pf, rc2);
     k_nbr<<<blocks_for(s.N, 128), 128, 0, st>>>(s.X, s.N, a, sc.cell_start, sc.cell_items, rc2, nullptr,
-                                                 row_ptr, col, sc.xf, prefilter_for(g, rc2));
+                                                 row_ptr, col, sc.xf, pf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sort_rows<<<blocks_for(s.N * 32, 256), 256, 0, st>>>(row_ptr, col, s.N);
@@ -681,10 +722,10 @@ __global__ void k_bounds(const double *X, int64_t N, double *out6)
 // the cell grid over a bounding box: cells a little wider than rc so rounding
 // in the cell coordinate can never put two particles closer than rc two cells
 // apart, widened until there are at most 2N + 4096 cells
-CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc)
+CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc, int div)
 {
     CellGrid g{};
-    double cs = rc * (1.0 + 1e-6);
+    double cs = rc / (double)div * (1.0 + 1e-6);
     const double cap = 2.0 * (double)N + 4096.0;
     for (;;) {
         double cells = 1.0;
@@ -698,6 +739,7 @@ CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, do
     }
     g.cs = cs;
     g.ncells = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    g.reach = cs >= rc ? 1 : (int32_t)ceil(rc / cs);
     return g;
 }
 
@@ -771,7 +813,7 @@ extern "C" int tlsph_neighbors_noalloc(const double *X, int64_t N, double rc, in
         return fail(TLSPH_ERR_CUDA, std::string("bounds: ") + cudaGetErrorString(e));
     for (int k = 0; k < 6; ++k)
         if (!isfinite(bb[k])) return fail(TLSPH_ERR_ARG, "X must be finite");
-    const CellGrid g = cell_grid_from_bounds(bb, bb + 3, N, rc);
+    const CellGrid g = cell_grid_from_bounds(bb, bb + 3, N, rc, 2);
     if (g.ncells > max_cells) return fail(TLSPH_ERR_ARG, "cell grid exceeds its bound");
 
     DevState s{};

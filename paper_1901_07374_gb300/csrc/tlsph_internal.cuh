@@ -164,9 +164,11 @@ struct CellGrid {
     double cs;
     int32_t nc[3];
     int64_t ncells;
+    int32_t reach;          // cells to either side that a neighbour within rc can lie in
 };
-CellGrid make_cell_grid(const double *X_host, int64_t N, double rc);
-CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc);
+// cell edge rc / div (div 1: the internal order's grid; div 2: the neighbour
+// search's), enlarged while the cells would exceed 2 N + 4096
+CellGrid cell_grid_from_bounds(const double *lo, const double *hi, int64_t N, double rc, int div = 1);
 cudaError_t build_neighbors_count(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
                                   int64_t *row_ptr, cudaStream_t st);
 cudaError_t build_neighbors_fill(const DevState &s, const CellGrid &g, const Scratch &sc, double rc2,
