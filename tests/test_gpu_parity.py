@@ -57,6 +57,36 @@ def test_neighbors_exact_lattice_ties():
     assert np.array_equal(g.get("NBR_COL"), col)
 
 
+@pytest.mark.parametrize("offset", [0.0, 1e3])
+def test_neighbors_bit_exact_random_cloud(offset):
+    """Unstructured cloud (uniform in a box, about 110 neighbours per row),
+    also far from the origin: the neighbour search, whose cells are clipped
+    to the cutoff ball in single precision, finds exactly the oracle's
+    pairs."""
+    rng = np.random.default_rng(11)
+    d, n = 0.5e-3, 4000
+    X = rng.uniform(0.0, 16 * d, size=(n, 3)) + np.array([offset, -offset / 4, offset / 9])
+    sp = S.Specimen("cloud", X, np.full(n, d ** 3), np.zeros(n, np.int32), np.zeros(n, np.uint8), np.zeros((n, 3)),
+                    np.zeros(n), d, ())
+    w = S.Workload("cloud", sp, [S.aluminium_cl()], 0.75e-3, 1.5e-3, 2e-8, 10.0, 1)
+    g = gpu_sim(w)
+    row_ptr, col = oracle.neighbors(X, w.rc)
+    assert np.array_equal(g.get("NBR_ROWPTR"), row_ptr)
+    assert np.array_equal(g.get("NBR_COL"), col)
+
+
+def test_neighbors_lattice_at_half_cutoff():
+    """Exact lattice of spacing rc/2, the search grid's cell edge up to 1e-6:
+    particles sit on and next to the cell boundaries, and the pairs at exactly
+    rc (two spacings) are excluded on both sides."""
+    sp = S.tensile_bar(12, 12, 12, 0.75e-3, jitter=0.0)
+    w = S.Workload("half", sp, [S.aluminium_cl()], 0.75e-3, 1.5e-3, 2e-8, 10.0, 1)
+    g = gpu_sim(w)
+    row_ptr, col = oracle.neighbors(sp.X, w.rc)
+    assert np.array_equal(g.get("NBR_ROWPTR"), row_ptr)
+    assert np.array_equal(g.get("NBR_COL"), col)
+
+
 @pytest.mark.parametrize("name,make", SMALL)
 def test_correction_matrix(name, make):
     w = make()
