@@ -431,7 +431,6 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
         if (e != cudaSuccess) { cudaGetLastError(); return bail(TLSPH_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
         ctx->owns_mem = true;
         ctx->mem = base;
-        ctx->mem_bytes = L.overlay_end;
     }
     bind_state(ctx, base, L);
     DevState &s = ctx->s;

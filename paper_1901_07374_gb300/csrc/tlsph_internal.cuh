@@ -119,7 +119,6 @@ struct tlsph_ctx {
     cudaStream_t stream = nullptr;
     bool owns_mem = false;
     void *mem = nullptr;
-    size_t mem_bytes = 0;
     tlsph::DevState s{};
     tlsph::DevMat mats_host[TLSPH_MAX_MATERIALS]{};
     bool mat_set[TLSPH_MAX_MATERIALS]{};
