@@ -162,15 +162,15 @@ def measured_peaks() -> dict:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_rate(seconds: float, max_steps: int | None = None, nz: int = 24):
+def oracle_rate(seconds: float, max_steps: int | None = None, nz: int = 24, warmup: int = 1):
     """Pair-interactions/s of the FP64 oracle (single thread) on the first
-    `nz` layers of the 40x40 bar; runs until `seconds` of stepping or
-    max_steps.  Returns (rate, steps, pairs per step, N)."""
+    `nz` layers of the 40x40 bar; `warmup` untimed steps, then stepping until
+    `seconds` or max_steps.  Returns (rate, steps, pairs per step, N, seconds)."""
     import oracle
     from paper_1901_07374_gb300 import specimen as S
     w = S.tensile_bar_jc(nx=40, ny=40, nz=nz)
     sim = oracle.Simulation.from_workload(w)
-    sim.step(1)       # warm
+    sim.step(max(1, warmup))
     steps = 0
     t0 = time.perf_counter()
     while True:
@@ -208,10 +208,11 @@ def oracle_rate_all_cores(seconds: float, cores: int | None = None):
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
-    rate, steps, nnz, N, el = oracle_rate(1e9, max_steps=args.steps)
+    warmup = max(1, args.warmup)
+    rate, steps, nnz, N, el = oracle_rate(1e9, max_steps=args.steps, warmup=warmup)
     sample = f"first 24 of 640 layers of the 40x40 bar ({N} particles, {nnz} pairs), {steps} steps in {el:.1f} s"
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
-            "steps": steps, "warmup": 1, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "sample": sample},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
