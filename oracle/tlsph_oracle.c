@@ -372,7 +372,8 @@ static double shear_modulus(const orc_material *m) { return m->E / (2.0 * (1.0 +
  * negative with eta = rho/rho0 = 1/J, multiplied by (1 - D) when tensile.
  * With S_alpha = Gamma0 = 0 and rho0 c0^2 = K this is sigma_m = K (J - 1)
  * exactly; the linear EOS (eos = 0) uses K = E / (3 (1 - 2 nu)).
- * Internal energy is not tracked (Gamma0 e term taken as zero). */
+ * e is the specific internal energy of Eq. (conservation3) at the start of
+ * the step; it enters through the Gamma0 rho0 e term below. */
 double orc_eos_mean_stress(const orc_material *m, double J, double D, double e)
 {
     double sm;
@@ -692,8 +693,10 @@ typedef struct {
  *   eps_a = F_a X_ab - x_ab,  eps_b = F_b X_ab - x_ab,
  *   delta = (eps_a + eps_b) . xhat_ab,
  *   f_hg = -1/2 alpha (1-D_a)(1-D_b) V_a V_b W(X_ab) E / X_ab^2 delta xhat_ab,
- * with x_ab = X_ab + u_b - u_a and E the geometric mean sqrt(E_a E_b) of
- * the pair's Young moduli (symmetric in a, b; E itself for one material). */
+ * with x_ab = X_ab + u_b - u_a and E the arithmetic mean (E_a + E_b) / 2
+ * of the pair's Young moduli (symmetric in a, b; E itself for one material:
+ * the bond's stiffness is the average of the two particles' stiffnesses, as
+ * delta is the sum of the two particles' errors). */
 static void pair_force(const orc_system *s, const orc_config *c, int64_t a, int64_t b, double *t)
 {
     const double *Xa = s->X + 3 * a, *Xb = s->X + 3 * b;
@@ -723,7 +726,7 @@ static void pair_force(const orc_system *s, const orc_config *c, int64_t a, int6
                 ea -= x[k]; eb -= x[k];
                 delta += (ea + eb) * xh[k];
             }
-            double E = sqrt(s->mats[s->mat_id[a]].E * s->mats[s->mat_id[b]].E);
+            double E = 0.5 * (s->mats[s->mat_id[a]].E + s->mats[s->mat_id[b]].E);
             double coef = -0.5 * c->hg_alpha * (1.0 - Da) * (1.0 - Db) * Va * Vb
                         * orc_kernel_w(r, c->h) * E / (r * r) * delta;
             for (int k = 0; k < 3; ++k) t[k] += coef * xh[k];
