@@ -25,7 +25,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 // base and 256-byte aligned.  The neighbour-build scratch overlays the
 // F / sd / sig / A block, which is only initialised after the build.
 struct Layout {
-    size_t X, vol, mass, inv_mass, sqrtE, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
+    size_t X, vol, mass, inv_mass, youngs, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, e, D0, D1, force, fail, status, mats, col, diag, inscan;
     size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
@@ -118,7 +118,7 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
     L.vol = c.take(n * d);
     L.mass = c.take(n * d);
     L.inv_mass = c.take(n * d);
-    L.sqrtE = c.take(n * d);
+    L.youngs = c.take(n * d);
     L.mat = c.take(n * sizeof(int32_t));
     L.bcm = c.take(n);
     L.bcv = c.take(3 * n * d);
@@ -256,7 +256,7 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
     s.vol = at<double>(base, L.vol);
     s.mass = at<double>(base, L.mass);
     s.inv_mass = at<double>(base, L.inv_mass);
-    s.sqrtE = at<double>(base, L.sqrtE);
+    s.youngs = at<double>(base, L.youngs);
     s.mat = at<int32_t>(base, L.mat);
     s.bcm = at<uint8_t>(base, L.bcm);
     s.bcv = at<double>(base, L.bcv);
@@ -348,7 +348,6 @@ DevMat make_dev_mat(const tlsph_material &m)
     d.E = m.E;
     d.K = m.E / (3.0 * (1.0 - 2.0 * m.nu));
     d.G = m.E / (2.0 * (1.0 + m.nu));
-    d.sqrtE = sqrt(m.E);
     d.eos = m.eos;
     d.damage = m.damage;
     d.rho0c02 = m.rho0 * m.c0 * m.c0;
@@ -369,7 +368,7 @@ DevMat make_dev_mat(const tlsph_material &m)
     d.fstar_slope = (m.fF > m.fc) ? (1.0 / m.q1 - m.fc) / (m.fF - m.fc) : 0.0;
     d.Kf = (float)d.K; d.Gf = (float)d.G; d.Af = (float)d.A; d.Bf = (float)d.B; d.nf = (float)d.n;
     d.Cf = (float)d.C; d.inv_epsdot0f = (float)d.inv_epsdot0; d.rho0c02f = (float)d.rho0c02;
-    d.S_alphaf = (float)d.S_alpha; d.Gamma0f = (float)d.Gamma0; d.sqrtEf = (float)d.sqrtE;
+    d.S_alphaf = (float)d.S_alpha; d.Gamma0f = (float)d.Gamma0;
     d.q1f = (float)d.q1; d.q2f = (float)d.q2; d.q3f = (float)d.q3; d.fcf = (float)d.fc; d.fFf = (float)d.fF;
     d.fstar_slopef = (float)d.fstar_slope;
     d.g0rho0f = (float)d.g0rho0;
@@ -456,7 +455,7 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     CK(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), st));
     CK(cudaMemsetAsync((void *)s.mass, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync((void *)s.inv_mass, 0, n * sizeof(double), st));
-    CK(cudaMemsetAsync((void *)s.sqrtE, 0, n * sizeof(double), st));
+    CK(cudaMemsetAsync((void *)s.youngs, 0, n * sizeof(double), st));
 
     // ---- one pass over the staged inputs: validation, bounding box, materials
     // in use and the sum of the initial velocities (the bulk reference of the

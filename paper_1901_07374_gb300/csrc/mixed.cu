@@ -33,7 +33,7 @@
 //   r1   {v^{n+1/2} - v_ref, V (1 - D)}                       pass-1 gather record
 //   r2k  k = 0..5 (at r2 + k N):                               pass-2 gather record
 //        {A00 A01 A02 A10} {A11 A12 A20 A21} {A22, V D, V, u_x}
-//        {u_y, u_z, G00, G01} {G02 G10 G11 G12} {G20, G21, G22, sqrt(E) V (1-D)}
+//        {u_y, u_z, G00, G01} {G02 G10 G11 G12} {G20, G21, G22, E V (1-D)}
 //        with G = F - I and u in fixed-point units.
 // Thread-per-row kernels read their neighbours through the sliced neighbour
 // lists (slices of 32 rows, aligned or explicit form, described below).
@@ -560,7 +560,7 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
     r2[2 * R2_STRIDE] = make_float4(A[8], Vf * (float)Dnew, Vf, u0);
     r2[3 * R2_STRIDE] = make_float4(u1, u2, G[0], G[1]);
     r2[4 * R2_STRIDE] = make_float4(G[2], G[3], G[4], G[5]);
-    r2[5 * R2_STRIDE] = make_float4(G[6], G[7], G[8], (float)s.sqrtE[i] * Vf * omd);
+    r2[5 * R2_STRIDE] = make_float4(G[6], G[7], G[8], (float)s.youngs[i] * Vf * omd);
     if (st) atomicOr(s.status, st);
 }
 
@@ -893,8 +893,8 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
     f[2] = vdw * ((Ai[6] * bx + Ai[7] * by + Ai[8] * bz) + omdf * keep[5]);
     if (HG) {
         // the pair sums are in fixed-point units (X_ij, u_ij and x_ij scaled by 1/unit): hg_w folds 1/unit in;
-        // r2 record 5 .w holds sqrt(E_i) V_i (1 - D_i)
-        const float hc = c.hg_w * ri[5 * R2_STRIDE].w;
+        // the sums carry (E_i + E_j) V_j (1 - D_j), the 1/2 of the pair modulus is taken here
+        const float hc = c.hg_w * 0.5f * Vf * omdf;
         f[0] += hc * keep[6];
         f[1] += hc * keep[7];
         f[2] += hc * keep[8];
@@ -945,6 +945,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
 struct Row2 {   // row i's own pass-2 record
     int4 o;
     float4 a0, a1, a2, a3, a4, a5;
+    float E;    // Young modulus of row i's material (hourglass term)
 };
 
 template <bool HG>
@@ -957,7 +958,9 @@ __device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, 
     w.a1 = ri[R2_STRIDE];
     w.a2 = ri[2 * R2_STRIDE];
     w.a3 = w.a4 = w.a5 = make_float4(0.f, 0.f, 0.f, 0.f);
+    w.E = 0.0f;
     if (HG) {
+        w.E = (float)s.youngs[i];
         w.a3 = ri[3 * R2_STRIDE];
         w.a4 = ri[4 * R2_STRIDE];
         w.a5 = ri[5 * R2_STRIDE];
@@ -994,8 +997,10 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
         const float ex = (w.a3.z + b3.z) * d.x + (w.a3.w + b3.w) * d.y + (w.a4.x + b4.x) * d.z - 2.0f * ux;
         const float ey = (w.a4.y + b4.y) * d.x + (w.a4.z + b4.z) * d.y + (w.a4.w + b4.w) * d.z - 2.0f * uy;
         const float ez = (w.a5.x + b5.x) * d.x + (w.a5.y + b5.y) * d.y + (w.a5.z + b5.z) * d.z - 2.0f * uz;
-        // sqrt(E_j) V_j (1 - D_j) W / X_ij^2 * delta / |x_ij| with delta = (e . x_ij) / |x_ij|
-        const float ch = b5.w * spline_w_ab(a, b) * rinv * rinv * (ex * xx + ey * xy + ez * xz) * lxi2;
+        // (E_i + E_j) V_j (1 - D_j) W / X_ij^2 * delta / |x_ij| with delta = (e . x_ij) / |x_ij|;
+        // V_j (1 - D_j) = V_j - V_j D_j, and the record carries E_j V_j (1 - D_j)
+        const float ev = fmaf(w.E, b2.z - b2.y, b5.w);
+        const float ch = ev * spline_w_ab(a, b) * rinv * rinv * (ex * xx + ey * xy + ez * xz) * lxi2;
         acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
     }
 }

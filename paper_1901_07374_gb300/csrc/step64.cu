@@ -236,10 +236,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass2_fp64(DevState s, StepCon
     for (int r = 0; r < nrows; ++r) {
         const int64_t i = row0 + r;
         const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
-        double uxi = 0, uyi = 0, uzi = 0;
+        double uxi = 0, uyi = 0, uzi = 0, Ei = 0;
         double Fi[9];
         if (HG) {
             uxi = un[3 * i]; uyi = un[3 * i + 1]; uzi = un[3 * i + 2];
+            Ei = s.youngs[i];
 #pragma unroll
             for (int k = 0; k < 9; ++k) Fi[k] = Fa[9 * i + k];
         }
@@ -275,7 +276,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass2_fp64(DevState s, StepCon
                     const double gz = (Fi[6] + Fj[6]) * dx + (Fi[7] + Fj[7]) * dy + (Fi[8] + Fj[8]) * dz;
                     // delta = (eps_i + eps_j) . xhat = ((F_i + F_j) X_ij) . xhat - 2 |x_ij|
                     const double delta = (gx * xx + gy * xy + gz * xz) * lxi - 2.0 * lx2 * lxi;
-                    const double ch = s.sqrtE[j] * omd * Vj * spline_w(q) * rinv * rinv * delta * lxi;
+                    // pair modulus (E_i + E_j) / 2; the 1/2 is in the epilogue's coefficient
+                    const double ch = (Ei + s.youngs[j]) * omd * Vj * spline_w(q) * rinv * rinv * delta * lxi;
                     acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
                 }
             }
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass2_fp64(DevState s, StepCon
     for (int k = 0; k < 3; ++k)
         f[k] = Vi * c.dw_norm * (Ai[3 * k] * keep[0] + Ai[3 * k + 1] * keep[1] + Ai[3 * k + 2] * keep[2] + omdi * keep[3 + k]);
     if (HG) {
-        const double hc = c.hg_coef * s.sqrtE[i] * omdi * Vi * c.w_norm;
+        const double hc = 0.5 * c.hg_coef * omdi * Vi * c.w_norm;
 #pragma unroll
         for (int k = 0; k < 3; ++k) f[k] += hc * keep[6 + k];
     }
@@ -372,7 +374,7 @@ __global__ void k_material_fields(DevState s, int mat_id, int dcur, int set_gtn_
     const DevMat &m = s.mats[mat_id];
     const_cast<double *>(s.mass)[i] = m.rho0 * s.vol[i];
     const_cast<double *>(s.inv_mass)[i] = 1.0 / (m.rho0 * s.vol[i]);
-    const_cast<double *>(s.sqrtE)[i] = m.sqrtE;
+    const_cast<double *>(s.youngs)[i] = m.E;
     if (set_gtn_damage && m.damage == TLSPH_DAMAGE_GTN) s.D[dcur][i] = m.q1 * gtn_fstar(m, s.por[i]);
 }
 

@@ -16,7 +16,7 @@ namespace tlsph {
 // derived moduli (K = E / (3 (1 - 2 nu)), G = E / (2 (1 + nu))) and the
 // reciprocals the inner loops would otherwise divide by.
 struct DevMat {
-    double rho0, E, K, G, sqrtE;
+    double rho0, E, K, G;
     int32_t eos, damage;
     double rho0c02, S_alpha, Gamma0;
     double A, B, n, C, inv_epsdot0;
@@ -28,7 +28,7 @@ struct DevMat {
     double g0rho0;       // Gamma0 rho0 (energy term of the Mie-Grueneisen EOS)
     double inv_rho0;
     // single-precision copies for the mixed path's elastic fast path
-    float Kf, Gf, Af, Bf, nf, Cf, inv_epsdot0f, rho0c02f, S_alphaf, Gamma0f, sqrtEf;
+    float Kf, Gf, Af, Bf, nf, Cf, inv_epsdot0f, rho0c02f, S_alphaf, Gamma0f;
     float q1f, q2f, q3f, fcf, fFf, fstar_slopef;
     float g0rho0f, inv_rho0f;
 };
@@ -51,7 +51,7 @@ struct DevState {
     const double *vol;      // N
     const double *mass;     // N   rho0 V
     const double *inv_mass; // N   1 / (rho0 V)
-    const double *sqrtE;    // N   sqrt of the particle's Young modulus (hourglass stiffness)
+    const double *youngs;   // N   Young modulus of the particle's material (hourglass stiffness)
     const int32_t *mat;     // N
     const uint8_t *bcm;     // N
     const double *bcv;      // N*3
