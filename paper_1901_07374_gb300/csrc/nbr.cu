@@ -694,19 +694,29 @@ static constexpr int64_t NOALLOC_MAX_N = 262144;
 static constexpr size_t NOALLOC_SCRATCH_BYTES = 10u << 20;   // 10 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-// bounding box of X (one block, deterministic min / max)
+// bounding box of X (one block, deterministic min / max); a coordinate that
+// is not finite (fmin / fmax would skip a NaN) makes every bound NaN, which
+// the host rejects
 __global__ void k_bounds(const double *X, int64_t N, double *out6)
 {
     __shared__ double lo[3][256], hi[3][256];
     const int t = threadIdx.x;
     double l[3] = { INFINITY, INFINITY, INFINITY }, h[3] = { -INFINITY, -INFINITY, -INFINITY };
+    int bad = 0;
     for (int64_t i = t; i < N; i += blockDim.x)
         for (int k = 0; k < 3; ++k) {
-            l[k] = fmin(l[k], X[3 * i + k]);
-            h[k] = fmax(h[k], X[3 * i + k]);
+            const double x = X[3 * i + k];
+            bad |= !isfinite(x);
+            l[k] = fmin(l[k], x);
+            h[k] = fmax(h[k], x);
         }
     for (int k = 0; k < 3; ++k) { lo[k][t] = l[k]; hi[k][t] = h[k]; }
-    __syncthreads();
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        if (t == 0)
+            for (int k = 0; k < 6; ++k) out6[k] = NAN;
+        return;
+    }
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (t < w)
             for (int k = 0; k < 3; ++k) {

@@ -452,15 +452,48 @@ class Simulation:
         self.close()
 
 
+def _check_tensor(name, t, dtype, shape=None, min_numel=None, ndim=None):
+    """Validate the form of a torch tensor whose data pointer crosses the ABI:
+    dtype, shape, contiguity.  Raises ValueError."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must be {ndim}-dimensional, got {t.dim()} dimensions")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} needs at least {min_numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _check_device(**tensors):
+    """Every tensor is a CUDA tensor, all on one device.  Raises ValueError."""
+    dev = None
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if dev is not None and t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, the other arguments on {dev}")
+        dev = t.device
+
+
 def material_point_batch(mat: dict, dt: float, deps, J, state, stream=None) -> None:
     """Constitutive update of n material points on the GPU (torch CUDA float64
     tensors: deps (n, 9), J (n,), state (n, 16) updated in place)."""
+    import torch
+    n = int(J.numel())
+    _check_tensor("J", J, torch.float64, shape=(n,))
+    _check_tensor("deps", deps, torch.float64, shape=(n, 9))
+    _check_tensor("state", state, torch.float64, shape=(n, 16))
+    _check_device(J=J, deps=deps, state=state)
     L = load()
     m = make_material(mat)
-    n = int(J.numel())
-    for t in (deps, J, state):
-        if not (t.is_cuda and t.is_contiguous()):
-            raise ValueError("material_point_batch needs contiguous CUDA tensors")
     code = L.tlsph_material_point_batch(ctypes.byref(m), float(dt), n, ctypes.c_void_p(deps.data_ptr()),
                                         ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(state.data_ptr()),
                                         ctypes.c_void_p(_stream_handle(stream)))
@@ -470,7 +503,17 @@ def material_point_batch(mat: dict, dt: float, deps, J, state, stream=None) -> N
 def neighbors_noalloc(X, rc: float, row_ptr, col, stream=None) -> int:
     """tlsph_neighbors_noalloc on torch CUDA tensors: X (N, 3) float64,
     row_ptr (N + 1,) int64, col (capacity,) int32.  Returns the pair count;
-    raises TlsphError (code -4) when col is too small."""
+    raises TlsphError (code -4) when col is too small, ValueError before any
+    launch when a tensor has the wrong dtype, shape, layout or device."""
+    import torch
+    if not isinstance(X, torch.Tensor) or X.dim() != 2:
+        raise ValueError("X must be a torch tensor of shape (N, 3)")
+    N = int(X.shape[0])
+    _check_tensor("X", X, torch.float64, shape=(N, 3))
+    _check_tensor("row_ptr", row_ptr, torch.int64, min_numel=N + 1, ndim=1)
+    if col is not None:
+        _check_tensor("col", col, torch.int32, ndim=1)
+    _check_device(X=X, row_ptr=row_ptr, col=col)
     L = load()
     fn = L.tlsph_neighbors_noalloc
     fn.restype = ctypes.c_int

@@ -7,6 +7,7 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+from paper_1901_07374_gb300 import specimen as S
 
 # library field name -> oracle state key
 ORACLE_KEY = {"U": "u", "V": "v", "F": "F", "SIGMA": "sigma", "STRESS_DEV": "sd", "EPSP": "ep",
@@ -85,3 +86,35 @@ def sub_workload(w, idx):
                               bc_mask=sp.bc_mask[idx], bc_vel=np.ascontiguousarray(sp.bc_vel[idx]), f0=sp.f0[idx],
                               dims=())
     return dataclasses.replace(w, specimen=sub)
+
+
+def taylor_energy_terms(mass, dt, v_n, f_n, v_n1, f_n1):
+    """Per-step terms of the velocity-Verlet energy balance with the rigid
+    wall, from the full-step velocities and forces alone (any path).
+
+    The half-step velocity the drift used is v_post = v^{n+1} - dt/2 f^{n+1}/m,
+    the one before the wall's projection is v_pre = v^n + dt/2 f^n/m; the wall
+    removes  W = 1/2 m (v_pre - v_post) . (2 v^n - v_pre + v_post)  in the
+    step (zero for a free particle and for one at rest against the wall), and
+    the conserved quantity of the scheme is the kinetic energy less
+    dt^2/8 sum |f|^2/m (the scheme's shadow term) plus the internal energy."""
+    m = mass[:, None]
+    v_pre = v_n + 0.5 * dt * f_n / m
+    v_post = v_n1 - 0.5 * dt * f_n1 / m
+    wall = 0.5 * np.sum(m * (v_pre - v_post) * (2.0 * v_n - v_pre + v_post))
+    return wall
+
+
+def shadow_energy(mass, dt, v, f, e):
+    return 0.5 * np.sum(mass[:, None] * v * v) - dt * dt / 8.0 * np.sum(f * f / mass[:, None]) + np.sum(mass * e)
+
+
+def taylor_energy_workload():
+    """Taylor impact at 250 m/s onto the wall, no damage and no hourglass term
+    (its work is not part of the internal energy), through 200 steps of plastic
+    impact."""
+    import dataclasses
+    w = S.taylor_impact(3000, v_impact=250.0, steps=200)
+    m = dict(w.materials[0])
+    m["damage"] = S.DAMAGE_NONE
+    return dataclasses.replace(w, materials=[m], hg_alpha=0.0)

@@ -86,3 +86,38 @@ def test_diagnostics_argument_errors(lib):
     lib.tlsph_diagnostics.restype = ctypes.c_int
     lib.tlsph_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     assert lib.tlsph_diagnostics(None, out, 11) == -1
+
+
+def test_tensor_bindings_reject_bad_tensors_before_any_launch():
+    """The bindings that pass torch data pointers straight to the kernels
+    (tlsph_neighbors_noalloc, tlsph_material_point_batch) check dtype, shape,
+    layout and device first: each bad argument raises ValueError on the host
+    (CPU tensors of the right form fail the device check last)."""
+    torch = pytest.importorskip("torch")
+    N = 8
+    X = torch.zeros((N, 3), dtype=torch.float64)
+    rp = torch.zeros(N + 1, dtype=torch.int64)
+    col = torch.zeros(100, dtype=torch.int32)
+    bad = [
+        (X.float(), rp, col, "float64"),                                  # X in FP32
+        (torch.zeros((N, 4), dtype=torch.float64), rp, col, "shape"),     # X not (N, 3)
+        (torch.zeros((N, 6), dtype=torch.float64)[:, ::2], rp, col, "contiguous"),
+        (X, rp.int(), col, "int64"),                                      # row_ptr in int32
+        (X, torch.zeros(N, dtype=torch.int64), col, "at least"),          # row_ptr too short
+        (X, rp, col.long(), "int32"),                                     # col in int64
+        (X, rp, torch.zeros((10, 10), dtype=torch.int32), "1-dimensional"),
+        (X, rp, col, "CUDA"),                                             # host tensors
+        ([[0.0, 0.0, 0.0]], rp, col, "torch tensor"),
+    ]
+    for x, r, c, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            tlsph.neighbors_noalloc(x, 1e-3, r, c)
+    n = 4
+    deps, J, st = torch.zeros((n, 9), dtype=torch.float64), torch.ones(n, dtype=torch.float64), \
+        torch.zeros((n, 16), dtype=torch.float64)
+    from paper_1901_07374_gb300 import specimen as S
+    m = S.aluminium_cl()
+    for args, msg in [((deps.float(), J, st), "float64"), ((deps, J, st[:, :15]), "shape"),
+                      ((deps.t().contiguous().t(), J, st), "contiguous"), ((deps, J, st), "CUDA")]:
+        with pytest.raises(ValueError, match=msg):
+            tlsph.material_point_batch(m, 1e-7, *args)

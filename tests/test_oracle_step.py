@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_1901_07374_gb300 import specimen as S
+from parity import shadow_energy, taylor_energy_terms, taylor_energy_workload
 
 
 def _free_bar(dims=(5, 5, 9), seed=0, hg_alpha=0.0, mat=None, spacing=0.5e-3):
@@ -399,3 +400,34 @@ def test_internal_energy_under_uniform_compression_closed_form():
     K = mat["E"] / (3.0 * (1.0 - 2.0 * mat["nu"]))
     exact = K * (J - 1.0) ** 2 / (2.0 * mat["rho0"])
     assert np.allclose(o["e"], exact, rtol=2e-3), (o["e"][:3], exact[:3])
+
+
+def test_taylor_impact_energy_balance():
+    """Kinetic plus internal energy (Sec. 2.1, Eq. conservation3) through a
+    Taylor impact: constant in free flight, then the wall removes energy and
+    the balance closes to the free-vibration tolerance once the wall's work is
+    added back.  The same terms from the GPU paths are checked in
+    test_gpu_taylor_energy.py."""
+    w = taylor_energy_workload()
+    o = oracle.Simulation.from_workload(w)
+    mass = w.specimen.vol * w.materials[0]["rho0"]
+    E0 = shadow_energy(mass, w.dt, o["v"], o["force"], o["e"])
+    wall = 0.0
+    contact = None
+    worst = 0.0
+    prev = E0
+    for k in range(w.steps):
+        v_n, f_n = o["v"].copy(), o["force"].copy()
+        o.step(1)
+        dW = taylor_energy_terms(mass, w.dt, v_n, f_n, o["v"], o["force"])
+        wall += dW
+        E = shadow_energy(mass, w.dt, o["v"], o["force"], o["e"])
+        if contact is None and dW > 1e-9 * E0:
+            contact = k
+        if contact is None:
+            assert E == pytest.approx(E0, rel=1e-13)     # rigid flight
+        worst = max(worst, abs(E + wall - E0) / E0)
+        assert E <= prev + 3e-3 * E0                       # the total never grows
+        prev = E
+    assert contact is not None and wall > 0.02 * E0 and o["ep"].max() > 0.3
+    assert worst < 3e-3, worst
