@@ -280,14 +280,18 @@ def test_material_point_batch_matches_oracle():
 
 # ------------------------------------------------------------------ full size
 
-def _full_size_sample_check(w, steps, samples):
+def _full_size_sample_check(w, steps, samples, precision="fp64", plan=None, tol=TOL_FP64, fields=None):
     """Run the whole workload on the GPU (the benchmark's launch
-    configuration) and reproduce sampled particles with the oracle on a ball
-    of radius (2 steps + 1) rc + rc around each."""
-    g = gpu_sim(w)
+    configuration: precision and launch plan) and reproduce sampled particles
+    with the oracle on a ball of radius (2 steps + 1) rc + rc around each."""
+    g = gpu_sim(w, precision)
+    if plan is not None:
+        g.set_plan(plan)
+        assert g.get_plan() == tuple(plan)
     g.step(steps)
     gs = g.state()
     X = w.specimen.X
+    worst = {}
     for c in samples:
         idx = ball(X, [c], (2 * steps + 2) * w.rc)
         sub = sub_workload(w, idx)
@@ -295,7 +299,11 @@ def _full_size_sample_check(w, steps, samples):
         o.step(steps)
         k = int(np.searchsorted(idx, c))
         os_ = o.state()
-        compare_state({f: v[[c]] for f, v in gs.items()}, {f: v[[k]] for f, v in os_.items()}, w)
+        errs = compare_state({f: v[[c]] for f, v in gs.items()}, {f: v[[k]] for f, v in os_.items()}, w,
+                             tol=tol, fields=fields)
+        for f, e in errs.items():
+            worst[f] = max(worst.get(f, 0.0), e)
+    print(w.name, precision, "largest sampled error per field", worst)
     return g
 
 
@@ -356,3 +364,53 @@ def test_mie_grueneisen_energy_term_taylor_impact():
     gm = gpu_sim(w, "mixed")
     gm.step(120)
     compare_state(gm.state(), os_, w, tol=2e-3, fields=("U", "V", "F", "ENERGY"))
+
+
+# the launch plan the benchmark times on the 1.02M-particle bar (autotuned)
+BENCH_PLAN = (4, 128, 7, 128)
+MIXED_TOL = 2e-4
+
+
+def _bar_samples(w, rng):
+    sp = w.specimen
+    nx, ny, nz = sp.dims
+    return [0, nx * ny * 2 + nx + 1, (nz // 2) * nx * ny + (ny // 2) * nx + nx // 2, sp.N - 1,
+            int(rng.integers(sp.N)), int(rng.integers(sp.N))]
+
+
+def test_full_size_tensile_bar_jc_mixed_sampled():
+    """The benchmarked mixed path (its tuned launch plan, every slice of the
+    sliced neighbour lists aligned) on the 1,024,000-particle bar: sampled
+    particles after two steps within the mixed tolerance of the oracle."""
+    w = S.tensile_bar_jc()
+    g = _full_size_sample_check(w, 2, _bar_samples(w, np.random.default_rng(1)), precision="mixed",
+                                plan=BENCH_PLAN, tol=MIXED_TOL,
+                                fields=("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "DINIT", "DAMAGE", "FORCE",
+                                        "ENERGY"))
+    lay = g.neighbor_layout()
+    assert lay["aligned_slices"] == lay["slices"]
+
+
+def _gtn_samples(w, rng):
+    X = w.specimen.X
+    c = X.mean(0)
+    r = np.hypot(X[:, 0] - c[0], X[:, 1] - c[1])
+    mid = np.nonzero(np.abs(X[:, 2] - c[2]) < w.specimen.spacing)[0]
+    notch = mid[np.argmax(r[mid])]              # notch root, on the surface at mid-height
+    centre = np.argmin(np.sum((X - c) ** 2, 1))
+    grip = int(np.nonzero(w.specimen.bc_mask)[0][0])
+    return [int(notch), int(centre), grip, int(rng.integers(w.specimen.N)), int(rng.integers(w.specimen.N))]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_notched_bar_gtn_sampled(precision):
+    """The 455,958-particle GTN notched round bar at both precisions: sampled
+    particles (notch root, centre, grip, random) after two steps against the
+    oracle on balls around them."""
+    w = S.notched_bar_gtn()
+    assert w.specimen.N > 450000
+    tol = TOL_FP64 if precision == "fp64" else MIXED_TOL
+    fields = None if precision == "fp64" else ("U", "V", "F", "SIGMA", "STRESS_DEV", "EPSP", "DINIT", "DAMAGE",
+                                                "POROSITY", "FORCE", "ENERGY")
+    _full_size_sample_check(w, 2, _gtn_samples(w, np.random.default_rng(2)), precision=precision, tol=tol,
+                            fields=fields)
