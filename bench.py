@@ -67,7 +67,7 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
     if precision == "fp64":
         p1 = 4 * nnz + 656 * N     # row_ptr 8, X 24, v 24, Linv 72, F rw 144, sd rw 96, scalars rw 64,
         #                            D r+w 16, fail 4, mat 4, sigma r+w 96, e r+w 16, A w 72, vol 16 (gathered only)
-        p2 = 4 * nnz + 357 * N     # row_ptr 8, X 24, u 24, F 72, A 72, D 8, vol 8, sqrtE 8, mass 8,
+        p2 = 4 * nnz + 357 * N     # row_ptr 8, X 24, u 24, F 72, A 72, D 8, vol 8, E 8, mass 8,
         #                            vh rw 48, v w 24, force w 24, u' w 24, fail 4, bc 1
     else:
         from paper_1901_07374_gb300 import tlsph
@@ -75,14 +75,33 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
     return {"pass1": p1, "pass2": p2}
 
 
-# DRAM bytes (read + write) per step of each pass from one ncu capture of the
-# same kernel build, keyed by (workload, precision, pass, plan form of that
-# pass); absent for other plans and once the kernels change after the capture
-TRAFFIC = {
-    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 597262848,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 319589888,   # k_pass2_mixed_tc
-    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 7): 319007232,   # k_pass2_mixed_tc5
-}
+# DRAM bytes (read + write) per launch of each pass from one ncu capture
+# (profiles/traffic_tensile_bar_jc_40x40x640.md), keyed by (workload,
+# precision, pass, plan form of that pass) and stamped with the digest of the
+# CUDA sources they were captured from: a figure is reported only while the
+# sources are unchanged (otherwise `traffic` is null until the next capture).
+TRAFFIC_SOURCES = None
+TRAFFIC = {}
+
+
+def kernel_sources_digest() -> str:
+    """SHA-256 over the library's CUDA sources and headers (sorted by name)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1901_07374_gb300", "csrc", "*.cu*"))
+                    + [os.path.join(ROOT, "include", "tlsph.h")]):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload: str, precision: str, kern: str, form: int):
+    """DRAM bytes of one launch from the ncu capture of the current sources, or None."""
+    if TRAFFIC_SOURCES is None or TRAFFIC_SOURCES != kernel_sources_digest():
+        return None
+    return TRAFFIC.get((workload, precision, kern, form))
 
 
 def max_over_ranks(value: float, dist, device=None) -> float:
@@ -370,8 +389,8 @@ def run_ours(args, rank: int, world: int, dist):
     achieved = ab[kern] / (k_ms * 1e-3) / 1e9
     hbm = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": achieved / peak, "peak_source": src,
-           "traffic": TRAFFIC.get((args.workload, args.precision, kern,
-                                   (r.get("plan") or (0, 0, 0, 0))[0 if kern == "pass1" else 2])),
+           "traffic": profiled_traffic(args.workload, args.precision, kern,
+                                       (r.get("plan") or (0, 0, 0, 0))[0 if kern == "pass1" else 2]),
            "algorithmic_bytes_per_launch": ab[kern]}
     roofline = hbm
     if args.precision == "mixed":
@@ -456,6 +475,25 @@ def run_ours(args, rank: int, world: int, dist):
                            "+ download of u, v, sigma, D",
                "final_kinetic_energy": diag["kinetic_energy"] if diag else None}
 
+    # ---- the metric's batched and served forms, small versions inside the default run
+    batched = served = None
+    if args.precision == "mixed" and not args.no_forms:
+        from paper_1901_07374_gb300 import specimen as S
+        batched = measure_batched(tlsph, torch, S.batched_specimens(args.forms_specimens, seed=0), args.steps,
+                                  args.warmup, stream, fp64_one_by_one=True)
+        batched["workload"] = (f"the first {args.forms_specimens} bars of the 256-bar batched workload "
+                               "(same generator and seed)")
+        summ = serve_once(args, args.rate, count=args.forms_requests, steps_range=(200, 1000))
+        served = {"workload": f"{args.forms_requests} requests of the serving stream (same generator and seed, "
+                              f"Poisson arrivals at {args.rate:g}/s, half Taylor cylinders and half bars) with "
+                              "200-1000 steps each instead of 1000-5000, 120 GB admission cap",
+                  "latency_s": {"p50": summ["p50_s"], "p95": summ["p95_s"], "p99": summ["p99_s"]},
+                  "pair_interactions_per_s": summ["pair_interactions_per_s"],
+                  "offered_pair_interactions_per_s": summ["offered_pair_interactions_per_s"],
+                  "makespan_s": summ["makespan_s"], "done": summ["done"], "failed": summ["failed"],
+                  "max_live": summ["max_live"], "peak_mem_gb": summ["peak_mem_gb"], "steps": summ["steps"],
+                  "clocks": summ["clocks"]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, steps, onnz, oN, oel = oracle_rate(args.cpu_seconds)
@@ -464,8 +502,9 @@ def run_ours(args, rank: int, world: int, dist):
                          f"{steps} steps in {oel:.1f} s, single thread"}
         if args.cpu_all_cores:
             agg, cores = oracle_rate_all_cores(args.cpu_seconds / 2)
-            cpu["all_cores"] = {"value": agg, "unit": UNIT, "cores": cores,
-                                "how": "independent single-thread replicas of the same sample, one per core"}
+            cpu["replicas_on_all_cores"] = {"value": agg, "unit": UNIT, "cores": cores,
+                                            "how": "independent single-thread oracle replicas of the same sample, "
+                                                   "one per host core (the oracle itself is single-threaded)"}
     if rank != 0:
         return
     cfg = {"workload": args.workload, "precision": args.precision, "particles": N, "pairs_per_step": nnz,
@@ -479,6 +518,10 @@ def run_ours(args, rank: int, world: int, dist):
         cfg["plastic_flow_window"] = plastic
     if guard:
         cfg["guard_sweep"] = guard
+    if batched:
+        cfg["batched"] = batched
+    if served:
+        cfg["served"] = served
     if ref is not None:
         cfg["plan"] = r.get("plan")
         cfg["fp64_gpu_value"] = world * nnz * args.steps / (ref["ms"] * 1e-3)
@@ -561,6 +604,70 @@ def run_accuracy(args):
         b.close()
 
 
+def measure_batched(tlsph, torch, ws, steps: int, warmup: int, stream, fp64_one_by_one: bool = False) -> dict:
+    """Advance the specimens `ws` together (one persistent launch per kernel
+    kind and step, replayed from a CUDA graph) and, for comparison, the same
+    mixed contexts stepped one by one and (optionally) FP64 contexts of the
+    same specimens stepped one by one.  Device-timed with CUDA events."""
+    t0 = time.perf_counter()
+    sims = [tlsph.Simulation.from_workload(w, precision="mixed", stream=stream, line_order=True) for w in ws]
+    setup = time.perf_counter() - t0
+    N = sum(s.N for s in sims)
+    nnz = sum(s.nnz for s in sims)
+    lays = [s.neighbor_layout() for s in sims]
+    b = tlsph.Batch(len(sims), stream=stream)
+    b.set(sims)
+    b.step(warmup)
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    # the same contexts, each with its own launches, one after another per step
+    for s in sims:
+        s.sync()
+    e0.record(stream)
+    for _ in range(steps):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for s in sims:
+        s.sync()
+    b.close()
+    for s in sims:
+        s.close()
+    out = {"specimens": len(ws), "particles": N, "pairs_per_step": nnz, "set_up_s": setup,
+           "ms_per_step": ms / steps, "value": nnz * steps / (ms * 1e-3),
+           "one_by_one_value": nnz * steps / (ms_seq * 1e-3), "one_by_one_ms_per_step": ms_seq / steps,
+           "kernel_launches_per_step": {"batched": 5, "one_by_one": 4 * len(ws)},
+           "list_words": sum(x["words"] for x in lays), "clocks": clocks}
+    if fp64_one_by_one:
+        f64 = [tlsph.Simulation.from_workload(w, precision="fp64", stream=stream) for w in ws]
+        for s in f64:
+            s.step(1)
+        torch.cuda.synchronize()
+        k = max(1, steps // 4)
+        e0.record(stream)
+        for _ in range(k):
+            for s in f64:
+                s.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["fp64_one_by_one_value"] = nnz * k / (e0.elapsed_time(e1) * 1e-3)
+        out["fp64_steps_timed"] = k
+        for s in f64:
+            s.close()
+    return out
+
+
 def run_batched(args):
     """256 independent bars (log-uniform 2k..200k particles, JC constants
     +-20%) advanced together: one persistent launch per kernel kind and step
@@ -572,67 +679,38 @@ def run_batched(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     ws = S.batched_specimens(args.specimens, seed=0)
     stream = torch.cuda.current_stream()
-    t0 = time.perf_counter()
-    sims = [tlsph.Simulation.from_workload(w, precision="mixed", stream=stream, line_order=True) for w in ws]
-    setup = time.perf_counter() - t0
-    N = sum(s.N for s in sims)
-    nnz = sum(s.nnz for s in sims)
-    b = tlsph.Batch(len(sims), stream=stream)
-    b.set(sims)
-    b.step(args.warmup)
-    torch.cuda.synchronize()
-    clk = ClockSampler(torch.cuda.current_device())
-    clk.start()
-    time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(args.steps, graph=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    clocks = clk.stop()
-    # the same contexts, each with its own launches, one after another per step
-    for s in sims:
-        s.sync()
-    e0.record(stream)
-    for _ in range(args.steps):
-        for s in sims:
-            s.step(1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1)
-    for s in sims:
-        s.sync()
-    p1, p2 = algorithmic_bytes(N, nnz, "mixed").values()
+    m = measure_batched(tlsph, torch, ws, args.steps, args.warmup, stream)
+    N, nnz, ms = m["particles"], m["pairs_per_step"], m["ms_per_step"] * args.steps
+    p1, p2 = algorithmic_bytes(N, nnz, "mixed", m["list_words"]).values()
     achieved = (p1 + p2) / (ms / args.steps * 1e-3) / 1e9
     peak = measured_peaks().get("hbm_gbs") or 6800.0
     ops = sum(tlsph.mixed_fp32_ops(nnz, True))       # every member with hourglass control
     peak_alu = tlsph.FP32_LANES * 2070e6 / 1e12
     ach_alu = ops / (ms / args.steps * 1e-3) / 1e12
-    line = {"metric": METRIC, "value": nnz * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+    line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded jittered lattices)",
-            "config": {"workload": f"batched_{len(sims)}", "specimens": len(sims), "particles": N,
-                       "pairs_per_step": nnz, "set_up_s": setup,
-                       "one_by_one_value": nnz * args.steps / (ms_seq * 1e-3),
-                       "one_by_one_ms_per_step": ms_seq / args.steps,
-                       "kernel_launches_per_step": {"batched": 5, "one_by_one": 4 * len(sims)}},
+            "config": {"workload": f"batched_{len(ws)}", "specimens": len(ws), "particles": N,
+                       "pairs_per_step": nnz, "set_up_s": m["set_up_s"],
+                       "one_by_one_value": m["one_by_one_value"],
+                       "one_by_one_ms_per_step": m["one_by_one_ms_per_step"],
+                       "kernel_launches_per_step": m["kernel_launches_per_step"]},
             "roofline": {"bound": "alu", "kernel": "whole step (five launches)", "achieved": ach_alu,
                          "peak": peak_alu, "unit": "TFLOP/s", "frac": ach_alu / peak_alu,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (an FMA counts as one op)",
                          "traffic": None, "algorithmic_ops_per_step": ops,
                          "hbm_view": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                       "frac": achieved / peak, "traffic": None}},
-            "gpu_launches": 5 * args.steps, "clocks": clocks}
+            "gpu_launches": 5 * args.steps, "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
 
 
-def serve_once(args, rate):
+def serve_once(args, rate, count=None, steps_range=(1000, 5000)):
     import torch
 
     from paper_1901_07374_gb300 import serve
     from paper_1901_07374_gb300 import specimen as S
-    stream_reqs = S.serving_requests(count=args.requests, rate=rate, seed=0)
+    stream_reqs = S.serving_requests(count=count or args.requests, rate=rate, seed=0, steps_range=steps_range)
     reqs = [serve.Request(k, t, w, n) for k, (t, w, n) in enumerate(stream_reqs)]
     srv = serve.Server(mem_cap_bytes=120e9, chunk_steps=args.chunk)
     clk = ClockSampler(torch.cuda.current_device())
@@ -706,6 +784,9 @@ def main():
     ap.add_argument("--plastic-steps", type=int, default=10)
     ap.add_argument("--prestep", type=int, default=0, help="untimed steps before the warm-up (both paths)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served records of the default run")
+    ap.add_argument("--forms-specimens", type=int, default=32, help="default run: bars in the batched record")
+    ap.add_argument("--forms-requests", type=int, default=16, help="default run: requests in the served record")
     ap.add_argument("--guard-sweep", action="store_true",
                     help="time the mixed path at several guard bands of its FP32 elastic screen")
     args = ap.parse_args()

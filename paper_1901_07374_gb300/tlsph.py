@@ -178,25 +178,26 @@ def mixed_algorithmic_bytes(N: int, list_words: int):
     neighbour records count as on-chip reuse).
     pass 1: position 16, v record 16, L^-1 36, F (compensated) rw 144,
             deviator (compensated) rw 96, eps_p / rate / D_init r 24, D r+w 16,
-            fail 4, material 4, V 8, u 24, sqrt E 8, sigma r+w 48,
+            fail 4, material 4, V 8, u 24, E 8, sigma r+w 48,
             internal energy r+w 16, pass-2 record w 96                  = 556
-    pass 2: position 16, own pass-2 record 96, S0 16, V 8, D 8, sqrt E 8,
+    pass 2: position 16, own pass-2 record 96, S0 16, V 8, D 8, E 8,
             1/m 8, v_half rw 48, v w 24, force w 24, u r+w 48, fail 4, bc 1,
             v record w 16                                               = 325"""
     return 4 * list_words + 556 * N, 4 * list_words + 325 * N
 
 
 # FP32 operations per pair-interaction of the mixed path's pair terms (an FMA,
-# a compare-and-select or a reciprocal square root counts as one), from the
-# formulas as written in the pair functions of the library:
+# a compare-and-select, a reciprocal or a reciprocal square root counts as
+# one), from the formulas as written in the pair functions of the library:
 #  pass 1 (velocity gradient): X_ij from fixed-point positions 6, r^2 3, 1/r 1,
-#         q 2, W'(q) 8, weight 3, v_ij 6, 9 sums                          = 38
-#  pass 2 (forces): X_ij 6, r^2 3, 1/r 1, q 2, W'(q) 8, weights 5, 3 sums of
-#         the S0 term, (A_j - A_i) X_ij 18, 3 sums                        = 49
-#         hourglass: u_ij 3, x_ij 3, 1/|x_ij| 4, error vector 21, projection 4,
-#         W(q) from the W' terms 5, coefficient 6, 3 sums                 = 49
+#         q 2, W'(q) 8, weight 2, v_ij 6, 9 sums                          = 37
+#  pass 2 (forces): X_ij 6, r^2 3, 1/r 1, q 2, W'(q) 8, weights 3, 3 sums of
+#         the S0 term, (A_j - A_i) X_ij 18, 3 sums                        = 47
+#         hourglass: u_ij 3, x_ij 3, 1/|x_ij|^2 4, error vector 21,
+#         projection 3, W(q) from the W' terms 5, pair modulus 2,
+#         coefficient 5, 3 sums                                           = 49
 # (an integer-to-float conversion of a position difference counts as one)
-MIXED_FP32_OPS_PER_PAIR = {"pass1": 37, "pass2": 48, "pass2_hourglass": 47}
+MIXED_FP32_OPS_PER_PAIR = {"pass1": 37, "pass2": 47, "pass2_hourglass": 49}
 
 
 def mixed_fp32_ops(nnz: int, hourglass: bool = True):
