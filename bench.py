@@ -275,8 +275,25 @@ def field_errors(sim, ref: dict, sc: dict) -> dict:
     return out
 
 
+def plastic_errors(a, b, sc: dict) -> dict:
+    """Field errors of `a` against `b` (normwise relative max with the floors
+    `sc`, and RMS), the number of particles whose plastic strain differs by
+    more than 1e-8, and the size of the symmetric difference of the failure
+    sets."""
+    import numpy as np
+    out = {}
+    for f in FIELDS:
+        x, y = a.get(f), b.get(f)
+        out[f] = float(np.max(np.abs(x - y)) / max(float(np.max(np.abs(y))), sc[f]))
+        out[f + "_rms"] = float(np.sqrt(np.mean((x - y) ** 2)) / max(float(np.sqrt(np.mean(y ** 2))), sc[f]))
+    d = np.abs(a.get("EPSP") - b.get("EPSP"))
+    out["particles_epsp_diff_above_1e-8"] = int((d > 1e-8).sum())
+    out["failure_set_symdiff"] = int(((a.get("FAIL_STEP") >= 0) ^ (b.get("FAIL_STEP") >= 0)).sum())
+    return out
+
+
 def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, plan=None, state=None, guard=None,
-              prestep=0):
+              prestep=0, accuracy=0):
     """Create, warm up, then time `steps` steps with CUDA events on the
     library's stream; per-kernel times from the library's own events.  A
     mixed context takes `plan`, else the autotuner's; `state` (caller-order
@@ -294,6 +311,8 @@ def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, pl
         words = (lw if pl[0] in (1, 2, 4) else nnz, lw if pl[2] != 0 else nnz)
         if guard is not None:
             sim.set_guard(guard)
+        if accuracy:
+            sim.set_accuracy(accuracy)
     for k, v in (state or {}).items():
         sim.set(k, v)
     if prestep:
@@ -355,6 +374,17 @@ def run_ours(args, rank: int, world: int, dist):
         accuracy["steps"] = args.prestep + args.warmup + args.steps
         ref_sim.close()
     sim.close()
+
+    # ---- accuracy options of the mixed step in the elastic window (same steps as the timed run)
+    elastic_sweep = None
+    if args.accuracy_sweep and args.precision == "mixed" and ref_state is not None:
+        elastic_sweep = []
+        for opts in (1, 2, 4, 7):
+            es_, er_ = timed_run(tlsph, torch, w, "mixed", args.steps, args.warmup, stream, plan=r.get("plan"),
+                                 accuracy=opts, prestep=args.prestep)
+            elastic_sweep.append({"options": opts, "ms_per_step": er_["ms"] / args.steps,
+                                  "accuracy_vs_fp64": field_errors(es_, ref_state, field_scales(w))})
+            es_.close()
 
     # ---- guard band of the FP32 elastic screen: throughput and accuracy per band
     guard = None
@@ -426,13 +456,29 @@ def run_ours(args, rank: int, world: int, dist):
             qs, qr = timed_run(tlsph, torch, w, "fp64", args.plastic_steps, args.warmup, stream, state=st)
             plastic["fp64_value"] = world * nnz * args.plastic_steps / (qr["ms"] * 1e-3)
             sc = field_scales(w)
-            acc = {}
-            for f in FIELDS:
-                a, b = ps.get(f), qs.get(f)
-                acc[f] = float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), sc[f]))
-            d = np.abs(ps.get("EPSP") - qs.get("EPSP"))
-            acc["particles_epsp_diff_above_1e-8"] = int((d > 1e-8).sum())
-            plastic["accuracy_vs_fp64"] = acc
+            plastic["accuracy_vs_fp64"] = plastic_errors(ps, qs, sc)
+            if args.accuracy_sweep:
+                # the accuracy options of the mixed step, one set at a time, on the same window
+                sweep = []
+                for opts in (0, 1, 2, 3, 4, 7):
+                    os_, orr = timed_run(tlsph, torch, w, "mixed", args.plastic_steps, args.warmup, stream,
+                                         plan=r.get("plan"), state=st, accuracy=opts)
+                    sweep.append({"options": opts, "ms_per_step": orr["ms"] / args.plastic_steps,
+                                  "ms_per_launch": {"pass1": orr["p1"], "pass2": orr["p2"]},
+                                  "accuracy_vs_fp64": plastic_errors(os_, qs, sc)})
+                    os_.close()
+                plastic["accuracy_options_sweep"] = sweep
+                # control: the same window without the rate term of Eq. JC_viscoplastic_model (C = 0)
+                import dataclasses
+                m0 = dict(w.materials[0])
+                m0["C"] = 0.0
+                w0 = dataclasses.replace(w, materials=[m0] + list(w.materials[1:]))
+                cs_, _ = timed_run(tlsph, torch, w0, "mixed", args.plastic_steps, args.warmup, stream,
+                                   plan=r.get("plan"), state=st)
+                cq_, _ = timed_run(tlsph, torch, w0, "fp64", args.plastic_steps, args.warmup, stream, state=st)
+                plastic["rate_free_control"] = {"C": 0.0, "accuracy_vs_fp64": plastic_errors(cs_, cq_, sc)}
+                cs_.close()
+                cq_.close()
             qs.close()
         ps.close()
 
@@ -518,6 +564,8 @@ def run_ours(args, rank: int, world: int, dist):
         cfg["plastic_flow_window"] = plastic
     if guard:
         cfg["guard_sweep"] = guard
+    if elastic_sweep:
+        cfg["accuracy_options_elastic"] = elastic_sweep
     if batched:
         cfg["batched"] = batched
     if served:
@@ -590,6 +638,8 @@ def run_accuracy(args):
         w = cases[name]()
         sc = field_scales(w)
         a = tlsph.Simulation.from_workload(w, precision="mixed")
+        if args.accuracy_options:
+            a.set_accuracy(args.accuracy_options)
         b = tlsph.Simulation.from_workload(w, precision="fp64")
         N, nnz, _ = b.info()
         rows, done, t0 = {}, 0, time.perf_counter()
@@ -598,7 +648,8 @@ def run_accuracy(args):
             b.step(k - done)
             done = k
             rows[str(k)] = trajectory_errors(a, b, sc)
-        print(json.dumps({"accuracy": name, "particles": N, "pairs": nnz, "checkpoints": rows,
+        print(json.dumps({"accuracy": name, "accuracy_options": args.accuracy_options, "particles": N,
+                          "pairs": nnz, "checkpoints": rows,
                           "seconds": time.perf_counter() - t0}), flush=True)
         a.close()
         b.close()
@@ -617,6 +668,10 @@ def measure_batched(tlsph, torch, ws, steps: int, warmup: int, stream, fp64_one_
     lays = [s.neighbor_layout() for s in sims]
     b = tlsph.Batch(len(sims), stream=stream)
     b.set(sims)
+    from paper_1901_07374_gb300 import autotune
+    t1 = time.perf_counter()
+    shape = autotune.tune_batch(b, sims)            # launch shapes of the batch kernels (state restored)
+    tune_s = time.perf_counter() - t1
     b.step(warmup)
     torch.cuda.synchronize()
     clk = ClockSampler(torch.cuda.current_device())
@@ -648,7 +703,8 @@ def measure_batched(tlsph, torch, ws, steps: int, warmup: int, stream, fp64_one_
            "ms_per_step": ms / steps, "value": nnz * steps / (ms * 1e-3),
            "one_by_one_value": nnz * steps / (ms_seq * 1e-3), "one_by_one_ms_per_step": ms_seq / steps,
            "kernel_launches_per_step": {"batched": 5, "one_by_one": 4 * len(ws)},
-           "list_words": sum(x["words"] for x in lays), "clocks": clocks}
+           "list_words": sum(x["words"] for x in lays), "launch_shape": list(shape), "tune_s": tune_s,
+           "clocks": clocks}
     if fp64_one_by_one:
         f64 = [tlsph.Simulation.from_workload(w, precision="fp64", stream=stream) for w in ws]
         for s in f64:
@@ -694,7 +750,8 @@ def run_batched(args):
                        "pairs_per_step": nnz, "set_up_s": m["set_up_s"],
                        "one_by_one_value": m["one_by_one_value"],
                        "one_by_one_ms_per_step": m["one_by_one_ms_per_step"],
-                       "kernel_launches_per_step": m["kernel_launches_per_step"]},
+                       "kernel_launches_per_step": m["kernel_launches_per_step"],
+                       "launch_shape": m["launch_shape"]},
             "roofline": {"bound": "alu", "kernel": "whole step (five launches)", "achieved": ach_alu,
                          "peak": peak_alu, "unit": "TFLOP/s", "frac": ach_alu / peak_alu,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (an FMA counts as one op)",
@@ -770,6 +827,8 @@ def main():
     ap.add_argument("--accuracy", action="store_true",
                     help="report mixed vs FP64 along whole trajectories (steps 1, 10, 100, 500, 2000) and exit")
     ap.add_argument("--accuracy-cases", default="", help="comma-separated subset of the accuracy workloads")
+    ap.add_argument("--accuracy-options", type=int, default=0,
+                    help="accuracy options of the mixed step in the --accuracy report (bitwise OR, tlsph_set_accuracy)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
                     help="skip the all-core oracle figure (one replica per host core)")
@@ -787,6 +846,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served records of the default run")
     ap.add_argument("--forms-specimens", type=int, default=32, help="default run: bars in the batched record")
     ap.add_argument("--forms-requests", type=int, default=16, help="default run: requests in the served record")
+    ap.add_argument("--accuracy-sweep", action="store_true",
+                    help="plastic-flow window: time and error of each accuracy option set of the mixed step")
     ap.add_argument("--guard-sweep", action="store_true",
                     help="time the mixed path at several guard bands of its FP32 elastic screen")
     args = ap.parse_args()

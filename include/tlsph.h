@@ -265,6 +265,33 @@ int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
  * tlsph_batch_set.  The FP64 path ignores it. */
 int tlsph_set_guard(tlsph_ctx *ctx, double band);
 
+/* Accuracy options of the mixed path's step (Secs. 3.1 and 4: the
+ * velocity gradient Fdot of Eq. Crack_approx_Fdot and the kinematics of the
+ * constitutive update; the options have no counterpart in the paper, which
+ * computes in FP64 throughout).  A bitwise OR of
+ *   TLSPH_ACC_COMP_VELOCITY  the pass-1 gather reads the half-step velocity
+ *                            as an unevaluated FP32 sum hi + lo (about 46
+ *                            bits) instead of one FP32 value (the rounding of
+ *                            velocities near the grip speed is the largest
+ *                            error of Fdot on a long bar);
+ *   TLSPH_ACC_COMP_SUMS      the nine Fdot row sums are accumulated as
+ *                            compensated FP32 pairs (TwoSum) and finished in
+ *                            FP64;
+ *   TLSPH_ACC_FP64_KIN       the per-particle update forms dF = dt Fdot L^-1
+ *                            with the FP64 L^-1, adds it to F in full and
+ *                            takes J = det F in FP64.
+ * 0 (the default) is the fastest form.  With any option set the context's
+ * pass-1 gather runs a thread-per-row kernel of its own (the plan's pass-1
+ * block size is kept).  Applies to the context's own steps; a context with
+ * options set cannot join a batch (TLSPH_ERR_ARG from tlsph_batch_set).
+ * TLSPH_ERR_ARG for unknown bits, TLSPH_ERR_STATE for an FP64 context or one
+ * without sliced neighbour lists. */
+#define TLSPH_ACC_COMP_VELOCITY 1
+#define TLSPH_ACC_COMP_SUMS 2
+#define TLSPH_ACC_FP64_KIN 4
+int tlsph_set_accuracy(tlsph_ctx *ctx, int options);
+int tlsph_get_accuracy(const tlsph_ctx *ctx, int *options);
+
 /* Grip velocity ramp (Sec. 6: the end rows move at v_max (1 - e^{-t}), with
  * v_max in mm/ms and t in ms).  With tau > 0 every prescribed velocity
  * (bc_mask set) holds as bc_vel (1 - exp(-t / tau)) at the time t of the
@@ -322,6 +349,23 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph);
 
 int tlsph_batch_sync(tlsph_batch *b);
 const char *tlsph_batch_last_error(const tlsph_batch *b);
+
+/* Launch shape of the batch's kernels (no paper counterpart; a performance
+ * setting): shape[k] selects a variant for kernel kind
+ * k = 0 (pass-1 gather), 1 (per-particle update), 2 (pass 2); a variant
+ * fixes how many blocks of 128 threads the kernel's registers are capped for
+ * and how many neighbour pairs a thread has in flight.  n must be 3 (the
+ * number of kinds).  Setting a different shape waits for the batch's
+ * launches in flight and re-captures its graph at the next tlsph_batch_step.
+ * Every variant computes the same method; the results of two variants agree
+ * to FP32 rounding (the compiler may fuse multiply-adds differently under
+ * another register cap), and with any one shape a member's result does not
+ * depend on the other members.  TLSPH_ERR_ARG for an index out of
+ * range.  tlsph_batch_get_shape writes the current variant of each kind into
+ * shape and the number of variants of each kind into variants (either may be
+ * NULL). */
+int tlsph_batch_set_shape(tlsph_batch *b, const int32_t *shape, int n);
+int tlsph_batch_get_shape(const tlsph_batch *b, int32_t *shape, int32_t *variants, int n);
 int tlsph_batch_destroy(tlsph_batch *b);
 
 /* Per-kernel device time of the step (CUDA events recorded around each

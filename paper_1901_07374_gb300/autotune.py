@@ -9,6 +9,12 @@ included), so tuning never changes a trajectory.  Results are cached per
 (GPU, precision, particle-count bucket, neighbours-per-row bucket, hourglass
 on/off, candidate set) in a JSON file ($TLSPH_PLAN_CACHE, default
 ~/.cache/tlsph_gb300/plans.json).
+
+Batches (tlsph.Batch) are tuned the same way: `tune_batch` chooses the
+launch-shape variant of each batch kernel kind (register cap and pairs in
+flight of the pass-1 gather, the per-particle update and pass 2) by timing
+whole batched steps one kind at a time, and restores every member's state
+bit for bit.
 """
 from __future__ import annotations
 
@@ -111,3 +117,63 @@ def tune(sim, steps: int = 3, warmup: int = 1, use_cache: bool = True, record=No
     if use_cache:
         _store(key, best)
     return best
+
+
+def _batch_key(batch, sims) -> str:
+    import torch
+    N = sum(s.N for s in sims)
+    nnz = sum(s.nnz for s in sims)
+    hg = "hg" if sims and sims[0].cfg.hg_alpha != 0 else "nohg"
+    _, nv = batch.get_shape()
+    return (f"batch|{torch.cuda.get_device_name()}|N2^{int(math.log2(max(N, 1)))}"
+            f"|m2^{int(math.log2(max(len(sims), 1)))}|row{int(round(nnz / max(N, 1) / 8.0)) * 8}|{hg}|v{nv}")
+
+
+def _time_batch(batch, shape, steps: int, warmup: int) -> float:
+    import torch
+    batch.set_shape(shape)
+    batch.step(warmup, graph=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(steps, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune_batch(batch, sims, steps: int = 3, warmup: int = 1, use_cache: bool = True, record=None):
+    """Choose and set the fastest launch shape for `batch` (whose members are
+    the Simulations `sims`); returns it.  Coordinate descent: each kernel
+    kind's variants are timed (whole graph-replayed steps, CUDA events on the
+    current stream) with the other kinds at their best so far.  Every member's
+    resumable state and step counter are restored bit for bit afterwards, so
+    tuning never changes a trajectory.  `record`, if a list, receives
+    (shape, ms per step) for every timed candidate."""
+    key = _batch_key(batch, sims)
+    if use_cache:
+        cached = _load().get(key)
+        if cached:
+            batch.set_shape(cached)
+            return tuple(cached)
+    cks = [s.checkpoint(device=True) for s in sims]
+    best, nv = batch.get_shape()
+    best = list(best)
+    for kind in range(3):
+        times = {}
+        for v in range(nv[kind]):
+            shape = list(best)
+            shape[kind] = v
+            t = _time_batch(batch, shape, steps, warmup)
+            times[v] = t
+            if record is not None:
+                record.append((tuple(shape), t))
+        best[kind] = min(times, key=times.get)
+    for s, ck in zip(sims, cks):
+        s.restore(ck)
+    batch.set(sims)
+    batch.set_shape(best)
+    if use_cache:
+        _store(key, best)
+    return tuple(best)

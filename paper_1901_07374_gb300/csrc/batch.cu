@@ -26,6 +26,7 @@ struct tlsph_batch {
     std::vector<tlsph_ctx *> members;
     std::vector<int64_t> steps_at;  // each member's step count the table was built for
     int hg = -1;                    // hourglass on/off shared by the members
+    int shape[BATCH_KINDS] = { 0, 0, 0 };                 // launch-shape variant per kernel kind
     int grid[2][4] = { { 0, 0, 0, 0 }, { 0, 0, 0, 0 } };   // persistent grids per kernel kind, without / with hourglass
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -90,6 +91,8 @@ int tlsph_batch_set(tlsph_batch *b, tlsph_ctx *const *ctxs, int n)
         if (c->sticky) return batch_fail(b, TLSPH_ERR_STATE, "a member context holds an error");
         if (c->cfg.precision != TLSPH_PRECISION_MIXED || !c->ell_ok)
             return batch_fail(b, TLSPH_ERR_ARG, "batched stepping needs mixed-precision contexts with sliced-ELL columns");
+        if (c->accuracy != 0)
+            return batch_fail(b, TLSPH_ERR_ARG, "batch members run the default accuracy options (tlsph_set_accuracy 0)");
         const int h = c->cfg.hg_alpha != 0.0 ? 1 : 0;
         if (hg >= 0 && h != hg) return batch_fail(b, TLSPH_ERR_ARG, "members must all use hourglass control or none");
         hg = h;
@@ -149,7 +152,7 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph)
     }
     const bool hg = b->hg == 1;
     int *grid = b->grid[hg ? 1 : 0];
-    if (grid[0] == 0) batch_grid(hg, grid);
+    if (grid[0] == 0) batch_grid(hg, b->shape, grid);
     // the batch's work follows everything already queued on the caller's stream
     cudaError_t e = cudaEventRecord(b->start, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->own, b->start, 0);
@@ -160,7 +163,7 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph)
             if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
             e = cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t le = launch_batch_step(b->hdr, b->slots, b->capacity, hg, grid, b->own);
+                cudaError_t le = launch_batch_step(b->hdr, b->slots, b->capacity, hg, b->shape, grid, b->own);
                 e = cudaStreamEndCapture(b->own, &b->graph);
                 if (le != cudaSuccess) e = le;
             }
@@ -174,7 +177,7 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph)
         for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->exec, b->own);
     } else {
         for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
-            e = launch_batch_step(b->hdr, b->slots, b->capacity, hg, grid, b->own);
+            e = launch_batch_step(b->hdr, b->slots, b->capacity, hg, b->shape, grid, b->own);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->done, b->own);
     // later work on the caller's stream and on each member's own stream is ordered after the batch
@@ -203,6 +206,37 @@ int tlsph_batch_sync(tlsph_batch *b)
 }
 
 const char *tlsph_batch_last_error(const tlsph_batch *b) { return b ? b->err.c_str() : ""; }
+
+int tlsph_batch_set_shape(tlsph_batch *b, const int32_t *shape, int n)
+{
+    if (!b || !shape || n != BATCH_KINDS) return TLSPH_ERR_ARG;
+    for (int k = 0; k < BATCH_KINDS; ++k)
+        if (shape[k] < 0 || shape[k] >= BATCH_VARIANTS[k])
+            return batch_fail(b, TLSPH_ERR_ARG, "launch-shape variant out of range for kernel kind " + std::to_string(k));
+    bool same = true;
+    for (int k = 0; k < BATCH_KINDS; ++k) same &= b->shape[k] == shape[k];
+    if (same) return TLSPH_OK;
+    // the launches in flight use the old kernels and grids: finish them before replacing the graph
+    cudaError_t e = cudaStreamSynchronize(b->own);
+    if (e != cudaSuccess) return batch_fail(b, TLSPH_ERR_CUDA, std::string("set_shape: ") + cudaGetErrorString(e));
+    for (int k = 0; k < BATCH_KINDS; ++k) b->shape[k] = shape[k];
+    for (auto &g : b->grid)
+        for (int &x : g) x = 0;             // recomputed for the new kernels at the next step
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_hg = -1;
+    return TLSPH_OK;
+}
+
+int tlsph_batch_get_shape(const tlsph_batch *b, int32_t *shape, int32_t *variants, int n)
+{
+    if (!b || n != BATCH_KINDS) return TLSPH_ERR_ARG;
+    for (int k = 0; k < BATCH_KINDS; ++k) {
+        if (shape) shape[k] = b->shape[k];
+        if (variants) variants[k] = BATCH_VARIANTS[k];
+    }
+    return TLSPH_OK;
+}
 
 int tlsph_batch_destroy(tlsph_batch *b)
 {

@@ -101,3 +101,81 @@ def test_batch_rejects_fp64_and_stale_members():
     b.set([g])
     b.step(1)
     assert g.steps == 4
+
+
+def test_every_launch_shape_computes_the_same_rows():
+    """Each variant of each batch kernel kind (register cap, pairs in flight)
+    changes only the launch: the members' states after the same steps agree
+    to FP32 rounding (under another register cap the compiler may fuse
+    multiply-adds differently), and with any one shape a member alone equals
+    the member in the mix bit for bit."""
+    ws = _specimens()[:4]
+    ref = None
+    b = tlsph.Batch(capacity=4)
+    _, nv = b.get_shape()
+    shapes = [(0, 0, 0)] + [tuple(v if k == kind else 0 for k in range(3)) for kind in range(3)
+                            for v in range(1, nv[kind])]
+    for shape in shapes:
+        mix = _make(ws)
+        b.set(mix)
+        b.set_shape(shape)
+        assert b.get_shape()[0] == shape
+        b.step(12)
+        st = [g.state() for g in mix]
+        if ref is None:
+            ref = st
+            continue
+        for a, r in zip(st, ref):
+            for k in ("U", "V", "F", "SIGMA", "STRESS_DEV"):
+                x, y = a[k], r[k]
+                assert np.max(np.abs(x - y)) <= 1e-5 * max(np.max(np.abs(y)), 1e-30), (shape, k)
+            assert np.array_equal(a["FAIL_STEP"] >= 0, r["FAIL_STEP"] >= 0)
+    last = shapes[-1]
+    alone = tlsph.Simulation.from_workload(ws[0], precision="mixed")
+    b1 = tlsph.Batch(capacity=1)
+    b1.set([alone])
+    b1.set_shape(last)
+    b1.step(12)
+    for k, v in alone.state().items():
+        assert np.array_equal(v, st[0][k]), (last, k)
+    with pytest.raises(tlsph.TlsphError) as e:
+        b.set_shape((nv[0], 0, 0))
+    assert e.value.code == -1
+
+
+def test_tuned_batch_restores_the_state_and_equals_the_shape_set_by_hand(tmp_path, monkeypatch):
+    """The batch autotuner times the launch shapes on the members' live state
+    and then restores every member bit for bit: its tuned batch steps exactly
+    like a batch that ran the same steps and was given the chosen shape by
+    hand."""
+    from paper_1901_07374_gb300 import autotune
+    monkeypatch.setenv("TLSPH_PLAN_CACHE", str(tmp_path / "plans.json"))
+    ws = _specimens()
+    tuned = _make(ws)
+    b = tlsph.Batch(capacity=8)
+    b.set(tuned)
+    b.step(7)
+    before = [g.checkpoint(device=False) for g in tuned]
+    rec = []
+    shape = autotune.tune_batch(b, tuned, steps=2, warmup=1, record=rec)
+    _, nv = b.get_shape()
+    assert len(rec) == sum(nv) and b.get_shape()[0] == shape
+    for g, ck in zip(tuned, before):
+        assert g.steps == 7
+        for k, v in ck.items():         # every resumable field, bit for bit
+            assert np.array_equal(v, g.get(k)), k
+    b.step(11)
+    # by hand: the same 7 steps with the default shape, then the tuned shape
+    byhand = _make(ws)
+    b2 = tlsph.Batch(capacity=8)
+    b2.set(byhand)
+    b2.step(7)
+    b2.set_shape(shape)
+    b2.step(11)
+    for g, h in zip(tuned, byhand):
+        assert g.steps == h.steps == 18
+        for k, v in h.state().items():
+            assert np.array_equal(v, g.get(k)), k
+    # the cached shape is reused without timing
+    rec2 = []
+    assert autotune.tune_batch(b2, byhand, record=rec2) == shape and rec2 == []
