@@ -293,7 +293,7 @@ def plastic_errors(a, b, sc: dict) -> dict:
 
 
 def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, plan=None, state=None, guard=None,
-              prestep=0, accuracy=0):
+              prestep=0):
     """Create, warm up, then time `steps` steps with CUDA events on the
     library's stream; per-kernel times from the library's own events.  A
     mixed context takes `plan`, else the autotuner's; `state` (caller-order
@@ -311,8 +311,6 @@ def timed_run(tlsph, torch, w, precision, steps, warmup, stream, clocks=None, pl
         words = (lw if pl[0] in (1, 2, 4) else nnz, lw if pl[2] != 0 else nnz)
         if guard is not None:
             sim.set_guard(guard)
-        if accuracy:
-            sim.set_accuracy(accuracy)
     for k, v in (state or {}).items():
         sim.set(k, v)
     if prestep:
@@ -374,17 +372,6 @@ def run_ours(args, rank: int, world: int, dist):
         accuracy["steps"] = args.prestep + args.warmup + args.steps
         ref_sim.close()
     sim.close()
-
-    # ---- accuracy options of the mixed step in the elastic window (same steps as the timed run)
-    elastic_sweep = None
-    if args.accuracy_sweep and args.precision == "mixed" and ref_state is not None:
-        elastic_sweep = []
-        for opts in (1, 2, 4, 7):
-            es_, er_ = timed_run(tlsph, torch, w, "mixed", args.steps, args.warmup, stream, plan=r.get("plan"),
-                                 accuracy=opts, prestep=args.prestep)
-            elastic_sweep.append({"options": opts, "ms_per_step": er_["ms"] / args.steps,
-                                  "accuracy_vs_fp64": field_errors(es_, ref_state, field_scales(w))})
-            es_.close()
 
     # ---- guard band of the FP32 elastic screen: throughput and accuracy per band
     guard = None
@@ -457,17 +444,7 @@ def run_ours(args, rank: int, world: int, dist):
             plastic["fp64_value"] = world * nnz * args.plastic_steps / (qr["ms"] * 1e-3)
             sc = field_scales(w)
             plastic["accuracy_vs_fp64"] = plastic_errors(ps, qs, sc)
-            if args.accuracy_sweep:
-                # the accuracy options of the mixed step, one set at a time, on the same window
-                sweep = []
-                for opts in (0, 1, 2, 3, 4, 7):
-                    os_, orr = timed_run(tlsph, torch, w, "mixed", args.plastic_steps, args.warmup, stream,
-                                         plan=r.get("plan"), state=st, accuracy=opts)
-                    sweep.append({"options": opts, "ms_per_step": orr["ms"] / args.plastic_steps,
-                                  "ms_per_launch": {"pass1": orr["p1"], "pass2": orr["p2"]},
-                                  "accuracy_vs_fp64": plastic_errors(os_, qs, sc)})
-                    os_.close()
-                plastic["accuracy_options_sweep"] = sweep
+            if args.rate_free_control:
                 # control: the same window without the rate term of Eq. JC_viscoplastic_model (C = 0)
                 import dataclasses
                 m0 = dict(w.materials[0])
@@ -564,8 +541,6 @@ def run_ours(args, rank: int, world: int, dist):
         cfg["plastic_flow_window"] = plastic
     if guard:
         cfg["guard_sweep"] = guard
-    if elastic_sweep:
-        cfg["accuracy_options_elastic"] = elastic_sweep
     if batched:
         cfg["batched"] = batched
     if served:
@@ -638,8 +613,6 @@ def run_accuracy(args):
         w = cases[name]()
         sc = field_scales(w)
         a = tlsph.Simulation.from_workload(w, precision="mixed")
-        if args.accuracy_options:
-            a.set_accuracy(args.accuracy_options)
         b = tlsph.Simulation.from_workload(w, precision="fp64")
         N, nnz, _ = b.info()
         rows, done, t0 = {}, 0, time.perf_counter()
@@ -648,8 +621,7 @@ def run_accuracy(args):
             b.step(k - done)
             done = k
             rows[str(k)] = trajectory_errors(a, b, sc)
-        print(json.dumps({"accuracy": name, "accuracy_options": args.accuracy_options, "particles": N,
-                          "pairs": nnz, "checkpoints": rows,
+        print(json.dumps({"accuracy": name, "particles": N, "pairs": nnz, "checkpoints": rows,
                           "seconds": time.perf_counter() - t0}), flush=True)
         a.close()
         b.close()
@@ -827,8 +799,6 @@ def main():
     ap.add_argument("--accuracy", action="store_true",
                     help="report mixed vs FP64 along whole trajectories (steps 1, 10, 100, 500, 2000) and exit")
     ap.add_argument("--accuracy-cases", default="", help="comma-separated subset of the accuracy workloads")
-    ap.add_argument("--accuracy-options", type=int, default=0,
-                    help="accuracy options of the mixed step in the --accuracy report (bitwise OR, tlsph_set_accuracy)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
                     help="skip the all-core oracle figure (one replica per host core)")
@@ -846,8 +816,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served records of the default run")
     ap.add_argument("--forms-specimens", type=int, default=32, help="default run: bars in the batched record")
     ap.add_argument("--forms-requests", type=int, default=16, help="default run: requests in the served record")
-    ap.add_argument("--accuracy-sweep", action="store_true",
-                    help="plastic-flow window: time and error of each accuracy option set of the mixed step")
+    ap.add_argument("--rate-free-control", action="store_true",
+                    help="plastic-flow window: also compare the paths with the Johnson-Cook rate term off (C = 0)")
     ap.add_argument("--guard-sweep", action="store_true",
                     help="time the mixed path at several guard bands of its FP32 elastic screen")
     args = ap.parse_args()

@@ -265,32 +265,6 @@ int tlsph_get_plan(const tlsph_ctx *ctx, int32_t *plan, int n);
  * tlsph_batch_set.  The FP64 path ignores it. */
 int tlsph_set_guard(tlsph_ctx *ctx, double band);
 
-/* Accuracy options of the mixed path's step (Secs. 3.1 and 4: the
- * velocity gradient Fdot of Eq. Crack_approx_Fdot and the kinematics of the
- * constitutive update; the options have no counterpart in the paper, which
- * computes in FP64 throughout).  A bitwise OR of
- *   TLSPH_ACC_COMP_VELOCITY  the pass-1 gather reads the half-step velocity
- *                            as an unevaluated FP32 sum hi + lo (about 46
- *                            bits) instead of one FP32 value (the rounding of
- *                            velocities near the grip speed is the largest
- *                            error of Fdot on a long bar);
- *   TLSPH_ACC_COMP_SUMS      the nine Fdot row sums are accumulated as
- *                            compensated FP32 pairs (TwoSum) and finished in
- *                            FP64;
- *   TLSPH_ACC_FP64_KIN       the per-particle update forms dF = dt Fdot L^-1
- *                            with the FP64 L^-1, adds it to F in full and
- *                            takes J = det F in FP64.
- * 0 (the default) is the fastest form.  With any option set the context's
- * pass-1 gather runs a thread-per-row kernel of its own (the plan's pass-1
- * block size is kept).  Applies to the context's own steps; a context with
- * options set cannot join a batch (TLSPH_ERR_ARG from tlsph_batch_set).
- * TLSPH_ERR_ARG for unknown bits, TLSPH_ERR_STATE for an FP64 context or one
- * without sliced neighbour lists. */
-#define TLSPH_ACC_COMP_VELOCITY 1
-#define TLSPH_ACC_COMP_SUMS 2
-#define TLSPH_ACC_FP64_KIN 4
-int tlsph_set_accuracy(tlsph_ctx *ctx, int options);
-int tlsph_get_accuracy(const tlsph_ctx *ctx, int *options);
 
 /* Grip velocity ramp (Sec. 6: the end rows move at v_max (1 - e^{-t}), with
  * v_max in mm/ms and t in ms).  With tau > 0 every prescribed velocity

@@ -27,7 +27,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 struct Layout {
     size_t X, vol, mass, inv_mass, youngs, mat, bcm, bcv, row_ptr, Linv, u0, u1, v, vh, F, sd, sig, A;
     size_t ep, epdot, dinit, por, e, D0, D1, force, fail, status, mats, col, diag, inscan;
-    size_t xo, s0, linv32, r1, r1lo, r2, fsum, fsum_lo, ell_off, ell_w;
+    size_t xo, s0, linv32, r1, r2, fsum, ell_off, ell_w;
     size_t Fh, Fl, sdh, sdl, sigf, slowq, slowq_n;
     size_t scratch, cell_start, cell_cursor, cell_items, scan_tmp, xf;
     size_t perm, iperm, stX, stvol, stmat, stbcm, stbcv, stf0;   // order, its inverse + staged caller-order inputs
@@ -150,10 +150,8 @@ Layout make_layout(int64_t N, int64_t nnz_cap, bool mixed)
         L.ell_w = c.take(((n + 31) / 32) * sizeof(int32_t));
         L.linv32 = c.take(9 * n * sizeof(float));
         L.r1 = c.take(n * 16);
-        L.r1lo = c.take(n * 16);
         L.r2 = c.take(6 * ((n + 31) / 32 * 32) * 16);   // tiles of 32 particles
         L.fsum = c.take(9 * n * sizeof(float));
-        L.fsum_lo = c.take(9 * n * sizeof(float));
         const size_t f = sizeof(float);
         L.Fh = c.take(9 * n * f); L.Fl = c.take(9 * n * f);
         L.sdh = c.take(6 * n * f); L.sdl = c.take(6 * n * f);
@@ -237,10 +235,8 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.ell_w = at<int32_t>(base, L.ell_w);
         s.linv32 = at<float>(base, L.linv32);
         s.r1 = at<float4>(base, L.r1);
-        s.r1lo = at<float4>(base, L.r1lo);
         s.r2 = at<float4>(base, L.r2);
         s.fsum = at<float>(base, L.fsum);
-        s.fsum_lo = at<float>(base, L.fsum_lo);
         s.Fh = at<float>(base, L.Fh); s.Fl = at<float>(base, L.Fl);
         s.sdh = at<float>(base, L.sdh); s.sdl = at<float>(base, L.sdl);
         s.sigf = at<float>(base, L.sigf);
@@ -248,8 +244,6 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.slowq_n = at<uint32_t>(base, L.slowq_n);
     } else {
         s.fsum = nullptr;
-        s.fsum_lo = nullptr;
-        s.r1lo = nullptr;
         s.xo = nullptr;
         s.s0 = s.r1 = s.r2 = nullptr;
         s.ell_off = nullptr;
@@ -724,33 +718,6 @@ int tlsph_set_guard(tlsph_ctx *ctx, double band)
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_guard sync");
     ctx->guard = band;
-    return TLSPH_OK;
-}
-
-int tlsph_set_accuracy(tlsph_ctx *ctx, int options)
-{
-    if (!ctx) return TLSPH_ERR_ARG;
-    if (ctx->sticky) return TLSPH_ERR_STATE;
-    if (options & ~(TLSPH_ACC_COMP_VELOCITY | TLSPH_ACC_COMP_SUMS | TLSPH_ACC_FP64_KIN)) {
-        ctx->err = "unknown accuracy option bits";
-        return TLSPH_ERR_ARG;
-    }
-    if (ctx->cfg.precision != TLSPH_PRECISION_MIXED || !ctx->ell_ok) {
-        ctx->err = "accuracy options need a mixed-precision context with sliced neighbour lists";
-        return TLSPH_ERR_STATE;
-    }
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_accuracy sync");
-    if ((options & TLSPH_ACC_COMP_VELOCITY) && !(ctx->accuracy & TLSPH_ACC_COMP_VELOCITY))
-        ctx->need_predict = true;       // the next predictor writes the velocity mirror's low parts
-    ctx->accuracy = options;
-    return TLSPH_OK;
-}
-
-int tlsph_get_accuracy(const tlsph_ctx *ctx, int *options)
-{
-    if (!ctx || !options) return TLSPH_ERR_ARG;
-    *options = ctx->accuracy;
     return TLSPH_OK;
 }
 

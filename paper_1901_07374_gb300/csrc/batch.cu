@@ -91,8 +91,6 @@ int tlsph_batch_set(tlsph_batch *b, tlsph_ctx *const *ctxs, int n)
         if (c->sticky) return batch_fail(b, TLSPH_ERR_STATE, "a member context holds an error");
         if (c->cfg.precision != TLSPH_PRECISION_MIXED || !c->ell_ok)
             return batch_fail(b, TLSPH_ERR_ARG, "batched stepping needs mixed-precision contexts with sliced-ELL columns");
-        if (c->accuracy != 0)
-            return batch_fail(b, TLSPH_ERR_ARG, "batch members run the default accuracy options (tlsph_set_accuracy 0)");
         const int h = c->cfg.hg_alpha != 0.0 ? 1 : 0;
         if (hg >= 0 && h != hg) return batch_fail(b, TLSPH_ERR_ARG, "members must all use hourglass control or none");
         hg = h;

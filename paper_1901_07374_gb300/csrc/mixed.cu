@@ -56,7 +56,6 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     c.half_dt = 0.5 * cfg.dt;
     c.inv_h = (float)(ctx.s.pack.unit / cfg.h);
     c.dt_dw = (float)(cfg.dt / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
-    c.dt_dw_d = cfg.dt / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h);
     c.dw_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h * cfg.h));
     c.w_norm = (float)(1.0 / (M_PI * cfg.h * cfg.h * cfg.h));
     c.hg_coef = (float)(-0.5 * cfg.hg_alpha);
@@ -72,7 +71,6 @@ static MixConst make_mix_const(const tlsph_ctx &ctx, int64_t step_index)
     c.ucur = ctx.ucur;
     c.dcur = ctx.dcur;
     c.wall = (cfg.flags & TLSPH_FLAG_WALL) != 0;
-    c.acc = ctx.accuracy;
     return c;
 }
 
@@ -574,29 +572,7 @@ __device__ __forceinline__ void load_u1(const DevState &s, const MixConst &c, in
     u2 = (float)un[3 * i + 2] * c.inv_unit_f;
 }
 
-// FP64 determinant and inverse of F = hi + lo (accuracy option FP64_KIN)
-__device__ __forceinline__ double det_inv_d(const float *Fh, const float *Fl, double *Fi)
-{
-    double F[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = (double)Fh[k] + (double)Fl[k];
-    const double c0 = F[4] * F[8] - F[5] * F[7], c1 = F[5] * F[6] - F[3] * F[8], c2 = F[3] * F[7] - F[4] * F[6];
-    const double J = F[0] * c0 + F[1] * c1 + F[2] * c2;
-    if (Fi) {
-        const double iJ = 1.0 / J;
-        Fi[0] = c0 * iJ; Fi[1] = (F[2] * F[7] - F[1] * F[8]) * iJ; Fi[2] = (F[1] * F[5] - F[2] * F[4]) * iJ;
-        Fi[3] = c1 * iJ; Fi[4] = (F[0] * F[8] - F[2] * F[6]) * iJ; Fi[5] = (F[2] * F[3] - F[0] * F[5]) * iJ;
-        Fi[6] = c2 * iJ; Fi[7] = (F[1] * F[6] - F[0] * F[7]) * iJ; Fi[8] = (F[0] * F[4] - F[1] * F[3]) * iJ;
-    }
-    return J;
-}
-
-// ACC: the context runs accuracy options (c.acc): the pass-1 sums may carry
-// low parts (keep_lo, option COMP_SUMS) and the kinematics may be FP64
-// (option FP64_KIN); otherwise keep_lo is not read
-template <bool ACC>
-__device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep,
-                                           const float *keep_lo = nullptr)
+__device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
     const double *__restrict__ Dn = s.D[c.dcur];
     double *__restrict__ Dnext = s.D[c.dcur ^ 1];
@@ -629,40 +605,14 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     for (int k = 0; k < 9; ++k) Li[k] = s.linv32[9 * i + k];
     // dF = dt Fdot (Fdot = M L^{-1}, Sec. 3.1); F^{n+1} = F^n + dF compensated
     float dF[9];
-    double dFd[9];
-    const bool kin64 = ACC && (c.acc & TLSPH_ACC_FP64_KIN);
-    if (kin64) {                // FP64 sums, FP64 L^{-1}, the whole increment added to the compensated F
-        double kd[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k)
-            kd[k] = (double)keep[k] + ((c.acc & TLSPH_ACC_COMP_SUMS) ? (double)keep_lo[k] : 0.0);
-        const double *Ld = s.Linv + 9 * i;
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int l = 0; l < 3; ++l)
-                dFd[3 * k + l] = c.dt_dw_d * (kd[3 * k] * Ld[l] + kd[3 * k + 1] * Ld[3 + l] + kd[3 * k + 2] * Ld[6 + l]);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            dF[k] = (float)dFd[k];
-            df_add(Fh[k], Fl[k], dF[k]);
-            df_add(Fh[k], Fl[k], (float)(dFd[k] - (double)dF[k]));
-        }
-    } else {
-        float kv[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-            kv[k] = (ACC && (c.acc & TLSPH_ACC_COMP_SUMS)) ? keep[k] + keep_lo[k] : keep[k];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int l = 0; l < 3; ++l)
-                dF[3 * k + l] = c.dt_dw * (kv[3 * k] * Li[l] + kv[3 * k + 1] * Li[3 + l] + kv[3 * k + 2] * Li[6 + l]);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) df_add(Fh[k], Fl[k], dF[k]);
-    }
+        for (int l = 0; l < 3; ++l)
+            dF[3 * k + l] = c.dt_dw * (keep[3 * k] * Li[l] + keep[3 * k + 1] * Li[3 + l] + keep[3 * k + 2] * Li[6 + l]);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
+        df_add(Fh[k], Fl[k], dF[k]);
         s.Fh[k * N + i] = Fh[k];
         s.Fl[k * N + i] = Fl[k];
     }
@@ -675,19 +625,7 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     }
     // unrotated strain increment dh = R^T sym(dt L_v) R with dt L_v = dF F^{-1}
     float Lv[9];
-    if (kin64) {                // J, F^{-1} and dt L_v in FP64
-        double Fid[9];
-        const double Jd = det_inv_d(Fh, Fl, Fid);
-        kin.Jm1 = (float)(Jd - 1.0);
-        kin.Jf = (float)Jd;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-                Lv[3 * a + b] = (float)(dFd[3 * a] * Fid[b] + dFd[3 * a + 1] * Fid[3 + b] + dFd[3 * a + 2] * Fid[6 + b]);
-    } else {
-        mul3f(dF, kin.Fi, Lv);
-    }
+    mul3f(dF, kin.Fi, Lv);
     const float d[6] = { Lv[0], Lv[4], Lv[8], 0.5f * (Lv[1] + Lv[3]), 0.5f * (Lv[5] + Lv[7]), 0.5f * (Lv[2] + Lv[6]) };
     float dh[6];
     sym_rotate_t_f(kin.R, d, dh);
@@ -786,8 +724,7 @@ __device__ __forceinline__ void epi1_slow(const DevState &s, const MixConst &c, 
         de[k] = (double)dh[k];
     }
     sym_rotate_f(kin.R, dh, dcur);      // the strain increment back in the current frame
-    const double Jd = (c.acc & TLSPH_ACC_FP64_KIN) ? det_inv_d(Fh, Fl, nullptr) : 1.0 + (double)kin.Jm1;
-    st |= material_update<true>(mat, c.dt, de, Jd, mp);
+    st |= material_update<true>(mat, c.dt, de, 1.0 + (double)kin.Jm1, mp);
     float sdh[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -883,7 +820,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass1_mixed(DevState s, MixCons
     float keep[9];
     gather1_w32(s, c, row0, nrows, lane, keep);
     if (lane >= nrows) return;
-    epi1_mixed<false>(s, c, row0 + lane, keep);
+    epi1_mixed(s, c, row0 + lane, keep);
 }
 
 __global__ void __launch_bounds__(256) k_pass1_mixed_t(DevState s, MixConst c)
@@ -892,7 +829,7 @@ __global__ void __launch_bounds__(256) k_pass1_mixed_t(DevState s, MixConst c)
     if (i >= s.N) return;
     float m[9];
     gather1_row<2>(s, c, i, m);
-    epi1_mixed<false>(s, c, i, m);
+    epi1_mixed(s, c, i, m);
 }
 
 // split form of pass 1: the gather kernel stores the 9 sums, a second kernel
@@ -930,87 +867,7 @@ __global__ void __launch_bounds__(128, EPI1_MINB) k_epi1_mixed(DevState s, MixCo
     float m[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = s.fsum[k * s.N + i];
-    epi1_mixed<false>(s, c, i, m);
-}
-
-// ------------------------------------------------------------------ pass 1 with accuracy options
-// Thread-per-row gather of the nine Fdot sums (two pairs in flight) with the
-// options of the context: COMPV, the half-step velocity as hi + lo (the
-// difference v_j - v_i formed from both parts); COMPS, every product summed as
-// a compensated pair (TwoProd by FMA for the product's rounding, TwoSum for the
-// addition's), low parts written to fsum_lo.
-template <bool COMPV, bool COMPS>
-__global__ void __launch_bounds__(256) k_gather1_acc(DevState s, MixConst c)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.N) return;
-    const int4 oi = s.xo[i];
-    const float4 vi = s.r1[i];
-    const float4 vil = COMPV ? s.r1lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float mh[9], ml[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) mh[k] = ml[k] = 0.0f;
-    for_slots<2>(s, i, [&](const int *j, const float *w) {
-        int4 o[2];
-        float4 v[2], vl[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            o[u] = s.xo[j[u]];
-            v[u] = s.r1[j[u]];
-            vl[u] = COMPV ? s.r1lo[j[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float3 d = xdiff(o[u], oi);
-            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-            const float rinv = rsqrtf(r2);
-            float a, b;
-            const float cw = v[u].w * spline_dw_ab(fmaf(r2 * rinv, c.inv_h, w[u]), a, b) * rinv;
-            float dv[3] = { v[u].x - vi.x, v[u].y - vi.y, v[u].z - vi.z };
-            if (COMPV) {
-                dv[0] += vl[u].x - vil.x;
-                dv[1] += vl[u].y - vil.y;
-                dv[2] += vl[u].z - vil.z;
-            }
-            const float dd[3] = { d.x, d.y, d.z };
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const float cr = cw * dv[r];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const int k = 3 * r + q;
-                    if (COMPS) {
-                        const float p = __fmul_rn(cr, dd[q]);
-                        const float pe = __fmaf_rn(cr, dd[q], -p);          // exact rounding error of the product
-                        float sh, se;
-                        two_sum(mh[k], p, sh, se);
-                        mh[k] = sh;
-                        ml[k] = __fadd_rn(ml[k], __fadd_rn(se, pe));
-                    } else {
-                        mh[k] += cr * dd[q];
-                    }
-                }
-            }
-        }
-    });
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        s.fsum[k * s.N + i] = mh[k];
-        if (COMPS) s.fsum_lo[k * s.N + i] = ml[k];
-    }
-}
-
-__global__ void __launch_bounds__(128) k_epi1_acc(DevState s, MixConst c)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.N) return;
-    float m[9], ml[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        m[k] = s.fsum[k * s.N + i];
-        ml[k] = (c.acc & TLSPH_ACC_COMP_SUMS) ? s.fsum_lo[k * s.N + i] : 0.0f;
-    }
-    epi1_mixed<true>(s, c, i, m, ml);
+    epi1_mixed(s, c, i, m);
 }
 
 // ------------------------------------------------------------------ pass 2
@@ -1081,12 +938,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         s.vh[3 * i + k] = v2[k];
         unext[3 * i + k] = un2[k];
     }
-    const double rv[3] = { v2[0] - c.vref0, v2[1] - c.vref1, v2[2] - c.vref2 };
-    const float4 rh = make_float4((float)rv[0], (float)rv[1], (float)rv[2], Vf * omdf);
-    s.r1[i] = rh;
-    if (c.acc & TLSPH_ACC_COMP_VELOCITY)      // the residuals of the FP32 velocity mirror
-        s.r1lo[i] = make_float4((float)(rv[0] - (double)rh.x), (float)(rv[1] - (double)rh.y),
-                                (float)(rv[2] - (double)rh.z), 0.0f);
+    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2), Vf * omdf);
     if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
 }
 
@@ -1320,11 +1172,8 @@ __global__ void k_mixed_r1(DevState s, int dcur)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
-    const double rv[3] = { s.vh[3 * i] - s.vref[0], s.vh[3 * i + 1] - s.vref[1], s.vh[3 * i + 2] - s.vref[2] };
-    const float4 rh = make_float4((float)rv[0], (float)rv[1], (float)rv[2], (float)(s.vol[i] * (1.0 - s.D[dcur][i])));
-    s.r1[i] = rh;
-    s.r1lo[i] = make_float4((float)(rv[0] - (double)rh.x), (float)(rv[1] - (double)rh.y), (float)(rv[2] - (double)rh.z),
-                            0.0f);
+    s.r1[i] = make_float4((float)(s.vh[3 * i] - s.vref[0]), (float)(s.vh[3 * i + 1] - s.vref[1]),
+                          (float)(s.vh[3 * i + 2] - s.vref[2]), (float)(s.vol[i] * (1.0 - s.D[dcur][i])));
 }
 
 // FP64 copy of A from the pass-2 records (for reading the state)
@@ -1529,16 +1378,7 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
     const bool hg = ctx.cfg.hg_alpha != 0.0;
     const int64_t rows32 = (s.N + 31) / 32 * 32;
     if (ev) cudaEventRecord(ev[0], st);
-    // accuracy options: their own gather (block size of the plan's pass 1) and per-particle kernel
-    const int acc_v = c.acc & (TLSPH_ACC_COMP_VELOCITY | TLSPH_ACC_COMP_SUMS);
-    const int ba = b1 >= 64 && b1 <= 256 ? b1 : 128;
-    switch (c.acc ? 8 + acc_v : v1) {
-    case 8: k_gather1_acc<false, false><<<nb(s.N, ba), ba, 0, st>>>(s, c); break;
-    case 8 + TLSPH_ACC_COMP_VELOCITY: k_gather1_acc<true, false><<<nb(s.N, ba), ba, 0, st>>>(s, c); break;
-    case 8 + TLSPH_ACC_COMP_SUMS: k_gather1_acc<false, true><<<nb(s.N, ba), ba, 0, st>>>(s, c); break;
-    case 8 + TLSPH_ACC_COMP_VELOCITY + TLSPH_ACC_COMP_SUMS:
-        k_gather1_acc<true, true><<<nb(s.N, ba), ba, 0, st>>>(s, c);
-        break;
+    switch (v1) {
     case 1: k_pass1_mixed_t<<<nb(s.N, b1), b1, 0, st>>>(s, c); break;
     case 2:
         k_gather1_mixed_t<<<nb(s.N, b1), b1, 0, st>>>(s, c);
@@ -1554,7 +1394,6 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
         break;
     default: k_pass1_mixed<<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c); break;
     }
-    if (c.acc) k_epi1_acc<<<nb(s.N, 128), 128, 0, st>>>(s, c);
     k_epi1_slow<<<ctx.slow_grid, 128, 0, st>>>(s, c);
     if (ev) cudaEventRecord(ev[1], st);
     if (v2 == 1) {
@@ -1591,10 +1430,7 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
     return cudaGetLastError();
 }
 
-int mixed_kernels_per_step(const tlsph_ctx &ctx)
-{
-    return (ctx.accuracy || ctx.plan[0] >= 2 ? 2 : 1) + 1 + (ctx.plan[2] == 2 ? 2 : 1);
-}
+int mixed_kernels_per_step(const tlsph_ctx &ctx) { return (ctx.plan[0] >= 2 ? 2 : 1) + 1 + (ctx.plan[2] == 2 ? 2 : 1); }
 
 cudaError_t mixed_sync_to_fp64(tlsph_ctx &ctx, int field, cudaStream_t st)
 {
@@ -1703,7 +1539,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchS
                     float mm[9];
 #pragma unroll
                     for (int k = 0; k < 9; ++k) mm[k] = st.fsum[k * st.N + i];
-                    epi1_mixed<false>(st, c, i, mm);
+                    epi1_mixed(st, c, i, mm);
                 } else {                    // pass 2
                     float acc[9];
                     gather2_row<HG, U>(st, c, i, acc);

@@ -76,10 +76,8 @@ struct DevState {
     float4 *s0;             // N   {sum_j V_j W'(r)/r (X_j - X_i), 0}  (static, FP64-accurate)
     float *linv32;          // N*9 L^{-1} rounded
     float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
-    float4 *r1lo;           // N   {the rounding residual of r1's velocity, 0} (compensated velocity mirror)
     float4 *r2;             // pass-2 gather record: 6 float4 per particle in tiles of 32 particles (r2_tile)
     float *fsum;            // 9 x N pass-1 pair sums (split launch plans)
-    float *fsum_lo;         // 9 x N low parts of compensated pass-1 sums
     // mixed path: F and the stress deviator as compensated FP32 pairs (value =
     // hi + lo, SoA by component: component k of particle i at k N + i); the
     // FP64 arrays F, sd and sig are refreshed from these when read
@@ -130,7 +128,6 @@ struct tlsph_ctx {
     // mixed launch plan: pass-1 form, block, pass-2 form, block (the fastest on
     // GB300 for the 1M-particle bar; the autotuner may choose another)
     int32_t plan[4] = { 4, 64, 4, 128 };
-    int accuracy = 0;           // accuracy options of the mixed step (tlsph_set_accuracy)
     double guard = 1e-5;        // relative guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)
     int slow_grid = 1;          // persistent grid of the mixed path's FP64-update kernel on the context's device
     bool need_predict = true;   // v^{n+1/2}, u^{n+1} must be recomputed before the next step
@@ -256,13 +253,11 @@ struct MixConst {
     float yield_keep;                               // 1 - guard band of the FP32 elastic screen
     float hg_w;                                     // -alpha/2 x W normalisation / unit (hourglass force factor)
     double inv_unit;
-    double dt_dw_d;                                 // dt x W' normalisation in FP64 (accuracy option FP64_KIN)
     double vref0, vref1, vref2;
     int64_t N;
     int64_t step_index;
     int ucur, dcur;
     int wall;
-    int acc;            // accuracy options of the mixed step (TLSPH_ACC_*)
 };
 
 // one context in a batch table (device memory)

@@ -81,7 +81,7 @@ EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph
            "tlsph_destroy", "tlsph_material_point_batch", "tlsph_profile_enable", "tlsph_profile_read",
            "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
            "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_batch_set_shape",
-           "tlsph_batch_get_shape", "tlsph_set_accuracy", "tlsph_get_accuracy", "tlsph_neighbor_layout",
+           "tlsph_batch_get_shape", "tlsph_neighbor_layout",
            "tlsph_fma_peak", "tlsph_set_guard", "tlsph_diagnostics", "tlsph_set_grip_ramp")
 
 _lib = None
@@ -140,10 +140,6 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_diagnostics.argtypes = [vp, ctypes.POINTER(dbl), i32]
         L.tlsph_set_guard.restype = i32
         L.tlsph_set_guard.argtypes = [vp, dbl]
-        L.tlsph_set_accuracy.restype = i32
-        L.tlsph_set_accuracy.argtypes = [vp, i32]
-        L.tlsph_get_accuracy.restype = i32
-        L.tlsph_get_accuracy.argtypes = [vp, ctypes.POINTER(i32)]
         L.tlsph_set_grip_ramp.restype = i32
         L.tlsph_set_grip_ramp.argtypes = [vp, dbl]
         L.tlsph_fma_peak.restype = i32
@@ -225,9 +221,6 @@ def fma_peak(fp64: bool = False, iters: int = 4096) -> float:
     _check(load().tlsph_fma_peak(1 if fp64 else 0, int(iters), ctypes.byref(v)))
     return v.value
 
-
-# accuracy options of the mixed step (tlsph_set_accuracy)
-ACC_COMP_VELOCITY, ACC_COMP_SUMS, ACC_FP64_KIN = 1, 2, 4
 
 FLAG_SPATIAL_ORDER = 1
 FLAG_WALL = 2
@@ -371,16 +364,6 @@ class Simulation:
     def set_guard(self, band: float) -> None:
         """Guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)."""
         _check(load().tlsph_set_guard(self.ctx, float(band)), self.ctx)
-
-    def set_accuracy(self, options: int) -> None:
-        """Accuracy options of the mixed step (tlsph_set_accuracy): a bitwise OR
-        of ACC_COMP_VELOCITY, ACC_COMP_SUMS and ACC_FP64_KIN; 0 is the default."""
-        _check(load().tlsph_set_accuracy(self.ctx, int(options)), self.ctx)
-
-    def get_accuracy(self) -> int:
-        v = ctypes.c_int()
-        _check(load().tlsph_get_accuracy(self.ctx, ctypes.byref(v)), self.ctx)
-        return v.value
 
     def set_grip_ramp(self, tau: float) -> None:
         """Prescribed velocities ramp up as bc_vel (1 - exp(-t / tau)) (Sec. 6
