@@ -752,6 +752,12 @@ __global__ void __launch_bounds__(128) k_epi1_slow(DevState s, MixConst c)
     if (blockIdx.x == 0 && threadIdx.x == 0) s.slowq_n[(c.step_index + 1) & 1] = 0u;
 }
 
+// weight V (1 - D) of the pass-1 record, formed the same way (FP32, each
+// rounding written out) by the pass-2 epilogue that refreshes the record every
+// step and by the kernel that rebuilds it after a state change, so that a
+// resumed run gathers exactly the records of the uninterrupted one
+__device__ __forceinline__ float r1_weight(float V, float D) { return __fmul_rn(V, __fsub_rn(1.0f, D)); }
+
 // ------------------------------------------------------------------ pass 1 pair terms
 __device__ __forceinline__ void pair1(const MixConst &c, const int4 oi, const float4 vi, const int4 oj,
                                       const float4 vj, float qpad, float *m)
@@ -900,16 +906,15 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         f[2] += hc * keep[8];
     }
     // the integrator in FP64 from the FP32 force; the half kick is the
-    // predictor's expression (v + dt/2 (f / m)), so a state reloaded from a
+    // predictor's (kick, explicitly rounded), so a state reloaded from a
     // checkpoint predicts exactly the v^{n+1/2} of the uninterrupted run
     const double im = s.inv_mass[i];
     const int fail = s.fail[i];
-    double fd[3], vn[3], v2[3];
+    double vn[3], v2[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        fd[k] = (double)f[k] * im;
         s.force[3 * i + k] = (double)f[k];
-        vn[k] = s.vh[3 * i + k] + c.half_dt * fd[k];
+        vn[k] = kick(s.vh[3 * i + k], c.half_dt, (double)f[k], im);
     }
     // velocity constraints (Sec. 3.1; grip ramp of Sec. 6 at t_{n+1} and at t_{n+3/2})
     if (fail >= 0) {
@@ -919,7 +924,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         vn[0] = s.bcv[3 * i] * r; vn[1] = s.bcv[3 * i + 1] * r; vn[2] = s.bcv[3 * i + 2] * r;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * fd[k];
+    for (int k = 0; k < 3; ++k) v2[k] = kick(vn[k], c.half_dt, (double)f[k], im);
     if (fail >= 0) {
         v2[0] = v2[1] = v2[2] = 0.0;
     } else if (s.bcm[i]) {
@@ -930,7 +935,7 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
     double *unext = s.u[c.ucur];
     double un2[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) un2[k] = un[3 * i + k] + c.dt * v2[k];
+    for (int k = 0; k < 3; ++k) un2[k] = drift(un[3 * i + k], c.dt, v2[k]);
     if (c.wall) wall_contact(s.X[3 * i + 2], un2[2], v2[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -938,7 +943,8 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
         s.vh[3 * i + k] = v2[k];
         unext[3 * i + k] = un2[k];
     }
-    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2), Vf * omdf);
+    s.r1[i] = make_float4((float)(v2[0] - c.vref0), (float)(v2[1] - c.vref1), (float)(v2[2] - c.vref2),
+                          r1_weight(Vf, Df));
     if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
 }
 
@@ -1173,7 +1179,7 @@ __global__ void k_mixed_r1(DevState s, int dcur)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
     s.r1[i] = make_float4((float)(s.vh[3 * i] - s.vref[0]), (float)(s.vh[3 * i + 1] - s.vref[1]),
-                          (float)(s.vh[3 * i + 2] - s.vref[2]), (float)(s.vol[i] * (1.0 - s.D[dcur][i])));
+                          (float)(s.vh[3 * i + 2] - s.vref[2]), r1_weight((float)s.vol[i], (float)s.D[dcur][i]));
 }
 
 // FP64 copy of A from the pass-2 records (for reading the state)

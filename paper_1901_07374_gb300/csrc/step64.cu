@@ -313,16 +313,16 @@ __global__ void __launch_bounds__(STEP_THREADS) k_pass2_fp64(DevState s, StepCon
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         s.force[3 * i + k] = f[k];
-        vn[k] = s.vh[3 * i + k] + c.half_dt * (f[k] * im);
+        vn[k] = kick(s.vh[3 * i + k], c.half_dt, f[k], im);
     }
     apply_bc(s, i, fail, ((double)c.step_index + 1.0) * c.dt, vn);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v2[k] = vn[k] + c.half_dt * (f[k] * im);
+    for (int k = 0; k < 3; ++k) v2[k] = kick(vn[k], c.half_dt, f[k], im);
     apply_bc(s, i, fail, ((double)(c.step_index + 1) + 0.5) * c.dt, v2);
     double *__restrict__ unext = s.u[c.ucur];
     double un2[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) un2[k] = un[3 * i + k] + c.dt * v2[k];
+    for (int k = 0; k < 3; ++k) un2[k] = drift(un[3 * i + k], c.dt, v2[k]);
     if (c.wall) wall_contact(s.X[3 * i + 2], un2[2], v2[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -386,10 +386,10 @@ __global__ void k_predict(DevState s, int ucur, double dt, int wall, double t_ha
     const double im = s.inv_mass[i];
     double v[3], u[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = s.v[3 * i + k] + 0.5 * dt * (s.force[3 * i + k] * im);
+    for (int k = 0; k < 3; ++k) v[k] = kick(s.v[3 * i + k], 0.5 * dt, s.force[3 * i + k], im);
     apply_bc(s, i, s.fail[i], t_half, v);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) u[k] = s.u[ucur][3 * i + k] + dt * v[k];
+    for (int k = 0; k < 3; ++k) u[k] = drift(s.u[ucur][3 * i + k], dt, v[k]);
     if (wall) wall_contact(s.X[3 * i + 2], u[2], v[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

@@ -52,6 +52,18 @@ __device__ __forceinline__ float spline_dw(float q)
 // at time t; tau = 0 keeps it constant
 __device__ __forceinline__ double grip_factor(double tau, double t) { return tau > 0.0 ? -expm1(-t / tau) : 1.0; }
 
+// Velocity-Verlet half kick v + h (f / m) (f / m as f times the stored 1/m) and
+// drift u + dt v, each rounding written out, so that every kernel that forms
+// them -- the predictor, the FP64 and mixed pass-2 epilogues in any launch
+// form -- produces the same bits whatever multiply-adds the compiler would
+// otherwise fuse (a state reloaded from a checkpoint then continues exactly
+// like the uninterrupted run)
+__device__ __forceinline__ double kick(double v, double h, double f, double inv_m)
+{
+    return __fma_rn(h, __dmul_rn(f, inv_m), v);
+}
+__device__ __forceinline__ double drift(double u, double dt, double v) { return __fma_rn(dt, v, u); }
+
 // ---------------------------------------------------------------- 3x3 algebra
 struct M3 { double a[9]; };
 

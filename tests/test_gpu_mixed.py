@@ -76,6 +76,27 @@ def test_mixed_resume_is_bitwise():
         assert np.array_equal(v, ref[k]), k
 
 
+def test_mixed_resume_is_bitwise_with_partial_damage():
+    """A GTN bar, whose every particle carries 0 < D = q1 f* < 1: the pass-1
+    record's weight V (1 - D) rebuilt after a reload equals the one the
+    uninterrupted run carries, so the resumed run is identical bit for bit."""
+    w = S.notched_bar_gtn(radius=1.5e-3, height=5e-3, spacing=0.3e-3, notch_radius=0.5e-3, v_grip=20.0, steps=60)
+    names = tlsph.CHECKPOINT_FIELDS
+    a = tlsph.Simulation.from_workload(w, precision="mixed")
+    a.step(30)
+    ck = {k: a.get(k) for k in names}
+    D = ck["DAMAGE"]
+    assert np.all((D > 0) & (D < 1))
+    a.step(30)
+    ref = a.state()
+    b = tlsph.Simulation.from_workload(w, precision="mixed")
+    for k, v in ck.items():
+        b.set(k, v)
+    b.step(30)
+    for k, v in b.state().items():
+        assert np.array_equal(v, ref[k]), k
+
+
 PLANS = [(0, 128, 0, 128), (1, 64, 1, 64), (2, 256, 1, 256), (3, 128, 0, 128), (1, 128, 1, 256), (4, 64, 3, 128),
          (2, 128, 4, 128), (4, 128, 2, 64), (4, 128, 5, 128), (4, 64, 6, 128), (4, 128, 7, 128)]
 
