@@ -80,8 +80,12 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # precision, pass, plan form of that pass) and stamped with the digest of the
 # CUDA sources they were captured from: a figure is reported only while the
 # sources are unchanged (otherwise `traffic` is null until the next capture).
-TRAFFIC_SOURCES = None
-TRAFFIC = {}
+TRAFFIC_SOURCES = "1f3336325ea5c22ac203f42e237e35ca104a124848e7d42eb4af860fb6eec0a4"
+TRAFFIC = {
+    ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 597179392,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 327658752,   # k_pass2_mixed_tc
+    ("tensile_bar_jc_40x40x640", "mixed", "pass2", 7): 327059456,   # k_pass2_mixed_tc5
+}
 
 
 def kernel_sources_digest() -> str:
