@@ -80,7 +80,7 @@ def algorithmic_bytes(N: int, nnz: int, precision: str, list_words: int | None =
 # precision, pass, plan form of that pass) and stamped with the digest of the
 # CUDA sources they were captured from: a figure is reported only while the
 # sources are unchanged (otherwise `traffic` is null until the next capture).
-TRAFFIC_SOURCES = "1f3336325ea5c22ac203f42e237e35ca104a124848e7d42eb4af860fb6eec0a4"
+TRAFFIC_SOURCES = "8087a364b4c3847283d26d6adcd500b411e0c0f47c68bc0908b4401975826258"
 TRAFFIC = {
     ("tensile_bar_jc_40x40x640", "mixed", "pass1", 4): 597179392,   # k_gather1_mixed_t4 + k_epi1_mixed + k_epi1_slow
     ("tensile_bar_jc_40x40x640", "mixed", "pass2", 4): 327658752,   # k_pass2_mixed_tc
@@ -89,15 +89,21 @@ TRAFFIC = {
 
 
 def kernel_sources_digest() -> str:
-    """SHA-256 over the library's CUDA sources and headers (sorted by name)."""
+    """SHA-256 over the code of the library's CUDA sources and headers (sorted
+    by name; comments and whitespace left out, so editing a comment keeps the
+    stamp while any change to the code drops it)."""
     import glob
     import hashlib
+    import re
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_1901_07374_gb300", "csrc", "*.cu*"))
                     + [os.path.join(ROOT, "include", "tlsph.h")]):
+        with open(p, encoding="utf-8") as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
         h.update(os.path.basename(p).encode())
-        with open(p, "rb") as f:
-            h.update(f.read())
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

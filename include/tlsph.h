@@ -19,7 +19,10 @@
  *     (Sec. 5.1-5.4); a fully damaged particle keeps no stress and rests
  *     (Sec. 3.1),
  *   - the damage-weighted nodal forces (Sec. 3.1, equation after
- *     Crack_approx_F) with hourglass control (Sec. 2, cited scheme),
+ *     Crack_approx_F) with hourglass control (Sec. 2 names the scheme
+ *     without a formula; here a spring along each current bond of stiffness
+ *     hg_alpha (E_i + E_j)/2 V_i V_j W(X_ij) / X_ij^2 on the mean of the two
+ *     particles' projected position errors, scaled by (1 - D_i)(1 - D_j)),
  *   - velocity-Verlet integration.
  *
  * Units are SI.  Every floating-point array crossing this ABI is IEEE double,
