@@ -509,6 +509,32 @@ __device__ __forceinline__ bool kin_from_F(const float *Fh, const float *Fl, Kin
     return true;
 }
 
+// Pass-2 record of a particle: six float4 components (tiled, r2_tile)
+//   c0 {A00, A10, A01, A11}   c1 {A02, A12, A20, A21}   c2 {A22, V D, V, E V (1 - D)}
+//   c3 {u0, u1, G00, G10}     c4 {G01, G11, G02, G12}   c5 {u2, G20, G21, G22}
+// with A row-major (A[3r + c]), G = F - I and u in fixed-point units.  Rows 0
+// and 1 of A and G and the first two components of u sit side by side in
+// aligned float pairs, so that the pair terms take them two at a time with
+// packed FP32x2 operations; a record without the hourglass term is c0..c2.
+__device__ __forceinline__ void r2_store(float4 *__restrict__ r2, const float *A, float VD, float V, float EV,
+                                         float u0, float u1, float u2, const float *G)
+{
+    r2[0] = make_float4(A[0], A[3], A[1], A[4]);
+    r2[R2_STRIDE] = make_float4(A[2], A[5], A[6], A[7]);
+    r2[2 * R2_STRIDE] = make_float4(A[8], VD, V, EV);
+    r2[3 * R2_STRIDE] = make_float4(u0, u1, G[0], G[3]);
+    r2[4 * R2_STRIDE] = make_float4(G[1], G[4], G[2], G[5]);
+    r2[5 * R2_STRIDE] = make_float4(u2, G[6], G[7], G[8]);
+}
+
+// A (row-major) from the first three components of a pass-2 record
+__device__ __forceinline__ void r2_A(const float4 c0, const float4 c1, const float4 c2, float *A)
+{
+    A[0] = c0.x; A[3] = c0.y; A[1] = c0.z; A[4] = c0.w;
+    A[2] = c1.x; A[5] = c1.y; A[6] = c1.z; A[7] = c1.w;
+    A[8] = c2.x;
+}
+
 // stress, A and the pass-2 record of a particle after its constitutive update
 // internal-energy increment (Eq. conservation3, de/dt = J sigma : d / rho0), trapezoidal in the step:
 // J / rho0 * (sigma^n + sigma^{n+1}) / 2 : dcur with dcur the step's strain increment in the current frame
@@ -554,13 +580,7 @@ __device__ __forceinline__ void epi1_finish(const DevState &s, const MixConst &c
     }
     s.e[i] = e_n + (double)(ejr * w);
     const float omd = 1.0f - (float)Dnew;
-    const float *G = k.G;
-    r2[0] = make_float4(A[0], A[1], A[2], A[3]);
-    r2[R2_STRIDE] = make_float4(A[4], A[5], A[6], A[7]);
-    r2[2 * R2_STRIDE] = make_float4(A[8], Vf * (float)Dnew, Vf, u0);
-    r2[3 * R2_STRIDE] = make_float4(u1, u2, G[0], G[1]);
-    r2[4 * R2_STRIDE] = make_float4(G[2], G[3], G[4], G[5]);
-    r2[5 * R2_STRIDE] = make_float4(G[6], G[7], G[8], (float)s.youngs[i] * Vf * omd);
+    r2_store(r2, A, Vf * (float)Dnew, Vf, (float)s.youngs[i] * Vf * omd, u0, u1, u2, k.G);
     if (st) atomicOr(s.status, st);
 }
 
@@ -590,14 +610,12 @@ __device__ __forceinline__ void epi1_mixed(const DevState &s, const MixConst &c,
     for (int k = 0; k < 6; ++k) sgn[k] = s.sigf[k * N + i];
     const double e_n = s.e[i];
     if (fail >= 0) {            // fully damaged: no stress, F frozen, record with A = 0 and 1 - D = 0
-        float4 *__restrict__ r2 = s.r2 + r2_tile(i);
         Dnext[i] = Dn[i];
-        r2[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2[R2_STRIDE] = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2[2 * R2_STRIDE] = make_float4(0.f, Vf, Vf, u0);     // V D with D = 1
-        r2[3 * R2_STRIDE] = make_float4(u1, u2, (Fh[0] - 1.0f) + Fl[0], Fh[1] + Fl[1]);
-        r2[4 * R2_STRIDE] = make_float4(Fh[2] + Fl[2], Fh[3] + Fl[3], (Fh[4] - 1.0f) + Fl[4], Fh[5] + Fl[5]);
-        r2[5 * R2_STRIDE] = make_float4(Fh[6] + Fl[6], Fh[7] + Fl[7], (Fh[8] - 1.0f) + Fl[8], 0.f);
+        const float A0[9] = { 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f };
+        float G[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) G[k] = ((k & 3) == 0 ? Fh[k] - 1.0f : Fh[k]) + Fl[k];
+        r2_store(s.r2 + r2_tile(i), A0, Vf, Vf, 0.f, u0, u1, u2, G);    // V D with D = 1
         return;
     }
     float Li[9];
@@ -882,10 +900,10 @@ __global__ void __launch_bounds__(128, EPI1_MINB) k_epi1_mixed(DevState s, MixCo
 template <bool HG>
 __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c, int64_t i, const float *keep)
 {
-    const int64_t N = c.N;
     const float4 *ri = s.r2 + r2_tile(i);
     const float4 a0 = ri[0], a1 = ri[R2_STRIDE], a2 = ri[2 * R2_STRIDE];
-    const float Ai[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
+    float Ai[9];
+    r2_A(a0, a1, a2, Ai);
     const float Vf = a2.z;                           // V_i
     const float Df = (float)s.D[c.dcur ^ 1][i];      // D_i^{n+1}
     const float omdf = 1.0f - Df;
@@ -948,11 +966,18 @@ __device__ __forceinline__ void epi2_mixed(const DevState &s, const MixConst &c,
     if (!(isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]))) atomicOr(s.status, TLSPH_ST_NONFINITE);
 }
 
-struct Row2 {   // row i's own pass-2 record
+struct Row2 {   // row i's own pass-2 record, negated where the pair terms subtract it
     int4 o;
-    float4 a0, a1, a2, a3, a4, a5;
-    float E;    // Young modulus of row i's material (hourglass term)
+    float2 nA0, nA1, nA2;     // -(A_0c, A_1c), c = 0, 1, 2
+    float nA20, nA21, nA22;   // -A_2c
+    float2 nu01;              // -(u_0, u_1)
+    float nu2;                // -u_2
+    float2 G0, G1, G2;        // (G_0c, G_1c)
+    float G20, G21, G22;
+    float E;                  // Young modulus of row i's material (hourglass term)
 };
+
+__device__ __forceinline__ float2 neg2(const float a, const float b) { return make_float2(-a, -b); }
 
 template <bool HG>
 __device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, int64_t i)
@@ -960,20 +985,35 @@ __device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, 
     const float4 *ri = s.r2 + r2_tile(i);
     Row2 w;
     w.o = s.xo[i];
-    w.a0 = ri[0];
-    w.a1 = ri[R2_STRIDE];
-    w.a2 = ri[2 * R2_STRIDE];
-    w.a3 = w.a4 = w.a5 = make_float4(0.f, 0.f, 0.f, 0.f);
-    w.E = 0.0f;
+    const float4 a0 = ri[0], a1 = ri[R2_STRIDE], a2 = ri[2 * R2_STRIDE];
+    w.nA0 = neg2(a0.x, a0.y);
+    w.nA1 = neg2(a0.z, a0.w);
+    w.nA2 = neg2(a1.x, a1.y);
+    w.nA20 = -a1.z;
+    w.nA21 = -a1.w;
+    w.nA22 = -a2.x;
+    w.nu01 = make_float2(0.f, 0.f);
+    w.G0 = w.G1 = w.G2 = make_float2(0.f, 0.f);
+    w.nu2 = w.G20 = w.G21 = w.G22 = w.E = 0.0f;
     if (HG) {
+        const float4 a3 = ri[3 * R2_STRIDE], a4 = ri[4 * R2_STRIDE], a5 = ri[5 * R2_STRIDE];
         w.E = (float)s.youngs[i];
-        w.a3 = ri[3 * R2_STRIDE];
-        w.a4 = ri[4 * R2_STRIDE];
-        w.a5 = ri[5 * R2_STRIDE];
+        w.nu01 = neg2(a3.x, a3.y);
+        w.nu2 = -a5.x;
+        w.G0 = make_float2(a3.z, a3.w);
+        w.G1 = make_float2(a4.x, a4.y);
+        w.G2 = make_float2(a4.z, a4.w);
+        w.G20 = a5.y;
+        w.G21 = a5.z;
+        w.G22 = a5.w;
     }
     return w;
 }
 
+// Pair terms of row i with neighbour j (qpad: 0, or SLOT_PAD_Q for a padding
+// slot).  Rows 0 and 1 of the 3x3 products (A_j - A_i) X_ij and
+// (G_i + G_j) X_ij - 2 u_ij are formed together by packed FP32x2 operations on
+// the record's column pairs; every element is rounded as in the scalar form.
 template <bool HG>
 __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, const Row2 &w, int j, float qpad,
                                       float *acc)
@@ -990,24 +1030,31 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
     const float g = b2.z * g0;                     // V_j W'/r
     const float gd = b2.y * g0;                    // V_j D_j W'/r
     acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
-    const float t0 = (b0.x - w.a0.x) * d.x + (b0.y - w.a0.y) * d.y + (b0.z - w.a0.z) * d.z;
-    const float t1 = (b0.w - w.a0.w) * d.x + (b1.x - w.a1.x) * d.y + (b1.y - w.a1.y) * d.z;
-    const float t2 = (b1.z - w.a1.z) * d.x + (b1.w - w.a1.w) * d.y + (b2.x - w.a2.x) * d.z;
-    acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
+    const float2 dx2 = make_float2(d.x, d.x), dy2 = make_float2(d.y, d.y), dz2 = make_float2(d.z, d.z);
+    // rows 0 and 1 of (A_j - A_i) X_ij, then row 2
+    const float2 t01 = __ffma2_rn(__fadd2_rn(make_float2(b1.x, b1.y), w.nA2), dz2,
+                                  __ffma2_rn(__fadd2_rn(make_float2(b0.z, b0.w), w.nA1), dy2,
+                                             __fmul2_rn(__fadd2_rn(make_float2(b0.x, b0.y), w.nA0), dx2)));
+    const float t2 = fmaf(b2.x + w.nA22, d.z, fmaf(b1.w + w.nA21, d.y, (b1.z + w.nA20) * d.x));
+    acc[3] += g * t01.x; acc[4] += g * t01.y; acc[5] += g * t2;
     if (HG) {
         const float4 b3 = rj[3 * R2_STRIDE], b4 = rj[4 * R2_STRIDE], b5 = rj[5 * R2_STRIDE];
         // u_ij, x_ij = X_ij + u_ij, e = ((F_i - I) + (F_j - I)) X_ij - 2 u_ij
-        const float ux = b2.w - w.a2.w, uy = b3.x - w.a3.x, uz = b3.y - w.a3.y;
-        const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
-        const float lxi2 = rcp_approx(xx * xx + xy * xy + xz * xz);    // 1 / |x_ij|^2
-        const float ex = (w.a3.z + b3.z) * d.x + (w.a3.w + b3.w) * d.y + (w.a4.x + b4.x) * d.z - 2.0f * ux;
-        const float ey = (w.a4.y + b4.y) * d.x + (w.a4.z + b4.z) * d.y + (w.a4.w + b4.w) * d.z - 2.0f * uy;
-        const float ez = (w.a5.x + b5.x) * d.x + (w.a5.y + b5.y) * d.y + (w.a5.z + b5.z) * d.z - 2.0f * uz;
+        const float2 u01 = __fadd2_rn(make_float2(b3.x, b3.y), w.nu01);
+        const float uz = b5.x + w.nu2;
+        const float2 x01 = __fadd2_rn(make_float2(d.x, d.y), u01);
+        const float xz = d.z + uz;
+        const float lxi2 = rcp_approx(fmaf(xz, xz, fmaf(x01.y, x01.y, x01.x * x01.x)));   // 1 / |x_ij|^2
+        const float2 e01 = __ffma2_rn(__fadd2_rn(make_float2(b4.z, b4.w), w.G2), dz2,
+                                      __ffma2_rn(__fadd2_rn(make_float2(b4.x, b4.y), w.G1), dy2,
+                                                 __ffma2_rn(__fadd2_rn(make_float2(b3.z, b3.w), w.G0), dx2,
+                                                            __fmul2_rn(make_float2(-2.0f, -2.0f), u01))));
+        const float ez = fmaf(b5.w + w.G22, d.z, fmaf(b5.z + w.G21, d.y, fmaf(b5.y + w.G20, d.x, -2.0f * uz)));
         // (E_i + E_j) V_j (1 - D_j) W / X_ij^2 * delta / |x_ij| with delta = (e . x_ij) / |x_ij|;
         // V_j (1 - D_j) = V_j - V_j D_j, and the record carries E_j V_j (1 - D_j)
-        const float ev = fmaf(w.E, b2.z - b2.y, b5.w);
-        const float ch = ev * spline_w_ab(a, b) * rinv * rinv * (ex * xx + ey * xy + ez * xz) * lxi2;
-        acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
+        const float ev = fmaf(w.E, b2.z - b2.y, b2.w);
+        const float ch = ev * spline_w_ab(a, b) * rinv * rinv * fmaf(ez, xz, fmaf(e01.y, x01.y, e01.x * x01.x)) * lxi2;
+        acc[6] += ch * x01.x; acc[7] += ch * x01.y; acc[8] += ch * xz;
     }
 }
 
@@ -1188,8 +1235,8 @@ __global__ void k_mixed_export_A(DevState s)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;
     const float4 *ri = s.r2 + r2_tile(i);
-    const float4 a0 = ri[0], a1 = ri[R2_STRIDE], a2 = ri[2 * R2_STRIDE];
-    const float A[9] = { a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x };
+    float A[9];
+    r2_A(ri[0], ri[R2_STRIDE], ri[2 * R2_STRIDE], A);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.A[9 * i + k] = (double)A[k];
 }

@@ -75,7 +75,7 @@ struct DevState {
     int4 *xo;               // N   {fixed-point position x, y, z (FixPack), 0}
     float4 *s0;             // N   {sum_j V_j W'(r)/r (X_j - X_i), 0}  (static, FP64-accurate)
     float *linv32;          // N*9 L^{-1} rounded
-    float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, 1 - D}
+    float4 *r1;             // N   pass-1 gather record {v^{n+1/2} - vref, V (1 - D)}
     float4 *r2;             // pass-2 gather record: 6 float4 per particle in tiles of 32 particles (r2_tile)
     float *fsum;            // 9 x N pass-1 pair sums (split launch plans)
     // mixed path: F and the stress deviator as compensated FP32 pairs (value =
