@@ -248,7 +248,9 @@ int tlsph_destroy(tlsph_ctx *ctx);
  * gather + per-particle kernel; 3 thread per row, one pair in flight; 4 as
  * 1 with registers capped for six resident blocks; 5 as 3 with registers
  * capped for eight resident blocks; 6 as 1 capped for seven resident blocks;
- * 7 as 1 capped for five resident blocks; block size at most 128 for 4 to 7),
+ * 7 as 1 capped for five resident blocks; 8 as 7 with rows 0 and 1 of the
+ * stress term formed by packed FP32x2 operations; block size at most 128 for
+ * 4 to 8),
  * plan[3] its block size (multiples of 32 up to 256).  Every plan computes
  * the same method; sums over a row are grouped differently, so results
  * differ only by FP32 rounding.  n must be 4.  TLSPH_ERR_ARG for a plan out
@@ -331,7 +333,8 @@ const char *tlsph_batch_last_error(const tlsph_batch *b);
  * setting): shape[k] selects a variant for kernel kind
  * k = 0 (pass-1 gather), 1 (per-particle update), 2 (pass 2); a variant
  * fixes how many blocks of 128 threads the kernel's registers are capped for
- * and how many neighbour pairs a thread has in flight.  n must be 3 (the
+ * and how many neighbour pairs a thread has in flight (and, for one pass-2
+ * variant, packed FP32x2 stress rows as in pass-2 plan form 8).  n must be 3 (the
  * number of kinds).  Setting a different shape waits for the batch's
  * launches in flight and re-captures its graph at the next tlsph_batch_step.
  * Every variant computes the same method; the results of two variants agree

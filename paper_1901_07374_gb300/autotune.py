@@ -26,7 +26,7 @@ import zlib
 
 PASS1 = [(0, 128), (1, 128), (2, 64), (2, 128), (2, 256), (3, 256), (4, 64), (4, 128), (4, 256)]
 PASS2 = [(0, 128), (1, 64), (1, 128), (1, 256), (2, 128), (3, 128), (3, 256), (4, 64), (4, 128), (5, 128), (6, 64),
-         (6, 128), (7, 64), (7, 128)]
+         (6, 128), (7, 64), (7, 128), (8, 128)]
 DEFAULT = (4, 64, 4, 128)
 
 _lock = threading.Lock()

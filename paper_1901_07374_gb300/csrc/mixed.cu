@@ -1011,10 +1011,12 @@ __device__ __forceinline__ Row2 load_row2(const DevState &s, const MixConst &c, 
 }
 
 // Pair terms of row i with neighbour j (qpad: 0, or SLOT_PAD_Q for a padding
-// slot).  Rows 0 and 1 of the 3x3 products (A_j - A_i) X_ij and
-// (G_i + G_j) X_ij - 2 u_ij are formed together by packed FP32x2 operations on
-// the record's column pairs; every element is rounded as in the scalar form.
-template <bool HG>
+// slot).  The row's own A and u are held negated, so the differences are sums.
+// With PK, rows 0 and 1 of (A_j - A_i) X_ij are formed together by packed
+// FP32x2 operations on the record's column pairs (same roundings as the
+// scalar form); the scalar form is the faster one on most lists, the packed
+// one on fully aligned lattice lists.
+template <bool HG, bool PK = false>
 __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, const Row2 &w, int j, float qpad,
                                       float *acc)
 {
@@ -1030,31 +1032,35 @@ __device__ __forceinline__ void pair2(const DevState &s, const MixConst &c, cons
     const float g = b2.z * g0;                     // V_j W'/r
     const float gd = b2.y * g0;                    // V_j D_j W'/r
     acc[0] += gd * d.x; acc[1] += gd * d.y; acc[2] += gd * d.z;
-    const float2 dx2 = make_float2(d.x, d.x), dy2 = make_float2(d.y, d.y), dz2 = make_float2(d.z, d.z);
-    // rows 0 and 1 of (A_j - A_i) X_ij, then row 2
-    const float2 t01 = __ffma2_rn(__fadd2_rn(make_float2(b1.x, b1.y), w.nA2), dz2,
-                                  __ffma2_rn(__fadd2_rn(make_float2(b0.z, b0.w), w.nA1), dy2,
-                                             __fmul2_rn(__fadd2_rn(make_float2(b0.x, b0.y), w.nA0), dx2)));
+    // (A_j - A_i) X_ij
+    float t0, t1;
+    if (PK) {
+        const float2 dx2 = make_float2(d.x, d.x), dy2 = make_float2(d.y, d.y), dz2 = make_float2(d.z, d.z);
+        const float2 t01 = __ffma2_rn(__fadd2_rn(make_float2(b1.x, b1.y), w.nA2), dz2,
+                                      __ffma2_rn(__fadd2_rn(make_float2(b0.z, b0.w), w.nA1), dy2,
+                                                 __fmul2_rn(__fadd2_rn(make_float2(b0.x, b0.y), w.nA0), dx2)));
+        t0 = t01.x;
+        t1 = t01.y;
+    } else {
+        t0 = (b0.x + w.nA0.x) * d.x + (b0.z + w.nA1.x) * d.y + (b1.x + w.nA2.x) * d.z;
+        t1 = (b0.y + w.nA0.y) * d.x + (b0.w + w.nA1.y) * d.y + (b1.y + w.nA2.y) * d.z;
+    }
     const float t2 = fmaf(b2.x + w.nA22, d.z, fmaf(b1.w + w.nA21, d.y, (b1.z + w.nA20) * d.x));
-    acc[3] += g * t01.x; acc[4] += g * t01.y; acc[5] += g * t2;
+    acc[3] += g * t0; acc[4] += g * t1; acc[5] += g * t2;
     if (HG) {
         const float4 b3 = rj[3 * R2_STRIDE], b4 = rj[4 * R2_STRIDE], b5 = rj[5 * R2_STRIDE];
         // u_ij, x_ij = X_ij + u_ij, e = ((F_i - I) + (F_j - I)) X_ij - 2 u_ij
-        const float2 u01 = __fadd2_rn(make_float2(b3.x, b3.y), w.nu01);
-        const float uz = b5.x + w.nu2;
-        const float2 x01 = __fadd2_rn(make_float2(d.x, d.y), u01);
-        const float xz = d.z + uz;
-        const float lxi2 = rcp_approx(fmaf(xz, xz, fmaf(x01.y, x01.y, x01.x * x01.x)));   // 1 / |x_ij|^2
-        const float2 e01 = __ffma2_rn(__fadd2_rn(make_float2(b4.z, b4.w), w.G2), dz2,
-                                      __ffma2_rn(__fadd2_rn(make_float2(b4.x, b4.y), w.G1), dy2,
-                                                 __ffma2_rn(__fadd2_rn(make_float2(b3.z, b3.w), w.G0), dx2,
-                                                            __fmul2_rn(make_float2(-2.0f, -2.0f), u01))));
+        const float ux = b3.x + w.nu01.x, uy = b3.y + w.nu01.y, uz = b5.x + w.nu2;
+        const float xx = d.x + ux, xy = d.y + uy, xz = d.z + uz;
+        const float lxi2 = rcp_approx(fmaf(xz, xz, fmaf(xy, xy, xx * xx)));   // 1 / |x_ij|^2
+        const float ex = (b3.z + w.G0.x) * d.x + (b4.x + w.G1.x) * d.y + (b4.z + w.G2.x) * d.z - 2.0f * ux;
+        const float ey = (b3.w + w.G0.y) * d.x + (b4.y + w.G1.y) * d.y + (b4.w + w.G2.y) * d.z - 2.0f * uy;
         const float ez = fmaf(b5.w + w.G22, d.z, fmaf(b5.z + w.G21, d.y, fmaf(b5.y + w.G20, d.x, -2.0f * uz)));
         // (E_i + E_j) V_j (1 - D_j) W / X_ij^2 * delta / |x_ij| with delta = (e . x_ij) / |x_ij|;
         // V_j (1 - D_j) = V_j - V_j D_j, and the record carries E_j V_j (1 - D_j)
         const float ev = fmaf(w.E, b2.z - b2.y, b2.w);
-        const float ch = ev * spline_w_ab(a, b) * rinv * rinv * fmaf(ez, xz, fmaf(e01.y, x01.y, e01.x * x01.x)) * lxi2;
-        acc[6] += ch * x01.x; acc[7] += ch * x01.y; acc[8] += ch * xz;
+        const float ch = ev * spline_w_ab(a, b) * rinv * rinv * fmaf(ez, xz, fmaf(ey, xy, ex * xx)) * lxi2;
+        acc[6] += ch * xx; acc[7] += ch * xy; acc[8] += ch * xz;
     }
 }
 
@@ -1088,7 +1094,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_pass2_mixed(DevState s, MixCons
 }
 
 // pass-2 pair sums of row i over its slots, U pairs in flight
-template <bool HG, int U>
+template <bool HG, int U, bool PK = false>
 __device__ __forceinline__ void gather2_row(const DevState &s, const MixConst &c, int64_t i, float *acc)
 {
     const Row2 w = load_row2<HG>(s, c, i);
@@ -1096,7 +1102,7 @@ __device__ __forceinline__ void gather2_row(const DevState &s, const MixConst &c
     for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
     for_slots<U>(s, i, [&](const int *j, const float *wm) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) pair2<HG>(s, c, w, j[u], wm[u], acc);
+        for (int u = 0; u < U; ++u) pair2<HG, PK>(s, c, w, j[u], wm[u], acc);
     });
 }
 
@@ -1151,6 +1157,17 @@ __global__ void __launch_bounds__(128, 5) k_pass2_mixed_tc5(DevState s, MixConst
     if (i >= s.N) return;
     float acc[9];
     gather2_row<HG, 2>(s, c, i, acc);
+    epi2_mixed<HG>(s, c, i, acc);
+}
+
+// as k_pass2_mixed_tc5 with the packed FP32x2 stress rows
+template <bool HG>
+__global__ void __launch_bounds__(128, 5) k_pass2_mixed_tc5p(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float acc[9];
+    gather2_row<HG, 2, true>(s, c, i, acc);
     epi2_mixed<HG>(s, c, i, acc);
 }
 
@@ -1421,8 +1438,8 @@ int mixed_slow_grid()
 //   pass 2: 0 = warp per 32 rows;  1 = thread per row;  2 = thread-per-row gather + per-particle kernel;
 //           3 = thread per row, one pair in flight;  4 = thread per row, registers capped for 6 blocks of 128;
 //           5 = as 3 with registers capped for 8 blocks of 128;  6 = as 1 with registers capped for 7 blocks of 128;
-//           7 = as 1 with registers capped for 5 blocks of 128
-// block sizes are multiples of 32 up to 256 (128 for the fused warp forms and pass-2 forms 4 to 7).
+//           7 = as 1 with registers capped for 5 blocks of 128;  8 = as 7 with packed FP32x2 stress rows
+// block sizes are multiples of 32 up to 256 (128 for the fused warp forms and pass-2 forms 4 to 8).
 cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t st, cudaEvent_t *ev)
 {
     const MixConst c = make_mix_const(ctx, step_index);
@@ -1464,6 +1481,9 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
     } else if (v2 == 7) {
         if (hg) k_pass2_mixed_tc5<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
         else k_pass2_mixed_tc5<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+    } else if (v2 == 8) {
+        if (hg) k_pass2_mixed_tc5p<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
+        else k_pass2_mixed_tc5p<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
     } else if (v2 == 5) {
         if (hg) k_pass2_mixed_t1c<true><<<nb(s.N, b2), b2, 0, st>>>(s, c);
         else k_pass2_mixed_t1c<false><<<nb(s.N, b2), b2, 0, st>>>(s, c);
@@ -1549,10 +1569,10 @@ __device__ __forceinline__ int batch_find(const int64_t *blk0, int n, int64_t w)
 // the compiler fuses).
 //   pass-1 gather:        (8, 4)  (6, 4)  (10, 4)  (8, 2)
 //   per-particle update:  5  4  3
-//   pass 2:               (5, 2)  (6, 2)  (4, 2)  (8, 1)
-const int BATCH_VARIANTS[BATCH_KINDS] = { 4, 3, 4 };
+//   pass 2:               (5, 2)  (6, 2)  (4, 2)  (8, 1)  (5, 2) with packed FP32x2 stress rows
+const int BATCH_VARIANTS[BATCH_KINDS] = { 4, 3, 5 };
 
-template <int KIND, bool HG, int MINB, int U>
+template <int KIND, bool HG, int MINB, int U, bool PK = false>
 __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchSlot *slots)
 {
     __shared__ uint64_t slot_words[(sizeof(BatchSlot) + 7) / 8];
@@ -1595,7 +1615,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchS
                     epi1_mixed(st, c, i, mm);
                 } else {                    // pass 2
                     float acc[9];
-                    gather2_row<HG, U>(st, c, i, acc);
+                    gather2_row<HG, U, PK>(st, c, i, acc);
                     epi2_mixed<HG>(st, c, i, acc);
                 }
             }
@@ -1681,6 +1701,7 @@ struct BatchKernel {
             case 1: return k_batch<2, HG, 6, 2>;
             case 2: return k_batch<2, HG, 4, 2>;
             case 3: return k_batch<2, HG, 8, 1>;
+            case 4: return k_batch<2, HG, 5, 2, true>;
             default: return k_batch<2, HG, 5, 2>;
             }
         }

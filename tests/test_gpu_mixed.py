@@ -98,7 +98,8 @@ def test_mixed_resume_is_bitwise_with_partial_damage():
 
 
 PLANS = [(0, 128, 0, 128), (1, 64, 1, 64), (2, 256, 1, 256), (3, 128, 0, 128), (1, 128, 1, 256), (4, 64, 3, 128),
-         (2, 128, 4, 128), (4, 128, 2, 64), (4, 128, 5, 128), (4, 64, 6, 128), (4, 128, 7, 128)]
+         (2, 128, 4, 128), (4, 128, 2, 64), (4, 128, 5, 128), (4, 64, 6, 128), (4, 128, 7, 128),
+         (4, 128, 8, 128)]
 
 
 def test_every_launch_plan_computes_the_same_step():
@@ -175,8 +176,8 @@ def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
 
 def test_plans_out_of_range_are_rejected():
     g = tlsph.Simulation.from_workload(S.tensile_bar_cl(nx=5, ny=5, nz=8), precision="mixed")
-    for plan in [(5, 128, 1, 128), (1, 128, 8, 128), (1, 100, 1, 128), (1, 128, 6, 256), (1, 128, 4, 256),
-                 (1, 128, 5, 256), (1, 128, 7, 256), (1, 512, 1, 128)]:
+    for plan in [(5, 128, 1, 128), (1, 128, 9, 128), (1, 100, 1, 128), (1, 128, 6, 256), (1, 128, 4, 256),
+                 (1, 128, 5, 256), (1, 128, 7, 256), (1, 128, 8, 256), (1, 512, 1, 128)]:
         with pytest.raises(tlsph.TlsphError) as e:
             g.set_plan(plan)
         assert e.value.code == -1, plan
