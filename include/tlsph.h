@@ -79,7 +79,8 @@ typedef struct {
     double dt;         /* time step [s], fixed for the run */
     double hg_alpha;   /* hourglass-control coefficient (0 disables it) */
     int32_t precision; /* TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED */
-    int32_t flags;     /* 0 or an OR of TLSPH_FLAG_SPATIAL_ORDER or TLSPH_FLAG_LINE_ORDER, TLSPH_FLAG_WALL */
+    int32_t flags;     /* 0 or an OR of at most one of TLSPH_FLAG_SPATIAL_ORDER, TLSPH_FLAG_LINE_ORDER,
+                          TLSPH_FLAG_AUTO_ORDER and of TLSPH_FLAG_WALL */
 } tlsph_config;
 
 /* Store particles in a spatially compact internal order (cells of the
@@ -101,8 +102,18 @@ typedef struct {
  * aligned slices with almost no padding slots.  Every field crossing the ABI
  * stays in the caller's order; results differ from the caller's order only by
  * the order of the sums over j.  Not combinable with TLSPH_FLAG_SPATIAL_ORDER
- * (TLSPH_ERR_ARG). */
+ * or TLSPH_FLAG_AUTO_ORDER (TLSPH_ERR_ARG). */
 #define TLSPH_FLAG_LINE_ORDER 4
+
+/* Choose the internal order at creation (mixed precision; an FP64 context
+ * keeps the caller's order): the caller's order when at least nine in ten of
+ * the mixed path's 32-row neighbour slices come out aligned
+ * (tlsph_neighbor_layout), otherwise TLSPH_FLAG_LINE_ORDER if that aligns
+ * more of them.  The choice costs one more creation (and the line sort) only
+ * for inputs whose order leaves their slices explicit, e.g. bodies whose
+ * lattice lines change length across the cross-section.  Not combinable with
+ * the other order flags (TLSPH_ERR_ARG). */
+#define TLSPH_FLAG_AUTO_ORDER 8
 
 /* A rigid frictionless wall on the plane z = 0 (current configuration): a
  * particle that would drift below it is put back on the plane and its

@@ -217,9 +217,14 @@ bool valid_config(const tlsph_config *c, std::string &why)
         why = "precision must be TLSPH_PRECISION_FP64 or TLSPH_PRECISION_MIXED";
         return false;
     }
-    if ((c->flags & ~(TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_LINE_ORDER | TLSPH_FLAG_WALL)) != 0) { why = "unknown flags"; return false; }
-    if ((c->flags & TLSPH_FLAG_SPATIAL_ORDER) && (c->flags & TLSPH_FLAG_LINE_ORDER)) {
-        why = "TLSPH_FLAG_SPATIAL_ORDER and TLSPH_FLAG_LINE_ORDER exclude each other";
+    if ((c->flags & ~(TLSPH_FLAG_SPATIAL_ORDER | TLSPH_FLAG_LINE_ORDER | TLSPH_FLAG_AUTO_ORDER | TLSPH_FLAG_WALL)) != 0) {
+        why = "unknown flags";
+        return false;
+    }
+    const int orders = ((c->flags & TLSPH_FLAG_SPATIAL_ORDER) != 0) + ((c->flags & TLSPH_FLAG_LINE_ORDER) != 0) +
+                       ((c->flags & TLSPH_FLAG_AUTO_ORDER) != 0);
+    if (orders > 1) {
+        why = "TLSPH_FLAG_SPATIAL_ORDER, TLSPH_FLAG_LINE_ORDER and TLSPH_FLAG_AUTO_ORDER exclude each other";
         return false;
     }
     return true;
@@ -387,6 +392,37 @@ size_t tlsph_workspace_bytes(const tlsph_config *cfg, int64_t N, int64_t nnz_cap
     return make_layout(N, nnz_cap, cfg->precision == TLSPH_PRECISION_MIXED).total + ALIGN;
 }
 
+// TLSPH_FLAG_AUTO_ORDER: the context in the caller's order, unless fewer than
+// nine in ten of its neighbour slices are aligned (mixed precision only; the
+// FP64 path reads the CSR); then the context is built again in lattice-line
+// order and kept if that aligns more slices, else built once more in the
+// caller's order.
+static int create_auto_order(const tlsph_config *cfg, int64_t N, const double *X, const double *vol,
+                             const int32_t *mat_id, const uint8_t *bc_mask, const double *bc_vel,
+                             const double *f0, void *arena, size_t arena_bytes, int64_t nnz_cap,
+                             void *stream, tlsph_ctx **out)
+{
+    tlsph_config caller = *cfg;
+    caller.flags &= ~TLSPH_FLAG_AUTO_ORDER;
+    int r = tlsph_create(&caller, N, X, vol, mat_id, bc_mask, bc_vel, f0, arena, arena_bytes, nnz_cap, stream, out);
+    if (r != TLSPH_OK || caller.precision != TLSPH_PRECISION_MIXED) return r;
+    int64_t slices = 0, aligned = 0;
+    if (tlsph_neighbor_layout(*out, &slices, &aligned, nullptr, nullptr) != TLSPH_OK || 10 * aligned >= 9 * slices)
+        return TLSPH_OK;
+    tlsph_destroy(*out);
+    *out = nullptr;
+    tlsph_config line = caller;
+    line.flags |= TLSPH_FLAG_LINE_ORDER;
+    r = tlsph_create(&line, N, X, vol, mat_id, bc_mask, bc_vel, f0, arena, arena_bytes, nnz_cap, stream, out);
+    if (r == TLSPH_OK) {
+        int64_t s2 = 0, a2 = 0;
+        if (tlsph_neighbor_layout(*out, &s2, &a2, nullptr, nullptr) == TLSPH_OK && a2 > aligned) return TLSPH_OK;
+        tlsph_destroy(*out);
+        *out = nullptr;
+    }
+    return tlsph_create(&caller, N, X, vol, mat_id, bc_mask, bc_vel, f0, arena, arena_bytes, nnz_cap, stream, out);
+}
+
 int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const double *vol,
                  const int32_t *mat_id, const uint8_t *bc_mask, const double *bc_vel,
                  const double *f0, void *arena, size_t arena_bytes, int64_t nnz_cap,
@@ -397,6 +433,8 @@ int tlsph_create(const tlsph_config *cfg, int64_t N, const double *X, const doub
     if (!out) { g_create_error = "out is NULL"; return TLSPH_ERR_ARG; }
     *out = nullptr;
     if (!valid_config(cfg, why)) { g_create_error = why; return TLSPH_ERR_ARG; }
+    if (cfg->flags & TLSPH_FLAG_AUTO_ORDER)
+        return create_auto_order(cfg, N, X, vol, mat_id, bc_mask, bc_vel, f0, arena, arena_bytes, nnz_cap, stream, out);
     if (N <= 0 || N > INT32_MAX) { g_create_error = "N must be in [1, 2^31)"; return TLSPH_ERR_ARG; }
     if (!X || !vol) { g_create_error = "X and vol are required"; return TLSPH_ERR_ARG; }
     if (arena && ((uintptr_t)arena % ALIGN) != 0) { g_create_error = "arena must be 256-byte aligned"; return TLSPH_ERR_ARG; }

@@ -225,6 +225,7 @@ def fma_peak(fp64: bool = False, iters: int = 4096) -> float:
 FLAG_SPATIAL_ORDER = 1
 FLAG_WALL = 2
 FLAG_LINE_ORDER = 4
+FLAG_AUTO_ORDER = 8
 
 
 def make_config(h, rc, dt, hg_alpha, precision="fp64", flags=0) -> Config:
@@ -266,7 +267,9 @@ class Simulation:
     nnz_cap); otherwise the library owns its memory.
     stream: torch.cuda.Stream or raw handle; default the current stream.
     spatial_order / line_order: internal particle order (TLSPH_FLAG_SPATIAL_ORDER
-    / TLSPH_FLAG_LINE_ORDER); both off by default (the caller's order).
+    / TLSPH_FLAG_LINE_ORDER); line_order=False keeps the caller's order, and
+    the default (None) lets a mixed-precision context choose between the two
+    (TLSPH_FLAG_AUTO_ORDER).
     wall: the rigid wall on z = 0 (TLSPH_FLAG_WALL)."""
 
     def __init__(self, X, vol, mat_id, bc_mask, bc_vel, f0, materials, h, rc, dt, hg_alpha,
@@ -281,11 +284,12 @@ class Simulation:
         bc_mask = _host(bc_mask, np.uint8)
         bc_vel = _host(bc_vel, np.float64, (N, 3))
         f0 = _host(f0, np.float64)
-        if line_order is None:      # opt-in: fewer padding slots, but a host sort at create and permuted reads
-            line_order = False
+        if line_order is None:
+            order = FLAG_AUTO_ORDER if precision == "mixed" and not spatial_order else 0
+        else:
+            order = FLAG_LINE_ORDER if line_order else 0
         self.cfg = make_config(h, rc, dt, hg_alpha, precision,
-                               (FLAG_SPATIAL_ORDER if spatial_order else 0) | (FLAG_WALL if wall else 0) |
-                               (FLAG_LINE_ORDER if line_order else 0))
+                               (FLAG_SPATIAL_ORDER if spatial_order else 0) | (FLAG_WALL if wall else 0) | order)
         self.precision = precision
         self.arena = arena
         self.stream = _stream_handle(stream)

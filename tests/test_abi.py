@@ -48,6 +48,20 @@ def test_workspace_bytes(lib):
     assert tlsph.workspace_bytes(cfg_rc, 1000, 10) == 0
 
 
+def test_order_flags_are_validated(lib):
+    """At most one internal-order flag; unknown flag bits are rejected (a
+    configuration the library rejects has no workspace size)."""
+    ok = [0, tlsph.FLAG_SPATIAL_ORDER, tlsph.FLAG_LINE_ORDER, tlsph.FLAG_AUTO_ORDER,
+          tlsph.FLAG_AUTO_ORDER | tlsph.FLAG_WALL]
+    bad = [tlsph.FLAG_SPATIAL_ORDER | tlsph.FLAG_LINE_ORDER, tlsph.FLAG_AUTO_ORDER | tlsph.FLAG_LINE_ORDER,
+           tlsph.FLAG_AUTO_ORDER | tlsph.FLAG_SPATIAL_ORDER, 16]
+    for precision in ("fp64", "mixed"):
+        for f in ok:
+            assert tlsph.workspace_bytes(tlsph.make_config(0.75e-3, 1.5e-3, 2e-8, 10.0, precision, f), 1000, 10) > 0
+        for f in bad:
+            assert tlsph.workspace_bytes(tlsph.make_config(0.75e-3, 1.5e-3, 2e-8, 10.0, precision, f), 1000, 10) == 0
+
+
 def _create(lib, cfg, N, X, vol, mat=None):
     ctx = ctypes.c_void_p()
     p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)

@@ -210,6 +210,40 @@ def test_autotune_restores_the_state_bitwise(tmp_path, monkeypatch):
     assert autotune.tune(a) == tuple(plan) and a.steps == steps
 
 
+def _order_layouts(w):
+    a = tlsph.Simulation.from_workload(w, precision="mixed")                     # TLSPH_FLAG_AUTO_ORDER
+    c = tlsph.Simulation.from_workload(w, precision="mixed", line_order=False)
+    l = tlsph.Simulation.from_workload(w, precision="mixed", line_order=True)
+    return a, c, l
+
+
+@pytest.mark.parametrize("name", ["box_bar", "notched_bar_gtn"])
+def test_auto_order_takes_the_better_aligned_order(name):
+    """The binding's default for mixed contexts (TLSPH_FLAG_AUTO_ORDER) keeps
+    the caller's order when nine in ten neighbour slices are aligned and takes
+    lattice-line order when that aligns more; the chosen context equals the
+    explicitly ordered one bit for bit.  On the 455,958-particle GTN notched
+    bar, whose x-lines change length across the round cross-section, the
+    caller's order leaves 28 % of the slices explicit and line order is taken."""
+    if name == "box_bar":
+        w = S.tensile_bar_jc(nx=12, ny=12, nz=96, steps=20)
+    else:
+        w = S.notched_bar_gtn()
+    a, c, l = _order_layouts(w)
+    la, lc, ll = a.neighbor_layout(), c.neighbor_layout(), l.neighbor_layout()
+    if 10 * lc["aligned_slices"] >= 9 * lc["slices"]:
+        expect, ref = lc, c
+    else:
+        expect, ref = (ll, l) if ll["aligned_slices"] > lc["aligned_slices"] else (lc, c)
+    assert la == expect
+    if name == "notched_bar_gtn":
+        assert expect is ll and lc["aligned_slices"] < 0.8 * lc["slices"]
+    a.step(3)
+    ref.step(3)
+    for k in ("U", "V", "F", "SIGMA", "FORCE", "DAMAGE"):
+        assert np.array_equal(a.get(k), ref.get(k)), k
+
+
 def test_line_order_removes_padding_slots():
     """Lattice lines along the longest axis as the internal order: every row of
     a slice shares its neighbourhood shape, so the aligned slices carry far
