@@ -244,6 +244,29 @@ def test_auto_order_takes_the_better_aligned_order(name):
         assert np.array_equal(a.get(k), ref.get(k)), k
 
 
+def test_auto_order_in_a_caller_arena():
+    """The automatic order builds a shuffled bar (its caller order leaves the
+    slices explicit) a second time, in line order, in the same caller-owned
+    arena; the context equals an explicitly line-ordered one in its own arena
+    bit for bit."""
+    import torch
+    w0 = S.failure_variant(S.tensile_bar_cl(nx=8, ny=8, nz=24), v_grip=10.0, scale=0.05)
+    w = _reordered(w0, np.random.default_rng(5).permutation(w0.specimen.N))
+    nnz = tlsph.Simulation.from_workload(w, precision="fp64").nnz
+    cfg = tlsph.make_config(w.h, w.rc, w.dt, w.hg_alpha, "mixed")
+    nbytes = tlsph.workspace_bytes(cfg, w.specimen.N, nnz)
+    arenas = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    a = tlsph.Simulation.from_workload(w, precision="mixed", arena=arenas[0], nnz_cap=nnz)
+    b = tlsph.Simulation.from_workload(w, precision="mixed", arena=arenas[1], nnz_cap=nnz, line_order=True)
+    c = tlsph.Simulation.from_workload(w, precision="mixed", line_order=False)
+    assert a.neighbor_layout() == b.neighbor_layout()
+    assert c.neighbor_layout()["aligned_slices"] < a.neighbor_layout()["aligned_slices"]
+    a.step(20)
+    b.step(20)
+    for k, v in b.state().items():
+        assert np.array_equal(a.get(k), v), k
+
+
 def test_line_order_removes_padding_slots():
     """Lattice lines along the longest axis as the internal order: every row of
     a slice shares its neighbourhood shape, so the aligned slices carry far
