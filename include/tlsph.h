@@ -254,7 +254,11 @@ int tlsph_destroy(tlsph_ctx *ctx);
 /* Launch plan of the mixed-precision step: plan[0] pass-1 form (0 warp per
  * 32 rows; 1 thread per row; 2 thread-per-row gather + per-particle kernel;
  * 3 warp-per-32-rows gather + per-particle kernel; 4 as 2 with four pairs in
- * flight per thread), plan[1] its block size, plan[2] pass-2 form (0 warp
+ * flight per thread; 5 as 4 with the kernel weight W'(q)/r of every slot read
+ * from a table the library builds when the form is set, 4 bytes per slot of
+ * the sliced lists, and frees when another form is set: the same bits as 4,
+ * TLSPH_ERR_ARG for a context in a caller arena, TLSPH_ERR_NOMEM if the table
+ * does not fit), plan[1] its block size, plan[2] pass-2 form (0 warp
  * per 32 rows; 1 thread per row, two pairs in flight; 2 thread-per-row
  * gather + per-particle kernel; 3 thread per row, one pair in flight; 4 as
  * 1 with registers capped for six resident blocks; 5 as 3 with registers
@@ -345,7 +349,12 @@ const char *tlsph_batch_last_error(const tlsph_batch *b);
  * k = 0 (pass-1 gather), 1 (per-particle update), 2 (pass 2); a variant
  * fixes how many blocks of 128 threads the kernel's registers are capped for
  * and how many neighbour pairs a thread has in flight (and, for one pass-2
- * variant, packed FP32x2 stress rows as in pass-2 plan form 8).  n must be 3 (the
+ * variant, packed FP32x2 stress rows as in pass-2 plan form 8; pass-1 variant
+ * 4 reads each member's per-slot weight table as pass-1 plan form 5 does,
+ * building the tables members lack: TLSPH_ERR_ARG for a member in a caller
+ * arena, and a member whose table is released by its own tlsph_set_plan
+ * stops tlsph_batch_step with TLSPH_ERR_STATE until tlsph_batch_set).  n must
+ * be 3 (the
  * number of kinds).  Setting a different shape waits for the batch's
  * launches in flight and re-captures its graph at the next tlsph_batch_step.
  * Every variant computes the same method; the results of two variants agree

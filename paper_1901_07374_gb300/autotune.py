@@ -24,7 +24,10 @@ import os
 import threading
 import zlib
 
-PASS1 = [(0, 128), (1, 128), (2, 64), (2, 128), (2, 256), (3, 256), (4, 64), (4, 128), (4, 256)]
+from .tlsph import TlsphError
+
+PASS1 = [(0, 128), (1, 128), (2, 64), (2, 128), (2, 256), (3, 256), (4, 64), (4, 128), (4, 256), (5, 64), (5, 128),
+         (5, 256)]
 PASS2 = [(0, 128), (1, 64), (1, 128), (1, 256), (2, 128), (3, 128), (3, 256), (4, 64), (4, 128), (5, 128), (6, 64),
          (6, 128), (7, 64), (7, 128), (8, 128)]
 DEFAULT = (4, 64, 4, 128)
@@ -99,7 +102,12 @@ def tune(sim, steps: int = 3, warmup: int = 1, use_cache: bool = True, record=No
     best1, best2 = None, None
     for v1, b1 in PASS1:
         plan = (v1, b1, DEFAULT[2], DEFAULT[3])
-        t1, t2 = _time(sim, plan, steps, warmup)
+        try:
+            t1, t2 = _time(sim, plan, steps, warmup)
+        except TlsphError:
+            if v1 != 5:         # pass-1 form 5 needs library-owned memory for its weight table
+                raise
+            continue
         if record is not None:
             record.append((plan, t1, t2))
         if best1 is None or t1 < best1[0]:

@@ -238,6 +238,8 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.s0 = at<float4>(base, L.s0);
         s.ell_off = at<int64_t>(base, L.ell_off);
         s.ell_w = at<int32_t>(base, L.ell_w);
+        s.w1t = nullptr;
+        s.w1t_off = nullptr;
         s.linv32 = at<float>(base, L.linv32);
         s.r1 = at<float4>(base, L.r1);
         s.r2 = at<float4>(base, L.r2);
@@ -254,6 +256,8 @@ void bind_state(tlsph_ctx *ctx, void *base, const Layout &L)
         s.ell_off = nullptr;
         s.ell_w = nullptr;
         s.colE = nullptr;
+        s.w1t = nullptr;
+        s.w1t_off = nullptr;
         s.linv32 = nullptr;
     }
     s.N = ctx->N;
@@ -379,6 +383,56 @@ DevMat make_dev_mat(const tlsph_material &m)
     d.g0rho0f = (float)d.g0rho0;
     d.inv_rho0f = (float)d.inv_rho0;
     return d;
+}
+
+// The per-slot weight table of pass-1 plan form 5 (library-owned memory;
+// 4 bytes per slot): slice offsets from the slice widths on the host, the
+// weights by k_w1t_fill.  Released again when a plan without it is set.
+void release_w1t(tlsph_ctx *ctx)
+{
+    if (ctx->w1t_mem) cudaFree(ctx->w1t_mem);
+    if (ctx->w1t_off_mem) cudaFree(ctx->w1t_off_mem);
+    ctx->w1t_mem = ctx->w1t_off_mem = nullptr;
+    ctx->s.w1t = nullptr;
+    ctx->s.w1t_off = nullptr;
+}
+
+int ctx_weight_table(tlsph_ctx *ctx)
+{
+    if (ctx->s.w1t) return TLSPH_OK;
+    if (!ctx->owns_mem) {
+        ctx->err = "pass-1 form 5 keeps a weight table in library-owned memory: not available with a caller arena";
+        return TLSPH_ERR_ARG;
+    }
+    const int64_t ng = (ctx->N + 31) / 32;
+    std::vector<int32_t> w((size_t)ng);
+    std::vector<int64_t> off((size_t)ng + 1);
+    cudaError_t e = cudaMemcpyAsync(w.data(), ctx->s.ell_w, (size_t)ng * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weight table widths");
+    off[0] = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+        const int wv = w[(size_t)g];
+        const int64_t W = wv < 0 ? (int64_t)((~wv) & 0xffffff) : (int64_t)wv;
+        off[(size_t)g + 1] = off[(size_t)g] + 8 * ((W + 3) & ~(int64_t)3);
+    }
+    if (cudaMalloc(&ctx->w1t_off_mem, ((size_t)ng + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->w1t_mem, (size_t)std::max<int64_t>(off[(size_t)ng], 1) * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        release_w1t(ctx);
+        ctx->err = "no device memory for the pass-1 weight table";
+        return TLSPH_ERR_NOMEM;
+    }
+    e = cudaMemcpyAsync(ctx->w1t_off_mem, off.data(), ((size_t)ng + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weight table offsets");
+    ctx->s.w1t = static_cast<const float4 *>(ctx->w1t_mem);
+    ctx->s.w1t_off = static_cast<const int64_t *>(ctx->w1t_off_mem);
+    e = mixed_w1t_fill(ctx->s, (float)(ctx->s.pack.unit / ctx->cfg.h), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);     // also keeps `off` alive for its copy
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weight table");
+    return TLSPH_OK;
 }
 
 }  // namespace tlsph
@@ -996,6 +1050,8 @@ int tlsph_destroy(tlsph_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     if (ctx->owns_mem && ctx->mem) cudaFree(ctx->mem);
     if (ctx->ell_mem) cudaFree(ctx->ell_mem);
+    if (ctx->w1t_mem) cudaFree(ctx->w1t_mem);
+    if (ctx->w1t_off_mem) cudaFree(ctx->w1t_off_mem);
     if (ctx->col_mem) cudaFree(ctx->col_mem);
     for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
     mixed_release(*ctx);
@@ -1008,15 +1064,25 @@ int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n)
     if (!ctx || !plan || n != 4) return TLSPH_ERR_ARG;
     if (ctx->sticky) return TLSPH_ERR_STATE;
     const int32_t v1 = plan[0], b1 = plan[1], v2 = plan[2], b2 = plan[3];
-    const bool ok = v1 >= 0 && v1 <= 4 && v2 >= 0 && v2 <= 8 && b1 >= 32 && b1 <= 256 && b1 % 32 == 0 &&
+    const bool ok = v1 >= 0 && v1 <= 5 && v2 >= 0 && v2 <= 8 && b1 >= 32 && b1 <= 256 && b1 % 32 == 0 &&
                     b2 >= 32 && b2 <= 256 && b2 % 32 == 0 && !(v2 >= 4 && b2 > 128);
     if (!ok) { ctx->err = "plan out of range"; return TLSPH_ERR_ARG; }
-    if (!ctx->ell_ok && (v1 == 1 || v1 == 2 || v1 == 4 || v2 >= 1)) {
+    if (ctx->cfg.precision != TLSPH_PRECISION_MIXED && v1 == 5) {
+        ctx->err = "pass-1 form 5 is a form of the mixed step";
+        return TLSPH_ERR_ARG;
+    }
+    if (!ctx->ell_ok && (v1 == 1 || v1 == 2 || v1 >= 4 || v2 >= 1)) {
         ctx->err = "this context has no sliced neighbour lists: only the warp-per-row plans (0, 3 / 0) apply";
         return TLSPH_ERR_ARG;
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_plan sync");
+    if (v1 == 5) {
+        const int r = ctx_weight_table(ctx);
+        if (r != TLSPH_OK) return r;
+    } else {
+        release_w1t(ctx);
+    }
     for (int k = 0; k < 4; ++k) ctx->plan[k] = plan[k];
     return TLSPH_OK;
 }

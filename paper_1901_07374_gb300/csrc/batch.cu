@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cstddef>
+
 #include "tlsph_internal.cuh"
 
 using namespace tlsph;
@@ -112,6 +114,11 @@ int tlsph_batch_set(tlsph_batch *b, tlsph_ctx *const *ctxs, int n)
         }
         if (e != cudaSuccess) return batch_fail(b, TLSPH_ERR_CUDA, std::string("member set-up: ") + cudaGetErrorString(e));
     }
+    if (b->shape[0] == BATCH_TABLE_VARIANT)       // the pass-1 gather variant reads the members' weight tables
+        for (int k = 0; k < n; ++k) {
+            const int r = ctx_weight_table(ctxs[k]);
+            if (r != TLSPH_OK) return batch_fail(b, r, std::string("member weight table: ") + ctxs[k]->err);
+        }
     b->host.resize(n);
     b->members.assign(ctxs, ctxs + n);
     b->steps_at.resize(n);
@@ -147,6 +154,8 @@ int tlsph_batch_step(tlsph_batch *b, int nsteps, int use_graph)
         if (c->sticky) return batch_fail(b, TLSPH_ERR_STATE, "a member context holds an error");
         if (c->steps != b->steps_at[k] || c->need_predict)
             return batch_fail(b, TLSPH_ERR_STATE, "a member was changed outside the batch: call tlsph_batch_set again");
+        if (b->shape[0] == BATCH_TABLE_VARIANT && (!c->s.w1t || c->s.w1t != b->host[k].s.w1t))
+            return batch_fail(b, TLSPH_ERR_STATE, "a member's weight table was released: call tlsph_batch_set again");
     }
     const bool hg = b->hg == 1;
     int *grid = b->grid[hg ? 1 : 0];
@@ -217,6 +226,24 @@ int tlsph_batch_set_shape(tlsph_batch *b, const int32_t *shape, int n)
     // the launches in flight use the old kernels and grids: finish them before replacing the graph
     cudaError_t e = cudaStreamSynchronize(b->own);
     if (e != cudaSuccess) return batch_fail(b, TLSPH_ERR_CUDA, std::string("set_shape: ") + cudaGetErrorString(e));
+    if (shape[0] == BATCH_TABLE_VARIANT) {
+        // the members' weight tables, and their pointers patched into the device slots (the rest of a
+        // slot carries state the device advances)
+        for (size_t k = 0; k < b->members.size(); ++k) {
+            tlsph_ctx *c = b->members[k];
+            const int r = ctx_weight_table(c);
+            if (r != TLSPH_OK) return batch_fail(b, r, std::string("member weight table: ") + c->err);
+            b->host[k].s.w1t = c->s.w1t;
+            b->host[k].s.w1t_off = c->s.w1t_off;
+            static_assert(offsetof(DevState, w1t_off) == offsetof(DevState, w1t) + sizeof(void *),
+                          "the two table pointers are adjacent");
+            e = cudaMemcpyAsync(reinterpret_cast<char *>(b->slots + k) + offsetof(BatchSlot, s) + offsetof(DevState, w1t),
+                                &b->host[k].s.w1t, 2 * sizeof(void *), cudaMemcpyHostToDevice, b->own);
+            if (e != cudaSuccess) return batch_fail(b, TLSPH_ERR_CUDA, std::string("set_shape: ") + cudaGetErrorString(e));
+        }
+        e = cudaStreamSynchronize(b->own);
+        if (e != cudaSuccess) return batch_fail(b, TLSPH_ERR_CUDA, std::string("set_shape: ") + cudaGetErrorString(e));
+    }
     for (int k = 0; k < BATCH_KINDS; ++k) b->shape[k] = shape[k];
     for (auto &g : b->grid)
         for (int &x : g) x = 0;             // recomputed for the new kernels at the next step

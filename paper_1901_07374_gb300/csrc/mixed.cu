@@ -331,7 +331,7 @@ __device__ __forceinline__ void aligned_slots(const int32_t *__restrict__ base, 
             w[u] = (bits & (1u << u)) ? 0.0f : SLOT_PAD_Q;
         }
         bits >>= U;
-        body(j, w);
+        body(j, w, k);
     }
 }
 
@@ -365,7 +365,7 @@ __device__ __forceinline__ void for_slots(const DevState &s, int64_t i, Body &&b
                 j[u] = jj >= 0 ? jj : ~jj;
                 w[u] = jj >= 0 ? 0.0f : SLOT_PAD_Q;
             }
-            body(j, w);
+            body(j, w, k);
         }
     }
 }
@@ -777,29 +777,61 @@ __global__ void __launch_bounds__(128) k_epi1_slow(DevState s, MixConst c)
 __device__ __forceinline__ float r1_weight(float V, float D) { return __fmul_rn(V, __fsub_rn(1.0f, D)); }
 
 // ------------------------------------------------------------------ pass 1 pair terms
-__device__ __forceinline__ void pair1(const MixConst &c, const int4 oi, const float4 vi, const int4 oj,
-                                      const float4 vj, float qpad, float *m)
+// W'(q)/r of a pair in fixed-point units (qpad as for the slots), every
+// rounding spelled out, so that the per-slot weight table and the kernels that
+// form the weight in place give the same bits
+__device__ __forceinline__ float w1_weight(const float3 d, float inv_h, float qpad)
 {
-    const float3 d = xdiff(oj, oi);
-    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    const float r2 = __fmaf_rn(d.z, d.z, __fmaf_rn(d.y, d.y, __fmul_rn(d.x, d.x)));
     const float rinv = rsqrtf(r2);
-    float a, b;
-    const float cw = vj.w * spline_dw_ab(fmaf(r2 * rinv, c.inv_h, qpad), a, b) * rinv;   // V_j (1 - D_j) W'/r
+    const float q = __fmaf_rn(__fmul_rn(r2, rinv), inv_h, qpad);
+    const float a = fmaxf(__fsub_rn(2.0f, q), 0.0f), b = fmaxf(__fsub_rn(1.0f, q), 0.0f);
+    return __fmul_rn(__fmaf_rn(__fmul_rn(3.0f, b), b, __fmul_rn(__fmul_rn(-0.75f, a), a)), rinv);
+}
+
+// the pair's terms of the nine sums M = sum_j V_j (1 - D_j) W'/r (v_j - v_i) (X_j - X_i)^T
+__device__ __forceinline__ void pair1w(const float3 d, const float4 vi, const float4 vj, float w, float *m)
+{
+    const float cw = __fmul_rn(vj.w, w);       // V_j (1 - D_j) W'/r
     const float cx = cw * (vj.x - vi.x), cy = cw * (vj.y - vi.y), cz = cw * (vj.z - vi.z);
     m[0] += cx * d.x; m[1] += cx * d.y; m[2] += cx * d.z;
     m[3] += cy * d.x; m[4] += cy * d.y; m[5] += cy * d.z;
     m[6] += cz * d.x; m[7] += cz * d.y; m[8] += cz * d.z;
 }
 
-// thread per row over the sliced neighbour lists, U pairs in flight
-template <int U>
+__device__ __forceinline__ void pair1(const MixConst &c, const int4 oi, const float4 vi, const int4 oj,
+                                      const float4 vj, float qpad, float *m)
+{
+    const float3 d = xdiff(oj, oi);
+    pair1w(d, vi, vj, w1_weight(d, c.inv_h, qpad), m);
+}
+
+// thread per row over the sliced neighbour lists, U pairs in flight; with TAB
+// (four pairs in flight) the weights come from the per-slot table, one float4
+// per group of four slots, laid out [group][lane] within the slice
+template <int U, bool TAB = false>
 __device__ __forceinline__ void gather1_row(const DevState &s, const MixConst &c, int64_t i, float *m)
 {
     const int4 oi = s.xo[i];
     const float4 vi = s.r1[i];
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = 0.0f;
-    for_slots<U>(s, i, [&](const int *j, const float *w) {
+    if constexpr (TAB) {
+        static_assert(U == 4, "the weight table holds groups of four slots");
+        const float4 *__restrict__ tb = s.w1t + s.w1t_off[i >> 5] + (i & 31);
+        for_slots<U>(s, i, [&](const int *j, const float *, int k) {
+            int4 o[U];
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) { o[u] = s.xo[j[u]]; v[u] = s.r1[j[u]]; }
+            const float4 t = tb[8 * k];      // group k / 4: float4 index 32 (k / 4) + lane
+            const float tw[4] = { t.x, t.y, t.z, t.w };
+#pragma unroll
+            for (int u = 0; u < U; ++u) pair1w(xdiff(o[u], oi), vi, v[u], tw[u % 4], m);
+        });
+        return;
+    }
+    for_slots<U>(s, i, [&](const int *j, const float *w, int) {
         int4 o[U];
         float4 v[U];
 #pragma unroll
@@ -1100,7 +1132,7 @@ __device__ __forceinline__ void gather2_row(const DevState &s, const MixConst &c
     const Row2 w = load_row2<HG>(s, c, i);
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-    for_slots<U>(s, i, [&](const int *j, const float *wm) {
+    for_slots<U>(s, i, [&](const int *j, const float *wm, int) {
 #pragma unroll
         for (int u = 0; u < U; ++u) pair2<HG, PK>(s, c, w, j[u], wm[u], acc);
     });
@@ -1188,6 +1220,17 @@ __global__ void __launch_bounds__(256) k_gather1_mixed_t4(DevState s, MixConst c
     if (i >= s.N) return;
     float m[9];
     gather1_row<4>(s, c, i, m);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = m[k];
+}
+
+// as k_gather1_mixed_t4 with the weights from the per-slot table
+__global__ void __launch_bounds__(256) k_gather1_mixed_t4w(DevState s, MixConst c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.N) return;
+    float m[9];
+    gather1_row<4, true>(s, c, i, m);
 #pragma unroll
     for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = m[k];
 }
@@ -1349,7 +1392,7 @@ __global__ void __launch_bounds__(256) k_shape_mixed(DevState s, float inv_h, do
     float sm[9], cp[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) sm[k] = cp[k] = 0.0f;
-    for_slots<2>(s, i, [&](const int *j, const float *w) {
+    for_slots<2>(s, i, [&](const int *j, const float *w, int) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const float3 d = xdiff(s.xo[j[u]], oi);
@@ -1413,6 +1456,37 @@ cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *c
     return cudaGetLastError();
 }
 
+// the weight W'(q)/r of every slot of the sliced lists (zero for a padding
+// slot), for pass-1 plan form 5: static, as it depends on the reference
+// configuration only; thread per row, rows past N of the last slice zeroed
+__global__ void __launch_bounds__(256) k_w1t_fill(DevState s, float inv_h)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = i >> 5;
+    if (g >= (s.N + 31) / 32) return;
+    float4 *tb = const_cast<float4 *>(s.w1t) + s.w1t_off[g] + (i & 31);
+    if (i >= s.N) {
+        const int wv = s.ell_w[g];
+        const int W = wv < 0 ? ((~wv) & 0xffffff) : wv;
+        for (int k = 0; k < W; k += 4) tb[8 * k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const int4 oi = s.xo[i];
+    for_slots<4>(s, i, [&](const int *j, const float *w, int k) {
+        float t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = w1_weight(xdiff(s.xo[j[u]], oi), inv_h, w[u]);
+        tb[8 * k] = make_float4(t[0], t[1], t[2], t[3]);
+    });
+}
+
+cudaError_t mixed_w1t_fill(const DevState &s, float inv_h, cudaStream_t st)
+{
+    const int64_t rows = (s.N + 31) / 32 * 32;
+    k_w1t_fill<<<nb(rows, 256), 256, 0, st>>>(s, inv_h);
+    return cudaGetLastError();
+}
+
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st)
 {
     k_mixed_r1<<<nb(s.N, 256), 256, 0, st>>>(s, dcur);
@@ -1434,7 +1508,7 @@ int mixed_slow_grid()
 // Launch plans (chosen per context, e.g. by the autotuner):
 //   pass 1: 0 = warp per 32 rows, fused;  1 = thread per row, fused;
 //           2 = thread-per-row gather + per-particle kernel;  3 = warp-per-32-rows gather + per-particle kernel;
-//           4 = as 2 with four pairs in flight per thread
+//           4 = as 2 with four pairs in flight per thread;  5 = as 4 with the weights W'/r from the per-slot table
 //   pass 2: 0 = warp per 32 rows;  1 = thread per row;  2 = thread-per-row gather + per-particle kernel;
 //           3 = thread per row, one pair in flight;  4 = thread per row, registers capped for 6 blocks of 128;
 //           5 = as 3 with registers capped for 8 blocks of 128;  6 = as 1 with registers capped for 7 blocks of 128;
@@ -1460,6 +1534,10 @@ cudaError_t launch_step_mixed(tlsph_ctx &ctx, int64_t step_index, cudaStream_t s
         break;
     case 4:
         k_gather1_mixed_t4<<<nb(s.N, b1), b1, 0, st>>>(s, c);
+        k_epi1_mixed<<<nb(s.N, 128), 128, 0, st>>>(s, c);
+        break;
+    case 5:
+        k_gather1_mixed_t4w<<<nb(s.N, b1), b1, 0, st>>>(s, c);
         k_epi1_mixed<<<nb(s.N, 128), 128, 0, st>>>(s, c);
         break;
     default: k_pass1_mixed<<<nb(rows32, MIX_THREADS), MIX_THREADS, 0, st>>>(s, c); break;
@@ -1567,12 +1645,15 @@ __device__ __forceinline__ int batch_find(const int64_t *blk0, int n, int64_t w)
 // gathers.  Variant 0 of each kind is the default.  The variants agree with
 // each other to FP32 rounding (a register cap can change which multiply-adds
 // the compiler fuses).
-//   pass-1 gather:        (8, 4)  (6, 4)  (10, 4)  (8, 2)
+//   pass-1 gather:        (8, 4)  (6, 4)  (10, 4)  (8, 2)  (8, 4) with the members' per-slot weight tables
 //   per-particle update:  5  4  3
 //   pass 2:               (5, 2)  (6, 2)  (4, 2)  (8, 1)  (5, 2) with packed FP32x2 stress rows
-const int BATCH_VARIANTS[BATCH_KINDS] = { 4, 3, 5 };
+const int BATCH_VARIANTS[BATCH_KINDS] = { 5, 3, 5 };
 
-template <int KIND, bool HG, int MINB, int U, bool PK = false>
+// ALT selects the alternative pair-term form of a kind: the per-slot weight
+// table in the pass-1 gather (members must hold one), the packed stress rows
+// in pass 2
+template <int KIND, bool HG, int MINB, int U, bool ALT = false>
 __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchSlot *slots)
 {
     __shared__ uint64_t slot_words[(sizeof(BatchSlot) + 7) / 8];
@@ -1603,9 +1684,9 @@ __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchS
             const MixConst &c = sl.c;
             const int64_t i = (w - sl.blk0) * blockDim.x + threadIdx.x;
             if (i < st.N) {
-                if (KIND == 0) {            // pass-1 gather
+                if constexpr (KIND == 0) {  // pass-1 gather
                     float mm[9];
-                    gather1_row<U>(st, c, i, mm);
+                    gather1_row<U, ALT>(st, c, i, mm);
 #pragma unroll
                     for (int k = 0; k < 9; ++k) st.fsum[k * st.N + i] = mm[k];
                 } else if (KIND == 1) {     // pass-1 per-particle update
@@ -1615,7 +1696,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch(BatchHdr *hdr, const BatchS
                     epi1_mixed(st, c, i, mm);
                 } else {                    // pass 2
                     float acc[9];
-                    gather2_row<HG, U, PK>(st, c, i, acc);
+                    gather2_row<HG, U, ALT>(st, c, i, acc);
                     epi2_mixed<HG>(st, c, i, acc);
                 }
             }
@@ -1688,6 +1769,7 @@ struct BatchKernel {
             case 1: return k_batch<0, false, 6, 4>;
             case 2: return k_batch<0, false, 10, 4>;
             case 3: return k_batch<0, false, 8, 2>;
+            case BATCH_TABLE_VARIANT: return k_batch<0, false, 8, 4, true>;
             default: return k_batch<0, false, 8, 4>;
             }
         } else if (KIND == 1) {

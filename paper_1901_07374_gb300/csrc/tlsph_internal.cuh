@@ -89,6 +89,8 @@ struct DevState {
     const int32_t *colE;    // sliced neighbour lists (slices of 32 rows, explicit or aligned form)
     const int64_t *ell_off; // (N + 31) / 32 + 1 slice word offsets
     const int32_t *ell_w;   // (N + 31) / 32 slice widths: W (explicit) or ~W (aligned)
+    const float4 *w1t;      // pass-1 weight W'(q)/r of every slot (groups of 4 slots), or NULL
+    const int64_t *w1t_off; // (N + 31) / 32 + 1 slice offsets into w1t (float4 units), or NULL
     double vref[3];         // bulk reference velocity of the r1 mirror
     FixPack pack;
     double grip_ramp = 0.0;  // tau of the grip velocity ramp (Sec. 6); 0: constant prescribed velocities
@@ -147,6 +149,8 @@ struct tlsph_ctx {
     int64_t ell_words = 0;      // 4-byte words of the sliced lists
     double *diag = nullptr;     // DIAG_BLOCKS x TLSPH_DIAG_COUNT partials; the first row holds the result
     void *ell_mem = nullptr;    // library-owned sliced-ELL columns
+    void *w1t_mem = nullptr;    // library-owned pass-1 weight table (pass-1 plan form 5) and its offsets
+    void *w1t_off_mem = nullptr;
     void *col_mem = nullptr;    // library-owned CSR columns
     int32_t *perm_dev = nullptr;
     int32_t *inv_dev = nullptr;   // device copy of inv when reordered, else null (identity)
@@ -273,11 +277,18 @@ struct BatchHdr {
     unsigned long long next[3];   // work-block counters of the three persistent kernels (zero between steps)
 };
 BatchSlot make_batch_slot(const tlsph_ctx &ctx);
+// build the per-slot pass-1 weight table of a mixed context if it has none
+// (library-owned memory only); a TLSPH_* code
+int ctx_weight_table(tlsph_ctx *ctx);
+// free it (its members and the state's pointers)
+void release_w1t(tlsph_ctx *ctx);
 // launch shape of the batch kernels: a variant index per kernel kind (pass-1
 // gather, per-particle update, pass 2), each variant a register cap (resident
 // blocks of 128 per SM) and a number of pairs in flight
 constexpr int BATCH_KINDS = 3;
 extern const int BATCH_VARIANTS[BATCH_KINDS];
+// the pass-1 gather variant that reads the members' per-slot weight tables
+constexpr int BATCH_TABLE_VARIANT = 4;
 // grid: the persistent grid of each of the four kernel kinds (batch_grid)
 cudaError_t launch_batch_step(BatchHdr *hdr, BatchSlot *slots, int nspec, bool hg, const int *shape, const int *grid,
                               cudaStream_t st);
@@ -292,6 +303,7 @@ cudaError_t mixed_shape_matrix(const DevState &s, double h, double *Linv, double
                                cudaStream_t st);
 cudaError_t mixed_ell_widths(const DevState &s, int64_t *ell_off, cudaStream_t st);
 cudaError_t mixed_ell_fill(const DevState &s, const int64_t *ell_off, int32_t *colE, cudaStream_t st);
+cudaError_t mixed_w1t_fill(const DevState &s, float inv_h, cudaStream_t st);
 cudaError_t mixed_after_predict(const DevState &s, int dcur, cudaStream_t st);
 // FP64 arrays -> compensated mixed state for one field (TLSPH_FIELD_F,
 // _STRESS_DEV, _SIGMA) or all of them (-1)

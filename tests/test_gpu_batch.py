@@ -143,6 +143,34 @@ def test_every_launch_shape_computes_the_same_rows():
     assert e.value.code == -1
 
 
+def test_weight_table_variant_equals_the_default_bitwise():
+    """Pass-1 variant 4 reads the members' per-slot weight tables (built when
+    the shape is set) and otherwise runs the default gather: the two batches
+    step bit for bit alike.  Releasing a member's table (its own plan leaves
+    form 5) stops the batch until it is set again."""
+    ws = _specimens()[:4]
+    base = _make(ws)
+    b0 = tlsph.Batch(capacity=4)
+    b0.set(base)
+    b0.step(15)
+    tab = _make(ws)
+    b1 = tlsph.Batch(capacity=4)
+    b1.set(tab)
+    b1.set_shape((4, 0, 0))
+    b1.step(15)
+    for a, r in zip(tab, base):
+        for k, v in r.state().items():
+            assert np.array_equal(a.get(k), v), k
+    tab[0].set_plan((4, 128, 7, 128))       # leaves form 5 (never set): its table is released
+    with pytest.raises(tlsph.TlsphError):
+        b1.step(1)
+    b1.set(tab)                             # rebuilds the table
+    b1.step(1)
+    b0.step(1)
+    for a, r in zip(tab, base):
+        assert np.array_equal(a.get("V"), r.get("V"))
+
+
 def test_tuned_batch_restores_the_state_and_equals_the_shape_set_by_hand(tmp_path, monkeypatch):
     """The batch autotuner times the launch shapes on the members' live state
     and then restores every member bit for bit: its tuned batch steps exactly

@@ -99,7 +99,7 @@ def test_mixed_resume_is_bitwise_with_partial_damage():
 
 PLANS = [(0, 128, 0, 128), (1, 64, 1, 64), (2, 256, 1, 256), (3, 128, 0, 128), (1, 128, 1, 256), (4, 64, 3, 128),
          (2, 128, 4, 128), (4, 128, 2, 64), (4, 128, 5, 128), (4, 64, 6, 128), (4, 128, 7, 128),
-         (4, 128, 8, 128)]
+         (4, 128, 8, 128), (5, 128, 8, 128)]
 
 
 def test_every_launch_plan_computes_the_same_step():
@@ -174,9 +174,40 @@ def test_aligned_and_explicit_slices_compute_the_same_step(shuffle):
     compare_state(a.state(), o.state(), w, tol=MIXED_TOL, fields=("U", "V", "F", "SIGMA", "FORCE"))
 
 
+def test_weight_table_form_equals_the_computed_weights():
+    """Pass-1 form 5 reads W'(q)/r of every slot from a table built when the
+    form is set; the weights are formed by the same explicitly rounded
+    expression as form 4 forms them in place, so the two step bit for bit
+    alike, also after switching back and forth (the table is freed and
+    rebuilt).  A context in a caller arena has no table: the form is refused."""
+    import torch
+    w = S.failure_variant(S.tensile_bar_cl(nx=8, ny=8, nz=40), v_grip=10.0, scale=0.05)
+    a = tlsph.Simulation.from_workload(w, precision="mixed", line_order=False)
+    b = tlsph.Simulation.from_workload(w, precision="mixed", line_order=False)
+    a.set_plan((4, 128, 7, 128))
+    b.set_plan((5, 128, 7, 128))
+    a.step(300)
+    b.step(150)
+    b.set_plan((4, 128, 7, 128))
+    b.step(30)
+    b.set_plan((5, 64, 7, 128))
+    b.step(120)
+    for k, v in a.state().items():
+        assert np.array_equal(b.get(k), v), k
+    nnz = a.nnz
+    cfg = tlsph.make_config(w.h, w.rc, w.dt, w.hg_alpha, "mixed")
+    arena = torch.empty(tlsph.workspace_bytes(cfg, w.specimen.N, nnz), dtype=torch.uint8, device="cuda")
+    c = tlsph.Simulation.from_workload(w, precision="mixed", arena=arena, nnz_cap=nnz, line_order=False)
+    with pytest.raises(tlsph.TlsphError) as e:
+        c.set_plan((5, 128, 7, 128))
+    assert e.value.code == -1
+    assert c.get_plan() != (5, 128, 7, 128)
+    c.step(2)
+
+
 def test_plans_out_of_range_are_rejected():
     g = tlsph.Simulation.from_workload(S.tensile_bar_cl(nx=5, ny=5, nz=8), precision="mixed")
-    for plan in [(5, 128, 1, 128), (1, 128, 9, 128), (1, 100, 1, 128), (1, 128, 6, 256), (1, 128, 4, 256),
+    for plan in [(6, 128, 1, 128), (1, 128, 9, 128), (1, 100, 1, 128), (1, 128, 6, 256), (1, 128, 4, 256),
                  (1, 128, 5, 256), (1, 128, 7, 256), (1, 128, 8, 256), (1, 512, 1, 128)]:
         with pytest.raises(tlsph.TlsphError) as e:
             g.set_plan(plan)
