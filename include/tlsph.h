@@ -258,7 +258,8 @@ int tlsph_destroy(tlsph_ctx *ctx);
  * from a table the library builds when the form is set, 4 bytes per slot of
  * the sliced lists, and frees when another form is set: the same bits as 4,
  * TLSPH_ERR_ARG for a context in a caller arena, TLSPH_ERR_NOMEM if the table
- * does not fit), plan[1] its block size, plan[2] pass-2 form (0 warp
+ * does not fit; block size at most 128), plan[1] its block size, plan[2]
+ * pass-2 form (0 warp
  * per 32 rows; 1 thread per row, two pairs in flight; 2 thread-per-row
  * gather + per-particle kernel; 3 thread per row, one pair in flight; 4 as
  * 1 with registers capped for six resident blocks; 5 as 3 with registers

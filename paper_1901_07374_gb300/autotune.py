@@ -26,8 +26,7 @@ import zlib
 
 from .tlsph import TlsphError
 
-PASS1 = [(0, 128), (1, 128), (2, 64), (2, 128), (2, 256), (3, 256), (4, 64), (4, 128), (4, 256), (5, 64), (5, 128),
-         (5, 256)]
+PASS1 = [(0, 128), (1, 128), (2, 64), (2, 128), (2, 256), (3, 256), (4, 64), (4, 128), (4, 256), (5, 64), (5, 128)]
 PASS2 = [(0, 128), (1, 64), (1, 128), (1, 256), (2, 128), (3, 128), (3, 256), (4, 64), (4, 128), (5, 128), (6, 64),
          (6, 128), (7, 64), (7, 128), (8, 128)]
 DEFAULT = (4, 64, 4, 128)

@@ -1065,7 +1065,7 @@ int tlsph_set_plan(tlsph_ctx *ctx, const int32_t *plan, int n)
     if (ctx->sticky) return TLSPH_ERR_STATE;
     const int32_t v1 = plan[0], b1 = plan[1], v2 = plan[2], b2 = plan[3];
     const bool ok = v1 >= 0 && v1 <= 5 && v2 >= 0 && v2 <= 8 && b1 >= 32 && b1 <= 256 && b1 % 32 == 0 &&
-                    b2 >= 32 && b2 <= 256 && b2 % 32 == 0 && !(v2 >= 4 && b2 > 128);
+                    b2 >= 32 && b2 <= 256 && b2 % 32 == 0 && !(v2 >= 4 && b2 > 128) && !(v1 == 5 && b1 > 128);
     if (!ok) { ctx->err = "plan out of range"; return TLSPH_ERR_ARG; }
     if (ctx->cfg.precision != TLSPH_PRECISION_MIXED && v1 == 5) {
         ctx->err = "pass-1 form 5 is a form of the mixed step";

@@ -1224,8 +1224,10 @@ __global__ void __launch_bounds__(256) k_gather1_mixed_t4(DevState s, MixConst c
     for (int k = 0; k < 9; ++k) s.fsum[k * s.N + i] = m[k];
 }
 
-// as k_gather1_mixed_t4 with the weights from the per-slot table
-__global__ void __launch_bounds__(256) k_gather1_mixed_t4w(DevState s, MixConst c)
+// as k_gather1_mixed_t4 with the weights from the per-slot table; registers
+// capped for nine resident blocks of 128, as the gather now waits on the
+// table's DRAM stream and more warps keep more of it in flight
+__global__ void __launch_bounds__(128, 9) k_gather1_mixed_t4w(DevState s, MixConst c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.N) return;

@@ -208,7 +208,8 @@ def test_weight_table_form_equals_the_computed_weights():
 def test_plans_out_of_range_are_rejected():
     g = tlsph.Simulation.from_workload(S.tensile_bar_cl(nx=5, ny=5, nz=8), precision="mixed")
     for plan in [(6, 128, 1, 128), (1, 128, 9, 128), (1, 100, 1, 128), (1, 128, 6, 256), (1, 128, 4, 256),
-                 (1, 128, 5, 256), (1, 128, 7, 256), (1, 128, 8, 256), (1, 512, 1, 128)]:
+                 (1, 128, 5, 256), (1, 128, 7, 256), (1, 128, 8, 256), (1, 512, 1, 128),
+                 (5, 256, 1, 128)]:
         with pytest.raises(tlsph.TlsphError) as e:
             g.set_plan(plan)
         assert e.value.code == -1, plan
