@@ -400,6 +400,10 @@ void release_w1t(tlsph_ctx *ctx)
 int ctx_weight_table(tlsph_ctx *ctx)
 {
     if (ctx->s.w1t) return TLSPH_OK;
+    if (ctx->cfg.precision != TLSPH_PRECISION_MIXED || !ctx->ell_ok) {
+        ctx->err = "the weight table belongs to the sliced lists of a mixed-precision context";
+        return TLSPH_ERR_ARG;
+    }
     if (!ctx->owns_mem) {
         ctx->err = "pass-1 form 5 keeps a weight table in library-owned memory: not available with a caller arena";
         return TLSPH_ERR_ARG;
