@@ -37,6 +37,36 @@ def test_exports_every_declared_symbol(lib):
     assert set(tlsph.EXPORTS) <= set(names)
 
 
+def _header_constants():
+    """Integer constants of include/tlsph.h: #define NAME value and enumerators NAME = value."""
+    src = open(os.path.join(ROOT, "include", "tlsph.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, val in re.findall(r"#define\s+(TLSPH_\w+)\s+(-?\d+)u?\b", src):
+        out[name] = int(val)
+    for name, val in re.findall(r"\b(TLSPH_\w+)\s*=\s*(-?\d+)", src):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """The binding's flags, precisions, field ids, status codes, status bits
+    and counts are the header's values."""
+    h = _header_constants()
+    for k in ("SPATIAL_ORDER", "WALL", "LINE_ORDER", "AUTO_ORDER"):
+        assert getattr(tlsph, "FLAG_" + k) == h["TLSPH_FLAG_" + k], k
+    for k, v in tlsph.PRECISION.items():
+        assert v == h["TLSPH_PRECISION_" + k.upper()], k
+    for k, v in tlsph.FIELD.items():
+        assert v == h["TLSPH_FIELD_" + k], k
+    assert len(tlsph.FIELD) == h["TLSPH_FIELD_COUNT"]
+    for v, k in tlsph.STATUS.items():
+        assert v == h["TLSPH_" + k], k
+    for k in ("POLAR_CAP", "NEWTON_CAP", "BAD_J", "NONFINITE"):
+        assert getattr(tlsph, "ST_" + k) == h["TLSPH_ST_" + k], k
+    assert tlsph.DIAG_COUNT == h["TLSPH_DIAG_COUNT"]
+
+
 def test_workspace_bytes(lib):
     cfg = tlsph.make_config(0.75e-3, 1.5e-3, 2e-8, 10.0)
     a = tlsph.workspace_bytes(cfg, 1000, 80000)
