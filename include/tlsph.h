@@ -248,6 +248,16 @@ const char *tlsph_last_error(const tlsph_ctx *ctx);
 #define TLSPH_DIAG_COUNT 11
 int tlsph_diagnostics(tlsph_ctx *ctx, double *out, int n);
 
+/* The same reductions without waiting: they and the copy of the
+ * TLSPH_DIAG_COUNT doubles into out are queued on the context's stream
+ * behind the work already queued there (so they describe the state after the
+ * steps queued before the call), and out holds them once the stream has
+ * passed that point (tlsph_sync, or an event recorded on the stream after the
+ * call).  out: host memory that stays valid until then, page-locked for the
+ * copy not to wait; several calls may be in flight, each into its own out.
+ * TLSPH_ERR_ARG for n != TLSPH_DIAG_COUNT or NULL out. */
+int tlsph_diagnostics_async(tlsph_ctx *ctx, double *out, int n);
+
 /* Release the context (and its device memory when the library owns it). */
 int tlsph_destroy(tlsph_ctx *ctx);
 

@@ -789,6 +789,18 @@ int tlsph_diagnostics(tlsph_ctx *ctx, double *out, int n)
     return TLSPH_OK;
 }
 
+int tlsph_diagnostics_async(tlsph_ctx *ctx, double *out, int n)
+{
+    if (!ctx || !out || n != TLSPH_DIAG_COUNT) return TLSPH_ERR_ARG;
+    if (ctx->sticky) return TLSPH_ERR_STATE;
+    // the reductions reuse one partials buffer: stream order keeps each call's copy ahead of the next call
+    cudaError_t e = launch_diagnostics(ctx->s, ctx->dcur, ctx->diag, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, ctx->diag, TLSPH_DIAG_COUNT * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics");
+    return TLSPH_OK;
+}
+
 int tlsph_sync(tlsph_ctx *ctx)
 {
     if (!ctx) return TLSPH_ERR_ARG;

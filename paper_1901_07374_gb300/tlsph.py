@@ -38,6 +38,14 @@ CHECKPOINT_FIELDS = ("U", "V", "F", "STRESS_DEV", "SIGMA", "EPSP", "EPSP_RATE", 
 # doubles returned by tlsph_diagnostics (TLSPH_DIAG_COUNT)
 DIAG_COUNT = 11
 
+
+def diagnostics_dict(out) -> dict:
+    """The named values of a tlsph_diagnostics result (a sequence or tensor of
+    DIAG_COUNT doubles)."""
+    v = [float(x) for x in out[:DIAG_COUNT]]
+    return {"momentum": tuple(v[0:3]), "force_sum": tuple(v[3:6]), "kinetic_energy": v[6], "failed": int(v[7]),
+            "max_damage": v[8], "max_epsp": v[9], "internal_energy": v[10]}
+
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_SINGULAR_L", -3: "ERR_NUMERICS", -4: "ERR_NOMEM",
           -5: "ERR_CUDA", -6: "ERR_STATE"}
 ST_POLAR_CAP, ST_NEWTON_CAP, ST_BAD_J, ST_NONFINITE = 1, 2, 4, 8
@@ -82,7 +90,8 @@ EXPORTS = ("tlsph_workspace_bytes", "tlsph_create", "tlsph_set_material", "tlsph
            "tlsph_set_plan", "tlsph_get_plan", "tlsph_batch_create", "tlsph_batch_set", "tlsph_batch_step",
            "tlsph_batch_sync", "tlsph_batch_last_error", "tlsph_batch_destroy", "tlsph_batch_set_shape",
            "tlsph_batch_get_shape", "tlsph_neighbor_layout",
-           "tlsph_fma_peak", "tlsph_set_guard", "tlsph_diagnostics", "tlsph_set_grip_ramp")
+           "tlsph_fma_peak", "tlsph_set_guard", "tlsph_diagnostics", "tlsph_diagnostics_async",
+           "tlsph_set_grip_ramp")
 
 _lib = None
 _lock = threading.Lock()
@@ -138,6 +147,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.tlsph_get_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i32]
         L.tlsph_diagnostics.restype = i32
         L.tlsph_diagnostics.argtypes = [vp, ctypes.POINTER(dbl), i32]
+        L.tlsph_diagnostics_async.restype = i32
+        L.tlsph_diagnostics_async.argtypes = [vp, ctypes.POINTER(dbl), i32]
         L.tlsph_set_guard.restype = i32
         L.tlsph_set_guard.argtypes = [vp, dbl]
         L.tlsph_set_grip_ramp.restype = i32
@@ -362,8 +373,19 @@ class Simulation:
         (tlsph_diagnostics)."""
         out = (ctypes.c_double * DIAG_COUNT)()
         _check(load().tlsph_diagnostics(self.ctx, out, DIAG_COUNT), self.ctx)
-        return {"momentum": tuple(out[0:3]), "force_sum": tuple(out[3:6]), "kinetic_energy": out[6],
-                "failed": int(out[7]), "max_damage": out[8], "max_epsp": out[9], "internal_energy": out[10]}
+        return diagnostics_dict(out)
+
+    def diagnostics_async(self, out) -> None:
+        """Queue the diagnostics of the state after the steps queued so far
+        into `out`, a page-locked float64 CPU tensor of DIAG_COUNT elements,
+        without waiting (tlsph_diagnostics_async); read it with
+        diagnostics_dict(out) once the stream has passed the call."""
+        import torch
+        _check_tensor("out", out, torch.float64, min_numel=DIAG_COUNT, ndim=1)
+        if out.is_cuda or not out.is_pinned():
+            raise ValueError("out must be a page-locked (pinned) CPU tensor")
+        _check(load().tlsph_diagnostics_async(self.ctx, ctypes.cast(out.data_ptr(), ctypes.POINTER(ctypes.c_double)),
+                                              DIAG_COUNT), self.ctx)
 
     def set_guard(self, band: float) -> None:
         """Guard band of the mixed path's FP32 elastic screen (tlsph_set_guard)."""

@@ -130,6 +130,9 @@ def test_diagnostics_argument_errors(lib):
     lib.tlsph_diagnostics.restype = ctypes.c_int
     lib.tlsph_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     assert lib.tlsph_diagnostics(None, out, 11) == -1
+    lib.tlsph_diagnostics_async.restype = ctypes.c_int
+    lib.tlsph_diagnostics_async.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    assert lib.tlsph_diagnostics_async(None, out, 11) == -1
 
 
 def test_tensor_bindings_reject_bad_tensors_before_any_launch():

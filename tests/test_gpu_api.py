@@ -176,6 +176,32 @@ def test_internal_order_is_invisible(order):
         compare_state(c.state(), ref, w, tol=2e-4, fields=("U", "V", "F", "SIGMA", "FORCE"))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_diagnostics_async_equals_the_synchronous_call(precision):
+    """tlsph_diagnostics_async queues the same reductions behind the queued
+    steps: two calls in flight (after steps 3 and 4) hold, once the stream has
+    passed them, the bits the synchronous call gives at those states.  The
+    binding takes only a page-locked float64 CPU tensor."""
+    import torch
+    w = S.failure_variant(S.tensile_bar_cl(nx=6, ny=6, nz=20))
+    a = tlsph.Simulation.from_workload(w, precision=precision)
+    b = tlsph.Simulation.from_workload(w, precision=precision)
+    bufs = [torch.zeros(tlsph.DIAG_COUNT, dtype=torch.float64).pin_memory() for _ in range(2)]
+    a.step(3)
+    a.diagnostics_async(bufs[0])
+    a.step(1)
+    a.diagnostics_async(bufs[1])
+    a.sync()
+    b.step(3)
+    assert tlsph.diagnostics_dict(bufs[0]) == b.diagnostics()
+    b.step(1)
+    assert tlsph.diagnostics_dict(bufs[1]) == b.diagnostics()
+    with pytest.raises(ValueError):
+        a.diagnostics_async(torch.zeros(tlsph.DIAG_COUNT, dtype=torch.float64))           # pageable
+    with pytest.raises(ValueError):
+        a.diagnostics_async(torch.zeros(tlsph.DIAG_COUNT, dtype=torch.float32).pin_memory())
+
+
 def test_fma_peak_microbenchmark():
     """The FMA-rate probe: FP32 well above FP64 on this part, both positive
     and below the nominal unit counts x 2.2 GHz."""
