@@ -43,8 +43,10 @@ def _lattice(nx, ny, nz, base, seed=0, n=None):
     return X[:n] if n is not None else X
 
 
-def _both(w, steps, precision):
+def _both(w, steps, precision, plan=None):
     g = tlsph.Simulation.from_workload(w, precision=precision)
+    if plan is not None:
+        g.set_plan(plan)
     o = oracle.Simulation.from_workload(w)
     g.step(steps)
     o.step(steps)
@@ -52,11 +54,17 @@ def _both(w, steps, precision):
     return g.state(), o.state()
 
 
+# the launch plans the benchmark tunes to: the per-slot weight table in pass 1
+# (padded, zero-filled slice tails) with packed or scalar pass-2 terms
+BENCH_PLANS = [(5, 128, 8, 128), (5, 64, 7, 128)]
+
+
 def _check(w, steps):
     gs, os_ = _both(w, steps, "fp64")
     compare_state(gs, os_, w, tol=TOL_FP64)
-    gm, om = _both(w, steps, "mixed")
-    compare_state(gm, om, w, tol=MIXED_TOL, fields=MIXED_FIELDS)
+    for plan in [None] + BENCH_PLANS:
+        gm, om = _both(w, steps, "mixed", plan)
+        compare_state(gm, om, w, tol=MIXED_TOL, fields=MIXED_FIELDS)
 
 
 def test_smallest_body_one_partial_warp():
